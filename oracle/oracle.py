@@ -1,0 +1,260 @@
+"""ctypes wrapper of the FP64 CPU oracle in hlbm_oracle.c.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it to check and time against; the product
+path never imports it.  It imports nothing from the CUDA package.
+"""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "hlbm_oracle.c")
+HDR = os.path.join(HERE, "hlbm_oracle.h")
+LIB = os.path.join(HERE, "liboracle.so")
+
+SPHERE, ELLIPSOID, CUBOID = 0, 1, 2
+WALL_X, WALL_Y, WALL_Z = 1, 2, 4
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force=False):
+    """Compile the oracle with gcc (C99, -O2, no contraction, no fast-math)."""
+    newest = max(os.path.getmtime(SRC), os.path.getmtime(HDR))
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
+        return LIB
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=HERE)
+    os.close(fd)
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.check_call(cmd)
+        os.replace(tmp, LIB)
+    finally:
+        if os.path.exists(tmp):
+            os.remove(tmp)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB)
+        L.oracle_create.restype = ctypes.c_void_p
+        L.oracle_create.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double, ctypes.c_double,
+                                                         ctypes.c_int, _dp, _dp]
+        L.oracle_destroy.argtypes = [ctypes.c_void_p]
+        L.oracle_add_particles.argtypes = [ctypes.c_void_p, ctypes.c_int, _ip, _dp, _dp, _dp,
+                                           _dp, _dp, _dp]
+        L.oracle_set_particle_state.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
+        L.oracle_particle_state.argtypes = [ctypes.c_void_p] + [_dp] * 6
+        L.oracle_get_populations.argtypes = [ctypes.c_void_p, _dp]
+        L.oracle_set_populations.argtypes = [ctypes.c_void_p, _dp]
+        L.oracle_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.oracle_steps_done.restype = ctypes.c_long
+        L.oracle_steps_done.argtypes = [ctypes.c_void_p]
+        L.oracle_num_particles.argtypes = [ctypes.c_void_p]
+        L.oracle_mea.restype = ctypes.c_long
+        L.oracle_mea.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp]
+        L.oracle_mea_printed_cell.argtypes = [ctypes.c_void_p, _ip, _dp, _dp]
+        L.oracle_indicator_field.argtypes = [ctypes.c_void_p, _dp, _ip]
+        L.oracle_collide_only.argtypes = [ctypes.c_void_p, _dp]
+        L.oracle_stream_only.argtypes = [ctypes.c_void_p, _dp]
+        L.oracle_integrate_only.argtypes = [ctypes.c_void_p, _dp, _dp]
+        L.oracle_velocity_set.argtypes = [_ip, _dp, _ip]
+        L.oracle_equilibrium.argtypes = [ctypes.c_double, _dp, _dp]
+        L.oracle_indicator.restype = ctypes.c_double
+        L.oracle_indicator.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.oracle_sdf_body.restype = ctypes.c_double
+        L.oracle_sdf_body.argtypes = [ctypes.c_int, _dp, _dp]
+        L.oracle_rotation.argtypes = [_dp, _dp]
+        L.oracle_inside_fp32.argtypes = [ctypes.c_int, _dp, _dp, _dp, _ip, _ip, ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_ip)
+
+
+def velocity_set():
+    c = np.zeros((19, 3), np.int32)
+    w = np.zeros(19)
+    opp = np.zeros(19, np.int32)
+    lib().oracle_velocity_set(c.ctypes.data_as(_ip), w.ctypes.data_as(_dp), opp.ctypes.data_as(_ip))
+    return c, w, opp
+
+
+def equilibrium(rho, u):
+    u, up = _d(u)
+    out = np.zeros(19)
+    lib().oracle_equilibrium(float(rho), up, out.ctypes.data_as(_dp))
+    return out
+
+
+def indicator(d, eps):
+    return lib().oracle_indicator(float(d), float(eps))
+
+
+def sdf_body(shape, a, r_body):
+    a, ap = _d(np.broadcast_to(np.asarray(a, float), (3,)) if np.ndim(a) == 0 else a)
+    r, rp = _d(r_body)
+    return lib().oracle_sdf_body(int(shape), ap, rp)
+
+
+def rotation(q):
+    q, qp = _d(q)
+    R = np.zeros(9)
+    lib().oracle_rotation(qp, R.ctypes.data_as(_dp))
+    return R.reshape(3, 3)
+
+
+def inside_fp32(shape, a, q, X, cell, n, bc):
+    a, ap = _d(np.broadcast_to(np.asarray(a, float), (3,)) if np.ndim(a) == 0 else a)
+    q, qp = _d(q)
+    X, Xp = _d(X)
+    cell, cp = _i(cell)
+    n, npp = _i(n)
+    return bool(lib().oracle_inside_fp32(int(shape), ap, qp, Xp, cp, npp, int(bc)))
+
+
+class Oracle:
+    """One FP64 HLBM lattice with its particles (two-lattice push streaming)."""
+
+    def __init__(self, n, tau, eps=0.5, bc=0, gravity=(0, 0, 0), fluid_force=(0, 0, 0)):
+        self.n = tuple(int(v) for v in n)
+        g, gp = _d(gravity)
+        ff, ffp = _d(fluid_force)
+        self._keep = (g, ff)
+        self.h = lib().oracle_create(self.n[0], self.n[1], self.n[2], float(tau), float(eps),
+                                     int(bc), gp, ffp)
+        if not self.h:
+            raise ValueError("oracle_create rejected the lattice arguments")
+        self.ncell = self.n[0] * self.n[1] * self.n[2]
+
+    def close(self):
+        if self.h:
+            lib().oracle_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_particles(self):
+        return lib().oracle_num_particles(self.h)
+
+    def add_particles(self, shape, a, X, U=None, omega=None, quat=None, rho_p=None):
+        shape, sp = _i(shape)
+        n = shape.shape[0]
+        a, ap = _d(np.asarray(a, float).reshape(n, -1) if n else np.zeros((0, 3)))
+        if a.shape[1] == 1:
+            a, ap = _d(np.repeat(a, 3, axis=1))
+        X, Xp = _d(np.asarray(X, float).reshape(n, 3))
+        U, Up = _d(np.zeros((n, 3)) if U is None else np.asarray(U, float).reshape(n, 3))
+        W, Wp = _d(np.zeros((n, 3)) if omega is None else np.asarray(omega, float).reshape(n, 3))
+        if quat is None:
+            quat = np.tile([1.0, 0, 0, 0], (n, 1))
+        qv, qp = _d(np.asarray(quat, float).reshape(n, 4))
+        rho, rp = _d(np.asarray(rho_p, float).reshape(n))
+        rc = lib().oracle_add_particles(self.h, n, sp, ap, Xp, Up, Wp, qp, rp)
+        if rc != 0:
+            raise ValueError(f"oracle_add_particles failed ({rc})")
+
+    def set_particle_state(self, X=None, U=None, omega=None, quat=None):
+        n = self.num_particles
+        args = []
+        keep = []
+        for v, k in ((X, 3), (U, 3), (omega, 3), (quat, 4)):
+            if v is None:
+                args.append(None)
+            else:
+                arr, p = _d(np.asarray(v, float).reshape(n, k))
+                keep.append(arr)
+                args.append(p)
+        if lib().oracle_set_particle_state(self.h, *args) != 0:
+            raise ValueError("oracle_set_particle_state failed")
+
+    def particle_state(self):
+        n = self.num_particles
+        out = {k: np.zeros((n, 4 if k == "quat" else 3)) for k in ("X", "U", "omega", "quat", "F", "T")}
+        lib().oracle_particle_state(self.h, *[out[k].ctypes.data_as(_dp) for k in
+                                              ("X", "U", "omega", "quat", "F", "T")])
+        return out
+
+    def populations(self):
+        f = np.zeros((19, self.n[2], self.n[1], self.n[0]))
+        lib().oracle_get_populations(self.h, f.ctypes.data_as(_dp))
+        return f
+
+    def set_populations(self, f):
+        f, fp = _d(np.asarray(f, float).reshape(19, self.n[2], self.n[1], self.n[0]))
+        lib().oracle_set_populations(self.h, fp)
+
+    def step(self, nsteps=1):
+        lib().oracle_step(self.h, int(nsteps))
+
+    @property
+    def steps_done(self):
+        return lib().oracle_steps_done(self.h)
+
+    def mea(self, p):
+        F = np.zeros(3)
+        T = np.zeros(3)
+        cnt = lib().oracle_mea(self.h, int(p), F.ctypes.data_as(_dp), T.ctypes.data_as(_dp))
+        return F, T, cnt
+
+    def mea_printed_cell(self, x, up):
+        x, xp = _i(x)
+        up, upp = _d(up)
+        Fh = np.zeros(3)
+        lib().oracle_mea_printed_cell(self.h, xp, upp, Fh.ctypes.data_as(_dp))
+        return Fh
+
+    def indicator_field(self):
+        B = np.zeros((self.n[2], self.n[1], self.n[0]))
+        pid = np.zeros((self.n[2], self.n[1], self.n[0]), np.int32)
+        lib().oracle_indicator_field(self.h, B.ctypes.data_as(_dp), pid.ctypes.data_as(_ip))
+        return B, pid
+
+    def collide_only(self):
+        post = np.zeros((19, self.n[2], self.n[1], self.n[0]))
+        lib().oracle_collide_only(self.h, post.ctypes.data_as(_dp))
+        return post
+
+    def stream_only(self, post):
+        post, pp = _d(post)
+        lib().oracle_stream_only(self.h, pp)
+
+    def integrate_only(self, F, T):
+        n = self.num_particles
+        F, Fp = _d(np.asarray(F, float).reshape(n, 3))
+        T, Tp = _d(np.asarray(T, float).reshape(n, 3))
+        lib().oracle_integrate_only(self.h, Fp, Tp)
+
+
+def from_workload(w):
+    """Build an oracle lattice from a workload description (see the workloads module)."""
+    o = Oracle(w["n"], w["tau"], w["eps"], w["bc"], w["gravity"], w.get("fluid_force", (0, 0, 0)))
+    P = w["particles"]
+    if len(P["shape"]):
+        o.add_particles(P["shape"], P["a"], P["X"], P["U"], P["omega"], P["quat"], P["rho_p"])
+    return o

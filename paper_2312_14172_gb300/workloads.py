@@ -1,0 +1,208 @@
+"""Seeded synthetic inputs: lattices and particle sets of the HLBM workloads.
+
+This module only draws inputs.  It holds none of the method's arithmetic (no
+distance function, indicator, collision, force or integrator), so that the
+CUDA path and the FP64 oracle can both be fed from it without sharing code.
+
+Random numbers come from numpy's PCG64 generator (``numpy.random.default_rng``)
+seeded with 2312014172 + workload index.  Particles are placed by random
+sequential insertion: a candidate centre is drawn uniformly and accepted when
+its circumscribed sphere keeps a gap of at least ``eps + 1`` lattice units to
+every accepted particle (minimum image on periodic axes) and to every wall.
+
+The workloads stand in for the hindered-settling study of the paper (Sec. 5.1:
+random non-overlapping spheres in a periodic box, particles initially at rest,
+fluid at rest) at the sizes of the five benchmark configurations:
+
+  0  48^3 periodic, one sphere r = 6 at the centre, tau 0.8
+  1  128^3, walls at z = 0 / z = 127, 200 spheres r ~ U(4, 8), tau 0.6
+  2  256^3 periodic, 2000 ellipsoids and cuboids, aspect ratio ~ U(1, 4),
+     equivalent radius 5, random orientation, eps 1.5, tau 0.6
+  3  512 x 512 x 1024 periodic, 50 000 spheres, lognormal diameters
+     (median 8, sigma 0.3, clipped to [4, 24]), tau 0.6
+  4  64 periodic boxes of 64..96 cells per edge, 10..200 spheres of
+     r ~ U(3, 7) each (capped at volume fraction 0.25), tau 0.6
+
+Parameters the configurations leave open are fixed as: gravity 1e-5 along -z,
+particle/fluid density ratio 2.5, eps 0.5 unless stated.
+"""
+import math
+
+import numpy as np
+
+SEED0 = 2312014172
+SPHERE, ELLIPSOID, CUBOID = 0, 1, 2
+WALL_Z = 4
+
+
+def _circ_radius(shape, a):
+    if shape == SPHERE:
+        return float(a[0])
+    if shape == ELLIPSOID:
+        return float(max(a))
+    return float(math.sqrt(a[0] ** 2 + a[1] ** 2 + a[2] ** 2))
+
+
+def random_quaternions(rng, n):
+    """Uniformly distributed unit quaternions (w, x, y, z), Shoemake's method."""
+    u1, u2, u3 = rng.random(n), rng.random(n), rng.random(n)
+    s1, s2 = np.sqrt(1.0 - u1), np.sqrt(u1)
+    return np.stack([s2 * np.cos(2 * np.pi * u3), s1 * np.sin(2 * np.pi * u2),
+                     s1 * np.cos(2 * np.pi * u2), s2 * np.sin(2 * np.pi * u3)], axis=1)
+
+
+def sequential_insertion(rng, n_box, radii, bc, gap, max_tries=200000):
+    """Random sequential insertion of circumscribed spheres of the given radii.
+
+    Returns centres (k, 3) for the first k radii that could be placed (k may be
+    below len(radii) when the box is too full).  Uses a uniform bucket grid so
+    that large particle counts stay fast.
+    """
+    n_box = np.asarray(n_box, float)
+    rmax = float(np.max(radii)) if len(radii) else 1.0
+    bucket = 2.0 * rmax + gap
+    nb = np.maximum(1, np.floor(n_box / bucket).astype(int))
+    bsize = n_box / nb
+    buckets = {}
+    centres = []
+    rad = []
+    wall = [(bc >> a) & 1 for a in range(3)]
+    for r in radii:
+        placed = False
+        for _ in range(max_tries):
+            lo = np.array([r + gap + 0.5 if wall[a] else 0.0 for a in range(3)])
+            hi = np.array([n_box[a] - 1.0 - r - gap + 0.5 if wall[a] else n_box[a] for a in range(3)])
+            if np.any(hi <= lo):
+                break
+            c = lo + rng.random(3) * (hi - lo)
+            b = np.floor(c / bsize).astype(int) % nb
+            ok = True
+            for dz in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        key = tuple(((b + np.array([dx, dy, dz])) % nb).tolist())
+                        for j in buckets.get(key, ()):
+                            d = c - centres[j]
+                            for a in range(3):
+                                if not wall[a]:
+                                    d[a] -= n_box[a] * np.round(d[a] / n_box[a])
+                            if np.dot(d, d) < (r + rad[j] + gap) ** 2:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                buckets.setdefault(tuple(b.tolist()), []).append(len(centres))
+                centres.append(c)
+                rad.append(r)
+                placed = True
+                break
+        if not placed:
+            break
+    return np.array(centres).reshape(-1, 3)
+
+
+def _particles(shape, a, X, rho_p, quat=None):
+    n = len(shape)
+    if quat is None:
+        quat = np.tile([1.0, 0.0, 0.0, 0.0], (n, 1))
+    return {
+        "shape": np.asarray(shape, np.int32),
+        "a": np.asarray(a, float).reshape(n, 3),
+        "X": np.asarray(X, float).reshape(n, 3),
+        "U": np.zeros((n, 3)),
+        "omega": np.zeros((n, 3)),
+        "quat": np.asarray(quat, float).reshape(n, 4),
+        "rho_p": np.full(n, float(rho_p)),
+    }
+
+
+def _workload(name, n, bc, tau, eps, particles, steps, precision, gravity=1e-5):
+    return {"name": name, "n": tuple(int(v) for v in n), "bc": int(bc), "tau": float(tau),
+            "eps": float(eps), "gravity": (0.0, 0.0, -float(gravity)), "fluid_force": (0.0, 0.0, 0.0),
+            "particles": particles, "steps": int(steps), "precision": precision}
+
+
+def single_sphere(n=48, radius=6.0, tau=0.8, rho_ratio=2.5, steps=200, centre=None):
+    """Workload 0: one sphere in a periodic cube, fluid at rest."""
+    c = np.full(3, (n - 1) / 2.0) if centre is None else np.asarray(centre, float)
+    P = _particles([SPHERE], [[radius] * 3], [c], rho_ratio)
+    return _workload(f"single_sphere_{n}^3", (n, n, n), 0, tau, 0.5, P, steps, "fp32")
+
+
+def hindered_settling(n=(128, 128, 128), count=200, r_range=(4.0, 8.0), tau=0.6, rho_ratio=2.5,
+                      eps=0.5, steps=1000, seed_index=1, walls=True):
+    """Workload 1: spheres between two walls (z), periodic in x and y."""
+    rng = np.random.default_rng(SEED0 + seed_index)
+    radii = rng.uniform(r_range[0], r_range[1], count)
+    bc = WALL_Z if walls else 0
+    X = sequential_insertion(rng, n, radii, bc, eps + 1.0)
+    k = len(X)
+    P = _particles([SPHERE] * k, np.repeat(radii[:k, None], 3, axis=1), X, rho_ratio)
+    return _workload(f"hindered_settling_{n[0]}x{n[1]}x{n[2]}_{k}", n, bc, tau, eps, P, steps, "fp32")
+
+
+def nonspherical(n=(256, 256, 256), count=2000, r_eq=5.0, ar_range=(1.0, 4.0), tau=0.6,
+                 rho_ratio=2.5, eps=1.5, steps=500, seed_index=2, precision="fp32"):
+    """Workload 2: prolate ellipsoids (even index) and elongated cuboids (odd
+    index) of equal volume 4/3 pi r_eq^3, aspect ratio AR ~ U(1, 4), uniform
+    random orientation, periodic box."""
+    rng = np.random.default_rng(SEED0 + seed_index)
+    ar = rng.uniform(ar_range[0], ar_range[1], count)
+    shapes, axes = [], []
+    vol = 4.0 / 3.0 * math.pi * r_eq ** 3
+    for k in range(count):
+        if k % 2 == 0:
+            a = (r_eq ** 3 / ar[k]) ** (1.0 / 3.0)          # a^3 AR = r_eq^3
+            shapes.append(ELLIPSOID)
+            axes.append([a, a, ar[k] * a])
+        else:
+            h = (vol / (8.0 * ar[k])) ** (1.0 / 3.0)        # 8 h^3 AR = volume
+            shapes.append(CUBOID)
+            axes.append([h, h, ar[k] * h])
+    radii = np.array([_circ_radius(s, a) for s, a in zip(shapes, axes)])
+    X = sequential_insertion(rng, n, radii, 0, eps + 1.0)
+    k = len(X)
+    quat = random_quaternions(rng, k)
+    P = _particles(shapes[:k], axes[:k], X, rho_ratio, quat)
+    return _workload(f"nonspherical_{n[0]}x{n[1]}x{n[2]}_{k}", n, 0, tau, eps, P, steps, precision)
+
+
+def dense_batch(n=(512, 512, 1024), count=50000, median_d=8.0, sigma=0.3, tau=0.6, rho_ratio=2.5,
+                eps=0.5, steps=200, seed_index=3, precision="fp16"):
+    """Workload 3: many spheres with lognormal diameters in a large periodic box."""
+    rng = np.random.default_rng(SEED0 + seed_index)
+    d = np.clip(median_d * np.exp(sigma * rng.standard_normal(count)), 4.0, 24.0)
+    radii = d / 2.0
+    X = sequential_insertion(rng, n, radii, 0, eps + 1.0)
+    k = len(X)
+    P = _particles([SPHERE] * k, np.repeat(radii[:k, None], 3, axis=1), X, rho_ratio)
+    return _workload(f"dense_batch_{n[0]}x{n[1]}x{n[2]}_{k}", n, 0, tau, eps, P, steps, precision)
+
+
+def ensemble(nboxes=64, edge=(64, 96), count=(10, 200), r_range=(3.0, 7.0), phi_max=0.25, tau=0.6,
+             rho_ratio=2.5, eps=0.5, steps=500, seed_index=4):
+    """Workload 4: independent periodic boxes, each with its own sphere set."""
+    rng = np.random.default_rng(SEED0 + seed_index)
+    boxes = []
+    for b in range(nboxes):
+        n = tuple(int(v) for v in rng.integers(edge[0], edge[1] + 1, 3))
+        want = int(rng.integers(count[0], count[1] + 1))
+        radii = rng.uniform(r_range[0], r_range[1], want)
+        vol = n[0] * n[1] * n[2]
+        frac = np.cumsum(4.0 / 3.0 * math.pi * radii ** 3) / vol
+        keep = int(np.searchsorted(frac, phi_max, side="right"))
+        radii = radii[:max(1, keep)]
+        X = sequential_insertion(rng, n, radii, 0, eps + 1.0)
+        k = len(X)
+        P = _particles([SPHERE] * k, np.repeat(radii[:k, None], 3, axis=1), X, rho_ratio)
+        boxes.append(_workload(f"box{b}", n, 0, tau, eps, P, steps, "fp32"))
+    return boxes
+
+
+def by_index(i, **kw):
+    return [single_sphere, hindered_settling, nonspherical, dense_batch, ensemble][i](**kw)

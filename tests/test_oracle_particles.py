@@ -1,0 +1,407 @@
+"""Pins of the oracle's particle coupling against the paper and the mathematics
+(Secs. 2.2, 3.2, 5.1 of arXiv:2312.14172): indicator, distances, rotation,
+inside test, momentum exchange, Newton-Euler update, gravity, momentum balance."""
+import math
+
+import numpy as np
+import pytest
+
+
+# --------------------------------------------------------------------- Eq. B
+def test_indicator_values(O):
+    for eps in (0.5, 1.5):
+        assert O.indicator(-eps / 2, eps) == 1.0
+        assert O.indicator(-10.0, eps) == 1.0
+        assert O.indicator(eps / 2, eps) == 0.0
+        assert O.indicator(3.0, eps) == 0.0
+        assert abs(O.indicator(0.0, eps) - 0.5) < 3e-16
+        # cos^2 ramp: B(d) + B(-d) = 1 (cos^2 t + sin^2 t) and its value at eps/4
+        for d in np.linspace(-eps / 2, eps / 2, 17):
+            assert abs(O.indicator(d, eps) + O.indicator(-d, eps) - 1.0) < 3e-15
+        assert abs(O.indicator(eps / 4, eps) - math.cos(3 * math.pi / 8) ** 2) < 1e-15
+        # continuous at both ends and monotone
+        assert abs(O.indicator(eps / 2 - 1e-9, eps)) < 1e-15
+        assert abs(O.indicator(-eps / 2 + 1e-9, eps) - 1.0) < 1e-15
+        v = [O.indicator(d, eps) for d in np.linspace(-eps, eps, 101)]
+        assert all(a >= b for a, b in zip(v, v[1:]))
+
+
+# --------------------------------------------------- signed distances, Sec. 3.2
+def test_sdf_sphere_and_ellipsoid_sphere_limit(O):
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        r = rng.uniform(-9, 9, 3)
+        R = rng.uniform(1, 7)
+        want = np.linalg.norm(r) - R
+        assert abs(O.sdf_body(0, [R, R, R], r) - want) < 1e-13
+        assert abs(O.sdf_body(1, [R, R, R], r) - want) < 1e-12  # ellipsoid, a = b = c
+
+
+def test_sdf_ellipsoid_axes_and_sign(O):
+    a = np.array([2.0, 3.0, 5.0])
+    for j in range(3):
+        for t in (0.5, 1.7, 4.0, 9.0):
+            r = np.zeros(3)
+            r[j] = t
+            assert abs(O.sdf_body(1, a, r) - (t - a[j])) < 1e-13
+    rng = np.random.default_rng(6)
+    for _ in range(500):
+        r = rng.uniform(-8, 8, 3)
+        k = np.sqrt(np.sum((r / a) ** 2))
+        d = O.sdf_body(1, a, r)
+        assert np.sign(d) == np.sign(k - 1.0)
+
+
+def _box_distance_bruteforce(a, r):
+    # nearest point of the solid box, or distance to the nearest face from inside
+    inside = np.all(np.abs(r) <= a)
+    if not inside:
+        return np.linalg.norm(r - np.clip(r, -a, a))
+    return -np.min(a - np.abs(r))
+
+
+def test_sdf_cuboid_exact(O):
+    a = np.array([1.5, 2.5, 4.0])
+    rng = np.random.default_rng(7)
+    for _ in range(500):
+        r = rng.uniform(-8, 8, 3)
+        assert abs(O.sdf_body(2, a, r) - _box_distance_bruteforce(a, r)) < 1e-13
+
+
+@pytest.mark.parametrize("shape,a", [(0, [4, 4, 4]), (1, [2, 2, 8]), (1, [1.3, 2.1, 5.2]),
+                                     (2, [1.2, 1.2, 4.8]), (2, [1.0, 2.0, 3.0])])
+@pytest.mark.parametrize("eps", [0.5, 1.5])
+def test_indicator_vanishes_outside_influence_radius(O, shape, a, eps):
+    """B is evaluated only inside |r| < R_inf; this holds exactly because d_s >=
+    eps/2 beyond it: R_inf = r_c + eps/2 for the exact distances of sphere and
+    cuboid (the body lies in its circumscribed ball), and a_max (1 + eps /
+    (2 a_min)) for the ellipsoid's algebraic distance."""
+    a = np.array(a, float)
+    rinf = {0: a[0] + eps / 2, 1: a.max() * (1 + eps / (2 * a.min())),
+            2: np.linalg.norm(a) + eps / 2}[shape]
+    rng = np.random.default_rng(8)
+    for _ in range(3000):
+        v = rng.standard_normal(3)
+        v /= np.linalg.norm(v)
+        t = rinf + rng.uniform(0, 3) ** 2
+        assert O.sdf_body(shape, a, t * v) >= eps / 2 - 1e-12
+        assert O.indicator(O.sdf_body(shape, a, t * v), eps) == 0.0
+
+
+# ---------------------------------------------------------------- rotation
+def _qmul(p, q):
+    w1, v1 = p[0], np.asarray(p[1:])
+    w2, v2 = q[0], np.asarray(q[1:])
+    return np.concatenate([[w1 * w2 - v1 @ v2], w1 * v2 + w2 * v1 + np.cross(v1, v2)])
+
+
+def test_rotation_matches_quaternion_sandwich(O):
+    rng = np.random.default_rng(9)
+    for _ in range(50):
+        q = rng.standard_normal(4)
+        q /= np.linalg.norm(q)
+        R = O.rotation(q)
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-14)
+        assert abs(np.linalg.det(R) - 1) < 1e-14
+        v = rng.standard_normal(3)
+        qc = q * np.array([1, -1, -1, -1])
+        rotated = _qmul(_qmul(q, np.concatenate([[0], v])), qc)[1:]
+        assert np.allclose(R @ v, rotated, atol=1e-14)
+    # a quarter turn about z maps x to y
+    q = np.array([math.cos(math.pi / 4), 0, 0, math.sin(math.pi / 4)])
+    assert np.allclose(O.rotation(q) @ [1, 0, 0], [0, 1, 0], atol=1e-15)
+
+
+# ------------------------------------------------ inside test (FP32 decision)
+def test_inside_fp32_agrees_with_fp64_away_from_surface(O):
+    rng = np.random.default_rng(10)
+    n = np.array([40, 40, 40])
+    for shape, a in ((0, [6, 6, 6]), (1, [3, 3, 9]), (2, [2, 2.5, 6])):
+        a = np.array(a, float)
+        for _ in range(300):
+            q = rng.standard_normal(4)
+            q /= np.linalg.norm(q)
+            X = rng.uniform(0, 40, 3)
+            cell = rng.integers(0, 40, 3)
+            r = cell - X
+            r -= 40 * np.round(r / 40)  # minimum image, periodic box
+            rb = O.rotation(q).T @ r
+            d = O.sdf_body(shape, a, rb)
+            if abs(d) > 1e-4:
+                assert O.inside_fp32(shape, a, q, X, cell, n, 0) == (d < 0)
+
+
+def test_inside_is_strict_and_wraps(O):
+    n = [20, 20, 20]
+    q = [1, 0, 0, 0]
+    # a cell centre exactly on the surface is not inside ("centre is inside")
+    assert not O.inside_fp32(0, [3, 3, 3], q, [10, 10, 10], [13, 10, 10], n, 0)
+    assert O.inside_fp32(0, [3, 3, 3], q, [10, 10, 10], [12, 10, 10], n, 0)
+    # near the periodic boundary the far side counts (minimum image) ...
+    assert O.inside_fp32(0, [3, 3, 3], q, [0.4, 10, 10], [19, 10, 10], n, 0)
+    # ... but not across a wall
+    assert not O.inside_fp32(0, [3, 3, 3], q, [0.4, 10, 10], [19, 10, 10], n, 1)
+
+
+# -------------------------------------------- momentum exchange, Eq. hlbm:mea
+@pytest.mark.parametrize("shape,a,q", [
+    (0, [3.3, 3.3, 3.3], [1, 0, 0, 0]),
+    (1, [2.0, 2.6, 4.1], [0.8, 0.2, -0.4, 0.4]),
+    (2, [1.5, 2.0, 3.0], [0.6, -0.3, 0.7, 0.2]),
+])
+def test_mea_equals_momentum_change_of_interior_cells(O, shape, a, q):
+    """Summed over the cells inside a particle, the force of Eqs. hlbm:mea and
+    hydrodynamicforce equals the momentum those cells gained in the last
+    streaming step, minus u_p(x) times the mass they gained (the Galilean
+    term), and the torque of Eq. hydrodynamictorque is the same sum with the
+    arm x - X_p.  Checked against a random post-collision field streamed by
+    the oracle, with every sum done here by brute force in numpy."""
+    n = (14, 13, 15)
+    o = O.Oracle(n, 0.8, 0.5, 0)
+    X = np.array([12.7, 6.2, 7.9])  # close to the x boundary: periodic images matter
+    U = np.array([2e-3, -1e-3, 3e-3])
+    W = np.array([1e-3, 4e-3, -2e-3])
+    qv = np.array(q, float) / np.linalg.norm(q)
+    o.add_particles([shape], [a], [X], U=[U], omega=[W], quat=[qv], rho_p=[3.0])
+    c, w, _ = O.velocity_set()
+    rng = np.random.default_rng(11)
+    post = w[:, None, None, None] * (1 + 0.05 * rng.standard_normal((19, n[2], n[1], n[0])))
+    o.stream_only(post)
+    f = o.populations()
+    F, T, cnt = o.mea(0)
+    Fw = np.zeros(3)
+    Tw = np.zeros(3)
+    k = 0
+    for z in range(n[2]):
+        for y in range(n[1]):
+            for x in range(n[0]):
+                if not O.inside_fp32(shape, a, qv, X, [x, y, z], n, 0):
+                    continue
+                k += 1
+                r = np.array([x, y, z], float) - X
+                r -= np.array(n) * np.round(r / np.array(n))
+                up = U + np.cross(W, r)
+                dp = c.T @ f[:, z, y, x] - c.T @ post[:, z, y, x]
+                dm = f[:, z, y, x].sum() - post[:, z, y, x].sum()
+                Fc = dp - up * dm
+                Fw += Fc
+                Tw += np.cross(r, Fc)
+    assert cnt == k and k > 20
+    assert np.allclose(F, Fw, rtol=1e-11, atol=1e-15)
+    assert np.allclose(T, Tw, rtol=1e-11, atol=1e-14)
+
+
+def test_mea_per_cell_printed_sum_is_minus_momentum_gain(O):
+    n = (6, 5, 7)
+    o = O.Oracle(n, 0.8, 0.5, 0)
+    c, w, _ = O.velocity_set()
+    rng = np.random.default_rng(12)
+    post = rng.random((19, n[2], n[1], n[0]))
+    o.stream_only(post)
+    f = o.populations()
+    for cell in ([0, 0, 0], [5, 4, 6], [2, 3, 1]):
+        up = rng.standard_normal(3) * 1e-2
+        Fh = o.mea_printed_cell(cell, up)
+        x, y, z = cell
+        gain = c.T @ f[:, z, y, x] - c.T @ post[:, z, y, x]
+        mgain = f[:, z, y, x].sum() - post[:, z, y, x].sum()
+        assert np.allclose(-Fh, gain - up * mgain, atol=1e-13)
+
+
+def test_mea_fluid_at_rest_is_zero(O):
+    o = O.Oracle((20, 20, 20), 0.8, 0.5, 0)
+    o.add_particles([0], [[5, 5, 5]], [[9.3, 10.1, 10.7]], rho_p=[2.0])
+    F, T, cnt = o.mea(0)
+    assert cnt > 400 and np.all(np.abs(F) < 1e-14) and np.all(np.abs(T) < 1e-13)
+
+
+# ------------------------------------------------- Newton-Euler, Sec. 2.2
+def test_constant_force_closed_form(O):
+    o = O.Oracle((40, 40, 40), 0.8, 0.5, 0)
+    R, rho = 4.0, 2.0
+    X0 = np.array([10.0, 11.0, 12.0])
+    U0 = np.array([1e-3, 0, -2e-3])
+    o.add_particles([0], [[R] * 3], [X0], U=[U0], rho_p=[rho])
+    m = rho * 4.0 / 3.0 * math.pi * R ** 3
+    F = np.array([[3e-3, -1e-3, 2e-3]])
+    Tq = np.array([[1e-2, 0, -3e-2]])
+    nsteps = 25
+    for _ in range(nsteps):
+        o.integrate_only(F, Tq)
+    s = o.particle_state()
+    assert np.allclose(s["U"][0], U0 + nsteps * F[0] / m, rtol=1e-13)
+    X = X0 + nsteps * U0 + F[0] / m * nsteps * (nsteps + 1) / 2
+    assert np.allclose(s["X"][0], X, rtol=1e-13)
+    I = 0.4 * m * R * R
+    assert np.allclose(s["omega"][0], nsteps * Tq[0] / I, rtol=1e-13)
+    assert abs(np.linalg.norm(s["quat"][0]) - 1) < 1e-15
+
+
+def test_torque_free_symmetric_top_one_step(O):
+    """Euler's equations (Eq. motionrot) for a symmetric top, one explicit step:
+    omega_3 stays, the transverse part turns by atan(Omega) and grows by
+    sqrt(1 + Omega^2), Omega = (I3 - I1) / I1 omega_3."""
+    o = O.Oracle((40, 40, 40), 0.8, 0.5, 0)
+    a = np.array([2.0, 2.0, 5.0])
+    w0 = np.array([3e-3, 0.0, 2e-2])
+    o.add_particles([1], [a], [[20, 20, 20]], omega=[w0], rho_p=[1.5])
+    o.integrate_only(np.zeros((1, 3)), np.zeros((1, 3)))
+    w = o.particle_state()["omega"][0]
+    I1 = (a[1] ** 2 + a[2] ** 2) / 5
+    I3 = (a[0] ** 2 + a[1] ** 2) / 5
+    Om = (I3 - I1) / I1 * w0[2]
+    assert abs(w[2] - w0[2]) < 1e-17
+    assert abs(math.atan2(w[1], w[0]) - math.atan(Om)) < 1e-12
+    assert abs(math.hypot(w[0], w[1]) - w0[0] * math.sqrt(1 + Om * Om)) < 1e-17
+
+
+def test_quaternion_kinematics_constant_rate(O):
+    """q <- normalise(q + q (x) (0, omega_b) / 2) turns by 2 atan(|omega| / 2)
+    per step about the body axis."""
+    o = O.Oracle((40, 40, 40), 0.8, 0.5, 0)
+    wz = 0.05
+    o.add_particles([0], [[3, 3, 3]], [[20, 20, 20]], omega=[[0, 0, wz]], rho_p=[1.5])
+    n = 30
+    for _ in range(n):
+        o.integrate_only(np.zeros((1, 3)), np.zeros((1, 3)))
+    q = o.particle_state()["quat"][0]
+    th = n * 2 * math.atan(wz / 2)
+    assert np.allclose(q, [math.cos(th / 2), 0, 0, math.sin(th / 2)], atol=1e-14)
+
+
+def test_first_step_gravity_closed_form(O):
+    """Fluid at rest exerts no force (Eq. hlbm:mea on f = w), so the first step
+    gives U = (rho_p - rho_f) V g / m = (1 - 1/rho_p) g (Sec. 5.1)."""
+    g = np.array([0, 0, -1e-5])
+    o = O.Oracle((48, 48, 48), 0.8, 0.5, 0, g)
+    o.add_particles([0], [[6, 6, 6]], [[23.5, 23.5, 23.5]], rho_p=[2.5])
+    o.step(1)
+    s = o.particle_state()
+    assert np.allclose(s["U"][0], (1 - 1 / 2.5) * g, rtol=1e-12, atol=1e-20)
+    assert np.all(np.abs(s["F"][0]) < 1e-15)
+
+
+def test_indicator_field_volume(O):
+    """Sum of B over the lattice approximates the particle volume (the cos^2
+    ramp is antisymmetric about d = 0)."""
+    o = O.Oracle((32, 32, 32), 0.8, 0.5, 0)
+    o.add_particles([0, 1, 2], [[5, 5, 5], [3, 3, 7], [2, 2.5, 5]],
+                    [[8.3, 8.1, 7.7], [23.2, 9.4, 20.1], [12.5, 23.3, 22.2]],
+                    quat=[[1, 0, 0, 0], [0.9, 0.3, 0.1, -0.2], [0.7, -0.1, 0.6, 0.3]],
+                    rho_p=[2, 2, 2])
+    B, pid = o.indicator_field()
+    V = [4 / 3 * math.pi * 125, 4 / 3 * math.pi * 63, 8 * 2 * 2.5 * 5]
+    for p in range(3):
+        assert abs(B[pid == p].sum() / V[p] - 1) < 0.02
+    assert np.all(B[pid < 0] == 0)
+    # and each value is Eq. B of the body-frame distance R^T (x - X_p)
+    s = o.particle_state()
+    for z, y, x in list(zip(*np.nonzero(pid >= 0)))[::37]:
+        p = pid[z, y, x]
+        r = np.array([x, y, z], float) - s["X"][p]
+        rb = O.rotation(s["quat"][p]).T @ r
+        a = [[5, 5, 5], [3, 3, 7], [2, 2.5, 5]][p]
+        assert abs(B[z, y, x] - O.indicator(O.sdf_body(p, a, rb), 0.5)) < 1e-15
+
+
+# ------------------------------------------------- whole step: balance laws
+def test_edm_momentum_of_one_step_is_exact(O):
+    """Eqs. hlbm:du and kupershtokh: in one step the fluid gains exactly
+    sum_x rho(x) B(x) (u_p(x) - u(x)) (streaming conserves momentum in a
+    periodic box), with B and u_p from the particle state after the update
+    (Algorithm 1 couples particles to fluid after the equations of motion)."""
+    n = (24, 22, 26)
+    g = (0, 0, -2e-4)
+    o = O.Oracle(n, 0.7, 0.5, 0, g)
+    o.add_particles([0, 1, 2], [[4, 4, 4], [2.5, 3.0, 5.0], [2.0, 2.5, 3.0]],
+                    [[6.1, 6.3, 7.2], [17.4, 10.2, 17.9], [8.8, 17.5, 19.6]],
+                    U=[[1e-3, 0, -2e-3], [0, 1e-3, 0], [-1e-3, 0, 1e-3]],
+                    omega=[[0, 2e-3, 1e-3], [1e-3, 0, 0], [0, 0, 3e-3]],
+                    quat=[[1, 0, 0, 0], [0.9, 0.1, -0.3, 0.2], [0.5, 0.5, -0.5, 0.5]],
+                    rho_p=[2.5, 2.0, 3.0])
+    o.step(5)
+    c, w, _ = O.velocity_set()
+    f0 = o.populations()
+    rho0 = f0.sum(axis=0)
+    u0 = np.einsum("ia,izyx->azyx", c, f0) / rho0
+    o.step(1)
+    s = o.particle_state()
+    B, pid = o.indicator_field()
+    gain = np.einsum("ia,izyx->a", c, o.populations()) - np.einsum("ia,izyx->a", c, f0)
+    want = np.zeros(3)
+    for z, y, x in zip(*np.nonzero(pid >= 0)):
+        p = pid[z, y, x]
+        r = np.array([x, y, z], float) - s["X"][p]
+        r -= np.array(n) * np.round(r / np.array(n))
+        up = s["U"][p] + np.cross(s["omega"][p], r)
+        want += rho0[z, y, x] * B[z, y, x] * (up - u0[:, z, y, x])
+    assert np.count_nonzero(pid >= 0) > 500
+    assert np.allclose(gain, want, rtol=1e-10, atol=1e-15)
+
+
+@pytest.mark.slow
+def test_free_settling(O):
+    """Single settling sphere (48^3 periodic, r = 6, tau = 0.8, density ratio
+    2.5, g = 1e-5).  The particle accelerates downward and stays below the
+    unbounded Stokes velocity u*_St = 2/9 (rho_p - rho_f) g r^2 / nu (Sec. 5).
+    Momentum: the only external force is F_g, and the force of Eq. hlbm:mea
+    includes the momentum change of the fluid inside the particle, so
+    m U + (fluid momentum outside the particle) grows by F_g per step; the EDM
+    forcing in the smooth zone outside the interior cells is not seen by the
+    momentum exchange, an O(eps / r) ~ 8 % leak, which bounds the tolerance."""
+    g = 1e-5
+    o = O.Oracle((48, 48, 48), 0.8, 0.5, 0, (0, 0, -g))
+    R, rho = 6.0, 2.5
+    o.add_particles([0], [[R] * 3], [[23.5, 23.5, 23.5]], rho_p=[rho])
+    V = 4 / 3 * math.pi * R ** 3
+    m = rho * V
+    Fg = (rho - 1) * V * g
+    c, w, _ = O.velocity_set()
+    Uz = []
+    for _ in range(8):
+        o.step(25)
+        Uz.append(o.particle_state()["U"][0][2])
+    s = o.particle_state()
+    X = s["X"][0]
+    f = o.populations()
+    pz = np.einsum("i,izyx->zyx", c[:, 2].astype(float), f)
+    zz, yy, xx = np.meshgrid(range(48), range(48), range(48), indexing="ij")
+    inside = (xx - X[0]) ** 2 + (yy - X[1]) ** 2 + (zz - X[2]) ** 2 < R * R
+    n = o.steps_done
+    ratio = (m * Uz[-1] + pz[~inside].sum()) / (-n * Fg)
+    assert 1.0 <= ratio < 1.0 + 0.5 / R
+    assert all(b < a for a, b in zip(Uz, Uz[1:]))
+    nu = (0.8 - 0.5) / 3
+    u_st = 2 / 9 * (rho - 1) * g * R * R / nu
+    assert 0 < -Uz[-1] < u_st
+
+
+@pytest.mark.slow
+def test_stokes_drag_magnitude_quasi_steady(O):
+    """Creeping flow through a periodic array of fixed spheres (Hasimoto's
+    closed form for a cubic array, F = 6 pi mu r u / K(phi) with
+    K = 1 - 1.7601 phi^(1/3) + phi - 1.5593 phi^2; Stokes drag, Sec. 5).
+    A sphere r = 4 (8 cells per diameter) is held still (huge density, no
+    gravity) in a periodic 32^3 box driven by a uniform force density.  After
+    ~8 viscous times the drag follows the mean velocity quasi-steadily.  The
+    momentum exchange over interior cells does not see the EDM forcing of the
+    smooth zone (an O(eps / r) share) and HLBM is first order in resolution
+    (Sec. 5.2), so the measured drag is expected 10-20 % below the closed
+    form at this resolution; a dropped term or a wrong viscosity would be off
+    by far more."""
+    L, r, tau = 32, 4.0, 1.0
+    nu = (tau - 0.5) / 3
+    fx = 1e-6
+    o = O.Oracle((L, L, L), tau, 0.5, 0, (0, 0, 0), (fx, 0, 0))
+    o.add_particles([0], [[r] * 3], [[(L - 1) / 2] * 3], rho_p=[1e15])
+    o.step(1200)
+    c, w, _ = O.velocity_set()
+    f = o.populations()
+    jx = np.einsum("i,izyx->zyx", c[:, 0].astype(float), f)
+    ubar = (jx + fx / 2).sum() / L ** 3
+    F = o.particle_state()["F"][0]
+    phi = 4 / 3 * math.pi * r ** 3 / L ** 3
+    K = 1 - 1.7601 * phi ** (1 / 3) + phi - 1.5593 * phi ** 2
+    ratio = F[0] / (6 * math.pi * nu * r * ubar / K)
+    assert 0.8 < ratio < 1.0
+    assert abs(F[1]) < 1e-6 * F[0] and abs(F[2]) < 1e-6 * F[0]
