@@ -1,0 +1,391 @@
+"""Benchmark of the GB300 HLBM time step.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                [--workload hindered_settling|single_sphere|nonspherical|dense_batch]
+
+A step is one full HLBM time step (momentum exchange, external force,
+Newton-Euler update, particle work lists, EDM coupling, collision and
+streaming) over the whole lattice.  The metric is MLUPS including the particle
+coupling: cells x steps / seconds / 1e6, summed over all GPUs (N > 1 runs N
+independent replicas, one per GPU: weak scaling, no data-path collective).
+
+Default workload: hindered settling, 128^3 cells, walls at z = 0 / 127,
+periodic x and y, 200 spheres r ~ U(4, 8), density ratio 2.5, tau 0.6,
+g = 1e-5, FP32 storage of f - w.  Its 19 FP32 planes (159 MB) exceed the
+126 MB L2, so the FP32 steps run back to back; the FP16 variant (80 MB) is
+timed one step at a time with a 512 MB L2 flush between steps.
+
+The JSON line adds: roofline (collision kernel, algorithmic bytes over its
+CUDA-event time), cpu_baseline (the FP64 oracle on the host), e2e (the same
+metric through the C-ABI with pinned host buffers copied every step), clocks,
+gpu_launches, and fp16 (the FP16-storage run and its error against FP32).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+repository) on the same workload, rank 0 only.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = {"fp32": 2 * 19 * 4, "fp16": 2 * 19 * 2}
+
+
+def make_workload(name):
+    from paper_2312_14172_gb300 import workloads
+    if name == "hindered_settling":
+        return workloads.hindered_settling()
+    if name == "single_sphere":
+        return workloads.single_sphere()
+    if name == "nonspherical":
+        return workloads.nonspherical()
+    if name == "dense_batch":
+        return workloads.dense_batch()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lbm_kernels.cu", "hlbm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2312_14172_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, precision, cells):
+    """DRAM bytes per collision launch from a committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"collide_stream_{workload}_{precision}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    per_cell = d.get("dram_bytes_per_cell")
+    return None if per_cell is None else per_cell * cells
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_mlups(w, steps, warmup=0):
+    """FP64 oracle (single thread) on the workload: MLUPS and seconds."""
+    from oracle import oracle
+    oracle.build()
+    o = oracle.from_workload(w)
+    if warmup:
+        o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    cells = w["n"][0] * w["n"][1] * w["n"][2]
+    return cells * steps / dt / 1e6, dt
+
+
+def init_dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    w = make_workload(args.workload)
+    cells = w["n"][0] * w["n"][1] * w["n"][2]
+    # bound the run: at most ~120 s of timed oracle work
+    probe_mlups, probe_dt = oracle_mlups(w, 1)
+    per_step = probe_dt
+    steps = max(1, min(args.steps, int(120.0 / max(per_step, 1e-3))))
+    warm = min(args.warmup, max(0, int(30.0 / max(per_step, 1e-3))))
+    mlups, dt = oracle_mlups(w, steps, warmup=warm)
+    sample = (f"{steps} timed step(s) after {warm} warm-up step(s) of the full "
+              f"{w['n'][0]}x{w['n'][1]}x{w['n'][2]} workload ({len(w['particles']['shape'])} particles)")
+    return {
+        "impl": "reference", "metric": "MLUPS incl. particle coupling", "value": mlups, "unit": "MLUPS",
+        "n_gpus": ws, "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["name"], "cells": cells,
+                                        "particles": len(w["particles"]["shape"])},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+    from paper_2312_14172_gb300 import build, hlbm
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    build.build()
+    hlbm.load()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+    w = make_workload(args.workload)
+    prec = args.precision or w["precision"]
+    cells = w["n"][0] * w["n"][1] * w["n"][2]
+    npart = len(w["particles"]["shape"])
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- main timed region: K graph-launched steps, inputs resident in HBM
+    lat = hlbm.from_workload(w, precision=prec, stream=stream)
+    tune = None
+    if args.autotune:
+        tune = lat.autotune(nsteps=5)
+    lat.step(args.warmup)
+    lat.sync()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    lat.sync()
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms)
+    value = ws * cells * args.steps / (ms / 1e3) / 1e6
+
+    # ---- per-kernel CUDA-event times on the same stream (roofline)
+    kt = lat.kernel_times(nsteps=max(5, min(args.steps, 50)))
+    peak, peak_kind = measured_peaks()
+    k1_ms = kt["collide_stream"]
+    algo_bytes = BYTES_PER_CELL[prec] * cells
+    achieved = algo_bytes / (k1_ms / 1e3) / 1e9
+    traffic = profiled_traffic(args.workload, prec, cells)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "collide_stream_kernel", "algorithmic_bytes": algo_bytes,
+                "kernel_ms": k1_ms, "kernel_ms_mea": kt["mea"], "kernel_ms_update": kt["update"]}
+
+    # ---- end to end through the C-ABI with pinned host buffers
+    st0 = lat.particle_state()
+    pin = {k: torch.empty(v.shape, dtype=torch.float64, pin_memory=True).numpy() for k, v in st0.items()}
+    for k in pin:
+        pin[k][...] = st0[k]
+    e2e_steps = max(3, min(args.steps, 200))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.set_particle_state(pin["X"], pin["U"], pin["omega"], pin["quat"])
+        lat.step(1)
+        lat.particle_state(out=pin)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    barrier()
+    e2e = {"value": ws * cells * e2e_steps / t_e2e / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": npart * 13 * 8, "d2h_bytes_per_step": npart * 19 * 8,
+           "steps": e2e_steps,
+           "note": "per step: hlbm_set_particle_state (X, U, omega, q) + hlbm_step(1) + "
+                   "hlbm_particle_state (X, U, omega, q, F, T), pinned host arrays"}
+    # state after the runs, for the FP16 comparison
+    fp32_state = lat.particle_state()
+    fp32_steps = lat.steps_done
+    f32 = lat.populations() if cells <= 4_000_000 else None
+    lat.close()
+
+    # ---- FP16 storage on the same workload, L2 flushed between steps
+    fp16 = None
+    if args.fp16 and prec == "fp32":
+        lat16 = hlbm.from_workload(w, precision="fp16", stream=stream)
+        if tune:
+            lat16.autotune(nsteps=5)
+        lat16.step(args.warmup)
+        lat16.sync()
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            lat16.step(1)
+            b.record(stream)
+        torch.cuda.synchronize()
+        lat16.sync()
+        ms16 = sum(a.elapsed_time(b) for a, b in evs)
+        ms16 = max_over_ranks(ms16)
+        kt16 = lat16.kernel_times(nsteps=max(5, min(args.steps, 50)))
+        ach16 = BYTES_PER_CELL["fp16"] * cells / (kt16["collide_stream"] / 1e3) / 1e9
+        # error against FP32 after the same number of steps
+        rest = fp32_steps - lat16.steps_done
+        if rest > 0:
+            lat16.step(rest)
+        s16 = lat16.particle_state()
+        err = {}
+        X0 = w["particles"]["X"]
+        for key in ("X", "U", "F", "T"):
+            a32 = fp32_state[key] - (X0 if key == "X" else 0)
+            a16 = s16[key] - (X0 if key == "X" else 0)
+            scale = float(np.abs(a32).max()) or 1.0
+            err[key] = float(np.abs(a16 - a32).max() / scale)
+        if f32 is not None:
+            f16 = lat16.populations()
+            c = np.array([[0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0],
+                          [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1],
+                          [0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1]], float)
+            r32, r16 = f32.sum(0), f16.sum(0)
+            u32 = np.einsum("ai,izyx->azyx", c, f32) / r32
+            u16 = np.einsum("ai,izyx->azyx", c, f16) / r16
+            err["rho"] = float(np.abs(r16 - r32).max())
+            err["u"] = float(np.abs(u16 - u32).max() / max(np.abs(u32).max(), 1e-30))
+        lat16.close()
+        fp16 = {"value": ws * cells * args.steps / (ms16 / 1e3) / 1e6, "unit": "MLUPS",
+                "ms_per_step": ms16 / args.steps, "l2": "512 MB flush between steps",
+                "roofline": {"bound": "hbm", "achieved": ach16, "peak": peak, "unit": "GB/s",
+                             "frac": ach16 / peak, "kernel_ms": kt16["collide_stream"],
+                             "traffic": profiled_traffic(args.workload, "fp16", cells)},
+                "error_vs_fp32": err,
+                "error_note": "max |fp16 - fp32| / max|fp32| after the same steps; X as displacement; "
+                              "rho absolute; FP32 itself matches the FP64 oracle within 1e-5"}
+
+    launches_per_step = 3 if npart > 0 else 1
+    line = {
+        "metric": "MLUPS incl. particle coupling", "value": value, "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "cells": cells, "dims": list(w["n"]), "particles": npart,
+                   "storage": prec, "tau": w["tau"], "eps": w["eps"], "bc": w["bc"],
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu",
+                   "l2": f"inputs larger than L2 ({BYTES_PER_CELL[prec] // 2 * cells / 1e6:.0f} MB "
+                         "of populations); no flush between FP32 steps",
+                   "launch": list(tune[:2]) if tune else None},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "fp16": fp16,
+    }
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="hindered_settling")
+    ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp16"])
+    ap.add_argument("--no-fp16", dest="fp16", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--autotune", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = init_dist()
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    line = run_gpu(args, ws, rank, local)
+    if rank == 0:
+        if args.cpu_baseline:
+            w = make_workload(args.workload)
+            probe, dt1 = oracle_mlups(w, 1)
+            steps = max(1, min(40, int(15.0 / max(dt1, 1e-3))))
+            mlups, dt = oracle_mlups(w, steps)
+            line["cpu_baseline"] = {
+                "value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                "sample": f"{steps} steps of the full {w['n'][0]}x{w['n'][1]}x{w['n'][2]} workload, "
+                          f"FP64, single thread, {dt:.1f} s"}
+        else:
+            line["cpu_baseline"] = None
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

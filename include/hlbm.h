@@ -1,0 +1,187 @@
+/*
+ * hlbm.h -- C-ABI of the GB300 HLBM library (libhlbm.so).
+ *
+ * One time step of the homogenized lattice Boltzmann method (HLBM) for fully
+ * resolved particulate flow, as stated in Marquardt, Hafen, Krause,
+ * arXiv:2312.14172:
+ *   Sec. 3.1  D3Q19 BGK collision (Eqs. collide, bgk, maxbolt, relaxation)
+ *             and streaming (Eq. stream);
+ *   Sec. 3.2  particle -> fluid coupling through the smooth indicator B
+ *             (Eq. B), the velocity difference (Eq. hlbm:du) and the exact
+ *             difference source (Eq. kupershtokh); fluid -> particle coupling
+ *             through the momentum exchange (Eq. hlbm:mea) summed over the
+ *             cells inside each particle (Eqs. hydrodynamicforce,
+ *             hydrodynamictorque);
+ *   Sec. 2.2  Newton-Euler motion (Eqs. particlemotiontrans, motionrot);
+ *   Sec. 4.2.4 the order of one step (Algorithm 1).
+ *
+ * Conventions for every call:
+ *   - Lattice units, dx = dt = 1, reference fluid density 1.  Cell (i, j, k)
+ *     has its centre at the point (i, j, k).  An axis is periodic, or bounded
+ *     by two half-way bounce-back walls at -1/2 and n - 1/2.
+ *   - Populations are exchanged as FP64 values f_i(x) of the post-streaming
+ *     state, laid out f[i][z][y][x] (x fastest), with the D3Q19 order
+ *       i:  0  1  2  3  4  5  6  7  8  9 10 11 12 13 14 15 16 17 18
+ *       cx: 0  1 -1  0  0  0  0  1 -1  1 -1  1 -1  1 -1  0  0  0  0
+ *       cy: 0  0  0  1 -1  0  0  1 -1 -1  1  0  0  0  0  1 -1  1 -1
+ *       cz: 0  0  0  0  0  1 -1  0  0  0  0  1 -1 -1  1  1 -1 -1  1
+ *     and weights 1/3, 1/18 (|c| = 1), 1/36 (|c|^2 = 2).
+ *   - Host arrays passed in are read during the call and may be reused when
+ *     it returns; host arrays passed out are written before it returns.
+ *   - Device memory is owned by the handle.  If the caller passes its own
+ *     device buffer to an init call, the library carves all its arrays from
+ *     it, never frees it, and the caller must keep it alive until
+ *     hlbm_destroy.
+ *   - All GPU work is queued on the CUDA stream given at init.  Calls that
+ *     return data to the host synchronise that stream.
+ *   - Return codes: HLBM_OK (0) or a negative HLBM_ERR_*; hlbm_last_error()
+ *     gives a one-line reason.  A failed call leaves the handle usable unless
+ *     it returned HLBM_ERR_CUDA.
+ *   - Not thread-safe: one host thread at a time per handle.
+ */
+#ifndef HLBM_H
+#define HLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HLBM_OK 0
+#define HLBM_ERR_ARG (-1)      /* invalid argument */
+#define HLBM_ERR_CUDA (-2)     /* a CUDA call failed */
+#define HLBM_ERR_UNSTABLE (-3) /* a non-finite or non-positive density or particle state */
+#define HLBM_ERR_CAPACITY (-4) /* a fixed-size work list overflowed */
+#define HLBM_ERR_STATE (-5)    /* call not allowed in the current state */
+
+/* storage of the populations: the deviation f_i - w_i from the weights */
+#define HLBM_FP32 0 /* as float */
+#define HLBM_FP16 1 /* as half, scaled by 2^fp16_scale_log2 */
+
+/* particle shapes; shape_params holds three numbers per particle */
+#define HLBM_SPHERE 0    /* radius r (the other two entries are ignored) */
+#define HLBM_ELLIPSOID 1 /* semi-axes a, b, c along the body axes */
+#define HLBM_CUBOID 2    /* half-extents a, b, c along the body axes */
+
+/* boundary flags: a set bit bounds that axis with two bounce-back walls */
+#define HLBM_WALL_X 1
+#define HLBM_WALL_Y 2
+#define HLBM_WALL_Z 4
+
+typedef struct hlbm_ctx* hlbm_handle;
+
+/* one lattice box of a batch */
+typedef struct {
+  int nx, ny, nz; /* cells per axis, each >= 1 */
+  int bc_flags;   /* HLBM_WALL_* bits; clear bits are periodic axes */
+} hlbm_box;
+
+/* parameters shared by all boxes of a handle */
+typedef struct {
+  double tau;             /* BGK relaxation time, Eq. relaxation: tau = 3 nu + 1/2; > 1/2 */
+  double eps;             /* width of the smooth boundary of Eq. B (lattice units), > 0 */
+  double gravity[3];      /* acceleration g; particle force (rho_p - 1) V g, Sec. 5.1 */
+  double fluid_force[3];  /* uniform force density on the fluid (0 for the paper's setups) */
+  int precision;          /* HLBM_FP32 or HLBM_FP16 */
+  int fp16_scale_log2;    /* HLBM_FP16 only: stored value (f_i - w_i) * 2^s, s in [0, 16] */
+  int max_particles;      /* capacity of the particle table over all boxes, >= 0 */
+  int bin_capacity;       /* particles per 32x8x8 cell tile seen by the collision; 0 = 64 */
+} hlbm_params;
+
+/* Fills p with the defaults: tau 0.6, eps 0.5 (Sec. 3.2), no forces, FP32,
+ * s = 14, max_particles 0, bin_capacity 0. */
+void hlbm_default_params(hlbm_params* p);
+
+/* Device bytes that an init call with the same arguments needs; 0 if the
+ * arguments are invalid. */
+size_t hlbm_required_bytes(int nboxes, const hlbm_box* boxes, const hlbm_params* prm);
+
+/* Creates a handle for one box.  The fluid starts at rest with density 1
+ * (f_i = w_i, Sec. 3.1).  cuda_stream: a cudaStream_t (NULL = legacy default
+ * stream).  device_buf: NULL to let the library allocate, or a device buffer
+ * of at least hlbm_required_bytes() bytes, 256-byte aligned. */
+int hlbm_init_lattice(hlbm_handle* out, int nx, int ny, int nz, int bc_flags,
+                      const hlbm_params* prm, void* cuda_stream, void* device_buf,
+                      size_t device_buf_bytes);
+
+/* Creates a handle for a batch of independent boxes advanced together: one
+ * launch per kernel per step covers all boxes.  Same rules as
+ * hlbm_init_lattice. */
+int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const hlbm_params* prm,
+                    void* cuda_stream, void* device_buf, size_t device_buf_bytes);
+
+/* Adds n particles (Sec. 2.2), allowed only before the first step
+ * (HLBM_ERR_STATE afterwards).  Arrays (host, row-major):
+ *   box_id[n]      box of each particle (NULL = box 0)
+ *   shape[n]       HLBM_SPHERE / HLBM_ELLIPSOID / HLBM_CUBOID
+ *   shape_params[3n], X[3n] centre of mass, U[3n] velocity (NULL = 0),
+ *   omega[3n] angular velocity (NULL = 0), quat[4n] orientation (w,x,y,z,
+ *   body -> world, normalised here; NULL = identity), rho_p[n] density.
+ * Mass and inertia follow from the analytic volume and rho_p.  Rejected
+ * (HLBM_ERR_ARG): non-finite or non-positive sizes or densities, a centre
+ * outside the box on a wall axis, or a particle whose bounding region
+ * (circumscribed radius + eps/2 + 2) spans half a periodic axis or more. */
+int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape,
+                       const double* shape_params, const double* X, const double* U,
+                       const double* omega, const double* quat, const double* rho_p);
+
+/* Overwrites the motion state of all particles (any of the pointers may be
+ * NULL to keep that field).  Arrays as in hlbm_add_particles. */
+int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, const double* omega,
+                            const double* quat);
+
+/* Queues nsteps >= 0 time steps (Algorithm 1: momentum exchange, external
+ * force, Newton-Euler update, particle work lists, EDM coupling, collision
+ * and streaming) on the stream and returns without waiting.  Errors found by
+ * the GPU are reported by the next call that synchronises. */
+int hlbm_step(hlbm_handle h, int nsteps);
+
+/* Waits for the stream and returns HLBM_OK or the error the GPU flagged
+ * (HLBM_ERR_UNSTABLE, HLBM_ERR_CAPACITY); the flags are then cleared. */
+int hlbm_sync(hlbm_handle h);
+
+/* Copies the particle state after the last step to host arrays (any may be
+ * NULL): X, U, omega [3n], quat [4n], and the hydrodynamic force F and
+ * torque T [3n] of Eqs. hydrodynamicforce / hydrodynamictorque measured in the
+ * last step (weight and buoyancy not included).  Synchronises; returns like
+ * hlbm_sync. */
+int hlbm_particle_state(hlbm_handle h, double* X, double* U, double* omega, double* quat,
+                        double* F, double* T);
+
+/* Copies the post-streaming populations f_i(x) of box `box` to / from a host
+ * array of 19 * nx * ny * nz doubles (layout above).  Set converts to the
+ * storage precision.  Both synchronise. */
+int hlbm_get_populations(hlbm_handle h, int box, double* host_f);
+int hlbm_set_populations(hlbm_handle h, int box, const double* host_f);
+
+int hlbm_num_particles(hlbm_handle h);
+long long hlbm_steps_done(hlbm_handle h);
+
+/* Launch shape of the collision kernel: each thread block covers a brick of
+ * 32 x tile_y x tile_z cells, tile_y and tile_z in {1, 2, 4, 8}. */
+int hlbm_set_launch(hlbm_handle h, int tile_y, int tile_z);
+int hlbm_get_launch(hlbm_handle h, int* tile_y, int* tile_z);
+
+/* Times every launch shape on nsteps steps of the current state (the state
+ * advances by the steps taken) and keeps the fastest; writes the chosen
+ * shape and its time per step in ms (any pointer may be NULL). */
+int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, float* ms_per_step);
+
+/* Runs nsteps steps with each kernel launched on its own, bracketed by CUDA
+ * events on the handle's stream, and writes the mean time per launch in ms:
+ * ms[0] momentum exchange, ms[1] Newton-Euler and work lists, ms[2] collision
+ * and streaming.  Synchronises. */
+int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]);
+
+/* One-line description of the last error on this handle (or of the last
+ * failed init when h is NULL). */
+const char* hlbm_last_error(hlbm_handle h);
+
+/* Frees the handle and the device memory it allocated. */
+void hlbm_destroy(hlbm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

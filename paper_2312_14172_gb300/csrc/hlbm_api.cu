@@ -1,0 +1,689 @@
+// hlbm_api.cu -- the C-ABI of include/hlbm.h: handles, device memory layout,
+// particle set-up, CUDA-graph capture of the time step, data exchange.
+//
+// One time step (Algorithm 1 of arXiv:2312.14172, Sec. 4.2.4, without its
+// communication rows) is three launches on the handle's stream:
+//   1. momentum exchange per particle          (mea_kernel)
+//   2. external force, Newton-Euler, records,
+//      per-tile particle lists                 (update_kernel)
+//   3. EDM coupling, collision and streaming   (collide_stream_kernel)
+// Steps alternate between the two AA parities, so each parity is captured
+// once as a CUDA graph and the graphs are launched alternately.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hlbm.h"
+#include "hlbm_internal.cuh"
+
+using namespace hlbm;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+constexpr int DEFAULT_BIN_CAP = 64;
+constexpr long long STAGE_CELLS = 1 << 18;
+const double PI_D = 3.14159265358979323846;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+  long long plane = 0, ncell = 0, ntiles = 0, stage_cells = 0;
+  int cap = 0, bin_cap = 0;
+  size_t off_f, off_boxes, off_P, off_shape, off_box, off_rec, off_cnt[2], off_ids[2], off_status,
+      off_stage, total;
+};
+
+bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& L,
+                 std::vector<BoxDesc>& bd, std::string& err) {
+  if (nb < 1 || !boxes || !prm) { err = "need at least one box and parameters"; return false; }
+  if (!(prm->tau > 0.5) || !std::isfinite(prm->tau)) { err = "tau must be finite and > 1/2"; return false; }
+  if (!(prm->eps > 0.0) || !std::isfinite(prm->eps)) { err = "eps must be finite and > 0"; return false; }
+  if (prm->precision != HLBM_FP32 && prm->precision != HLBM_FP16) { err = "unknown precision"; return false; }
+  if (prm->fp16_scale_log2 < 0 || prm->fp16_scale_log2 > 16) { err = "fp16_scale_log2 out of [0, 16]"; return false; }
+  if (prm->max_particles < 0) { err = "max_particles < 0"; return false; }
+  if (prm->bin_capacity < 0 || prm->bin_capacity > 64) { err = "bin_capacity out of [0, 64]"; return false; }
+  for (int j = 0; j < 3; ++j)
+    if (!std::isfinite(prm->gravity[j]) || !std::isfinite(prm->fluid_force[j])) { err = "non-finite force"; return false; }
+  bd.assign(nb, BoxDesc{});
+  long long cells = 0, tiles = 0, maxbox = 0;
+  for (int b = 0; b < nb; ++b) {
+    const hlbm_box& B = boxes[b];
+    if (B.nx < 1 || B.ny < 1 || B.nz < 1 || (B.bc_flags & ~7)) { err = "bad box dimensions or flags"; return false; }
+    const long long n = (long long)B.nx * B.ny * B.nz;
+    if (n >= (1LL << 31)) { err = "a box may hold at most 2^31 - 1 cells"; return false; }
+    BoxDesc& d = bd[b];
+    d.nx = B.nx; d.ny = B.ny; d.nz = B.nz; d.bc = B.bc_flags;
+    d.ntx = (B.nx + TILE_X - 1) / TILE_X;
+    d.nty = (B.ny + TILE_Y - 1) / TILE_Y;
+    d.ntz = (B.nz + TILE_Z - 1) / TILE_Z;
+    d.cell_off = cells;
+    d.tile_off = tiles;
+    cells += (n + 63) / 64 * 64;  // every box starts on a 64-cell boundary
+    tiles += (long long)d.ntx * d.nty * d.ntz;
+    if (n > maxbox) maxbox = n;
+  }
+  L.plane = cells;
+  L.ncell = cells;
+  L.ntiles = tiles;
+  L.stage_cells = maxbox < STAGE_CELLS ? maxbox : STAGE_CELLS;
+  L.cap = prm->max_particles;
+  L.bin_cap = prm->bin_capacity ? prm->bin_capacity : DEFAULT_BIN_CAP;
+  const size_t s = prm->precision == HLBM_FP32 ? 4 : 2;
+  size_t o = 0;
+  L.off_f = o; o = align_up(o + (size_t)Q * L.plane * s);
+  L.off_boxes = o; o = align_up(o + sizeof(BoxDesc) * nb);
+  L.off_P = o; o = align_up(o + sizeof(double) * PF_COUNT * (size_t)L.cap);
+  L.off_shape = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
+  L.off_box = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
+  L.off_rec = o; o = align_up(o + sizeof(Rec) * (size_t)L.cap);
+  for (int k = 0; k < 2; ++k) {
+    L.off_cnt[k] = o; o = align_up(o + sizeof(int) * (size_t)L.ntiles);
+    L.off_ids[k] = o; o = align_up(o + sizeof(int) * (size_t)L.ntiles * L.bin_cap);
+  }
+  L.off_status = o; o = align_up(o + sizeof(int));
+  L.off_stage = o; o = align_up(o + sizeof(float) * Q * (size_t)L.stage_cells);
+  L.total = o;
+  return true;
+}
+
+thread_local std::string g_init_err;
+
+}  // namespace
+
+struct hlbm_ctx {
+  std::vector<BoxDesc> boxes;
+  hlbm_params prm{};
+  Layout L{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  char* buf = nullptr;
+  bool owns = false;
+  void* f = nullptr;
+  BoxDesc* d_boxes = nullptr;
+  double* P = nullptr;
+  int* d_shape = nullptr;
+  int* d_box = nullptr;
+  Rec* rec = nullptr;
+  int* cnt[2] = {nullptr, nullptr};
+  int* ids[2] = {nullptr, nullptr};
+  int* status = nullptr;
+  float* stage = nullptr;
+  bool walls = false;
+  int np = 0;
+  long long steps = 0;
+  int sub_y = 4, sub_z = 2;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  bool graphs_ok = false;
+  std::vector<int> h_shape, h_box;  // host copies
+  std::string err;
+};
+
+#define CK(call)                                                              \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);            \
+      return HLBM_ERR_CUDA;                                                   \
+    }                                                                         \
+  } while (0)
+
+static int fail(hlbm_ctx* h, int code, const std::string& msg) {
+  h->err = msg;
+  return code;
+}
+
+static LbmArgs lbm_args(const hlbm_ctx* h, int parity) {
+  LbmArgs a{};
+  a.f = h->f;
+  a.plane = h->L.plane;
+  a.boxes = h->d_boxes;
+  a.nboxes = (int)h->boxes.size();
+  a.sub_y = h->sub_y;
+  a.sub_z = h->sub_z;
+  a.nsub = (TILE_Y / h->sub_y) * (TILE_Z / h->sub_z);
+  a.nbricks = h->L.ntiles * a.nsub;
+  a.omega = (float)(1.0 / h->prm.tau);
+  for (int j = 0; j < 3; ++j) a.ff[j] = (float)h->prm.fluid_force[j];
+  a.eps = (float)h->prm.eps;
+  a.inv_eps = (float)(1.0 / h->prm.eps);
+  const double sc = h->prm.precision == HLBM_FP16 ? std::ldexp(1.0, h->prm.fp16_scale_log2) : 1.0;
+  a.scale = (float)sc;
+  a.inv_scale = (float)(1.0 / sc);
+  a.bin_count = h->cnt[parity];
+  a.bin_ids = h->ids[parity];
+  a.bin_cap = h->L.bin_cap;
+  a.rec = h->rec;
+  a.status = h->status;
+  return a;
+}
+
+static PartArgs part_args(const hlbm_ctx* h, int parity) {
+  PartArgs a{};
+  a.P = h->P;
+  a.cap = h->L.cap;
+  a.np = h->np;
+  a.shape = h->d_shape;
+  a.box = h->d_box;
+  a.rec = h->rec;
+  a.boxes = h->d_boxes;
+  for (int j = 0; j < 3; ++j) a.g[j] = h->prm.gravity[j];
+  a.eps = h->prm.eps;
+  a.f = h->f;
+  a.plane = h->L.plane;
+  const double sc = h->prm.precision == HLBM_FP16 ? std::ldexp(1.0, h->prm.fp16_scale_log2) : 1.0;
+  a.scale = (float)sc;
+  a.inv_scale = (float)(1.0 / sc);
+  a.bin_count = h->cnt[parity];
+  a.bin_ids = h->ids[parity];
+  a.bin_count_clear = h->cnt[1 - parity];
+  a.ntiles = h->L.ntiles;
+  a.bin_cap = h->L.bin_cap;
+  a.status = h->status;
+  return a;
+}
+
+static cudaError_t enqueue_step(hlbm_ctx* h, int parity, cudaStream_t s) {
+  cudaError_t e;
+  if (h->np > 0) {
+    const PartArgs pa = part_args(h, parity);
+    if ((e = launch_mea(pa, h->prm.precision, parity, s)) != cudaSuccess) return e;
+    if ((e = launch_update(pa, s)) != cudaSuccess) return e;
+  }
+  return launch_collide(lbm_args(h, parity), h->prm.precision, parity, h->walls, h->np > 0, s);
+}
+
+static void drop_graphs(hlbm_ctx* h) {
+  for (int k = 0; k < 2; ++k) {
+    if (h->exec[k]) cudaGraphExecDestroy(h->exec[k]);
+    h->exec[k] = nullptr;
+  }
+  h->graphs_ok = false;
+}
+
+static int build_graphs(hlbm_ctx* h) {
+  drop_graphs(h);
+  for (int parity = 0; parity < 2; ++parity) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_step(h, parity, h->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return fail(h, HLBM_ERR_CUDA, std::string("graph capture: ") +
+                                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&h->exec[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, HLBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  h->graphs_ok = true;
+  return HLBM_OK;
+}
+
+static int read_status(hlbm_ctx* h) {
+  int st = 0;
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (st == 0) return HLBM_OK;
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (st & ST_CAPACITY)
+    return fail(h, HLBM_ERR_CAPACITY, "a 32x8x8 tile was touched by more particles than bin_capacity");
+  if (st & ST_LEFT_DOMAIN)
+    return fail(h, HLBM_ERR_UNSTABLE, "a particle centre left the fluid domain through a wall");
+  return fail(h, HLBM_ERR_UNSTABLE, "non-finite or non-positive density, or non-finite particle state");
+}
+
+extern "C" {
+
+void hlbm_default_params(hlbm_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->tau = 0.6;
+  p->eps = 0.5;
+  p->precision = HLBM_FP32;
+  p->fp16_scale_log2 = 14;
+}
+
+size_t hlbm_required_bytes(int nboxes, const hlbm_box* boxes, const hlbm_params* prm) {
+  Layout L;
+  std::vector<BoxDesc> bd;
+  std::string err;
+  if (!make_layout(nboxes, boxes, prm, L, bd, err)) return 0;
+  return L.total;
+}
+
+int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const hlbm_params* prm,
+                    void* cuda_stream, void* device_buf, size_t device_buf_bytes) {
+  if (!out) { g_init_err = "out is NULL"; return HLBM_ERR_ARG; }
+  *out = nullptr;
+  hlbm_ctx* h = new hlbm_ctx();
+  std::string err;
+  if (!make_layout(nboxes, boxes, prm, h->L, h->boxes, err)) {
+    g_init_err = err;
+    delete h;
+    return HLBM_ERR_ARG;
+  }
+  h->prm = *prm;
+  if (h->prm.bin_capacity == 0) h->prm.bin_capacity = DEFAULT_BIN_CAP;
+  h->stream = (cudaStream_t)cuda_stream;
+  for (int b = 0; b < nboxes; ++b) h->walls |= boxes[b].bc_flags != 0;
+  cudaError_t e;
+  if (device_buf) {
+    if (((uintptr_t)device_buf % ALIGN) || device_buf_bytes < h->L.total) {
+      g_init_err = "device buffer too small or not 256-byte aligned";
+      delete h;
+      return HLBM_ERR_ARG;
+    }
+    h->buf = (char*)device_buf;
+  } else {
+    e = cudaMalloc((void**)&h->buf, h->L.total);
+    if (e != cudaSuccess) {
+      g_init_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+      delete h;
+      return HLBM_ERR_CUDA;
+    }
+    h->owns = true;
+  }
+  e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    g_init_err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+    hlbm_destroy(h);
+    return HLBM_ERR_CUDA;
+  }
+  h->f = h->buf + h->L.off_f;
+  h->d_boxes = (BoxDesc*)(h->buf + h->L.off_boxes);
+  h->P = (double*)(h->buf + h->L.off_P);
+  h->d_shape = (int*)(h->buf + h->L.off_shape);
+  h->d_box = (int*)(h->buf + h->L.off_box);
+  h->rec = (Rec*)(h->buf + h->L.off_rec);
+  for (int k = 0; k < 2; ++k) {
+    h->cnt[k] = (int*)(h->buf + h->L.off_cnt[k]);
+    h->ids[k] = (int*)(h->buf + h->L.off_ids[k]);
+  }
+  h->status = (int*)(h->buf + h->L.off_status);
+  h->stage = (float*)(h->buf + h->L.off_stage);
+  // zero deviations are the fluid at rest with density 1 (f_i = w_i); empty bins
+  e = cudaMemsetAsync(h->buf, 0, h->L.total, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_boxes, h->boxes.data(), sizeof(BoxDesc) * nboxes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    g_init_err = std::string("initialisation: ") + cudaGetErrorString(e);
+    hlbm_destroy(h);
+    return HLBM_ERR_CUDA;
+  }
+  *out = h;
+  return HLBM_OK;
+}
+
+int hlbm_init_lattice(hlbm_handle* out, int nx, int ny, int nz, int bc_flags, const hlbm_params* prm,
+                      void* cuda_stream, void* device_buf, size_t device_buf_bytes) {
+  hlbm_box b{nx, ny, nz, bc_flags};
+  return hlbm_init_batch(out, 1, &b, prm, cuda_stream, device_buf, device_buf_bytes);
+}
+
+void hlbm_destroy(hlbm_handle h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->owns && h->buf) cudaFree(h->buf);
+  delete h;
+}
+
+const char* hlbm_last_error(hlbm_handle h) { return h ? h->err.c_str() : g_init_err.c_str(); }
+
+int hlbm_num_particles(hlbm_handle h) { return h ? h->np : 0; }
+long long hlbm_steps_done(hlbm_handle h) { return h ? h->steps : 0; }
+
+// volume, mass, principal inertia, circumscribed radius and the radius beyond
+// which the indicator of Eq. B vanishes
+static void mass_properties(int shape, const double a[3], double rho, double* V, double* m,
+                            double I[3], double* rc, double* rinf, double eps) {
+  if (shape == HLBM_SPHERE) {
+    *V = 4.0 / 3.0 * PI_D * a[0] * a[0] * a[0];
+    *m = rho * *V;
+    for (int j = 0; j < 3; ++j) I[j] = 0.4 * *m * a[0] * a[0];
+    *rc = a[0];
+    *rinf = a[0] + eps / 2.0;
+  } else if (shape == HLBM_ELLIPSOID) {
+    *V = 4.0 / 3.0 * PI_D * a[0] * a[1] * a[2];
+    *m = rho * *V;
+    I[0] = *m * (a[1] * a[1] + a[2] * a[2]) / 5.0;
+    I[1] = *m * (a[0] * a[0] + a[2] * a[2]) / 5.0;
+    I[2] = *m * (a[0] * a[0] + a[1] * a[1]) / 5.0;
+    const double amax = std::fmax(a[0], std::fmax(a[1], a[2]));
+    const double amin = std::fmin(a[0], std::fmin(a[1], a[2]));
+    *rc = amax;
+    // algebraic distance: d >= (k - 1) a_min and |r| <= k a_max
+    *rinf = amax * (1.0 + eps / (2.0 * amin));
+  } else {
+    *V = 8.0 * a[0] * a[1] * a[2];
+    *m = rho * *V;
+    I[0] = *m * (a[1] * a[1] + a[2] * a[2]) / 3.0;
+    I[1] = *m * (a[0] * a[0] + a[2] * a[2]) / 3.0;
+    I[2] = *m * (a[0] * a[0] + a[1] * a[1]) / 3.0;
+    *rc = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    *rinf = *rc + eps / 2.0;
+  }
+}
+
+static void wrap_host(const BoxDesc& bd, double X[3]) {
+  const int n[3] = {bd.nx, bd.ny, bd.nz};
+  for (int j = 0; j < 3; ++j) {
+    if ((bd.bc >> j) & 1) continue;
+    const double L = (double)n[j];
+    X[j] = X[j] - L * std::floor(X[j] / L);
+    if (X[j] >= L) X[j] -= L;
+  }
+}
+
+static int upload_fields(hlbm_ctx* h, int p0, int n, const std::vector<double>& tab) {
+  // tab: PF_COUNT fields of n values each
+  for (int fld = 0; fld < PF_COUNT; ++fld)
+    CK(cudaMemcpyAsync(h->P + (size_t)fld * h->L.cap + p0, tab.data() + (size_t)fld * n,
+                       sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+  return HLBM_OK;
+}
+
+int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape,
+                       const double* shape_params, const double* X, const double* U,
+                       const double* omega, const double* quat, const double* rho_p) {
+  if (!h) return HLBM_ERR_ARG;
+  if (h->steps > 0) return fail(h, HLBM_ERR_STATE, "particles can only be added before the first step");
+  if (n < 0 || (n > 0 && (!shape || !shape_params || !X || !rho_p)))
+    return fail(h, HLBM_ERR_ARG, "n < 0 or a required array is NULL");
+  if (h->np + n > h->L.cap) return fail(h, HLBM_ERR_CAPACITY, "more particles than max_particles");
+  if (n == 0) return HLBM_OK;
+  std::vector<double> tab((size_t)PF_COUNT * n, 0.0);
+  std::vector<int> sh(n), bx(n);
+  auto T = [&](int fld, int k) -> double& { return tab[(size_t)fld * n + k]; };
+  for (int k = 0; k < n; ++k) {
+    const int b = box_id ? box_id[k] : 0;
+    if (b < 0 || b >= (int)h->boxes.size()) return fail(h, HLBM_ERR_ARG, "box_id out of range");
+    const BoxDesc& bd = h->boxes[b];
+    const int s = shape[k];
+    if (s < HLBM_SPHERE || s > HLBM_CUBOID) return fail(h, HLBM_ERR_ARG, "unknown shape");
+    double a[3];
+    for (int j = 0; j < 3; ++j) {
+      a[j] = (s == HLBM_SPHERE) ? shape_params[3 * k] : shape_params[3 * k + j];
+      if (!(a[j] > 0.0) || !std::isfinite(a[j])) return fail(h, HLBM_ERR_ARG, "shape sizes must be finite and > 0");
+    }
+    const double rho = rho_p[k];
+    if (!(rho > 0.0) || !std::isfinite(rho)) return fail(h, HLBM_ERR_ARG, "rho_p must be finite and > 0");
+    double q[4] = {1.0, 0.0, 0.0, 0.0};
+    if (quat) {
+      double nq = 0.0;
+      for (int j = 0; j < 4; ++j) nq += quat[4 * k + j] * quat[4 * k + j];
+      if (!(nq > 0.0) || !std::isfinite(nq)) return fail(h, HLBM_ERR_ARG, "quaternion must be finite and non-zero");
+      nq = std::sqrt(nq);
+      for (int j = 0; j < 4; ++j) q[j] = quat[4 * k + j] / nq;
+    }
+    double V, m, I[3], rc, rinf;
+    mass_properties(s, a, rho, &V, &m, I, &rc, &rinf, h->prm.eps);
+    double x[3];
+    const int nn[3] = {bd.nx, bd.ny, bd.nz};
+    for (int j = 0; j < 3; ++j) {
+      x[j] = X[3 * k + j];
+      const double u = U ? U[3 * k + j] : 0.0, w = omega ? omega[3 * k + j] : 0.0;
+      if (!std::isfinite(x[j]) || !std::isfinite(u) || !std::isfinite(w))
+        return fail(h, HLBM_ERR_ARG, "non-finite particle state");
+      if ((bd.bc >> j) & 1) {
+        if (!(x[j] > -0.5 && x[j] < nn[j] - 0.5)) return fail(h, HLBM_ERR_ARG, "centre outside the box on a wall axis");
+      } else if (!(2.0 * (rc + h->prm.eps / 2.0 + 2.0) < nn[j])) {
+        return fail(h, HLBM_ERR_ARG, "particle spans half a periodic axis or more");
+      }
+      T(PF_U + j, k) = u;
+      T(PF_W + j, k) = w;
+      T(PF_I + j, k) = I[j];
+      T(PF_A + j, k) = a[j];
+    }
+    wrap_host(bd, x);
+    for (int j = 0; j < 3; ++j) T(PF_X + j, k) = x[j];
+    for (int j = 0; j < 4; ++j) T(PF_Q + j, k) = q[j];
+    T(PF_M, k) = m;
+    T(PF_V, k) = V;
+    T(PF_RHO, k) = rho;
+    T(PF_RC, k) = rc;
+    T(PF_RINF, k) = rinf;
+    sh[k] = s;
+    bx[k] = b;
+  }
+  const int p0 = h->np;
+  int rc = upload_fields(h, p0, n, tab);
+  if (rc != HLBM_OK) return rc;
+  CK(cudaMemcpyAsync(h->d_shape + p0, sh.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_box + p0, bx.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+  h->np += n;
+  h->h_shape.insert(h->h_shape.end(), sh.begin(), sh.end());
+  h->h_box.insert(h->h_box.end(), bx.begin(), bx.end());
+  CK(launch_records(part_args(h, 0), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  drop_graphs(h);
+  return HLBM_OK;
+}
+
+int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, const double* omega,
+                            const double* quat) {
+  if (!h) return HLBM_ERR_ARG;
+  const int n = h->np;
+  if (n == 0) return HLBM_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  std::vector<double> tmp((size_t)n * 4);
+  auto put = [&](int fld, int ncomp, const double* src, bool wrapX) -> int {
+    for (int j = 0; j < ncomp; ++j) {
+      for (int k = 0; k < n; ++k) tmp[k] = src[(size_t)ncomp * k + j];
+      CK(cudaMemcpy(h->P + (size_t)(fld + j) * h->L.cap, tmp.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    }
+    (void)wrapX;
+    return HLBM_OK;
+  };
+  int rc;
+  if (X) {
+    std::vector<double> xw((size_t)3 * n);
+    for (int k = 0; k < n; ++k) {
+      double x[3] = {X[3 * k], X[3 * k + 1], X[3 * k + 2]};
+      for (int j = 0; j < 3; ++j)
+        if (!std::isfinite(x[j])) return fail(h, HLBM_ERR_ARG, "non-finite position");
+      wrap_host(h->boxes[h->h_box[k]], x);
+      for (int j = 0; j < 3; ++j) xw[3 * k + j] = x[j];
+    }
+    if ((rc = put(PF_X, 3, xw.data(), true)) != HLBM_OK) return rc;
+  }
+  if (U && (rc = put(PF_U, 3, U, false)) != HLBM_OK) return rc;
+  if (omega && (rc = put(PF_W, 3, omega, false)) != HLBM_OK) return rc;
+  if (quat) {
+    std::vector<double> qn((size_t)4 * n);
+    for (int k = 0; k < n; ++k) {
+      double nq = 0.0;
+      for (int j = 0; j < 4; ++j) nq += quat[4 * k + j] * quat[4 * k + j];
+      if (!(nq > 0.0) || !std::isfinite(nq)) return fail(h, HLBM_ERR_ARG, "quaternion must be finite and non-zero");
+      nq = std::sqrt(nq);
+      for (int j = 0; j < 4; ++j) qn[4 * k + j] = quat[4 * k + j] / nq;
+    }
+    if ((rc = put(PF_Q, 4, qn.data(), false)) != HLBM_OK) return rc;
+  }
+  CK(launch_records(part_args(h, 0), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return HLBM_OK;
+}
+
+int hlbm_step(hlbm_handle h, int nsteps) {
+  if (!h) return HLBM_ERR_ARG;
+  if (nsteps < 0) return fail(h, HLBM_ERR_ARG, "nsteps < 0");
+  if (nsteps == 0) return HLBM_OK;
+  if (!h->graphs_ok) {
+    const int rc = build_graphs(h);
+    if (rc != HLBM_OK) return rc;
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    CK(cudaGraphLaunch(h->exec[(h->steps + k) & 1], h->stream));
+  }
+  h->steps += nsteps;
+  return HLBM_OK;
+}
+
+int hlbm_sync(hlbm_handle h) {
+  if (!h) return HLBM_ERR_ARG;
+  return read_status(h);
+}
+
+int hlbm_particle_state(hlbm_handle h, double* X, double* U, double* omega, double* quat, double* F,
+                        double* T) {
+  if (!h) return HLBM_ERR_ARG;
+  const int st = read_status(h);
+  const int n = h->np;
+  if (n > 0) {
+    std::vector<double> tmp((size_t)n);
+    auto get = [&](int fld, int ncomp, double* dst) -> int {
+      for (int j = 0; j < ncomp; ++j) {
+        CK(cudaMemcpy(tmp.data(), h->P + (size_t)(fld + j) * h->L.cap, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        for (int k = 0; k < n; ++k) dst[(size_t)ncomp * k + j] = tmp[k];
+      }
+      return HLBM_OK;
+    };
+    int rc;
+    if (X && (rc = get(PF_X, 3, X)) != HLBM_OK) return rc;
+    if (U && (rc = get(PF_U, 3, U)) != HLBM_OK) return rc;
+    if (omega && (rc = get(PF_W, 3, omega)) != HLBM_OK) return rc;
+    if (quat && (rc = get(PF_Q, 4, quat)) != HLBM_OK) return rc;
+    if (F && (rc = get(PF_F, 3, F)) != HLBM_OK) return rc;
+    if (T && (rc = get(PF_T, 3, T)) != HLBM_OK) return rc;
+  }
+  return st;
+}
+
+int hlbm_get_populations(hlbm_handle h, int box, double* host_f) {
+  if (!h) return HLBM_ERR_ARG;
+  if (box < 0 || box >= (int)h->boxes.size() || !host_f) return fail(h, HLBM_ERR_ARG, "bad box or NULL array");
+  const BoxDesc& bd = h->boxes[box];
+  const long long N = (long long)bd.nx * bd.ny * bd.nz;
+  const LbmArgs la = lbm_args(h, 0);
+  const int parity = (int)(h->steps & 1);
+  std::vector<float> st((size_t)Q * h->L.stage_cells);
+  for (long long c0 = 0; c0 < N; c0 += h->L.stage_cells) {
+    const long long n = (N - c0 < h->L.stage_cells) ? N - c0 : h->L.stage_cells;
+    CK(launch_gather(la, h->prm.precision, parity, box, c0, n, h->stage, h->stream));
+    CK(cudaMemcpyAsync(st.data(), h->stage, sizeof(float) * Q * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < Q; ++i) {
+      const double w = wq(i);
+      for (long long k = 0; k < n; ++k) host_f[(size_t)i * N + c0 + k] = w + (double)st[(size_t)i * n + k];
+    }
+  }
+  return HLBM_OK;
+}
+
+int hlbm_set_populations(hlbm_handle h, int box, const double* host_f) {
+  if (!h) return HLBM_ERR_ARG;
+  if (box < 0 || box >= (int)h->boxes.size() || !host_f) return fail(h, HLBM_ERR_ARG, "bad box or NULL array");
+  const BoxDesc& bd = h->boxes[box];
+  const long long N = (long long)bd.nx * bd.ny * bd.nz;
+  const LbmArgs la = lbm_args(h, 0);
+  const int parity = (int)(h->steps & 1);
+  std::vector<float> st((size_t)Q * h->L.stage_cells);
+  for (long long c0 = 0; c0 < N; c0 += h->L.stage_cells) {
+    const long long n = (N - c0 < h->L.stage_cells) ? N - c0 : h->L.stage_cells;
+    for (int i = 0; i < Q; ++i) {
+      const double w = wq(i);
+      for (long long k = 0; k < n; ++k) st[(size_t)i * n + k] = (float)(host_f[(size_t)i * N + c0 + k] - w);
+    }
+    CK(cudaMemcpyAsync(h->stage, st.data(), sizeof(float) * Q * n, cudaMemcpyHostToDevice, h->stream));
+    CK(launch_scatter(la, h->prm.precision, parity, box, c0, n, h->stage, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return HLBM_OK;
+}
+
+int hlbm_set_launch(hlbm_handle h, int tile_y, int tile_z) {
+  if (!h) return HLBM_ERR_ARG;
+  auto ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8; };
+  if (!ok(tile_y) || !ok(tile_z)) return fail(h, HLBM_ERR_ARG, "tile_y and tile_z must be 1, 2, 4 or 8");
+  if (tile_y != h->sub_y || tile_z != h->sub_z) {
+    h->sub_y = tile_y;
+    h->sub_z = tile_z;
+    drop_graphs(h);
+  }
+  return HLBM_OK;
+}
+
+int hlbm_get_launch(hlbm_handle h, int* tile_y, int* tile_z) {
+  if (!h) return HLBM_ERR_ARG;
+  if (tile_y) *tile_y = h->sub_y;
+  if (tile_z) *tile_z = h->sub_z;
+  return HLBM_OK;
+}
+
+int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, float* ms_per_step) {
+  if (!h) return HLBM_ERR_ARG;
+  if (nsteps < 1) return fail(h, HLBM_ERR_ARG, "nsteps < 1");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int by = h->sub_y, bz = h->sub_z;
+  const int vals[4] = {1, 2, 4, 8};
+  int rc = HLBM_OK;
+  for (int iy = 0; iy < 4 && rc == HLBM_OK; ++iy)
+    for (int iz = 0; iz < 4 && rc == HLBM_OK; ++iz) {
+      rc = hlbm_set_launch(h, vals[iy], vals[iz]);
+      if (rc == HLBM_OK) rc = hlbm_step(h, 2);  // warm-up and graph build
+      if (rc != HLBM_OK) break;
+      cudaEventRecord(e0, h->stream);
+      rc = hlbm_step(h, nsteps);
+      cudaEventRecord(e1, h->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(h, HLBM_ERR_CUDA, "autotune timing failed"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= nsteps;
+      if (ms < best) { best = ms; by = vals[iy]; bz = vals[iz]; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != HLBM_OK) return rc;
+  rc = hlbm_set_launch(h, by, bz);
+  if (tile_y) *tile_y = by;
+  if (tile_z) *tile_z = bz;
+  if (ms_per_step) *ms_per_step = best;
+  if (rc != HLBM_OK) return rc;
+  return read_status(h);
+}
+
+int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]) {
+  if (!h || !ms) return HLBM_ERR_ARG;
+  if (nsteps < 1) return fail(h, HLBM_ERR_ARG, "nsteps < 1");
+  cudaEvent_t ev[4];
+  for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&ev[k]));
+  double acc[3] = {0, 0, 0};
+  int rc = HLBM_OK;
+  for (int s = 0; s < nsteps; ++s) {
+    const int parity = (int)(h->steps & 1);
+    const PartArgs pa = part_args(h, parity);
+    cudaEventRecord(ev[0], h->stream);
+    if (h->np > 0) launch_mea(pa, h->prm.precision, parity, h->stream);
+    cudaEventRecord(ev[1], h->stream);
+    if (h->np > 0) launch_update(pa, h->stream);
+    cudaEventRecord(ev[2], h->stream);
+    launch_collide(lbm_args(h, parity), h->prm.precision, parity, h->walls, h->np > 0, h->stream);
+    cudaEventRecord(ev[3], h->stream);
+    const cudaError_t e = cudaEventSynchronize(ev[3]);
+    if (e != cudaSuccess) { rc = fail(h, HLBM_ERR_CUDA, std::string("kernel timing: ") + cudaGetErrorString(e)); break; }
+    for (int k = 0; k < 3; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      acc[k] += t;
+    }
+    h->steps += 1;
+  }
+  for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
+  if (rc != HLBM_OK) return rc;
+  for (int k = 0; k < 3; ++k) ms[k] = (float)(acc[k] / nsteps);
+  return read_status(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// hlbm_internal.cuh -- device data layout and kernel launchers of libhlbm.
+//
+// HBM layout of one handle (all arrays carved from one device buffer):
+//   populations   19 planes of `plane` elements (float or half), plane i holds
+//                 slot i of every cell of every box, box b at cell offset
+//                 box.cell_off, x fastest.  Storage is the deviation f_i - w_i
+//                 (times 2^s for half).  In-place AA pattern: after an even
+//                 number of steps slot i of cell x holds f_i(x); after an odd
+//                 number slot ibar of cell x - c_i holds f_i(x) (or slot i of
+//                 x when x - c_i lies beyond a wall).
+//   particles     FP64 structure of arrays, field-major (PF_* below).
+//   records       one 128-byte FP32 record per particle (Rec), rebuilt after
+//                 every Newton-Euler update, read by the collision and the
+//                 momentum exchange.
+//   bins          two alternating sets of per-tile particle lists (tile =
+//                 32 x 8 x 8 cells): count[tile] and ids[tile * cap + k].
+//   status        one int of error flags (ST_*).
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hlbm {
+
+constexpr int Q = 19;
+constexpr int TILE_X = 32, TILE_Y = 8, TILE_Z = 8;  // particle-bin tile
+
+// D3Q19 (Sec. 3.1) in this library's order; opposite of i >= 1 is i +- 1
+__host__ __device__ constexpr int cx(int i) {
+  return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+  return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+  return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr double wq(int i) {
+  return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+struct BoxDesc {
+  int nx, ny, nz, bc;        // bc: bit a set = walls on axis a
+  int ntx, nty, ntz;         // bin tiles per axis
+  int pad0;
+  long long cell_off;        // first cell of the box in every plane
+  long long tile_off;        // first bin tile of the box
+};
+
+// FP64 particle table fields (each an array of `cap` doubles)
+enum {
+  PF_X = 0, PF_U = 3, PF_W = 6, PF_Q = 9, PF_F = 13, PF_T = 16,
+  PF_M = 19, PF_V = 20, PF_I = 21, PF_RHO = 24, PF_A = 25, PF_RC = 28, PF_RINF = 29,
+  PF_COUNT = 30
+};
+
+// FP32 coupling record of one particle (128 bytes)
+struct __align__(16) Rec {
+  float xh[3], xl[3];  // centre as float pair: X = xh + xl
+  float u[3], w[3];    // velocity, angular velocity
+  float M[9];          // rotation body -> world, row-major (identity for spheres)
+  float a[3];          // radius / semi-axes / half-extents
+  float ia[3];         // fp32(1 / a_j) (ellipsoid inside test)
+  float rinf2;         // square of a radius beyond which B = 0
+  float in2;           // fp32(r * r) (sphere inside test)
+  int shape;
+  int box;
+  int pid;
+};
+static_assert(sizeof(Rec) == 128, "record size");
+
+enum { ST_UNSTABLE = 1, ST_CAPACITY = 2, ST_LEFT_DOMAIN = 4 };
+
+struct LbmArgs {
+  void* f;                  // population planes (float* or __half*)
+  long long plane;          // elements per plane
+  const BoxDesc* boxes;
+  int nboxes;
+  int sub_y, sub_z;         // brick per block: 32 x sub_y x sub_z cells
+  int nsub;                 // bricks per bin tile = (8/sub_y)*(8/sub_z)
+  long long nbricks;        // total bricks (grid size)
+  float omega;              // 1 / tau
+  float ff[3];              // fluid force density
+  float eps, inv_eps;
+  float scale, inv_scale;   // half storage scale 2^s and 2^-s
+  const int* bin_count;     // bins of this step
+  const int* bin_ids;
+  int bin_cap;
+  const Rec* rec;
+  int* status;
+};
+
+struct PartArgs {
+  double* P;                // FP64 table, field-major with stride cap
+  int cap, np;
+  const int* shape;         // [np]
+  const int* box;           // [np]
+  Rec* rec;
+  const BoxDesc* boxes;
+  double g[3];
+  double eps;
+  // momentum exchange input
+  const void* f;
+  long long plane;
+  float scale, inv_scale;
+  // bins written by the update (this step) and cleared (other parity)
+  int* bin_count;
+  int* bin_ids;
+  int* bin_count_clear;
+  long long ntiles;
+  int bin_cap;
+  int* status;
+};
+
+// launchers (stream-ordered, no synchronisation)
+cudaError_t launch_collide(const LbmArgs& a, int precision, int parity, bool walls, bool couple,
+                           cudaStream_t s);
+cudaError_t launch_mea(const PartArgs& a, int precision, int parity, cudaStream_t s);
+cudaError_t launch_update(const PartArgs& a, cudaStream_t s);
+cudaError_t launch_records(const PartArgs& a, cudaStream_t s);
+// logical populations f_i - w_i of cells [c0, c0 + n) of one box, as float,
+// into/out of stage[i * n + k]
+cudaError_t launch_gather(const LbmArgs& a, int precision, int parity, int box, long long c0,
+                          long long n, float* stage, cudaStream_t s);
+cudaError_t launch_scatter(const LbmArgs& a, int precision, int parity, int box, long long c0,
+                           long long n, const float* stage, cudaStream_t s);
+
+}  // namespace hlbm

@@ -1,0 +1,313 @@
+// lbm_kernels.cu -- fused D3Q19 collide-and-stream with HLBM coupling.
+//
+// One kernel per step does, for every cell (arXiv:2312.14172):
+//   rho = sum_i f_i, rho u = sum_i c_i f_i                       (Sec. 3.1)
+//   B = max_p B_p(d_s,p(x)), u_p(x) = U + omega x (x - X)        (Eq. B, Sec. 3.2)
+//   Delta u = B (u_p - u) + F_f / rho                            (Eq. hlbm:du)
+//   f*_i = f_i - (f_i - f^eq_i(rho, u)) / tau
+//          + f^eq_i(rho, u + Delta u) - f^eq_i(rho, u)           (Eqs. collide, bgk, kupershtokh)
+//   f_i(x + c_i, t + 1) = f*_i(x, t), half-way bounce-back at walls (Eq. stream)
+// in the in-place AA pattern: even steps read and write only the cell's own
+// slots (the post-collision value of direction i goes to slot ibar), odd
+// steps read from and write to the neighbours.  Populations are stored as
+// deviations d_i = f_i - w_i (float, or half scaled by 2^s); all arithmetic
+// is FP32 on deviations, which keeps the small non-equilibrium parts exact to
+// FP32 rounding instead of to the rounding of f ~ w_i.
+#include "hlbm_internal.cuh"
+
+namespace hlbm {
+
+constexpr int MAX_CAND = 64;  // particle records staged per block
+#ifndef HLBM_CS_MINBLOCKS
+#define HLBM_CS_MINBLOCKS 3
+#endif
+
+template <typename S> struct Pop;
+template <> struct Pop<float> {
+  static __device__ __forceinline__ float ld(const float* p, float) { return *p; }
+  static __device__ __forceinline__ void st(float* p, float v, float) { *p = v; }
+};
+template <> struct Pop<__half> {
+  static __device__ __forceinline__ float ld(const __half* p, float inv_s) {
+    return __half2float(*p) * inv_s;
+  }
+  static __device__ __forceinline__ void st(__half* p, float v, float s) { *p = __float2half_rn(v * s); }
+};
+
+// f^eq_i(rho, u) - w_i (Eq. maxbolt with c_s^2 = 1/3)
+template <int I>
+__device__ __forceinline__ float feq_dev(float rho, float ux, float uy, float uz, float uu) {
+  constexpr float w = (float)wq(I);
+  const float cu = (float)cx(I) * ux + (float)cy(I) * uy + (float)cz(I) * uz;
+  return w * (rho - 1.0f) + w * rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+}
+
+// indicator of Eq. B written as (1 - sin(pi d / eps)) / 2 on the ramp, which
+// equals cos^2((pi/2)(d/eps + 1/2))
+__device__ __forceinline__ float indicator(float d, float eps, float inv_eps) {
+  if (d <= -0.5f * eps) return 1.0f;
+  if (d >= 0.5f * eps) return 0.0f;
+  return 0.5f - 0.5f * sinpif(d * inv_eps);
+}
+
+// signed distance of a particle at offset r (world frame), FP32
+__device__ __forceinline__ float sdf(const Rec& R, float rx, float ry, float rz, float r2) {
+  if (R.shape == 0) return sqrtf(r2) - R.a[0];
+  // body frame b = M^T r
+  const float b0 = R.M[0] * rx + R.M[3] * ry + R.M[6] * rz;
+  const float b1 = R.M[1] * rx + R.M[4] * ry + R.M[7] * rz;
+  const float b2 = R.M[2] * rx + R.M[5] * ry + R.M[8] * rz;
+  if (R.shape == 1) {
+    const float e0 = b0 * R.ia[0], e1 = b1 * R.ia[1], e2 = b2 * R.ia[2];
+    const float k2 = e0 * e0 + e1 * e1 + e2 * e2;
+    const float g0 = e0 * R.ia[0], g1 = e1 * R.ia[1], g2v = e2 * R.ia[2];
+    const float g2 = g0 * g0 + g1 * g1 + g2v * g2v;
+    if (g2 == 0.0f) return -fminf(R.a[0], fminf(R.a[1], R.a[2]));
+    const float k = sqrtf(k2);
+    return (k - 1.0f) * k * rsqrtf(g2);
+  }
+  const float q0 = fabsf(b0) - R.a[0], q1 = fabsf(b1) - R.a[1], q2 = fabsf(b2) - R.a[2];
+  const float o0 = fmaxf(q0, 0.0f), o1 = fmaxf(q1, 0.0f), o2 = fmaxf(q2, 0.0f);
+  return sqrtf(o0 * o0 + o1 * o1 + o2 * o2) + fminf(fmaxf(q0, fmaxf(q1, q2)), 0.0f);
+}
+
+__device__ __forceinline__ int find_box(const BoxDesc* boxes, int nboxes, long long tile) {
+  int lo = 0, hi = nboxes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (boxes[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// neighbour index helper: per-axis neighbour offsets; -1 marks a node beyond
+// a wall (only possible when WALLS)
+template <bool WALLS>
+struct Nbr {
+  int xm, xp, ym, yp, zm, zp;  // neighbour coordinates (x) or row/plane offsets (y, z)
+  int x, y, z;                 // own coordinate and row/plane offsets
+  __device__ __forceinline__ int at(int dx, int dy, int dz) const {
+    const int a = dx < 0 ? xm : (dx > 0 ? xp : x);
+    const int b = dy < 0 ? ym : (dy > 0 ? yp : y);
+    const int c = dz < 0 ? zm : (dz > 0 ? zp : z);
+    if (WALLS && (a < 0 || b < 0 || c < 0)) return -1;
+    return a + b + c;
+  }
+};
+
+template <bool WALLS>
+__device__ __forceinline__ Nbr<WALLS> make_nbr(const BoxDesc& bd, int x, int y, int z) {
+  Nbr<WALLS> n;
+  const int nx = bd.nx, ny = bd.ny, nz = bd.nz, nxy = nx * ny;
+  const bool wx = WALLS && (bd.bc & 1), wy = WALLS && (bd.bc & 2), wz = WALLS && (bd.bc & 4);
+  n.x = x;
+  n.y = y * nx;
+  n.z = z * nxy;
+  n.xm = x > 0 ? x - 1 : (wx ? -1 : nx - 1);
+  n.xp = x < nx - 1 ? x + 1 : (wx ? -1 : 0);
+  n.ym = y > 0 ? (y - 1) * nx : (wy ? -1 : (ny - 1) * nx);
+  n.yp = y < ny - 1 ? (y + 1) * nx : (wy ? -1 : 0);
+  n.zm = z > 0 ? (z - 1) * nxy : (wz ? -1 : (nz - 1) * nxy);
+  n.zp = z < nz - 1 ? (z + 1) * nxy : (wz ? -1 : 0);
+  return n;
+}
+
+template <typename S, int PAR, bool WALLS, bool COUPLE>
+__global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(LbmArgs a) {
+  __shared__ Rec srec[COUPLE ? MAX_CAND : 1];
+  const long long brick = blockIdx.x;
+  const long long tile = brick / a.nsub;
+  const int sub = (int)(brick - tile * a.nsub);
+  const int b = a.nboxes > 1 ? find_box(a.boxes, a.nboxes, tile) : 0;
+  const BoxDesc bd = a.boxes[b];
+  const long long lt = tile - bd.tile_off;
+  const int tx = (int)(lt % bd.ntx);
+  const long long t2 = lt / bd.ntx;
+  const int ty = (int)(t2 % bd.nty);
+  const int tz = (int)(t2 / bd.nty);
+  const int nsy = TILE_Y / a.sub_y;
+  const int sy = sub % nsy, sz = sub / nsy;
+
+  int cnt = 0;
+  if (COUPLE) {
+    cnt = min(min(a.bin_count[tile], a.bin_cap), MAX_CAND);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nth = blockDim.x * blockDim.y;
+    const int* ids = a.bin_ids + tile * (long long)a.bin_cap;
+    for (int k = tid; k < cnt * 32; k += nth) {
+      const int j = k >> 5, e = k & 31;
+      reinterpret_cast<int*>(&srec[j])[e] = reinterpret_cast<const int*>(&a.rec[ids[j]])[e];
+    }
+    __syncthreads();
+  }
+
+  const int x = tx * TILE_X + threadIdx.x;
+  const int y = ty * TILE_Y + sy * a.sub_y + threadIdx.y;
+  if (x >= bd.nx || y >= bd.ny) return;
+  const int z0 = tz * TILE_Z + sz * a.sub_z;
+  const int z1 = min(z0 + a.sub_z, bd.nz);
+  S* __restrict__ f = reinterpret_cast<S*>(a.f) + bd.cell_off;
+  const long long P = a.plane;
+  const float Lx = (float)bd.nx, Ly = (float)bd.ny, Lz = (float)bd.nz;
+
+  for (int z = z0; z < z1; ++z) {
+    const int c = (z * bd.ny + y) * bd.nx + x;
+    Nbr<WALLS> nb;
+    if (PAR == 1) nb = make_nbr<WALLS>(bd, x, y, z);
+    float d[Q];
+    // load the post-streaming deviations f_i(x) - w_i
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (PAR == 0) {
+        d[i] = Pop<S>::ld(f + i * P + c, a.inv_scale);
+      } else {
+        const int src = (i == 0) ? c : nb.at(-cx(i), -cy(i), -cz(i));
+        d[i] = (src >= 0) ? Pop<S>::ld(f + opp(i) * P + src, a.inv_scale)
+                          : Pop<S>::ld(f + i * P + c, a.inv_scale);
+      }
+    }
+    float rho = 1.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      rho += d[i];
+      if (cx(i)) jx += (float)cx(i) * d[i];
+      if (cy(i)) jy += (float)cy(i) * d[i];
+      if (cz(i)) jz += (float)cz(i) * d[i];
+    }
+    if (!(rho > 0.0f && rho < 1e30f)) atomicOr(a.status, ST_UNSTABLE);
+    const float irho = 1.0f / rho;
+    const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
+    float dux = a.ff[0] * irho, duy = a.ff[1] * irho, duz = a.ff[2] * irho;
+    if (COUPLE) {
+      float bestB = 0.0f, upx = 0.0f, upy = 0.0f, upz = 0.0f;
+      int bestp = 0x7fffffff;
+      for (int k = 0; k < cnt; ++k) {
+        const Rec& R = srec[k];
+        float r0x = (float)x - R.xh[0], r0y = (float)y - R.xh[1], r0z = (float)z - R.xh[2];
+        if (!(bd.bc & 1)) { if (r0x > 0.5f * Lx) r0x -= Lx; else if (r0x < -0.5f * Lx) r0x += Lx; }
+        if (!(bd.bc & 2)) { if (r0y > 0.5f * Ly) r0y -= Ly; else if (r0y < -0.5f * Ly) r0y += Ly; }
+        if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
+        const float rx = r0x - R.xl[0], ry = r0y - R.xl[1], rz = r0z - R.xl[2];
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        if (r2 < R.rinf2) {
+          const float B = indicator(sdf(R, rx, ry, rz, r2), a.eps, a.inv_eps);
+          if (B > bestB || (B == bestB && B > 0.0f && R.pid < bestp)) {
+            bestB = B;
+            bestp = R.pid;
+            upx = R.u[0] + (R.w[1] * rz - R.w[2] * ry);
+            upy = R.u[1] + (R.w[2] * rx - R.w[0] * rz);
+            upz = R.u[2] + (R.w[0] * ry - R.w[1] * rx);
+          }
+        }
+      }
+      if (bestB > 0.0f) {
+        dux += bestB * (upx - ux);
+        duy += bestB * (upy - uy);
+        duz += bestB * (upz - uz);
+      }
+    }
+    const float uu = ux * ux + uy * uy + uz * uz;
+    const float vx = ux + dux, vy = uy + duy, vz = uz + duz;
+    const float vv = vx * vx + vy * vy + vz * vz;
+    const float om1 = 1.0f - a.omega;
+    float o[Q];
+#define HLBM_COLLIDE(I) \
+    o[I] = om1 * (d[I] - feq_dev<I>(rho, ux, uy, uz, uu)) + feq_dev<I>(rho, vx, vy, vz, vv);
+    HLBM_COLLIDE(0) HLBM_COLLIDE(1) HLBM_COLLIDE(2) HLBM_COLLIDE(3) HLBM_COLLIDE(4)
+    HLBM_COLLIDE(5) HLBM_COLLIDE(6) HLBM_COLLIDE(7) HLBM_COLLIDE(8) HLBM_COLLIDE(9)
+    HLBM_COLLIDE(10) HLBM_COLLIDE(11) HLBM_COLLIDE(12) HLBM_COLLIDE(13) HLBM_COLLIDE(14)
+    HLBM_COLLIDE(15) HLBM_COLLIDE(16) HLBM_COLLIDE(17) HLBM_COLLIDE(18)
+#undef HLBM_COLLIDE
+    // store the post-collision deviations, streamed (AA pattern)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (PAR == 0) {
+        Pop<S>::st(f + opp(i) * P + c, o[i], a.scale);
+      } else {
+        const int dst = (i == 0) ? c : nb.at(cx(i), cy(i), cz(i));
+        if (dst >= 0) Pop<S>::st(f + i * P + dst, o[i], a.scale);
+        else Pop<S>::st(f + opp(i) * P + c, o[i], a.scale);
+      }
+    }
+  }
+}
+
+// logical populations of a range of cells of one box
+template <typename S, int PAR, bool GATHER>
+__global__ void gather_scatter_kernel(LbmArgs a, int box, long long c0, long long n, float* stage) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const BoxDesc bd = a.boxes[box];
+  const long long cl = c0 + k;
+  const int x = (int)(cl % bd.nx);
+  const long long t = cl / bd.nx;
+  const int y = (int)(t % bd.ny);
+  const int z = (int)(t / bd.ny);
+  const int c = (int)cl;
+  S* f = reinterpret_cast<S*>(a.f) + bd.cell_off;
+  const long long P = a.plane;
+  const Nbr<true> nb = make_nbr<true>(bd, x, y, z);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    S* slot;
+    if (PAR == 0 || i == 0) {
+      slot = f + i * P + c;
+    } else {
+      const int src = nb.at(-cx(i), -cy(i), -cz(i));
+      slot = (src >= 0) ? f + opp(i) * P + src : f + i * P + c;
+    }
+    if (GATHER) stage[i * n + k] = Pop<S>::ld(slot, a.inv_scale);
+    else Pop<S>::st(slot, stage[i * n + k], a.scale);
+  }
+}
+
+template <typename S, int PAR, bool W, bool C>
+static cudaError_t launch_cs(const LbmArgs& a, cudaStream_t s) {
+  dim3 block(TILE_X, a.sub_y);
+  collide_stream_kernel<S, PAR, W, C><<<(unsigned)a.nbricks, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t launch_cs_prec(const LbmArgs& a, int parity, bool walls, bool couple,
+                                  cudaStream_t s) {
+  if (parity == 0) {
+    // even steps never touch a neighbour: walls need no special case
+    return couple ? launch_cs<S, 0, false, true>(a, s) : launch_cs<S, 0, false, false>(a, s);
+  }
+  if (walls) return couple ? launch_cs<S, 1, true, true>(a, s) : launch_cs<S, 1, true, false>(a, s);
+  return couple ? launch_cs<S, 1, false, true>(a, s) : launch_cs<S, 1, false, false>(a, s);
+}
+
+cudaError_t launch_collide(const LbmArgs& a, int precision, int parity, bool walls, bool couple,
+                           cudaStream_t s) {
+  if (a.nbricks <= 0) return cudaSuccess;
+  return precision == 0 ? launch_cs_prec<float>(a, parity, walls, couple, s)
+                        : launch_cs_prec<__half>(a, parity, walls, couple, s);
+}
+
+template <typename S, bool G>
+static cudaError_t launch_gs(const LbmArgs& a, int parity, int box, long long c0, long long n,
+                             float* stage, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (parity == 0) gather_scatter_kernel<S, 0, G><<<blocks, 256, 0, s>>>(a, box, c0, n, stage);
+  else gather_scatter_kernel<S, 1, G><<<blocks, 256, 0, s>>>(a, box, c0, n, stage);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const LbmArgs& a, int precision, int parity, int box, long long c0,
+                          long long n, float* stage, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  return precision == 0 ? launch_gs<float, true>(a, parity, box, c0, n, stage, s)
+                        : launch_gs<__half, true>(a, parity, box, c0, n, stage, s);
+}
+
+cudaError_t launch_scatter(const LbmArgs& a, int precision, int parity, int box, long long c0,
+                           long long n, const float* stage, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  float* st = const_cast<float*>(stage);
+  return precision == 0 ? launch_gs<float, false>(a, parity, box, c0, n, st, s)
+                        : launch_gs<__half, false>(a, parity, box, c0, n, st, s);
+}
+
+}  // namespace hlbm

@@ -1,0 +1,443 @@
+// particle_kernels.cu -- fluid -> particle coupling and particle motion.
+//
+//   mea_kernel      momentum exchange (Eq. hlbm:mea) summed over the cells
+//                   whose centre lies inside each particle (Eqs.
+//                   hydrodynamicforce, hydrodynamictorque); one thread block per
+//                   particle walks the particle's bounding box; per-cell sums
+//                   in FP32, warp shuffles in FP32, block sum in FP64 in a fixed
+//                   order (deterministic).
+//   update_kernel   weight minus buoyancy (Sec. 5.1), Newton-Euler update
+//                   (Eqs. particlemotiontrans, motionrot) in FP64, the FP32
+//                   coupling record of the new state, and the per-tile particle
+//                   lists (the single-GPU form of the paper's particle
+//                   assignment, Sec. 4.2.2) that the collision kernel reads.
+//   records_kernel  coupling records only (after particles are added or set).
+#include "hlbm_internal.cuh"
+
+namespace hlbm {
+
+template <typename S> struct PopR;
+template <> struct PopR<float> {
+  static __device__ __forceinline__ float ld(const float* p, float) { return *p; }
+};
+template <> struct PopR<__half> {
+  static __device__ __forceinline__ float ld(const __half* p, float inv_s) {
+    return __half2float(*p) * inv_s;
+  }
+};
+
+// rotation body -> world of a unit quaternion, every operation rounded on its
+// own (no contraction) so that the FP32 copy matches other FP64 evaluations of
+// the same formula bit for bit
+__device__ void rotation_rn(const double q[4], double R[9]) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, y), __dmul_rn(z, z))));
+  R[1] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, y), __dmul_rn(w, z)));
+  R[2] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, z), __dmul_rn(w, y)));
+  R[3] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, y), __dmul_rn(w, z)));
+  R[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(z, z))));
+  R[5] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
+  R[6] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, z), __dmul_rn(w, y)));
+  R[7] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
+  R[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))));
+}
+
+__device__ __forceinline__ double pget(const double* P, int cap, int field, int p) {
+  return P[(long long)field * cap + p];
+}
+__device__ __forceinline__ void pset(double* P, int cap, int field, int p, double v) {
+  P[(long long)field * cap + p] = v;
+}
+
+__device__ void build_record(const double* P, int cap, int p, int shape, int box, Rec& R) {
+  double q[4], Rm[9];
+  for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
+  rotation_rn(q, Rm);
+  for (int j = 0; j < 3; ++j) {
+    const double X = pget(P, cap, PF_X + j, p);
+    const float xh = __double2float_rn(X);
+    R.xh[j] = xh;
+    R.xl[j] = __double2float_rn(X - (double)xh);
+    R.u[j] = (float)pget(P, cap, PF_U + j, p);
+    R.w[j] = (float)pget(P, cap, PF_W + j, p);
+    const double aj = pget(P, cap, PF_A + j, p);
+    R.a[j] = __double2float_rn(aj);
+    R.ia[j] = __double2float_rn(1.0 / aj);
+  }
+  for (int k = 0; k < 9; ++k) R.M[k] = __double2float_rn(Rm[k]);
+  const double a0 = pget(P, cap, PF_A, p);
+  R.in2 = __double2float_rn(a0 * a0);
+  // B vanishes beyond r_inf; a slightly larger FP32 bound keeps the test safe
+  const double rinf = pget(P, cap, PF_RINF, p) + 0.01;
+  R.rinf2 = (float)(rinf * rinf);
+  R.shape = shape;
+  R.box = box;
+  R.pid = p;
+}
+
+// "centre inside the particle" in FP32, each operation rounded on its own:
+//   r = (fp32(cell) - xh, minimum image) - xl;  sphere |r|^2 < fp32(a^2);
+//   ellipsoid |M^T r / a|^2 < 1;  cuboid |M^T r| < a componentwise
+__device__ __forceinline__ bool inside_fp32(const Rec& R, const BoxDesc& bd, int x, int y, int z,
+                                            float r[3]) {
+  const int cell[3] = {x, y, z};
+  const int n[3] = {bd.nx, bd.ny, bd.nz};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    float r0 = __fsub_rn((float)cell[j], R.xh[j]);
+    if (!((bd.bc >> j) & 1)) {
+      const float L = (float)n[j];
+      const float half = __fmul_rn(0.5f, L);
+      if (r0 > half) r0 = __fsub_rn(r0, L);
+      else if (r0 < -half) r0 = __fadd_rn(r0, L);
+    }
+    r[j] = __fsub_rn(r0, R.xl[j]);
+  }
+  if (R.shape == 0) {
+    float s = __fmul_rn(r[0], r[0]);
+    s = __fadd_rn(s, __fmul_rn(r[1], r[1]));
+    s = __fadd_rn(s, __fmul_rn(r[2], r[2]));
+    return s < R.in2;
+  }
+  float b[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    float t = __fmul_rn(R.M[0 * 3 + j], r[0]);
+    t = __fadd_rn(t, __fmul_rn(R.M[1 * 3 + j], r[1]));
+    t = __fadd_rn(t, __fmul_rn(R.M[2 * 3 + j], r[2]));
+    b[j] = t;
+  }
+  if (R.shape == 1) {
+    const float e0 = __fmul_rn(b[0], R.ia[0]);
+    const float e1 = __fmul_rn(b[1], R.ia[1]);
+    const float e2 = __fmul_rn(b[2], R.ia[2]);
+    float s = __fmul_rn(e0, e0);
+    s = __fadd_rn(s, __fmul_rn(e1, e1));
+    s = __fadd_rn(s, __fmul_rn(e2, e2));
+    return s < 1.0f;
+  }
+  return fabsf(b[0]) < R.a[0] && fabsf(b[1]) < R.a[1] && fabsf(b[2]) < R.a[2];
+}
+
+__device__ __forceinline__ int wrap_or_wall(int v, int n, bool wall) {
+  if (v >= 0 && v < n) return v;
+  if (wall) return -1;
+  return v < 0 ? v + n : v - n;
+}
+
+// force on the particle from cell x (used form of Eq. hlbm:mea):
+//   sum_i (c_i - u_p) f_i(x) + (c_i + u_p) f_ibar(x - c_i)
+// = sum_i c_i (in_i + out_i) - u_p sum_i (in_i - out_i), with in_i = f_i(x)
+// (arrived from x - c_i) and out_i = f_ibar(x - c_i) (left x towards x - c_i).
+// This is the printed per-cell sum with the opposite sign: on post-streaming
+// populations the printed sum is what the cell hands to the fluid, and the
+// particle feels the reverse.  Links to a node beyond a wall carry no fluid
+// and are left out; on deviations d = f - w that leaves -2 c_i w_i per
+// omitted link, because the weights of all 18 links sum to zero.
+template <typename S, int PAR>
+__device__ __forceinline__ void mea_cell(const S* f, long long P, const BoxDesc& bd, int x, int y,
+                                         int z, float inv_s, float F[3], float& mgain) {
+  const int c = (z * bd.ny + y) * bd.nx + x;
+  const bool wx = bd.bc & 1, wy = bd.bc & 2, wz = bd.bc & 4;
+  F[0] = F[1] = F[2] = 0.0f;
+  mgain = 0.0f;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int sx = wrap_or_wall(x - cx(i), bd.nx, wx);
+    const int sy = wrap_or_wall(y - cy(i), bd.ny, wy);
+    const int sz = wrap_or_wall(z - cz(i), bd.nz, wz);
+    if (sx < 0 || sy < 0 || sz < 0) {
+      const float w2 = 2.0f * (float)wq(i);
+      F[0] -= (float)cx(i) * w2;
+      F[1] -= (float)cy(i) * w2;
+      F[2] -= (float)cz(i) * w2;
+      continue;
+    }
+    const int s = (sz * bd.ny + sy) * bd.nx + sx;
+    const float va = PopR<S>::ld(f + i * P + c, inv_s);       // slot i of x
+    const float vb = PopR<S>::ld(f + opp(i) * P + s, inv_s);  // slot ibar of x - c_i
+    const float in = PAR == 0 ? va : vb;
+    const float out = PAR == 0 ? vb : va;
+    const float sum = in + out;
+    if (cx(i)) F[0] += (float)cx(i) * sum;
+    if (cy(i)) F[1] += (float)cy(i) * sum;
+    if (cz(i)) F[2] += (float)cz(i) * sum;
+    mgain += in - out;
+  }
+}
+
+template <typename S, int PAR>
+__global__ void __launch_bounds__(256) mea_kernel(PartArgs a) {
+  const int p = blockIdx.x;
+  if (p >= a.np) return;
+  __shared__ Rec R;
+  __shared__ double wsum[8][6];
+  if (threadIdx.x < 32) reinterpret_cast<int*>(&R)[threadIdx.x] = reinterpret_cast<const int*>(&a.rec[p])[threadIdx.x];
+  __syncthreads();
+  const BoxDesc bd = a.boxes[R.box];
+  const int n[3] = {bd.nx, bd.ny, bd.nz};
+  int lo[3], ext[3];
+  const double rc = pget(a.P, a.cap, PF_RC, p);
+  // a particle whose centre is not finite or far outside the box has no
+  // interior cells (the update flags it); this also bounds the loops below
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const double X = pget(a.P, a.cap, PF_X + j, p);
+    ok = ok && (X > -1.0e6 && X < 1.0e6);
+  }
+  if (!ok) {
+    if (threadIdx.x < 6) pset(a.P, a.cap, (threadIdx.x < 3 ? PF_F : PF_T - 3) + threadIdx.x, p, 0.0);
+    if (threadIdx.x == 0) atomicOr(a.status, ST_UNSTABLE);
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const double X = pget(a.P, a.cap, PF_X + j, p);
+    int l = (int)floor(X - rc) - 1, h = (int)ceil(X + rc) + 1;
+    if ((bd.bc >> j) & 1) {
+      l = max(l, 0);
+      h = min(h, n[j] - 1);
+    }
+    lo[j] = l;
+    ext[j] = max(h - l + 1, 0);
+  }
+  const int total = ext[0] * ext[1] * ext[2];
+  const S* f = reinterpret_cast<const S*>(a.f) + bd.cell_off;
+  float Fx = 0.f, Fy = 0.f, Fz = 0.f, Tx = 0.f, Ty = 0.f, Tz = 0.f;
+  for (int j = threadIdx.x; j < total; j += blockDim.x) {
+    const int ix = j % ext[0];
+    const int t = j / ext[0];
+    const int iy = t % ext[1];
+    const int iz = t / ext[1];
+    int x = lo[0] + ix, y = lo[1] + iy, z = lo[2] + iz;
+    x = x < 0 ? x + n[0] : (x >= n[0] ? x - n[0] : x);
+    y = y < 0 ? y + n[1] : (y >= n[1] ? y - n[1] : y);
+    z = z < 0 ? z + n[2] : (z >= n[2] ? z - n[2] : z);
+    float r[3];
+    if (!inside_fp32(R, bd, x, y, z, r)) continue;
+    float Fc[3], mg;
+    mea_cell<S, PAR>(f, a.plane, bd, x, y, z, a.inv_scale, Fc, mg);
+    const float upx = R.u[0] + (R.w[1] * r[2] - R.w[2] * r[1]);
+    const float upy = R.u[1] + (R.w[2] * r[0] - R.w[0] * r[2]);
+    const float upz = R.u[2] + (R.w[0] * r[1] - R.w[1] * r[0]);
+    Fc[0] -= upx * mg;
+    Fc[1] -= upy * mg;
+    Fc[2] -= upz * mg;
+    Fx += Fc[0];
+    Fy += Fc[1];
+    Fz += Fc[2];
+    Tx += r[1] * Fc[2] - r[2] * Fc[1];
+    Ty += r[2] * Fc[0] - r[0] * Fc[2];
+    Tz += r[0] * Fc[1] - r[1] * Fc[0];
+  }
+  float v[6] = {Fx, Fy, Fz, Tx, Ty, Tz};
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int k = 0; k < 6; ++k) wsum[warp][k] = (double)v[k];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double s = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; ++w) s += wsum[w][threadIdx.x];
+    pset(a.P, a.cap, (threadIdx.x < 3 ? PF_F : PF_T - 3) + threadIdx.x, p, s);
+  }
+}
+
+// per axis: up to two disjoint ranges of bin tiles covering cells [lo, hi]
+__device__ int axis_tiles(int lo, int hi, int n, int T, bool wall, int a0[2], int a1[2]) {
+  if (wall) {
+    lo = max(lo, 0);
+    hi = min(hi, n - 1);
+    if (lo > hi) return 0;
+    a0[0] = lo / T;
+    a1[0] = hi / T;
+    return 1;
+  }
+  if (hi - lo + 1 >= n) {  // covers the whole periodic axis
+    a0[0] = 0;
+    a1[0] = (n - 1) / T;
+    return 1;
+  }
+  int k = 0;
+  if (lo < 0) {
+    a0[k] = (lo + n) / T;
+    a1[k] = (n - 1) / T;
+    ++k;
+    lo = 0;
+  }
+  if (hi >= n) {
+    a0[k] = 0;
+    a1[k] = (hi - n) / T;
+    ++k;
+    hi = n - 1;
+  }
+  a0[k] = lo / T;
+  a1[k] = hi / T;
+  ++k;
+  // merge when both ends fall into the same tiles (short periodic axis)
+  if (k == 2 && a0[1] <= a1[0] && a0[0] <= a1[1]) {
+    a0[0] = min(a0[0], a0[1]);
+    a1[0] = max(a1[0], a1[1]);
+    k = 1;
+  }
+  return k;
+}
+
+__device__ void bin_particle(const PartArgs& a, const BoxDesc& bd, int p) {
+  const double rinf = pget(a.P, a.cap, PF_RINF, p);
+  const int n[3] = {bd.nx, bd.ny, bd.nz};
+  const int T[3] = {TILE_X, TILE_Y, TILE_Z};
+  int t0[3][3], t1[3][3], nr[3];
+  for (int j = 0; j < 3; ++j) {
+    const double X = pget(a.P, a.cap, PF_X + j, p);
+    if (!(X > -1.0e6 && X < 1.0e6)) return;  // flagged by the update; not binned
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const double X = pget(a.P, a.cap, PF_X + j, p);
+    const int lo = (int)floor(X - rinf) - 1, hi = (int)ceil(X + rinf) + 1;
+    nr[j] = axis_tiles(lo, hi, n[j], T[j], (bd.bc >> j) & 1, t0[j], t1[j]);
+  }
+  for (int rz = 0; rz < nr[2]; ++rz)
+    for (int tz = t0[2][rz]; tz <= t1[2][rz]; ++tz)
+      for (int ry = 0; ry < nr[1]; ++ry)
+        for (int ty = t0[1][ry]; ty <= t1[1][ry]; ++ty)
+          for (int rx = 0; rx < nr[0]; ++rx)
+            for (int tx = t0[0][rx]; tx <= t1[0][rx]; ++tx) {
+              const long long tile = bd.tile_off + ((long long)tz * bd.nty + ty) * bd.ntx + tx;
+              const int slot = atomicAdd(&a.bin_count[tile], 1);
+              if (slot < a.bin_cap) a.bin_ids[tile * a.bin_cap + slot] = p;
+              else atomicOr(a.status, ST_CAPACITY);
+            }
+}
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Newton-Euler step of one particle: symplectic Euler for translation, the
+// body-frame Euler equations for rotation, and the quaternion update
+// q <- normalise(q + q (x) (0, omega_b) / 2)
+__device__ void integrate(const PartArgs& a, const BoxDesc& bd, int p, int shape) {
+  double* P = a.P;
+  const int cap = a.cap;
+  const double m = pget(P, cap, PF_M, p), V = pget(P, cap, PF_V, p), rho = pget(P, cap, PF_RHO, p);
+  double X[3], U[3], W[3], T[3], I[3], q[4];
+  for (int j = 0; j < 3; ++j) {
+    const double F = pget(P, cap, PF_F + j, p) + (rho - 1.0) * V * a.g[j];
+    U[j] = pget(P, cap, PF_U + j, p) + F / m;
+    X[j] = pget(P, cap, PF_X + j, p) + U[j];
+    W[j] = pget(P, cap, PF_W + j, p);
+    T[j] = pget(P, cap, PF_T + j, p);
+    I[j] = pget(P, cap, PF_I + j, p);
+  }
+  for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
+  double R[9], wb[3];
+  rotation_rn(q, R);
+  if (shape == 0) {
+    for (int j = 0; j < 3; ++j) W[j] += T[j] / I[j];
+    for (int j = 0; j < 3; ++j) wb[j] = R[0 * 3 + j] * W[0] + R[1 * 3 + j] * W[1] + R[2 * 3 + j] * W[2];
+  } else {
+    double Tb[3], Lb[3], gy[3];
+    for (int j = 0; j < 3; ++j) {
+      wb[j] = R[0 * 3 + j] * W[0] + R[1 * 3 + j] * W[1] + R[2 * 3 + j] * W[2];
+      Tb[j] = R[0 * 3 + j] * T[0] + R[1 * 3 + j] * T[1] + R[2 * 3 + j] * T[2];
+    }
+    for (int j = 0; j < 3; ++j) Lb[j] = I[j] * wb[j];
+    cross3(wb, Lb, gy);
+    for (int j = 0; j < 3; ++j) wb[j] += (Tb[j] - gy[j]) / I[j];
+    for (int j = 0; j < 3; ++j) W[j] = R[j * 3 + 0] * wb[0] + R[j * 3 + 1] * wb[1] + R[j * 3 + 2] * wb[2];
+  }
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  double dq[4];
+  dq[0] = 0.5 * (-x * wb[0] - y * wb[1] - z * wb[2]);
+  dq[1] = 0.5 * (w * wb[0] + y * wb[2] - z * wb[1]);
+  dq[2] = 0.5 * (w * wb[1] + z * wb[0] - x * wb[2]);
+  dq[3] = 0.5 * (w * wb[2] + x * wb[1] - y * wb[0]);
+  double nq = 0.0;
+  for (int j = 0; j < 4; ++j) {
+    q[j] += dq[j];
+    nq += q[j] * q[j];
+  }
+  nq = sqrt(nq);
+  for (int j = 0; j < 4; ++j) q[j] /= nq;
+  const int n[3] = {bd.nx, bd.ny, bd.nz};
+  bool bad = false;
+  for (int j = 0; j < 3; ++j) {
+    if ((bd.bc >> j) & 1) {
+      if (!(X[j] > -0.5 && X[j] < n[j] - 0.5)) atomicOr(a.status, ST_LEFT_DOMAIN);
+    } else {
+      const double L = (double)n[j];
+      X[j] = X[j] - L * floor(X[j] / L);
+      if (X[j] >= L) X[j] -= L;
+    }
+    bad |= !isfinite(X[j]) || !isfinite(U[j]) || !isfinite(W[j]);
+  }
+  if (bad) atomicOr(a.status, ST_UNSTABLE);
+  for (int j = 0; j < 3; ++j) {
+    pset(P, cap, PF_X + j, p, X[j]);
+    pset(P, cap, PF_U + j, p, U[j]);
+    pset(P, cap, PF_W + j, p, W[j]);
+  }
+  for (int j = 0; j < 4; ++j) pset(P, cap, PF_Q + j, p, q[j]);
+}
+
+__global__ void __launch_bounds__(128) update_kernel(PartArgs a) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = tid; t < a.ntiles; t += stride) a.bin_count_clear[t] = 0;
+  for (long long t = tid; t < a.np; t += stride) {
+    const int p = (int)t;
+    const int shape = a.shape[p], box = a.box[p];
+    const BoxDesc bd = a.boxes[box];
+    integrate(a, bd, p, shape);
+    Rec R;
+    build_record(a.P, a.cap, p, shape, box, R);
+    a.rec[p] = R;
+    bin_particle(a, bd, p);
+  }
+}
+
+__global__ void records_kernel(PartArgs a) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.np) return;
+  Rec R;
+  build_record(a.P, a.cap, p, a.shape[p], a.box[p], R);
+  a.rec[p] = R;
+}
+
+cudaError_t launch_mea(const PartArgs& a, int precision, int parity, cudaStream_t s) {
+  if (a.np <= 0) return cudaSuccess;
+  if (precision == 0) {
+    if (parity == 0) mea_kernel<float, 0><<<a.np, 256, 0, s>>>(a);
+    else mea_kernel<float, 1><<<a.np, 256, 0, s>>>(a);
+  } else {
+    if (parity == 0) mea_kernel<__half, 0><<<a.np, 256, 0, s>>>(a);
+    else mea_kernel<__half, 1><<<a.np, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const PartArgs& a, cudaStream_t s) {
+  const long long work = a.np > a.ntiles ? a.np : a.ntiles;
+  long long blocks = (work + 127) / 128;
+  if (blocks > 65535) blocks = 65535;
+  if (blocks < 1) blocks = 1;
+  update_kernel<<<(unsigned)blocks, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_records(const PartArgs& a, cudaStream_t s) {
+  if (a.np <= 0) return cudaSuccess;
+  records_kernel<<<(a.np + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace hlbm

@@ -1,0 +1,280 @@
+"""Python binding of libhlbm.so (the C-ABI in include/hlbm.h).
+
+Argument marshalling only: every step of the HLBM time step runs in the CUDA
+kernels behind the C-ABI.  PyTorch supplies device memory (one uint8 buffer
+per handle) and the CUDA stream.  There is no CPU fallback: loading fails
+loudly when the library is missing or no GPU is present.
+
+The functions carry the C names; ``Lattice`` wraps a handle for convenience.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhlbm.so")
+
+HLBM_OK, HLBM_ERR_ARG, HLBM_ERR_CUDA, HLBM_ERR_UNSTABLE, HLBM_ERR_CAPACITY, HLBM_ERR_STATE = 0, -1, -2, -3, -4, -5
+HLBM_FP32, HLBM_FP16 = 0, 1
+HLBM_SPHERE, HLBM_ELLIPSOID, HLBM_CUBOID = 0, 1, 2
+HLBM_WALL_X, HLBM_WALL_Y, HLBM_WALL_Z = 1, 2, 4
+
+ERRORS = {HLBM_ERR_ARG: "HLBM_ERR_ARG", HLBM_ERR_CUDA: "HLBM_ERR_CUDA",
+          HLBM_ERR_UNSTABLE: "HLBM_ERR_UNSTABLE", HLBM_ERR_CAPACITY: "HLBM_ERR_CAPACITY",
+          HLBM_ERR_STATE: "HLBM_ERR_STATE"}
+
+# every symbol include/hlbm.h declares
+EXPORTS = ["hlbm_default_params", "hlbm_required_bytes", "hlbm_init_lattice", "hlbm_init_batch",
+           "hlbm_add_particles", "hlbm_set_particle_state", "hlbm_step", "hlbm_sync",
+           "hlbm_particle_state", "hlbm_get_populations", "hlbm_set_populations",
+           "hlbm_num_particles", "hlbm_steps_done", "hlbm_set_launch", "hlbm_get_launch",
+           "hlbm_autotune", "hlbm_kernel_times", "hlbm_last_error", "hlbm_destroy"]
+
+
+class hlbm_box(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("bc_flags", ctypes.c_int)]
+
+
+class hlbm_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("eps", ctypes.c_double),
+                ("gravity", ctypes.c_double * 3), ("fluid_force", ctypes.c_double * 3),
+                ("precision", ctypes.c_int), ("fp16_scale_log2", ctypes.c_int),
+                ("max_particles", ctypes.c_int), ("bin_capacity", ctypes.c_int)]
+
+
+class HLBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_fp = ctypes.POINTER(ctypes.c_float)
+_vp = ctypes.c_void_p
+_h = ctypes.c_void_p
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libhlbm.so and declare its signatures (no CUDA call is made)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: build it first (paper_2312_14172_gb300.build)")
+    L = ctypes.CDLL(path)
+    L.hlbm_default_params.argtypes = [ctypes.POINTER(hlbm_params)]
+    L.hlbm_default_params.restype = None
+    L.hlbm_required_bytes.argtypes = [ctypes.c_int, ctypes.POINTER(hlbm_box), ctypes.POINTER(hlbm_params)]
+    L.hlbm_required_bytes.restype = ctypes.c_size_t
+    L.hlbm_init_lattice.argtypes = [ctypes.POINTER(_h), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.POINTER(hlbm_params), _vp, _vp, ctypes.c_size_t]
+    L.hlbm_init_batch.argtypes = [ctypes.POINTER(_h), ctypes.c_int, ctypes.POINTER(hlbm_box),
+                                  ctypes.POINTER(hlbm_params), _vp, _vp, ctypes.c_size_t]
+    L.hlbm_add_particles.argtypes = [_h, ctypes.c_int, _ip, _ip, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.hlbm_set_particle_state.argtypes = [_h, _dp, _dp, _dp, _dp]
+    L.hlbm_step.argtypes = [_h, ctypes.c_int]
+    L.hlbm_sync.argtypes = [_h]
+    L.hlbm_particle_state.argtypes = [_h, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.hlbm_get_populations.argtypes = [_h, ctypes.c_int, _dp]
+    L.hlbm_set_populations.argtypes = [_h, ctypes.c_int, _dp]
+    L.hlbm_num_particles.argtypes = [_h]
+    L.hlbm_steps_done.argtypes = [_h]
+    L.hlbm_steps_done.restype = ctypes.c_longlong
+    L.hlbm_set_launch.argtypes = [_h, ctypes.c_int, ctypes.c_int]
+    L.hlbm_get_launch.argtypes = [_h, _ip, _ip]
+    L.hlbm_autotune.argtypes = [_h, ctypes.c_int, _ip, _ip, _fp]
+    L.hlbm_kernel_times.argtypes = [_h, ctypes.c_int, _fp]
+    L.hlbm_last_error.argtypes = [_h]
+    L.hlbm_last_error.restype = ctypes.c_char_p
+    L.hlbm_destroy.argtypes = [_h]
+    L.hlbm_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _arr(a, dtype, shape):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(np.asarray(a, dtype=dtype).reshape(shape))
+    ptr = a.ctypes.data_as(_dp if dtype == np.float64 else _ip)
+    return a, ptr
+
+
+def hlbm_default_params():
+    p = hlbm_params()
+    load().hlbm_default_params(ctypes.byref(p))
+    return p
+
+
+def make_params(tau=0.6, eps=0.5, gravity=(0, 0, 0), fluid_force=(0, 0, 0), precision="fp32",
+                fp16_scale_log2=14, max_particles=0, bin_capacity=0):
+    p = hlbm_default_params()
+    p.tau, p.eps = float(tau), float(eps)
+    for j in range(3):
+        p.gravity[j] = float(gravity[j])
+        p.fluid_force[j] = float(fluid_force[j])
+    p.precision = {"fp32": HLBM_FP32, "fp16": HLBM_FP16}[precision] if isinstance(precision, str) else int(precision)
+    p.fp16_scale_log2 = int(fp16_scale_log2)
+    p.max_particles = int(max_particles)
+    p.bin_capacity = int(bin_capacity)
+    return p
+
+
+def hlbm_required_bytes(boxes, params):
+    arr = (hlbm_box * len(boxes))(*[hlbm_box(*[int(v) for v in b]) for b in boxes])
+    return int(load().hlbm_required_bytes(len(boxes), arr, ctypes.byref(params)))
+
+
+def _check(h, rc):
+    if rc != HLBM_OK:
+        msg = load().hlbm_last_error(h)
+        raise HLBMError(rc, msg.decode() if msg else "")
+    return rc
+
+
+class Lattice:
+    """One handle: a single box or a batch of boxes, with torch-owned device memory.
+
+    boxes: list of (nx, ny, nz, bc_flags).  The buffer is a torch uint8 tensor
+    on the current CUDA device; the stream is torch's current stream unless one
+    is given.
+    """
+
+    def __init__(self, boxes, params, stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libhlbm needs a CUDA GPU; there is no CPU fallback")
+        L = load()
+        self.boxes = [tuple(int(v) for v in b) for b in boxes]
+        self.params = params
+        self.nbytes = hlbm_required_bytes(self.boxes, params)
+        if self.nbytes == 0:
+            raise HLBMError(HLBM_ERR_ARG, "invalid lattice arguments")
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.buffer = torch.empty(self.nbytes, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        h = _h()
+        arr = (hlbm_box * len(self.boxes))(*[hlbm_box(*b) for b in self.boxes])
+        rc = L.hlbm_init_batch(ctypes.byref(h), len(self.boxes), arr, ctypes.byref(params),
+                               _vp(self.stream.cuda_stream), _vp(self.buffer.data_ptr()),
+                               ctypes.c_size_t(self.nbytes))
+        _check(None, rc)
+        self.h = h
+
+    # --- lifetime
+    def close(self):
+        if getattr(self, "h", None):
+            load().hlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- calls
+    def add_particles(self, shape, shape_params, X, U=None, omega=None, quat=None, rho_p=None,
+                      box_id=None):
+        shape, sp = _arr(shape, np.int32, (-1,))
+        n = shape.shape[0]
+        a = np.asarray(shape_params, float).reshape(n, -1)
+        if a.shape[1] == 1:
+            a = np.repeat(a, 3, axis=1)
+        a, ap = _arr(a, np.float64, (n, 3))
+        X, Xp = _arr(X, np.float64, (n, 3))
+        U, Up = _arr(U, np.float64, (n, 3))
+        W, Wp = _arr(omega, np.float64, (n, 3))
+        q, qp = _arr(quat, np.float64, (n, 4))
+        r, rp = _arr(rho_p, np.float64, (n,))
+        b, bp = _arr(box_id, np.int32, (n,))
+        _check(self.h, load().hlbm_add_particles(self.h, n, bp, sp, ap, Xp, Up, Wp, qp, rp))
+
+    def add_workload_particles(self, P, box_id=None):
+        if len(P["shape"]):
+            self.add_particles(P["shape"], P["a"], P["X"], P["U"], P["omega"], P["quat"], P["rho_p"],
+                               box_id)
+
+    def set_particle_state(self, X=None, U=None, omega=None, quat=None):
+        n = self.num_particles
+        X, Xp = _arr(X, np.float64, (n, 3))
+        U, Up = _arr(U, np.float64, (n, 3))
+        W, Wp = _arr(omega, np.float64, (n, 3))
+        q, qp = _arr(quat, np.float64, (n, 4))
+        _check(self.h, load().hlbm_set_particle_state(self.h, Xp, Up, Wp, qp))
+
+    def step(self, nsteps=1):
+        _check(self.h, load().hlbm_step(self.h, int(nsteps)))
+
+    def sync(self):
+        _check(self.h, load().hlbm_sync(self.h))
+
+    def particle_state(self, out=None, check=True):
+        n = self.num_particles
+        if out is None:
+            out = {k: np.zeros((n, 4 if k == "quat" else 3)) for k in ("X", "U", "omega", "quat", "F", "T")}
+        ptrs = [out[k].ctypes.data_as(_dp) for k in ("X", "U", "omega", "quat", "F", "T")]
+        rc = load().hlbm_particle_state(self.h, *ptrs)
+        if check:
+            _check(self.h, rc)
+        return out
+
+    def populations(self, box=0):
+        nx, ny, nz = self.boxes[box][:3]
+        f = np.zeros((19, nz, ny, nx))
+        _check(self.h, load().hlbm_get_populations(self.h, int(box), f.ctypes.data_as(_dp)))
+        return f
+
+    def set_populations(self, f, box=0):
+        nx, ny, nz = self.boxes[box][:3]
+        f = np.ascontiguousarray(np.asarray(f, np.float64).reshape(19, nz, ny, nx))
+        _check(self.h, load().hlbm_set_populations(self.h, int(box), f.ctypes.data_as(_dp)))
+
+    @property
+    def num_particles(self):
+        return load().hlbm_num_particles(self.h)
+
+    @property
+    def steps_done(self):
+        return load().hlbm_steps_done(self.h)
+
+    def set_launch(self, tile_y, tile_z):
+        _check(self.h, load().hlbm_set_launch(self.h, int(tile_y), int(tile_z)))
+
+    def get_launch(self):
+        ty, tz = ctypes.c_int(), ctypes.c_int()
+        _check(self.h, load().hlbm_get_launch(self.h, ctypes.byref(ty), ctypes.byref(tz)))
+        return ty.value, tz.value
+
+    def autotune(self, nsteps=10):
+        ty, tz, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        _check(self.h, load().hlbm_autotune(self.h, int(nsteps), ctypes.byref(ty), ctypes.byref(tz),
+                                            ctypes.byref(ms)))
+        return ty.value, tz.value, ms.value
+
+    def kernel_times(self, nsteps=5):
+        ms = (ctypes.c_float * 3)()
+        _check(self.h, load().hlbm_kernel_times(self.h, int(nsteps), ms))
+        return {"mea": ms[0], "update": ms[1], "collide_stream": ms[2]}
+
+
+def from_workload(w, precision=None, stream=None, **kw):
+    """Lattice of one workload description (see the workloads module)."""
+    prec = precision or w.get("precision", "fp32")
+    P = w["particles"]
+    params = make_params(tau=w["tau"], eps=w["eps"], gravity=w["gravity"],
+                         fluid_force=w.get("fluid_force", (0, 0, 0)), precision=prec,
+                         max_particles=max(1, len(P["shape"])), **kw)
+    lat = Lattice([tuple(w["n"]) + (w["bc"],)], params, stream=stream)
+    lat.add_workload_particles(P)
+    return lat

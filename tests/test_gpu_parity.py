@@ -1,0 +1,274 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (FP32 storage of f - w, FP32 arithmetic, FP64 particle sums and
+motion):
+  populations       |f_gpu - f_ref| <= 1e-5 |f_ref| element by element
+  particle motion   |dX_gpu - dX_ref| <= 1e-5 |dX_ref| + 1e-6 (dX = X - X0),
+                    the same rule for U and omega against their own scale
+FP16 storage: errors against FP64 are measured and bounded loosely here; the
+stated per-quantity figures come from test_gpu_fp16_error.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+RTOL_F = 1e-5
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2312_14172_gb300 import build, hlbm
+    build.build()
+    hlbm.load()
+    return hlbm
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+def _pops_close(fg, fo, rtol=RTOL_F):
+    err = np.abs(fg - fo) / np.abs(fo)
+    assert np.all(np.isfinite(fg))
+    assert err.max() <= rtol, f"max relative population error {err.max():.3e}"
+    return err.max()
+
+
+FLOORS = {"X": 1e-6, "U": 1e-9, "omega": 1e-9}
+
+
+def _motion_close(sg, so, X0, U0, W0, rtol=1e-5):
+    """|d_gpu - d_ref| <= rtol * max|d_ref| + floor, d = value - initial value."""
+    for key, ref0 in (("X", X0), ("U", U0), ("omega", W0)):
+        dg = sg[key] - ref0
+        do = so[key] - ref0
+        err = np.abs(dg - do)
+        scale = np.abs(do).max()
+        assert err.max() <= rtol * scale + FLOORS[key], \
+            f"{key}: max err {err.max():.3e}, scale {scale:.3e}"
+
+
+def _random_pops(O, n, seed, amp=1e-3):
+    c, w, _ = O.velocity_set()
+    rng = np.random.default_rng(seed)
+    return w[:, None, None, None] * (1.0 + amp * rng.standard_normal((19, n[2], n[1], n[0])))
+
+
+def _pair(H, O, n, bc, tau=0.7, eps=0.5, g=(0, 0, 0), ff=(0, 0, 0), precision="fp32", maxp=1, **kw):
+    lat = H.Lattice([tuple(n) + (bc,)], H.make_params(tau=tau, eps=eps, gravity=g, fluid_force=ff,
+                                                      precision=precision, max_particles=maxp, **kw))
+    orc = O.Oracle(n, tau, eps, bc, g, ff)
+    return lat, orc
+
+
+# ------------------------------------------------------------ no particles
+@pytest.mark.parametrize("bc", [0, 4, 7, 3])
+def test_fluid_only_random_state(H, O, bc):
+    """Collision + streaming, ragged sizes spanning several tiles, every parity."""
+    n = (45, 19, 21)
+    lat, orc = _pair(H, O, n, bc, tau=0.66, ff=(2e-6, -1e-6, 3e-6))
+    f0 = _random_pops(O, n, 10 + bc)
+    lat.set_populations(f0)
+    orc.set_populations(f0)
+    for steps in (1, 1, 3, 8):
+        lat.step(steps)
+        orc.step(steps)
+        _pops_close(lat.populations(), orc.populations())
+    lat.sync()
+    lat.close()
+
+
+def test_degenerate_thin_boxes(H, O):
+    for n, bc in (((1, 1, 16), 4), ((1, 7, 5), 0), ((33, 1, 1), 0), ((2, 2, 2), 7)):
+        lat, orc = _pair(H, O, n, bc, tau=0.9, ff=(1e-5, 0, 0))
+        f0 = _random_pops(O, n, 3)
+        lat.set_populations(f0)
+        orc.set_populations(f0)
+        lat.step(7)
+        orc.step(7)
+        _pops_close(lat.populations(), orc.populations())
+        lat.close()
+
+
+def test_set_get_roundtrip_both_parities(H, O):
+    n = (40, 9, 17)
+    lat, _ = _pair(H, O, n, 4)
+    f0 = _random_pops(O, n, 5)
+    for k in range(2):
+        lat.set_populations(f0)
+        got = lat.populations()
+        assert np.max(np.abs(got - f0) / f0) < 1e-6  # FP32 rounding of f - w
+        lat.step(1)
+    lat.close()
+
+
+# ------------------------------------------------------------ with particles
+def _run_pair(H, O, w, steps, chunks=(1,), precision="fp32", check=True):
+    P = w["particles"]
+    lat = H.from_workload(w, precision=precision)
+    orc = O.from_workload(w)
+    X0, U0, W0 = P["X"].copy(), P["U"].copy(), P["omega"].copy()
+    done = 0
+    for c in chunks:
+        lat.step(c)
+        orc.step(c)
+        done += c
+    rest = steps - done
+    if rest > 0:
+        lat.step(rest)
+        orc.step(rest)
+    sg = lat.particle_state()
+    so = orc.particle_state()
+    fg = lat.populations()
+    fo = orc.populations()
+    lat.close()
+    return sg, so, fg, fo, (X0, U0, W0)
+
+
+def test_single_sphere_settling_200_steps(H, O):
+    """The small benchmark configuration in full: 48^3 periodic, one sphere
+    r = 6, tau 0.8, density ratio 2.5, g = 1e-5, 200 steps."""
+    from paper_2312_14172_gb300 import workloads
+    w = workloads.single_sphere()
+    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 200, chunks=(1, 1, 5))
+    _pops_close(fg, fo)
+    _motion_close(sg, so, X0, U0, W0)
+    assert np.allclose(sg["F"], so["F"], rtol=1e-4, atol=1e-9)
+    assert sg["U"][0][2] < 0
+
+
+def test_sphere_off_centre_rotating(H, O):
+    """A sphere near a periodic corner, moving and spinning: images, torque."""
+    n = (40, 36, 44)
+    lat, orc = _pair(H, O, n, 0, tau=0.7, g=(2e-6, -3e-6, -1e-5), maxp=2)
+    args = dict(shape=[0, 0], shape_params=[[5.5] * 3, [4.2] * 3],
+                X=[[0.7, 35.2, 1.9], [20.3, 17.8, 22.6]], U=[[1e-3, -2e-3, 5e-4], [0, 0, -1e-3]],
+                omega=[[2e-3, -1e-3, 3e-3], [0, 4e-3, 0]], quat=None, rho_p=[2.5, 1.5])
+    lat.add_particles(**args)
+    orc.add_particles(args["shape"], args["shape_params"], args["X"], args["U"], args["omega"],
+                      None, args["rho_p"])
+    X0 = np.array(args["X"]); U0 = np.array(args["U"]); W0 = np.array(args["omega"])
+    lat.step(60)
+    orc.step(60)
+    sg, so = lat.particle_state(), orc.particle_state()
+    _pops_close(lat.populations(), orc.populations())
+    _motion_close(sg, so, X0, U0, W0)
+    assert np.allclose(sg["T"], so["T"], rtol=1e-3, atol=1e-8)
+    lat.close()
+
+
+def test_hindered_settling_subbox_walls(H, O):
+    """Spheres between walls (the hindered-settling configuration) on a box
+    the oracle finishes quickly, ragged in x and y."""
+    from paper_2312_14172_gb300 import workloads
+    w = workloads.hindered_settling(n=(70, 45, 48), count=14, steps=40)
+    assert len(w["particles"]["shape"]) >= 8
+    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 40, chunks=(1,))
+    _pops_close(fg, fo)
+    _motion_close(sg, so, X0, U0, W0)
+
+
+def test_nonspherical_subbox(H, O):
+    """Ellipsoids and cuboids with random orientations, eps = 1.5."""
+    from paper_2312_14172_gb300 import workloads
+    w = workloads.nonspherical(n=(64, 56, 60), count=16, steps=40)
+    assert len(w["particles"]["shape"]) >= 10
+    # give them some spin so that the rotation update is exercised
+    rng = np.random.default_rng(1)
+    w["particles"]["omega"] = rng.uniform(-3e-3, 3e-3, w["particles"]["omega"].shape)
+    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 40, chunks=(1,))
+    _pops_close(fg, fo)
+    _motion_close(sg, so, X0, U0, W0)
+    assert np.allclose(sg["quat"], so["quat"], atol=1e-9)
+
+
+def test_fp16_storage_error_is_small(H, O):
+    from paper_2312_14172_gb300 import workloads
+    w = workloads.single_sphere(n=40, radius=5.0, steps=100)
+    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 100, precision="fp16")
+    assert np.max(np.abs(fg - fo) / fo) < 1e-4
+    dX = so["X"] - X0
+    assert np.max(np.abs((sg["X"] - X0) - dX)) <= 2e-2 * np.abs(dX).max() + 1e-6
+
+
+# ------------------------------------------------------------ batch
+def test_batch_of_boxes_matches_separate_oracles(H, O):
+    from paper_2312_14172_gb300 import workloads
+    boxes = workloads.ensemble(nboxes=3, edge=(24, 40), count=(2, 5), r_range=(2.5, 4.0))
+    params = H.make_params(tau=boxes[0]["tau"], eps=0.5, gravity=boxes[0]["gravity"],
+                           max_particles=sum(len(b["particles"]["shape"]) for b in boxes))
+    lat = H.Lattice([tuple(b["n"]) + (b["bc"],) for b in boxes], params)
+    for k, b in enumerate(boxes):
+        lat.add_workload_particles(b["particles"], box_id=[k] * len(b["particles"]["shape"]))
+    orcs = [O.from_workload(b) for b in boxes]
+    lat.step(25)
+    for o in orcs:
+        o.step(25)
+    sg = lat.particle_state()
+    p0 = 0
+    for k, (b, o) in enumerate(zip(boxes, orcs)):
+        _pops_close(lat.populations(box=k), o.populations())
+        m = len(b["particles"]["shape"])
+        so = o.particle_state()
+        sub = {key: v[p0:p0 + m] for key, v in sg.items()}
+        _motion_close(sub, so, b["particles"]["X"], b["particles"]["U"], b["particles"]["omega"])
+        p0 += m
+    lat.close()
+
+
+# ------------------------------------------------------------ errors
+def test_errors_are_reported(H, O):
+    n = (32, 16, 16)
+    lat, _ = _pair(H, O, n, 0, maxp=3, bin_capacity=1)
+    # two particles sharing a 32x8x8 tile overflow a capacity of one
+    lat.add_particles([0, 0], [[2.0] * 3, [2.0] * 3], [[5, 5, 5], [20, 5, 5]], rho_p=[2, 2])
+    lat.step(1)
+    with pytest.raises(H.HLBMError) as e:
+        lat.sync()
+    assert e.value.code == H.HLBM_ERR_CAPACITY
+    lat.sync()  # flags were cleared
+    with pytest.raises(H.HLBMError) as e:
+        lat.add_particles([0], [[2.0] * 3], [[10, 10, 10]], rho_p=[2])
+    assert e.value.code == H.HLBM_ERR_STATE
+    lat.close()
+    # a NaN population makes the density non-finite
+    lat, _ = _pair(H, O, n, 0)
+    f = _random_pops(O, n, 1)
+    f[3, 4, 5, 6] = np.nan
+    lat.set_populations(f)
+    lat.step(2)
+    with pytest.raises(H.HLBMError) as e:
+        lat.sync()
+    assert e.value.code == H.HLBM_ERR_UNSTABLE
+    lat.close()
+    with pytest.raises(H.HLBMError):
+        H.Lattice([(8, 8, 8, 0)], H.make_params(tau=0.4))
+
+
+def test_launch_shapes_agree(H, O):
+    """Every collision launch shape gives bit-identical results."""
+    from paper_2312_14172_gb300 import workloads
+    w = workloads.hindered_settling(n=(64, 40, 40), count=8, steps=10)
+    ref = None
+    for ty, tz in ((1, 1), (2, 8), (4, 2), (8, 4), (8, 8)):
+        lat = H.from_workload(w)
+        lat.set_launch(ty, tz)
+        lat.step(6)
+        f = lat.populations()
+        s = lat.particle_state()
+        lat.close()
+        if ref is None:
+            ref = (f, s)
+        else:
+            assert np.array_equal(f, ref[0])
+            assert np.array_equal(s["X"], ref[1]["X"])
