@@ -120,8 +120,11 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
  *   body -> world, normalised here; NULL = identity), rho_p[n] density.
  * Mass and inertia follow from the analytic volume and rho_p.  Rejected
  * (HLBM_ERR_ARG): non-finite or non-positive sizes or densities, a centre
- * outside the box on a wall axis, or a particle whose bounding region
- * (circumscribed radius + eps/2 + 2) spans half a periodic axis or more. */
+ * outside the box on a wall axis, or a particle whose influence sphere (the
+ * radius beyond which B of Eq. B vanishes, plus 2 cells) spans half a
+ * periodic axis or more.  The influence radius is r + eps/2 for spheres, the
+ * circumscribed radius + eps/2 for cuboids and a_max (1 + eps / (2 a_min))
+ * for ellipsoids. */
 int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape,
                        const double* shape_params, const double* X, const double* U,
                        const double* omega, const double* quat, const double* rho_p);

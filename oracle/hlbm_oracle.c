@@ -220,6 +220,8 @@ struct oracle_sim {
   long steps;
 };
 
+static double influence_radius(const particle* P, double eps);
+
 static long cell_index(const oracle_sim* s, int x, int y, int z) {
   return ((long)z * s->n[1] + y) * s->n[0] + x;
 }
@@ -369,7 +371,7 @@ int oracle_add_particles(oracle_sim* s, int n, const int* shape, const double* a
     for (int j = 0; j < 3; ++j) {
       if (is_wall(s, j)) {
         if (!(P.X[j] > -0.5 && P.X[j] < s->n[j] - 0.5)) return -1;
-      } else if (!(2.0 * (P.rc + s->eps / 2.0 + 2.0) < s->n[j])) {
+      } else if (!(2.0 * (influence_radius(&P, s->eps) + 2.0) < s->n[j])) {
         return -1;
       }
     }

@@ -32,8 +32,8 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 struct Layout {
   long long plane = 0, ncell = 0, ntiles = 0, stage_cells = 0;
   int cap = 0, bin_cap = 0;
-  size_t off_f, off_boxes, off_P, off_shape, off_box, off_rec, off_cnt[2], off_ids[2], off_status,
-      off_stage, total;
+  size_t off_f, off_boxes, off_P, off_shape, off_box, off_rec, off_part, off_cnt[2], off_ids[2],
+      off_status, off_stage, total;
 };
 
 bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& L,
@@ -79,6 +79,7 @@ bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& 
   L.off_shape = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
   L.off_box = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
   L.off_rec = o; o = align_up(o + sizeof(Rec) * (size_t)L.cap);
+  L.off_part = o; o = align_up(o + sizeof(double) * 6 * MEA_CHUNKS * (size_t)L.cap);
   for (int k = 0; k < 2; ++k) {
     L.off_cnt[k] = o; o = align_up(o + sizeof(int) * (size_t)L.ntiles);
     L.off_ids[k] = o; o = align_up(o + sizeof(int) * (size_t)L.ntiles * L.bin_cap);
@@ -107,6 +108,7 @@ struct hlbm_ctx {
   int* d_shape = nullptr;
   int* d_box = nullptr;
   Rec* rec = nullptr;
+  double* partial = nullptr;
   int* cnt[2] = {nullptr, nullptr};
   int* ids[2] = {nullptr, nullptr};
   int* status = nullptr;
@@ -176,6 +178,7 @@ static PartArgs part_args(const hlbm_ctx* h, int parity) {
   const double sc = h->prm.precision == HLBM_FP16 ? std::ldexp(1.0, h->prm.fp16_scale_log2) : 1.0;
   a.scale = (float)sc;
   a.inv_scale = (float)(1.0 / sc);
+  a.partial = h->partial;
   a.bin_count = h->cnt[parity];
   a.bin_ids = h->ids[parity];
   a.bin_count_clear = h->cnt[1 - parity];
@@ -301,6 +304,7 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
   h->d_shape = (int*)(h->buf + h->L.off_shape);
   h->d_box = (int*)(h->buf + h->L.off_box);
   h->rec = (Rec*)(h->buf + h->L.off_rec);
+  h->partial = (double*)(h->buf + h->L.off_part);
   for (int k = 0; k < 2; ++k) {
     h->cnt[k] = (int*)(h->buf + h->L.off_cnt[k]);
     h->ids[k] = (int*)(h->buf + h->L.off_ids[k]);
@@ -435,18 +439,21 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
         return fail(h, HLBM_ERR_ARG, "non-finite particle state");
       if ((bd.bc >> j) & 1) {
         if (!(x[j] > -0.5 && x[j] < nn[j] - 0.5)) return fail(h, HLBM_ERR_ARG, "centre outside the box on a wall axis");
-      } else if (!(2.0 * (rc + h->prm.eps / 2.0 + 2.0) < nn[j])) {
+      } else if (!(2.0 * (rinf + 2.0) < nn[j])) {
         return fail(h, HLBM_ERR_ARG, "particle spans half a periodic axis or more");
       }
       T(PF_U + j, k) = u;
       T(PF_W + j, k) = w;
       T(PF_I + j, k) = I[j];
+      T(PF_II + j, k) = 1.0 / I[j];
       T(PF_A + j, k) = a[j];
+      T(PF_IA + j, k) = (double)(float)(1.0 / a[j]);
     }
     wrap_host(bd, x);
     for (int j = 0; j < 3; ++j) T(PF_X + j, k) = x[j];
     for (int j = 0; j < 4; ++j) T(PF_Q + j, k) = q[j];
     T(PF_M, k) = m;
+    T(PF_IM, k) = 1.0 / m;
     T(PF_V, k) = V;
     T(PF_RHO, k) = rho;
     T(PF_RC, k) = rc;

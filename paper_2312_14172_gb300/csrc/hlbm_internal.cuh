@@ -51,12 +51,19 @@ struct BoxDesc {
   long long tile_off;        // first bin tile of the box
 };
 
-// FP64 particle table fields (each an array of `cap` doubles)
+// FP64 particle table fields (each an array of `cap` doubles).  PF_IM and
+// PF_II hold 1/m and 1/I, PF_IA holds fp32(1/a_j) (exact in a double).
 enum {
   PF_X = 0, PF_U = 3, PF_W = 6, PF_Q = 9, PF_F = 13, PF_T = 16,
   PF_M = 19, PF_V = 20, PF_I = 21, PF_RHO = 24, PF_A = 25, PF_RC = 28, PF_RINF = 29,
-  PF_COUNT = 30
+  PF_IM = 30, PF_II = 31, PF_IA = 34,
+  PF_COUNT = 37
 };
+
+// the momentum exchange of one particle is split over this many thread
+// blocks, each taking a slab of the bounding box's z-planes; their FP64
+// partial sums (6 per block) are added in a fixed order by the update
+constexpr int MEA_CHUNKS = 8;
 
 // FP32 coupling record of one particle (128 bytes)
 struct __align__(16) Rec {
@@ -74,6 +81,39 @@ struct __align__(16) Rec {
 static_assert(sizeof(Rec) == 128, "record size");
 
 enum { ST_UNSTABLE = 1, ST_CAPACITY = 2, ST_LEFT_DOMAIN = 4 };
+
+// neighbour index helper: per-axis neighbour offsets; -1 marks a node beyond
+// a wall (only possible when WALLS)
+template <bool WALLS>
+struct Nbr {
+  int xm, xp, ym, yp, zm, zp;  // neighbour coordinates (x) or row/plane offsets (y, z)
+  int x, y, z;                 // own coordinate and row/plane offsets
+  __device__ __forceinline__ int at(int dx, int dy, int dz) const {
+    const int a = dx < 0 ? xm : (dx > 0 ? xp : x);
+    const int b = dy < 0 ? ym : (dy > 0 ? yp : y);
+    const int c = dz < 0 ? zm : (dz > 0 ? zp : z);
+    if (WALLS && (a < 0 || b < 0 || c < 0)) return -1;
+    return a + b + c;
+  }
+};
+
+template <bool WALLS>
+__device__ __forceinline__ Nbr<WALLS> make_nbr(const BoxDesc& bd, int x, int y, int z) {
+  Nbr<WALLS> n;
+  const int nx = bd.nx, ny = bd.ny, nz = bd.nz, nxy = nx * ny;
+  const bool wx = WALLS && (bd.bc & 1), wy = WALLS && (bd.bc & 2), wz = WALLS && (bd.bc & 4);
+  n.x = x;
+  n.y = y * nx;
+  n.z = z * nxy;
+  n.xm = x > 0 ? x - 1 : (wx ? -1 : nx - 1);
+  n.xp = x < nx - 1 ? x + 1 : (wx ? -1 : 0);
+  n.ym = y > 0 ? (y - 1) * nx : (wy ? -1 : (ny - 1) * nx);
+  n.yp = y < ny - 1 ? (y + 1) * nx : (wy ? -1 : 0);
+  n.zm = z > 0 ? (z - 1) * nxy : (wz ? -1 : (nz - 1) * nxy);
+  n.zp = z < nz - 1 ? (z + 1) * nxy : (wz ? -1 : 0);
+  return n;
+}
+
 
 struct LbmArgs {
   void* f;                  // population planes (float* or __half*)
@@ -107,6 +147,8 @@ struct PartArgs {
   const void* f;
   long long plane;
   float scale, inv_scale;
+  // partial force/torque sums of the momentum exchange, [cap][MEA_CHUNKS][6]
+  double* partial;
   // bins written by the update (this step) and cleared (other parity)
   int* bin_count;
   int* bin_ids;

@@ -34,14 +34,6 @@ template <> struct Pop<__half> {
   static __device__ __forceinline__ void st(__half* p, float v, float s) { *p = __float2half_rn(v * s); }
 };
 
-// f^eq_i(rho, u) - w_i (Eq. maxbolt with c_s^2 = 1/3)
-template <int I>
-__device__ __forceinline__ float feq_dev(float rho, float ux, float uy, float uz, float uu) {
-  constexpr float w = (float)wq(I);
-  const float cu = (float)cx(I) * ux + (float)cy(I) * uy + (float)cz(I) * uz;
-  return w * (rho - 1.0f) + w * rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
-}
-
 // indicator of Eq. B written as (1 - sin(pi d / eps)) / 2 on the ramp, which
 // equals cos^2((pi/2)(d/eps + 1/2))
 __device__ __forceinline__ float indicator(float d, float eps, float inv_eps) {
@@ -78,38 +70,6 @@ __device__ __forceinline__ int find_box(const BoxDesc* boxes, int nboxes, long l
     if (boxes[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
   }
   return lo;
-}
-
-// neighbour index helper: per-axis neighbour offsets; -1 marks a node beyond
-// a wall (only possible when WALLS)
-template <bool WALLS>
-struct Nbr {
-  int xm, xp, ym, yp, zm, zp;  // neighbour coordinates (x) or row/plane offsets (y, z)
-  int x, y, z;                 // own coordinate and row/plane offsets
-  __device__ __forceinline__ int at(int dx, int dy, int dz) const {
-    const int a = dx < 0 ? xm : (dx > 0 ? xp : x);
-    const int b = dy < 0 ? ym : (dy > 0 ? yp : y);
-    const int c = dz < 0 ? zm : (dz > 0 ? zp : z);
-    if (WALLS && (a < 0 || b < 0 || c < 0)) return -1;
-    return a + b + c;
-  }
-};
-
-template <bool WALLS>
-__device__ __forceinline__ Nbr<WALLS> make_nbr(const BoxDesc& bd, int x, int y, int z) {
-  Nbr<WALLS> n;
-  const int nx = bd.nx, ny = bd.ny, nz = bd.nz, nxy = nx * ny;
-  const bool wx = WALLS && (bd.bc & 1), wy = WALLS && (bd.bc & 2), wz = WALLS && (bd.bc & 4);
-  n.x = x;
-  n.y = y * nx;
-  n.z = z * nxy;
-  n.xm = x > 0 ? x - 1 : (wx ? -1 : nx - 1);
-  n.xp = x < nx - 1 ? x + 1 : (wx ? -1 : 0);
-  n.ym = y > 0 ? (y - 1) * nx : (wy ? -1 : (ny - 1) * nx);
-  n.yp = y < ny - 1 ? (y + 1) * nx : (wy ? -1 : 0);
-  n.zm = z > 0 ? (z - 1) * nxy : (wz ? -1 : (nz - 1) * nxy);
-  n.zp = z < nz - 1 ? (z + 1) * nxy : (wz ? -1 : 0);
-  return n;
 }
 
 template <typename S, int PAR, bool WALLS, bool COUPLE>
@@ -166,14 +126,15 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
                           : Pop<S>::ld(f + i * P + c, a.inv_scale);
       }
     }
-    float rho = 1.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      rho += d[i];
+      drho += d[i];
       if (cx(i)) jx += (float)cx(i) * d[i];
       if (cy(i)) jy += (float)cy(i) * d[i];
       if (cz(i)) jz += (float)cz(i) * d[i];
     }
+    const float rho = 1.0f + drho;
     if (!(rho > 0.0f && rho < 1e30f)) atomicOr(a.status, ST_UNSTABLE);
     const float irho = 1.0f / rho;
     const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
@@ -183,12 +144,18 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
       int bestp = 0x7fffffff;
       for (int k = 0; k < cnt; ++k) {
         const Rec& R = srec[k];
-        float r0x = (float)x - R.xh[0], r0y = (float)y - R.xh[1], r0z = (float)z - R.xh[2];
-        if (!(bd.bc & 1)) { if (r0x > 0.5f * Lx) r0x -= Lx; else if (r0x < -0.5f * Lx) r0x += Lx; }
+        // y and z offsets are the same for the whole warp (one row of x):
+        // most candidates miss the row and are rejected without divergence
+        float r0y = (float)y - R.xh[1], r0z = (float)z - R.xh[2];
         if (!(bd.bc & 2)) { if (r0y > 0.5f * Ly) r0y -= Ly; else if (r0y < -0.5f * Ly) r0y += Ly; }
         if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
-        const float rx = r0x - R.xl[0], ry = r0y - R.xl[1], rz = r0z - R.xl[2];
-        const float r2 = rx * rx + ry * ry + rz * rz;
+        const float ry = r0y - R.xl[1], rz = r0z - R.xl[2];
+        const float d2 = ry * ry + rz * rz;
+        if (d2 >= R.rinf2) continue;
+        float r0x = (float)x - R.xh[0];
+        if (!(bd.bc & 1)) { if (r0x > 0.5f * Lx) r0x -= Lx; else if (r0x < -0.5f * Lx) r0x += Lx; }
+        const float rx = r0x - R.xl[0];
+        const float r2 = rx * rx + d2;
         if (r2 < R.rinf2) {
           const float B = indicator(sdf(R, rx, ry, rz, r2), a.eps, a.inv_eps);
           if (B > bestB || (B == bestB && B > 0.0f && R.pid < bestp)) {
@@ -206,18 +173,41 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
         duz += bestB * (upz - uz);
       }
     }
-    const float uu = ux * ux + uy * uy + uz * uz;
-    const float vx = ux + dux, vy = uy + duy, vz = uz + duz;
-    const float vv = vx * vx + vy * vy + vz * vz;
+    // f*_i - w_i = (1 - 1/tau) (d_i - E_i(u)) + E_i(u + Delta u), E = f^eq - w.
+    // Opposite directions share the even part of E and flip the odd part:
+    // E_i = w drho + w rho (4.5 (c.u)^2 - 1.5 u.u) +- 3 w rho (c.u)
     const float om1 = 1.0f - a.omega;
+    const float vx = ux + dux, vy = uy + duy, vz = uz + duz;
+    const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float vsq = 1.5f * (vx * vx + vy * vy + vz * vz);
     float o[Q];
-#define HLBM_COLLIDE(I) \
-    o[I] = om1 * (d[I] - feq_dev<I>(rho, ux, uy, uz, uu)) + feq_dev<I>(rho, vx, vy, vz, vv);
-    HLBM_COLLIDE(0) HLBM_COLLIDE(1) HLBM_COLLIDE(2) HLBM_COLLIDE(3) HLBM_COLLIDE(4)
-    HLBM_COLLIDE(5) HLBM_COLLIDE(6) HLBM_COLLIDE(7) HLBM_COLLIDE(8) HLBM_COLLIDE(9)
-    HLBM_COLLIDE(10) HLBM_COLLIDE(11) HLBM_COLLIDE(12) HLBM_COLLIDE(13) HLBM_COLLIDE(14)
-    HLBM_COLLIDE(15) HLBM_COLLIDE(16) HLBM_COLLIDE(17) HLBM_COLLIDE(18)
-#undef HLBM_COLLIDE
+    {
+      constexpr float w0 = 1.0f / 3.0f;
+      const float eu = w0 * drho - w0 * rho * usq, ev = w0 * drho - w0 * rho * vsq;
+      o[0] = om1 * d[0] + (ev - om1 * eu);
+    }
+    const float wr1 = rho * (1.0f / 18.0f), wd1 = drho * (1.0f / 18.0f);
+    const float wr2 = rho * (1.0f / 36.0f), wd2 = drho * (1.0f / 36.0f);
+#define HLBM_PAIR(I, WR, WD, CU, CV)                                          \
+    {                                                                         \
+      const float cu_ = (CU), cv_ = (CV);                                     \
+      const float eu = WD + WR * (4.5f * cu_ * cu_ - usq);                    \
+      const float ev = WD + WR * (4.5f * cv_ * cv_ - vsq);                    \
+      const float C = ev - om1 * eu;                                          \
+      const float A = 3.0f * WR * (cv_ - om1 * cu_);                          \
+      o[I] = om1 * d[I] + C + A;                                              \
+      o[I + 1] = om1 * d[I + 1] + C - A;                                      \
+    }
+    HLBM_PAIR(1, wr1, wd1, ux, vx)
+    HLBM_PAIR(3, wr1, wd1, uy, vy)
+    HLBM_PAIR(5, wr1, wd1, uz, vz)
+    HLBM_PAIR(7, wr2, wd2, ux + uy, vx + vy)
+    HLBM_PAIR(9, wr2, wd2, ux - uy, vx - vy)
+    HLBM_PAIR(11, wr2, wd2, ux + uz, vx + vz)
+    HLBM_PAIR(13, wr2, wd2, ux - uz, vx - vz)
+    HLBM_PAIR(15, wr2, wd2, uy + uz, vy + vz)
+    HLBM_PAIR(17, wr2, wd2, uy - uz, vy - vz)
+#undef HLBM_PAIR
     // store the post-collision deviations, streamed (AA pattern)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {

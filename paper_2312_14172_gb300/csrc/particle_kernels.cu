@@ -2,10 +2,11 @@
 //
 //   mea_kernel      momentum exchange (Eq. hlbm:mea) summed over the cells
 //                   whose centre lies inside each particle (Eqs.
-//                   hydrodynamicforce, hydrodynamictorque); one thread block per
-//                   particle walks the particle's bounding box; per-cell sums
-//                   in FP32, warp shuffles in FP32, block sum in FP64 in a fixed
-//                   order (deterministic).
+//                   hydrodynamicforce, hydrodynamictorque); MEA_CHUNKS thread
+//                   blocks per particle each walk a slab of z-planes of the
+//                   particle's bounding box; per-cell sums in FP32, warp
+//                   shuffles in FP32, block sums in FP64, written as partials
+//                   that the update adds in a fixed order (deterministic).
 //   update_kernel   weight minus buoyancy (Sec. 5.1), Newton-Euler update
 //                   (Eqs. particlemotiontrans, motionrot) in FP64, the FP32
 //                   coupling record of the new state, and the per-tile particle
@@ -50,9 +51,12 @@ __device__ __forceinline__ void pset(double* P, int cap, int field, int p, doubl
 }
 
 __device__ void build_record(const double* P, int cap, int p, int shape, int box, Rec& R) {
-  double q[4], Rm[9];
-  for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
-  rotation_rn(q, Rm);
+  double Rm[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // a sphere needs no orientation
+  if (shape != 0) {
+    double q[4];
+    for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
+    rotation_rn(q, Rm);
+  }
   for (int j = 0; j < 3; ++j) {
     const double X = pget(P, cap, PF_X + j, p);
     const float xh = __double2float_rn(X);
@@ -62,7 +66,7 @@ __device__ void build_record(const double* P, int cap, int p, int shape, int box
     R.w[j] = (float)pget(P, cap, PF_W + j, p);
     const double aj = pget(P, cap, PF_A + j, p);
     R.a[j] = __double2float_rn(aj);
-    R.ia[j] = __double2float_rn(1.0 / aj);
+    R.ia[j] = (float)pget(P, cap, PF_IA + j, p);
   }
   for (int k = 0; k < 9; ++k) R.M[k] = __double2float_rn(Rm[k]);
   const double a0 = pget(P, cap, PF_A, p);
@@ -119,12 +123,6 @@ __device__ __forceinline__ bool inside_fp32(const Rec& R, const BoxDesc& bd, int
   return fabsf(b[0]) < R.a[0] && fabsf(b[1]) < R.a[1] && fabsf(b[2]) < R.a[2];
 }
 
-__device__ __forceinline__ int wrap_or_wall(int v, int n, bool wall) {
-  if (v >= 0 && v < n) return v;
-  if (wall) return -1;
-  return v < 0 ? v + n : v - n;
-}
-
 // force on the particle from cell x (used form of Eq. hlbm:mea):
 //   sum_i (c_i - u_p) f_i(x) + (c_i + u_p) f_ibar(x - c_i)
 // = sum_i c_i (in_i + out_i) - u_p sum_i (in_i - out_i), with in_i = f_i(x)
@@ -133,27 +131,24 @@ __device__ __forceinline__ int wrap_or_wall(int v, int n, bool wall) {
 // populations the printed sum is what the cell hands to the fluid, and the
 // particle feels the reverse.  Links to a node beyond a wall carry no fluid
 // and are left out; on deviations d = f - w that leaves -2 c_i w_i per
-// omitted link, because the weights of all 18 links sum to zero.
+// omitted link, because the weights of all 18 links sum to zero.  In both AA
+// parities the pair of slots is {slot i of x, slot ibar of x - c_i}; only
+// which of the two is the arrival differs.
 template <typename S, int PAR>
-__device__ __forceinline__ void mea_cell(const S* f, long long P, const BoxDesc& bd, int x, int y,
-                                         int z, float inv_s, float F[3], float& mgain) {
-  const int c = (z * bd.ny + y) * bd.nx + x;
-  const bool wx = bd.bc & 1, wy = bd.bc & 2, wz = bd.bc & 4;
+__device__ __forceinline__ void mea_cell(const S* f, long long P, const Nbr<true>& nb, int c,
+                                         float inv_s, float F[3], float& mgain) {
   F[0] = F[1] = F[2] = 0.0f;
   mgain = 0.0f;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    const int sx = wrap_or_wall(x - cx(i), bd.nx, wx);
-    const int sy = wrap_or_wall(y - cy(i), bd.ny, wy);
-    const int sz = wrap_or_wall(z - cz(i), bd.nz, wz);
-    if (sx < 0 || sy < 0 || sz < 0) {
+    const int s = nb.at(-cx(i), -cy(i), -cz(i));
+    if (s < 0) {
       const float w2 = 2.0f * (float)wq(i);
-      F[0] -= (float)cx(i) * w2;
-      F[1] -= (float)cy(i) * w2;
-      F[2] -= (float)cz(i) * w2;
+      if (cx(i)) F[0] -= (float)cx(i) * w2;
+      if (cy(i)) F[1] -= (float)cy(i) * w2;
+      if (cz(i)) F[2] -= (float)cz(i) * w2;
       continue;
     }
-    const int s = (sz * bd.ny + sy) * bd.nx + sx;
     const float va = PopR<S>::ld(f + i * P + c, inv_s);       // slot i of x
     const float vb = PopR<S>::ld(f + opp(i) * P + s, inv_s);  // slot ibar of x - c_i
     const float in = PAR == 0 ? va : vb;
@@ -166,35 +161,40 @@ __device__ __forceinline__ void mea_cell(const S* f, long long P, const BoxDesc&
   }
 }
 
+constexpr int MEA_LPR = 8;  // lanes per bounding-box row
+
 template <typename S, int PAR>
-__global__ void __launch_bounds__(256) mea_kernel(PartArgs a) {
+__global__ void __launch_bounds__(128, 6) mea_kernel(PartArgs a) {
   const int p = blockIdx.x;
+  const int chunk = blockIdx.y;
   if (p >= a.np) return;
   __shared__ Rec R;
-  __shared__ double wsum[8][6];
+  __shared__ double wsum[4][6];
   if (threadIdx.x < 32) reinterpret_cast<int*>(&R)[threadIdx.x] = reinterpret_cast<const int*>(&a.rec[p])[threadIdx.x];
   __syncthreads();
+  double* out = a.partial + ((long long)p * MEA_CHUNKS + chunk) * 6;
   const BoxDesc bd = a.boxes[R.box];
   const int n[3] = {bd.nx, bd.ny, bd.nz};
-  int lo[3], ext[3];
   const double rc = pget(a.P, a.cap, PF_RC, p);
+  double X[3];
   // a particle whose centre is not finite or far outside the box has no
   // interior cells (the update flags it); this also bounds the loops below
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const double X = pget(a.P, a.cap, PF_X + j, p);
-    ok = ok && (X > -1.0e6 && X < 1.0e6);
+    X[j] = pget(a.P, a.cap, PF_X + j, p);
+    ok = ok && (X[j] > -1.0e6 && X[j] < 1.0e6);
   }
   if (!ok) {
-    if (threadIdx.x < 6) pset(a.P, a.cap, (threadIdx.x < 3 ? PF_F : PF_T - 3) + threadIdx.x, p, 0.0);
+    if (threadIdx.x < 6) out[threadIdx.x] = 0.0;
     if (threadIdx.x == 0) atomicOr(a.status, ST_UNSTABLE);
     return;
   }
+  // cells that can be inside: [floor(X - r_c), ceil(X + r_c)] per axis
+  int lo[3], ext[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const double X = pget(a.P, a.cap, PF_X + j, p);
-    int l = (int)floor(X - rc) - 1, h = (int)ceil(X + rc) + 1;
+    int l = (int)floor(X[j] - rc), h = (int)ceil(X[j] + rc);
     if ((bd.bc >> j) & 1) {
       l = max(l, 0);
       h = min(h, n[j] - 1);
@@ -202,118 +202,102 @@ __global__ void __launch_bounds__(256) mea_kernel(PartArgs a) {
     lo[j] = l;
     ext[j] = max(h - l + 1, 0);
   }
-  const int total = ext[0] * ext[1] * ext[2];
+  const int pz = (ext[2] + MEA_CHUNKS - 1) / MEA_CHUNKS;
+  const int z0 = chunk * pz, z1 = min(z0 + pz, ext[2]);
+  const int nrows = max(z1 - z0, 0) * ext[1];
   const S* f = reinterpret_cast<const S*>(a.f) + bd.cell_off;
+  const float rc2 = (float)(rc * rc) * 1.0001f + 1e-3f;
   float Fx = 0.f, Fy = 0.f, Fz = 0.f, Tx = 0.f, Ty = 0.f, Tz = 0.f;
-  for (int j = threadIdx.x; j < total; j += blockDim.x) {
-    const int ix = j % ext[0];
-    const int t = j / ext[0];
-    const int iy = t % ext[1];
-    const int iz = t / ext[1];
-    int x = lo[0] + ix, y = lo[1] + iy, z = lo[2] + iz;
-    x = x < 0 ? x + n[0] : (x >= n[0] ? x - n[0] : x);
-    y = y < 0 ? y + n[1] : (y >= n[1] ? y - n[1] : y);
-    z = z < 0 ? z + n[2] : (z >= n[2] ? z - n[2] : z);
-    float r[3];
-    if (!inside_fp32(R, bd, x, y, z, r)) continue;
-    float Fc[3], mg;
-    mea_cell<S, PAR>(f, a.plane, bd, x, y, z, a.inv_scale, Fc, mg);
-    const float upx = R.u[0] + (R.w[1] * r[2] - R.w[2] * r[1]);
-    const float upy = R.u[1] + (R.w[2] * r[0] - R.w[0] * r[2]);
-    const float upz = R.u[2] + (R.w[0] * r[1] - R.w[1] * r[0]);
-    Fc[0] -= upx * mg;
-    Fc[1] -= upy * mg;
-    Fc[2] -= upz * mg;
-    Fx += Fc[0];
-    Fy += Fc[1];
-    Fz += Fc[2];
-    Tx += r[1] * Fc[2] - r[2] * Fc[1];
-    Ty += r[2] * Fc[0] - r[0] * Fc[2];
-    Tz += r[0] * Fc[1] - r[1] * Fc[0];
+  const int lane = threadIdx.x & 31;
+  const int rows_per_iter = blockDim.x / MEA_LPR;
+  for (int row = threadIdx.x / MEA_LPR; row < nrows; row += rows_per_iter) {
+    const int iz = z0 + row / ext[1], iy = row % ext[1];
+    const int zu = lo[2] + iz, yu = lo[1] + iy;  // unwrapped coordinates
+    const float dz = (float)((double)zu - X[2]), dy = (float)((double)yu - X[1]);
+    const float d2 = dy * dy + dz * dz;
+    if (d2 >= rc2) continue;  // the row misses the circumscribed sphere
+    const float sx = sqrtf(rc2 - d2);
+    const int xa = max(lo[0], (int)floorf((float)X[0] - sx) - 1);
+    const int xb = min(lo[0] + ext[0] - 1, (int)ceilf((float)X[0] + sx) + 1);
+    const int z = zu < 0 ? zu + n[2] : (zu >= n[2] ? zu - n[2] : zu);
+    const int y = yu < 0 ? yu + n[1] : (yu >= n[1] ? yu - n[1] : yu);
+    for (int xu = xa + (lane % MEA_LPR); xu <= xb; xu += MEA_LPR) {
+      const int x = xu < 0 ? xu + n[0] : (xu >= n[0] ? xu - n[0] : xu);
+      float r[3];
+      if (!inside_fp32(R, bd, x, y, z, r)) continue;
+      const Nbr<true> nb = make_nbr<true>(bd, x, y, z);
+      const int c = (z * bd.ny + y) * bd.nx + x;
+      float Fc[3], mg;
+      mea_cell<S, PAR>(f, a.plane, nb, c, a.inv_scale, Fc, mg);
+      const float upx = R.u[0] + (R.w[1] * r[2] - R.w[2] * r[1]);
+      const float upy = R.u[1] + (R.w[2] * r[0] - R.w[0] * r[2]);
+      const float upz = R.u[2] + (R.w[0] * r[1] - R.w[1] * r[0]);
+      Fc[0] -= upx * mg;
+      Fc[1] -= upy * mg;
+      Fc[2] -= upz * mg;
+      Fx += Fc[0];
+      Fy += Fc[1];
+      Fz += Fc[2];
+      Tx += r[1] * Fc[2] - r[2] * Fc[1];
+      Ty += r[2] * Fc[0] - r[0] * Fc[2];
+      Tz += r[0] * Fc[1] - r[1] * Fc[0];
+    }
   }
+  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   float v[6] = {Fx, Fy, Fz, Tx, Ty, Tz};
 #pragma unroll
   for (int k = 0; k < 6; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0)
     for (int k = 0; k < 6; ++k) wsum[warp][k] = (double)v[k];
   __syncthreads();
   if (threadIdx.x < 6) {
     double s = 0.0;
-    const int nw = blockDim.x >> 5;
-    for (int w = 0; w < nw; ++w) s += wsum[w][threadIdx.x];
-    pset(a.P, a.cap, (threadIdx.x < 3 ? PF_F : PF_T - 3) + threadIdx.x, p, s);
+    for (int w = 0; w < nwarp; ++w) s += wsum[w][threadIdx.x];
+    out[threadIdx.x] = s;
   }
 }
 
-// per axis: up to two disjoint ranges of bin tiles covering cells [lo, hi]
-__device__ int axis_tiles(int lo, int hi, int n, int T, bool wall, int a0[2], int a1[2]) {
+// the bin tiles along one axis touched by cells [lo, hi]: one range
+// [a0, a1], plus a second range [b0, b1] (empty when b1 < b0) where the cell
+// range wraps around a periodic axis
+struct AxisTiles {
+  int a0, a1, b0, b1;
+  __device__ __forceinline__ int count() const { return (a1 - a0 + 1) + max(b1 - b0 + 1, 0); }
+  __device__ __forceinline__ int at(int t) const {
+    const int na = a1 - a0 + 1;
+    return t < na ? a0 + t : b0 + (t - na);
+  }
+};
+
+__device__ AxisTiles axis_tiles(int lo, int hi, int n, int T, bool wall) {
+  AxisTiles r{0, -1, 0, -1};
   if (wall) {
     lo = max(lo, 0);
     hi = min(hi, n - 1);
-    if (lo > hi) return 0;
-    a0[0] = lo / T;
-    a1[0] = hi / T;
-    return 1;
+    if (lo <= hi) { r.a0 = lo / T; r.a1 = hi / T; }
+    return r;
   }
-  if (hi - lo + 1 >= n) {  // covers the whole periodic axis
-    a0[0] = 0;
-    a1[0] = (n - 1) / T;
-    return 1;
+  if (hi - lo + 1 >= n) {  // the whole periodic axis
+    r.a0 = 0; r.a1 = (n - 1) / T;
+    return r;
   }
-  int k = 0;
-  if (lo < 0) {
-    a0[k] = (lo + n) / T;
-    a1[k] = (n - 1) / T;
-    ++k;
-    lo = 0;
+  if (lo < 0) {            // [lo + n, n - 1] and [0, hi]
+    r.a0 = (lo + n) / T; r.a1 = (n - 1) / T;
+    r.b0 = 0; r.b1 = hi / T;
+  } else if (hi >= n) {    // [lo, n - 1] and [0, hi - n]
+    r.a0 = lo / T; r.a1 = (n - 1) / T;
+    r.b0 = 0; r.b1 = (hi - n) / T;
+  } else {
+    r.a0 = lo / T; r.a1 = hi / T;
   }
-  if (hi >= n) {
-    a0[k] = 0;
-    a1[k] = (hi - n) / T;
-    ++k;
-    hi = n - 1;
+  // both ends in the same tiles (an axis of one or two tiles): merge
+  if (r.b1 >= r.b0 && r.b1 >= r.a0) {
+    r.a0 = 0; r.a1 = max(r.a1, r.b1);
+    r.b0 = 0; r.b1 = -1;
   }
-  a0[k] = lo / T;
-  a1[k] = hi / T;
-  ++k;
-  // merge when both ends fall into the same tiles (short periodic axis)
-  if (k == 2 && a0[1] <= a1[0] && a0[0] <= a1[1]) {
-    a0[0] = min(a0[0], a0[1]);
-    a1[0] = max(a1[0], a1[1]);
-    k = 1;
-  }
-  return k;
-}
-
-__device__ void bin_particle(const PartArgs& a, const BoxDesc& bd, int p) {
-  const double rinf = pget(a.P, a.cap, PF_RINF, p);
-  const int n[3] = {bd.nx, bd.ny, bd.nz};
-  const int T[3] = {TILE_X, TILE_Y, TILE_Z};
-  int t0[3][3], t1[3][3], nr[3];
-  for (int j = 0; j < 3; ++j) {
-    const double X = pget(a.P, a.cap, PF_X + j, p);
-    if (!(X > -1.0e6 && X < 1.0e6)) return;  // flagged by the update; not binned
-  }
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const double X = pget(a.P, a.cap, PF_X + j, p);
-    const int lo = (int)floor(X - rinf) - 1, hi = (int)ceil(X + rinf) + 1;
-    nr[j] = axis_tiles(lo, hi, n[j], T[j], (bd.bc >> j) & 1, t0[j], t1[j]);
-  }
-  for (int rz = 0; rz < nr[2]; ++rz)
-    for (int tz = t0[2][rz]; tz <= t1[2][rz]; ++tz)
-      for (int ry = 0; ry < nr[1]; ++ry)
-        for (int ty = t0[1][ry]; ty <= t1[1][ry]; ++ty)
-          for (int rx = 0; rx < nr[0]; ++rx)
-            for (int tx = t0[0][rx]; tx <= t1[0][rx]; ++tx) {
-              const long long tile = bd.tile_off + ((long long)tz * bd.nty + ty) * bd.ntx + tx;
-              const int slot = atomicAdd(&a.bin_count[tile], 1);
-              if (slot < a.bin_cap) a.bin_ids[tile * a.bin_cap + slot] = p;
-              else atomicOr(a.status, ST_CAPACITY);
-            }
+  return r;
 }
 
 __device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
@@ -325,34 +309,34 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 // Newton-Euler step of one particle: symplectic Euler for translation, the
 // body-frame Euler equations for rotation, and the quaternion update
 // q <- normalise(q + q (x) (0, omega_b) / 2)
-__device__ void integrate(const PartArgs& a, const BoxDesc& bd, int p, int shape) {
+__device__ void integrate(const PartArgs& a, const BoxDesc& bd, int p, int shape, const double Fh[3],
+                          const double Th[3]) {
   double* P = a.P;
   const int cap = a.cap;
-  const double m = pget(P, cap, PF_M, p), V = pget(P, cap, PF_V, p), rho = pget(P, cap, PF_RHO, p);
-  double X[3], U[3], W[3], T[3], I[3], q[4];
+  const double im = pget(P, cap, PF_IM, p), V = pget(P, cap, PF_V, p), rho = pget(P, cap, PF_RHO, p);
+  double X[3], U[3], W[3], iI[3], q[4];
   for (int j = 0; j < 3; ++j) {
-    const double F = pget(P, cap, PF_F + j, p) + (rho - 1.0) * V * a.g[j];
-    U[j] = pget(P, cap, PF_U + j, p) + F / m;
+    const double F = Fh[j] + (rho - 1.0) * V * a.g[j];
+    U[j] = pget(P, cap, PF_U + j, p) + F * im;
     X[j] = pget(P, cap, PF_X + j, p) + U[j];
     W[j] = pget(P, cap, PF_W + j, p);
-    T[j] = pget(P, cap, PF_T + j, p);
-    I[j] = pget(P, cap, PF_I + j, p);
+    iI[j] = pget(P, cap, PF_II + j, p);
   }
   for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
   double R[9], wb[3];
   rotation_rn(q, R);
   if (shape == 0) {
-    for (int j = 0; j < 3; ++j) W[j] += T[j] / I[j];
+    for (int j = 0; j < 3; ++j) W[j] += Th[j] * iI[j];
     for (int j = 0; j < 3; ++j) wb[j] = R[0 * 3 + j] * W[0] + R[1 * 3 + j] * W[1] + R[2 * 3 + j] * W[2];
   } else {
     double Tb[3], Lb[3], gy[3];
     for (int j = 0; j < 3; ++j) {
       wb[j] = R[0 * 3 + j] * W[0] + R[1 * 3 + j] * W[1] + R[2 * 3 + j] * W[2];
-      Tb[j] = R[0 * 3 + j] * T[0] + R[1 * 3 + j] * T[1] + R[2 * 3 + j] * T[2];
+      Tb[j] = R[0 * 3 + j] * Th[0] + R[1 * 3 + j] * Th[1] + R[2 * 3 + j] * Th[2];
     }
-    for (int j = 0; j < 3; ++j) Lb[j] = I[j] * wb[j];
+    for (int j = 0; j < 3; ++j) Lb[j] = wb[j] / iI[j];
     cross3(wb, Lb, gy);
-    for (int j = 0; j < 3; ++j) wb[j] += (Tb[j] - gy[j]) / I[j];
+    for (int j = 0; j < 3; ++j) wb[j] += (Tb[j] - gy[j]) * iI[j];
     for (int j = 0; j < 3; ++j) W[j] = R[j * 3 + 0] * wb[0] + R[j * 3 + 1] * wb[1] + R[j * 3 + 2] * wb[2];
   }
   const double w = q[0], x = q[1], y = q[2], z = q[3];
@@ -366,17 +350,18 @@ __device__ void integrate(const PartArgs& a, const BoxDesc& bd, int p, int shape
     q[j] += dq[j];
     nq += q[j] * q[j];
   }
-  nq = sqrt(nq);
-  for (int j = 0; j < 4; ++j) q[j] /= nq;
+  const double inq = 1.0 / sqrt(nq);
+  for (int j = 0; j < 4; ++j) q[j] *= inq;
   const int n[3] = {bd.nx, bd.ny, bd.nz};
   bool bad = false;
   for (int j = 0; j < 3; ++j) {
     if ((bd.bc >> j) & 1) {
       if (!(X[j] > -0.5 && X[j] < n[j] - 0.5)) atomicOr(a.status, ST_LEFT_DOMAIN);
     } else {
+      // a particle moves far less than a box length per step
       const double L = (double)n[j];
-      X[j] = X[j] - L * floor(X[j] / L);
       if (X[j] >= L) X[j] -= L;
+      else if (X[j] < 0.0) X[j] += L;
     }
     bad |= !isfinite(X[j]) || !isfinite(U[j]) || !isfinite(W[j]);
   }
@@ -385,23 +370,80 @@ __device__ void integrate(const PartArgs& a, const BoxDesc& bd, int p, int shape
     pset(P, cap, PF_X + j, p, X[j]);
     pset(P, cap, PF_U + j, p, U[j]);
     pset(P, cap, PF_W + j, p, W[j]);
+    pset(P, cap, PF_F + j, p, Fh[j]);
+    pset(P, cap, PF_T + j, p, Th[j]);
   }
   for (int j = 0; j < 4; ++j) pset(P, cap, PF_Q + j, p, q[j]);
 }
 
-__global__ void __launch_bounds__(128) update_kernel(PartArgs a) {
+__global__ void __launch_bounds__(32) update_kernel(PartArgs a) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long t = tid; t < a.ntiles; t += stride) a.bin_count_clear[t] = 0;
-  for (long long t = tid; t < a.np; t += stride) {
-    const int p = (int)t;
-    const int shape = a.shape[p], box = a.box[p];
+  const int lane = threadIdx.x & 31;
+  const long long wbase = tid - lane;  // first particle of this warp
+  if (wbase >= a.np) return;           // whole warp past the end
+  const int p = (int)tid;
+  int binnable = 0;
+  AxisTiles tx{0, -1, 0, -1}, ty{0, -1, 0, -1}, tz{0, -1, 0, -1};
+  int box = 0;
+  if (p < a.np) {
+    const int shape = a.shape[p];
+    box = a.box[p];
     const BoxDesc bd = a.boxes[box];
-    integrate(a, bd, p, shape);
+    // force and torque: the momentum-exchange partials in a fixed order
+    double Fh[3] = {0, 0, 0}, Th[3] = {0, 0, 0};
+    const double* part = a.partial + (long long)p * MEA_CHUNKS * 6;
+    for (int k = 0; k < MEA_CHUNKS; ++k) {
+      for (int j = 0; j < 3; ++j) {
+        Fh[j] += part[k * 6 + j];
+        Th[j] += part[k * 6 + 3 + j];
+      }
+    }
+    integrate(a, bd, p, shape, Fh, Th);
     Rec R;
     build_record(a.P, a.cap, p, shape, box, R);
     a.rec[p] = R;
-    bin_particle(a, bd, p);
+    // tiles touched by the influence sphere of the new state
+    const double rinf = pget(a.P, a.cap, PF_RINF, p);
+    binnable = 1;
+    const int n[3] = {bd.nx, bd.ny, bd.nz};
+    AxisTiles* at[3] = {&tx, &ty, &tz};
+    const int T[3] = {TILE_X, TILE_Y, TILE_Z};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double X = pget(a.P, a.cap, PF_X + j, p);
+      if (!(X > -1.0e6 && X < 1.0e6)) { binnable = 0; continue; }
+      const int lo = (int)floor(X - rinf) - 1, hi = (int)ceil(X + rinf) + 1;
+      *at[j] = axis_tiles(lo, hi, n[j], T[j], (bd.bc >> j) & 1);
+    }
+  }
+  // the 32 particles of this warp are binned one after another, each by all
+  // lanes together
+  for (int j = 0; j < 32; ++j) {
+    if (!__shfl_sync(0xffffffffu, binnable, j)) continue;
+    const int pj = __shfl_sync(0xffffffffu, p, j);
+    const int bj = __shfl_sync(0xffffffffu, box, j);
+    AxisTiles X{__shfl_sync(0xffffffffu, tx.a0, j), __shfl_sync(0xffffffffu, tx.a1, j),
+                __shfl_sync(0xffffffffu, tx.b0, j), __shfl_sync(0xffffffffu, tx.b1, j)};
+    AxisTiles Y{__shfl_sync(0xffffffffu, ty.a0, j), __shfl_sync(0xffffffffu, ty.a1, j),
+                __shfl_sync(0xffffffffu, ty.b0, j), __shfl_sync(0xffffffffu, ty.b1, j)};
+    AxisTiles Z{__shfl_sync(0xffffffffu, tz.a0, j), __shfl_sync(0xffffffffu, tz.a1, j),
+                __shfl_sync(0xffffffffu, tz.b0, j), __shfl_sync(0xffffffffu, tz.b1, j)};
+    const BoxDesc bd = a.boxes[bj];
+    const int cx_ = X.count(), cy_ = Y.count(), cz_ = Z.count();
+    const int total = cx_ * cy_ * cz_;
+    for (int t = lane; t < total; t += 32) {
+      const int ix = t % cx_;
+      const int r = t / cx_;
+      const int iy = r % cy_;
+      const int iz = r / cy_;
+      const long long tile =
+          bd.tile_off + ((long long)Z.at(iz) * bd.nty + Y.at(iy)) * bd.ntx + X.at(ix);
+      const int slot = atomicAdd(&a.bin_count[tile], 1);
+      if (slot < a.bin_cap) a.bin_ids[tile * a.bin_cap + slot] = pj;
+      else atomicOr(a.status, ST_CAPACITY);
+    }
   }
 }
 
@@ -415,22 +457,25 @@ __global__ void records_kernel(PartArgs a) {
 
 cudaError_t launch_mea(const PartArgs& a, int precision, int parity, cudaStream_t s) {
   if (a.np <= 0) return cudaSuccess;
+  const dim3 grid(a.np, MEA_CHUNKS);
   if (precision == 0) {
-    if (parity == 0) mea_kernel<float, 0><<<a.np, 256, 0, s>>>(a);
-    else mea_kernel<float, 1><<<a.np, 256, 0, s>>>(a);
+    if (parity == 0) mea_kernel<float, 0><<<grid, 128, 0, s>>>(a);
+    else mea_kernel<float, 1><<<grid, 128, 0, s>>>(a);
   } else {
-    if (parity == 0) mea_kernel<__half, 0><<<a.np, 256, 0, s>>>(a);
-    else mea_kernel<__half, 1><<<a.np, 256, 0, s>>>(a);
+    if (parity == 0) mea_kernel<__half, 0><<<grid, 128, 0, s>>>(a);
+    else mea_kernel<__half, 1><<<grid, 128, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(const PartArgs& a, cudaStream_t s) {
-  const long long work = a.np > a.ntiles ? a.np : a.ntiles;
-  long long blocks = (work + 127) / 128;
-  if (blocks > 65535) blocks = 65535;
+  // one warp per block spreads the FP64 work of the particles over many SMs
+  long long blocks = (a.np + 31) / 32;
+  long long clear_blocks = (a.ntiles + 31) / 32;
+  if (clear_blocks > 8192) clear_blocks = 8192;
+  if (clear_blocks > blocks) blocks = clear_blocks;
   if (blocks < 1) blocks = 1;
-  update_kernel<<<(unsigned)blocks, 128, 0, s>>>(a);
+  update_kernel<<<(unsigned)blocks, 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -156,9 +156,9 @@ def test_mea_equals_momentum_change_of_interior_cells(O, shape, a, q):
     term), and the torque of Eq. hydrodynamictorque is the same sum with the
     arm x - X_p.  Checked against a random post-collision field streamed by
     the oracle, with every sum done here by brute force in numpy."""
-    n = (14, 13, 15)
+    n = (16, 15, 17)
     o = O.Oracle(n, 0.8, 0.5, 0)
-    X = np.array([12.7, 6.2, 7.9])  # close to the x boundary: periodic images matter
+    X = np.array([14.7, 6.2, 7.9])  # close to the x boundary: periodic images matter
     U = np.array([2e-3, -1e-3, 3e-3])
     W = np.array([1e-3, 4e-3, -2e-3])
     qv = np.array(q, float) / np.linalg.norm(q)
