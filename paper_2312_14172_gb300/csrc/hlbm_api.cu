@@ -32,8 +32,8 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 struct Layout {
   long long plane = 0, ncell = 0, ntiles = 0, stage_cells = 0;
   int cap = 0, bin_cap = 0;
-  size_t off_f, off_boxes, off_P, off_shape, off_box, off_rec, off_part, off_cnt[2], off_ids[2],
-      off_status, off_stage, total;
+  size_t off_f, off_boxes, off_P, off_shape, off_box, off_rec, off_part, off_acc, off_cnt[2],
+      off_ids[2], off_status, off_stage, total;
 };
 
 bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& L,
@@ -80,6 +80,7 @@ bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& 
   L.off_box = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
   L.off_rec = o; o = align_up(o + sizeof(Rec) * (size_t)L.cap);
   L.off_part = o; o = align_up(o + sizeof(double) * 6 * MEA_CHUNKS * (size_t)L.cap);
+  L.off_acc = o; o = align_up(o + sizeof(double) * 6 * (size_t)L.cap);
   for (int k = 0; k < 2; ++k) {
     L.off_cnt[k] = o; o = align_up(o + sizeof(int) * (size_t)L.ntiles);
     L.off_ids[k] = o; o = align_up(o + sizeof(int) * (size_t)L.ntiles * L.bin_cap);
@@ -109,6 +110,7 @@ struct hlbm_ctx {
   int* d_box = nullptr;
   Rec* rec = nullptr;
   double* partial = nullptr;
+  double* acc = nullptr;
   int* cnt[2] = {nullptr, nullptr};
   int* ids[2] = {nullptr, nullptr};
   int* status = nullptr;
@@ -117,8 +119,11 @@ struct hlbm_ctx {
   int np = 0;
   long long steps = 0;
   int sub_y = 4, sub_z = 2;
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  // [0][parity]: step with the momentum-exchange kernel (after any change of
+  // state); [1][parity]: step that takes the sums the previous collision made
+  cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool graphs_ok = false;
+  bool fused_valid = false;  // the accumulator holds this state's momentum exchange
   std::vector<int> h_shape, h_box;  // host copies
   std::string err;
 };
@@ -158,6 +163,7 @@ static LbmArgs lbm_args(const hlbm_ctx* h, int parity) {
   a.bin_ids = h->ids[parity];
   a.bin_cap = h->L.bin_cap;
   a.rec = h->rec;
+  a.acc = h->acc;
   a.status = h->status;
   return a;
 }
@@ -179,6 +185,8 @@ static PartArgs part_args(const hlbm_ctx* h, int parity) {
   a.scale = (float)sc;
   a.inv_scale = (float)(1.0 / sc);
   a.partial = h->partial;
+  a.acc = h->acc;
+  a.use_partials = 1;
   a.bin_count = h->cnt[parity];
   a.bin_ids = h->ids[parity];
   a.bin_count_clear = h->cnt[1 - parity];
@@ -188,37 +196,40 @@ static PartArgs part_args(const hlbm_ctx* h, int parity) {
   return a;
 }
 
-static cudaError_t enqueue_step(hlbm_ctx* h, int parity, cudaStream_t s) {
+static cudaError_t enqueue_step(hlbm_ctx* h, int parity, bool fused, cudaStream_t s) {
   cudaError_t e;
   if (h->np > 0) {
-    const PartArgs pa = part_args(h, parity);
-    if ((e = launch_mea(pa, h->prm.precision, parity, s)) != cudaSuccess) return e;
+    PartArgs pa = part_args(h, parity);
+    pa.use_partials = fused ? 0 : 1;
+    if (!fused && (e = launch_mea(pa, h->prm.precision, parity, s)) != cudaSuccess) return e;
     if ((e = launch_update(pa, s)) != cudaSuccess) return e;
   }
   return launch_collide(lbm_args(h, parity), h->prm.precision, parity, h->walls, h->np > 0, s);
 }
 
 static void drop_graphs(hlbm_ctx* h) {
-  for (int k = 0; k < 2; ++k) {
-    if (h->exec[k]) cudaGraphExecDestroy(h->exec[k]);
-    h->exec[k] = nullptr;
-  }
+  for (int f = 0; f < 2; ++f)
+    for (int k = 0; k < 2; ++k) {
+      if (h->exec[f][k]) cudaGraphExecDestroy(h->exec[f][k]);
+      h->exec[f][k] = nullptr;
+    }
   h->graphs_ok = false;
 }
 
 static int build_graphs(hlbm_ctx* h) {
   drop_graphs(h);
-  for (int parity = 0; parity < 2; ++parity) {
+  for (int gi = 0; gi < 4; ++gi) {
+    const int fused = gi >> 1, parity = gi & 1;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_step(h, parity, h->cap_stream);
+    cudaError_t e = enqueue_step(h, parity, fused != 0, h->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       return fail(h, HLBM_ERR_CUDA, std::string("graph capture: ") +
                                         cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&h->exec[parity], g, 0);
+    e = cudaGraphInstantiate(&h->exec[fused][parity], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, HLBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
@@ -305,6 +316,7 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
   h->d_box = (int*)(h->buf + h->L.off_box);
   h->rec = (Rec*)(h->buf + h->L.off_rec);
   h->partial = (double*)(h->buf + h->L.off_part);
+  h->acc = (double*)(h->buf + h->L.off_acc);
   for (int k = 0; k < 2; ++k) {
     h->cnt[k] = (int*)(h->buf + h->L.off_cnt[k]);
     h->ids[k] = (int*)(h->buf + h->L.off_ids[k]);
@@ -472,6 +484,7 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
   CK(launch_records(part_args(h, 0), h->stream));
   CK(cudaStreamSynchronize(h->stream));
   drop_graphs(h);
+  h->fused_valid = false;
   return HLBM_OK;
 }
 
@@ -517,6 +530,7 @@ int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, con
   }
   CK(launch_records(part_args(h, 0), h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  h->fused_valid = false;
   return HLBM_OK;
 }
 
@@ -529,7 +543,9 @@ int hlbm_step(hlbm_handle h, int nsteps) {
     if (rc != HLBM_OK) return rc;
   }
   for (int k = 0; k < nsteps; ++k) {
-    CK(cudaGraphLaunch(h->exec[(h->steps + k) & 1], h->stream));
+    const int fused = (h->fused_valid && h->np > 0) ? 1 : 0;
+    CK(cudaGraphLaunch(h->exec[fused][(h->steps + k) & 1], h->stream));
+    h->fused_valid = true;
   }
   h->steps += nsteps;
   return HLBM_OK;
@@ -604,6 +620,7 @@ int hlbm_set_populations(hlbm_handle h, int box, const double* host_f) {
     CK(launch_scatter(la, h->prm.precision, parity, box, c0, n, h->stage, h->stream));
     CK(cudaStreamSynchronize(h->stream));
   }
+  h->fused_valid = false;
   return HLBM_OK;
 }
 
@@ -670,9 +687,11 @@ int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]) {
   int rc = HLBM_OK;
   for (int s = 0; s < nsteps; ++s) {
     const int parity = (int)(h->steps & 1);
-    const PartArgs pa = part_args(h, parity);
+    PartArgs pa = part_args(h, parity);
+    const bool fused = h->fused_valid && h->np > 0;
+    pa.use_partials = fused ? 0 : 1;
     cudaEventRecord(ev[0], h->stream);
-    if (h->np > 0) launch_mea(pa, h->prm.precision, parity, h->stream);
+    if (h->np > 0 && !fused) launch_mea(pa, h->prm.precision, parity, h->stream);
     cudaEventRecord(ev[1], h->stream);
     if (h->np > 0) launch_update(pa, h->stream);
     cudaEventRecord(ev[2], h->stream);
@@ -686,6 +705,7 @@ int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]) {
       acc[k] += t;
     }
     h->steps += 1;
+    h->fused_valid = true;
   }
   for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
   if (rc != HLBM_OK) return rc;

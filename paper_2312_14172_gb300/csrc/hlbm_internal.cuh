@@ -131,6 +131,7 @@ struct LbmArgs {
   const int* bin_ids;
   int bin_cap;
   const Rec* rec;
+  double* acc;              // [cap][6] force/torque of the next step's momentum exchange
   int* status;
 };
 
@@ -147,8 +148,11 @@ struct PartArgs {
   const void* f;
   long long plane;
   float scale, inv_scale;
-  // partial force/torque sums of the momentum exchange, [cap][MEA_CHUNKS][6]
+  // partial force/torque sums of the momentum-exchange kernel, [cap][MEA_CHUNKS][6]
   double* partial;
+  // the same sums accumulated by the previous collision, [cap][6]
+  double* acc;
+  int use_partials;         // 1: take the kernel's partials, 0: take acc
   // bins written by the update (this step) and cleared (other parity)
   int* bin_count;
   int* bin_ids;

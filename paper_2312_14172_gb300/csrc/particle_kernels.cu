@@ -380,68 +380,66 @@ __global__ void __launch_bounds__(32) update_kernel(PartArgs a) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long t = tid; t < a.ntiles; t += stride) a.bin_count_clear[t] = 0;
-  const int lane = threadIdx.x & 31;
-  const long long wbase = tid - lane;  // first particle of this warp
-  if (wbase >= a.np) return;           // whole warp past the end
+  if (tid >= a.np) return;
   const int p = (int)tid;
-  int binnable = 0;
-  AxisTiles tx{0, -1, 0, -1}, ty{0, -1, 0, -1}, tz{0, -1, 0, -1};
-  int box = 0;
-  if (p < a.np) {
-    const int shape = a.shape[p];
-    box = a.box[p];
-    const BoxDesc bd = a.boxes[box];
-    // force and torque: the momentum-exchange partials in a fixed order
-    double Fh[3] = {0, 0, 0}, Th[3] = {0, 0, 0};
+  const int shape = a.shape[p], box = a.box[p];
+  const BoxDesc bd = a.boxes[box];
+  // force and torque of the momentum exchange: the kernel's partials in a
+  // fixed order, or the sums the previous collision accumulated; the
+  // accumulator is cleared for the collision of this step
+  double Fh[3] = {0, 0, 0}, Th[3] = {0, 0, 0};
+  double* acc = a.acc + (long long)p * 6;
+  if (a.use_partials) {
     const double* part = a.partial + (long long)p * MEA_CHUNKS * 6;
-    for (int k = 0; k < MEA_CHUNKS; ++k) {
+    for (int k = 0; k < MEA_CHUNKS; ++k)
       for (int j = 0; j < 3; ++j) {
         Fh[j] += part[k * 6 + j];
         Th[j] += part[k * 6 + 3 + j];
       }
-    }
-    integrate(a, bd, p, shape, Fh, Th);
-    Rec R;
-    build_record(a.P, a.cap, p, shape, box, R);
-    a.rec[p] = R;
-    // tiles touched by the influence sphere of the new state
-    const double rinf = pget(a.P, a.cap, PF_RINF, p);
-    binnable = 1;
-    const int n[3] = {bd.nx, bd.ny, bd.nz};
-    AxisTiles* at[3] = {&tx, &ty, &tz};
-    const int T[3] = {TILE_X, TILE_Y, TILE_Z};
-#pragma unroll
+  } else {
     for (int j = 0; j < 3; ++j) {
-      const double X = pget(a.P, a.cap, PF_X + j, p);
-      if (!(X > -1.0e6 && X < 1.0e6)) { binnable = 0; continue; }
-      const int lo = (int)floor(X - rinf) - 1, hi = (int)ceil(X + rinf) + 1;
-      *at[j] = axis_tiles(lo, hi, n[j], T[j], (bd.bc >> j) & 1);
+      Fh[j] = acc[j];
+      Th[j] = acc[3 + j];
     }
   }
-  // the 32 particles of this warp are binned one after another, each by all
-  // lanes together
-  for (int j = 0; j < 32; ++j) {
-    if (!__shfl_sync(0xffffffffu, binnable, j)) continue;
-    const int pj = __shfl_sync(0xffffffffu, p, j);
-    const int bj = __shfl_sync(0xffffffffu, box, j);
-    AxisTiles X{__shfl_sync(0xffffffffu, tx.a0, j), __shfl_sync(0xffffffffu, tx.a1, j),
-                __shfl_sync(0xffffffffu, tx.b0, j), __shfl_sync(0xffffffffu, tx.b1, j)};
-    AxisTiles Y{__shfl_sync(0xffffffffu, ty.a0, j), __shfl_sync(0xffffffffu, ty.a1, j),
-                __shfl_sync(0xffffffffu, ty.b0, j), __shfl_sync(0xffffffffu, ty.b1, j)};
-    AxisTiles Z{__shfl_sync(0xffffffffu, tz.a0, j), __shfl_sync(0xffffffffu, tz.a1, j),
-                __shfl_sync(0xffffffffu, tz.b0, j), __shfl_sync(0xffffffffu, tz.b1, j)};
-    const BoxDesc bd = a.boxes[bj];
-    const int cx_ = X.count(), cy_ = Y.count(), cz_ = Z.count();
-    const int total = cx_ * cy_ * cz_;
-    for (int t = lane; t < total; t += 32) {
-      const int ix = t % cx_;
-      const int r = t / cx_;
-      const int iy = r % cy_;
-      const int iz = r / cy_;
-      const long long tile =
-          bd.tile_off + ((long long)Z.at(iz) * bd.nty + Y.at(iy)) * bd.ntx + X.at(ix);
-      const int slot = atomicAdd(&a.bin_count[tile], 1);
-      if (slot < a.bin_cap) a.bin_ids[tile * a.bin_cap + slot] = pj;
+  for (int j = 0; j < 6; ++j) acc[j] = 0.0;
+  integrate(a, bd, p, shape, Fh, Th);
+  Rec R;
+  build_record(a.P, a.cap, p, shape, box, R);
+  a.rec[p] = R;
+  // bin tiles touched by the influence sphere, widened so that the cells next
+  // to the particle's interior (which feed its momentum exchange) see it too
+  const double rbin = fmax(pget(a.P, a.cap, PF_RINF, p), pget(a.P, a.cap, PF_RC, p) + 1.5);
+  const int n[3] = {bd.nx, bd.ny, bd.nz};
+  AxisTiles at[3];
+  const int T[3] = {TILE_X, TILE_Y, TILE_Z};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const double X = pget(a.P, a.cap, PF_X + j, p);
+    if (!(X > -1.0e6 && X < 1.0e6)) return;  // flagged by the update; not binned
+    const int lo = (int)floor(X - rbin) - 1, hi = (int)ceil(X + rbin) + 1;
+    at[j] = axis_tiles(lo, hi, n[j], T[j], (bd.bc >> j) & 1);
+  }
+  const int cx_ = at[0].count(), cy_ = at[1].count(), cz_ = at[2].count();
+  const int total = cx_ * cy_ * cz_;
+  // four atomics in flight per lane
+  for (int t = 0; t < total; t += 4) {
+    long long tile[4];
+    int slot[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = t + u;
+      tile[u] = -1;
+      if (q < total) {
+        const int ix = q % cx_, r = q / cx_, iy = r % cy_, iz = r / cy_;
+        tile[u] = bd.tile_off + ((long long)at[2].at(iz) * bd.nty + at[1].at(iy)) * bd.ntx + at[0].at(ix);
+        slot[u] = atomicAdd(&a.bin_count[tile[u]], 1);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (tile[u] < 0) continue;
+      if (slot[u] < a.bin_cap) a.bin_ids[tile[u] * a.bin_cap + slot[u]] = p;
       else atomicOr(a.status, ST_CAPACITY);
     }
   }
