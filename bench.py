@@ -218,6 +218,9 @@ def run_gpu(args, ws, rank, local):
     tune = None
     if args.autotune:
         tune = lat.autotune(nsteps=5)
+    if args.mea_mode:
+        lat.set_mea_mode(args.mea_mode)
+    mea_mode = lat.get_mea_mode()
     lat.step(args.warmup)
     lat.sync()
     sampler = ClockSampler(local)
@@ -237,6 +240,7 @@ def run_gpu(args, ws, rank, local):
     ms = max_over_ranks(ms)
     value = ws * cells * args.steps / (ms / 1e3) / 1e6
 
+    lat_launch = lat.get_launch()
     # ---- per-kernel CUDA-event times on the same stream (roofline)
     kt = lat.kernel_times(nsteps=max(5, min(args.steps, 50)))
     peak, peak_kind = measured_peaks()
@@ -280,8 +284,10 @@ def run_gpu(args, ws, rank, local):
     fp16 = None
     if args.fp16 and prec == "fp32":
         lat16 = hlbm.from_workload(w, precision="fp16", stream=stream)
-        if tune:
+        if args.autotune:
             lat16.autotune(nsteps=5)
+        if args.mea_mode:
+            lat16.set_mea_mode(args.mea_mode)
         lat16.step(args.warmup)
         lat16.sync()
         flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -341,7 +347,9 @@ def run_gpu(args, ws, rank, local):
                    "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu",
                    "l2": f"inputs larger than L2 ({BYTES_PER_CELL[prec] // 2 * cells / 1e6:.0f} MB "
                          "of populations); no flush between FP32 steps",
-                   "launch": list(tune[:2]) if tune else None},
+                   "launch": {"tile_y": lat_launch[0], "tile_z": lat_launch[1],
+                              "momentum_exchange": mea_mode,
+                              "autotuned": bool(args.autotune)}},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
@@ -361,7 +369,8 @@ def main():
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp16"])
     ap.add_argument("--no-fp16", dest="fp16", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--mea-mode", default=None, choices=[None, "kernel", "moments"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -124,7 +124,7 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
  * radius beyond which B of Eq. B vanishes, plus 2 cells) spans half a
  * periodic axis or more.  The influence radius is r + eps/2 for spheres, the
  * circumscribed radius + eps/2 for cuboids and a_max (1 + eps / (2 a_min))
- * for ellipsoids. */
+ * for ellipsoids.  The circumscribed radius may be at most 30 cells. */
 int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape,
                        const double* shape_params, const double* X, const double* U,
                        const double* omega, const double* quat, const double* rho_p);
@@ -166,9 +166,28 @@ long long hlbm_steps_done(hlbm_handle h);
 int hlbm_set_launch(hlbm_handle h, int tile_y, int tile_z);
 int hlbm_get_launch(hlbm_handle h, int* tile_y, int* tile_z);
 
-/* Times every launch shape on nsteps steps of the current state (the state
- * advances by the steps taken) and keeps the fastest; writes the chosen
- * shape and its time per step in ms (any pointer may be NULL). */
+/* How the momentum exchange (Eq. hlbm:mea) of a step is computed:
+ *   HLBM_MEA_KERNEL   from the populations alone, by a kernel that walks the
+ *                     bounding box of each particle (default);
+ *   HLBM_MEA_MOMENTS  the collision of the previous step lists the cells
+ *                     inside particles with the mass and momentum their
+ *                     post-collision populations carry away; the momentum
+ *                     exchange is then, per listed cell, the momentum gained
+ *                     minus u_p times the mass gained, from the arrivals alone.
+ *                     The bounding-box kernel still runs on the first step
+ *                     after any change of state.  Needs max_particles > 0; the
+ *                     list holds up to half the lattice's cells
+ *                     (HLBM_ERR_CAPACITY beyond).
+ * Both give the same force and torque up to FP32 summation order. */
+#define HLBM_MEA_KERNEL 0
+#define HLBM_MEA_MOMENTS 1
+int hlbm_set_mea_mode(hlbm_handle h, int mode);
+int hlbm_get_mea_mode(hlbm_handle h);
+
+/* Times every momentum-exchange mode and launch shape on nsteps steps of the
+ * current state (the state advances by the steps taken) and keeps the
+ * fastest; writes the chosen shape and its time per step in ms (any pointer
+ * may be NULL). */
 int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, float* ms_per_step);
 
 /* Runs nsteps steps with each kernel launched on its own, bracketed by CUDA

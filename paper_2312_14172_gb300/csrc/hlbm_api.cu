@@ -32,8 +32,10 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 struct Layout {
   long long plane = 0, ncell = 0, ntiles = 0, stage_cells = 0;
   int cap = 0, bin_cap = 0;
-  size_t off_f, off_boxes, off_P, off_shape, off_box, off_rec, off_part, off_acc, off_cnt[2],
-      off_ids[2], off_status, off_stage, total;
+  size_t off_f, off_boxes, off_P, off_shape, off_box, off_rec, off_part, off_acc, off_chp, off_chq,
+      off_pc0, off_pnc, off_done, off_lcnt, off_lidx, off_lmom, off_cnt[2], off_ids[2], off_status,
+      off_stage, total;
+  long long ilist_cap = 0;
 };
 
 bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& L,
@@ -79,8 +81,19 @@ bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& 
   L.off_shape = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
   L.off_box = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
   L.off_rec = o; o = align_up(o + sizeof(Rec) * (size_t)L.cap);
-  L.off_part = o; o = align_up(o + sizeof(double) * 6 * MEA_CHUNKS * (size_t)L.cap);
+  L.off_part = o; o = align_up(o + sizeof(double) * 6 * MAX_PLANES * (size_t)L.cap);
   L.off_acc = o; o = align_up(o + sizeof(double) * 6 * (size_t)L.cap);
+  L.off_chp = o; o = align_up(o + sizeof(int) * MAX_PLANES * (size_t)L.cap);
+  L.off_chq = o; o = align_up(o + sizeof(int) * MAX_PLANES * (size_t)L.cap);
+  L.off_pc0 = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
+  L.off_pnc = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
+  L.off_done = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
+  // interior-cell list for the momentum exchange from moments: room for half
+  // of all cells (more than any packing of non-overlapping particles needs)
+  L.ilist_cap = L.cap > 0 ? (L.plane + 1) / 2 : 0;
+  L.off_lcnt = o; o = align_up(o + sizeof(int));
+  L.off_lidx = o; o = align_up(o + sizeof(int2) * (size_t)L.ilist_cap);
+  L.off_lmom = o; o = align_up(o + sizeof(float4) * (size_t)L.ilist_cap);
   for (int k = 0; k < 2; ++k) {
     L.off_cnt[k] = o; o = align_up(o + sizeof(int) * (size_t)L.ntiles);
     L.off_ids[k] = o; o = align_up(o + sizeof(int) * (size_t)L.ntiles * L.bin_cap);
@@ -111,6 +124,18 @@ struct hlbm_ctx {
   Rec* rec = nullptr;
   double* partial = nullptr;
   double* acc = nullptr;
+  int* chunk_p = nullptr;
+  int* chunk_q = nullptr;
+  int* p_chunk0 = nullptr;
+  int* p_nchunk = nullptr;
+  int* done = nullptr;
+  int* ilist_count = nullptr;
+  int2* ilist_idx = nullptr;
+  float4* ilist_mom = nullptr;
+  int nsm = 0;
+  int nchunks = 0;
+  std::vector<int> h_nchunk;  // bounding-box planes per particle
+  int mea_mode = HLBM_MEA_KERNEL;
   int* cnt[2] = {nullptr, nullptr};
   int* ids[2] = {nullptr, nullptr};
   int* status = nullptr;
@@ -123,7 +148,7 @@ struct hlbm_ctx {
   // state); [1][parity]: step that takes the sums the previous collision made
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool graphs_ok = false;
-  bool fused_valid = false;  // the accumulator holds this state's momentum exchange
+  bool moments_valid = false;  // the accumulator holds this state's momentum exchange
   std::vector<int> h_shape, h_box;  // host copies
   std::string err;
 };
@@ -163,6 +188,11 @@ static LbmArgs lbm_args(const hlbm_ctx* h, int parity) {
   a.bin_ids = h->ids[parity];
   a.bin_cap = h->L.bin_cap;
   a.rec = h->rec;
+  const bool rec = h->mea_mode == HLBM_MEA_MOMENTS && h->ilist_idx;
+  a.ilist_count = h->ilist_count;
+  a.ilist_idx = rec ? h->ilist_idx : nullptr;
+  a.ilist_mom = rec ? h->ilist_mom : nullptr;
+  a.ilist_cap = h->L.ilist_cap;
   a.acc = h->acc;
   a.status = h->status;
   return a;
@@ -184,9 +214,16 @@ static PartArgs part_args(const hlbm_ctx* h, int parity) {
   const double sc = h->prm.precision == HLBM_FP16 ? std::ldexp(1.0, h->prm.fp16_scale_log2) : 1.0;
   a.scale = (float)sc;
   a.inv_scale = (float)(1.0 / sc);
+  a.chunk_p = h->chunk_p;
+  a.chunk_q = h->chunk_q;
+  a.p_chunk0 = h->p_chunk0;
+  a.p_nchunk = h->p_nchunk;
+  a.nchunks = h->nchunks;
   a.partial = h->partial;
+  a.done = h->done;
   a.acc = h->acc;
-  a.use_partials = 1;
+  a.from_acc = 0;
+  a.ilist_count = h->ilist_count;
   a.bin_count = h->cnt[parity];
   a.bin_ids = h->ids[parity];
   a.bin_count_clear = h->cnt[1 - parity];
@@ -196,12 +233,21 @@ static PartArgs part_args(const hlbm_ctx* h, int parity) {
   return a;
 }
 
-static cudaError_t enqueue_step(hlbm_ctx* h, int parity, bool fused, cudaStream_t s) {
+// moments: the collision of the previous step recorded the post-collision
+// moments of the cells inside particles, and the momentum exchange of this
+// step runs from them; otherwise the bounding-box kernel computes it from
+// the populations alone (always on the first step after a change of state).
+static cudaError_t enqueue_step(hlbm_ctx* h, int parity, bool moments, cudaStream_t s) {
   cudaError_t e;
   if (h->np > 0) {
     PartArgs pa = part_args(h, parity);
-    pa.use_partials = fused ? 0 : 1;
-    if (!fused && (e = launch_mea(pa, h->prm.precision, parity, s)) != cudaSuccess) return e;
+    pa.from_acc = moments ? 1 : 0;
+    if (moments) {
+      if ((e = launch_mea_moments(lbm_args(h, parity), h->prm.precision, parity, h->walls, h->nsm, s)) != cudaSuccess)
+        return e;
+    } else if ((e = launch_mea(pa, h->prm.precision, parity, s)) != cudaSuccess) {
+      return e;
+    }
     if ((e = launch_update(pa, s)) != cudaSuccess) return e;
   }
   return launch_collide(lbm_args(h, parity), h->prm.precision, parity, h->walls, h->np > 0, s);
@@ -219,17 +265,18 @@ static void drop_graphs(hlbm_ctx* h) {
 static int build_graphs(hlbm_ctx* h) {
   drop_graphs(h);
   for (int gi = 0; gi < 4; ++gi) {
-    const int fused = gi >> 1, parity = gi & 1;
+    const int moments = gi >> 1, parity = gi & 1;
+    if (moments && h->mea_mode != HLBM_MEA_MOMENTS) continue;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_step(h, parity, fused != 0, h->cap_stream);
+    cudaError_t e = enqueue_step(h, parity, moments != 0, h->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       return fail(h, HLBM_ERR_CUDA, std::string("graph capture: ") +
                                         cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&h->exec[fused][parity], g, 0);
+    e = cudaGraphInstantiate(&h->exec[moments][parity], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, HLBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
@@ -317,6 +364,19 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
   h->rec = (Rec*)(h->buf + h->L.off_rec);
   h->partial = (double*)(h->buf + h->L.off_part);
   h->acc = (double*)(h->buf + h->L.off_acc);
+  h->chunk_p = (int*)(h->buf + h->L.off_chp);
+  h->chunk_q = (int*)(h->buf + h->L.off_chq);
+  h->p_chunk0 = (int*)(h->buf + h->L.off_pc0);
+  h->p_nchunk = (int*)(h->buf + h->L.off_pnc);
+  h->done = (int*)(h->buf + h->L.off_done);
+  h->ilist_count = (int*)(h->buf + h->L.off_lcnt);
+  h->ilist_idx = h->L.ilist_cap > 0 ? (int2*)(h->buf + h->L.off_lidx) : nullptr;
+  h->ilist_mom = h->L.ilist_cap > 0 ? (float4*)(h->buf + h->L.off_lmom) : nullptr;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) h->nsm = 0;
+  }
   for (int k = 0; k < 2; ++k) {
     h->cnt[k] = (int*)(h->buf + h->L.off_cnt[k]);
     h->ids[k] = (int*)(h->buf + h->L.off_ids[k]);
@@ -417,7 +477,7 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
   if (h->np + n > h->L.cap) return fail(h, HLBM_ERR_CAPACITY, "more particles than max_particles");
   if (n == 0) return HLBM_OK;
   std::vector<double> tab((size_t)PF_COUNT * n, 0.0);
-  std::vector<int> sh(n), bx(n);
+  std::vector<int> sh(n), bx(n), nch(n);
   auto T = [&](int fld, int k) -> double& { return tab[(size_t)fld * n + k]; };
   for (int k = 0; k < n; ++k) {
     const int b = box_id ? box_id[k] : 0;
@@ -442,6 +502,7 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
     }
     double V, m, I[3], rc, rinf;
     mass_properties(s, a, rho, &V, &m, I, &rc, &rinf, h->prm.eps);
+    if (!(rc <= 30.0)) return fail(h, HLBM_ERR_ARG, "circumscribed radius above 30 cells");
     double x[3];
     const int nn[3] = {bd.nx, bd.ny, bd.nz};
     for (int j = 0; j < 3; ++j) {
@@ -472,6 +533,7 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
     T(PF_RINF, k) = rinf;
     sh[k] = s;
     bx[k] = b;
+    nch[k] = (int)std::ceil(2.0 * rc) + 2;  // bounding-box planes, at most MAX_PLANES
   }
   const int p0 = h->np;
   int rc = upload_fields(h, p0, n, tab);
@@ -481,10 +543,29 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
   h->np += n;
   h->h_shape.insert(h->h_shape.end(), sh.begin(), sh.end());
   h->h_box.insert(h->h_box.end(), bx.begin(), bx.end());
+  h->h_nchunk.insert(h->h_nchunk.end(), nch.begin(), nch.end());
+  {
+    // one momentum-exchange block per (particle, bounding-box plane)
+    std::vector<int> cp, cq, c0(h->np), cn(h->np);
+    for (int q = 0; q < h->np; ++q) {
+      c0[q] = (int)cp.size();
+      cn[q] = h->h_nchunk[q];
+      for (int k = 0; k < cn[q]; ++k) {
+        cp.push_back(q);
+        cq.push_back(k);
+      }
+    }
+    h->nchunks = (int)cp.size();
+    CK(cudaMemcpyAsync(h->chunk_p, cp.data(), sizeof(int) * cp.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->chunk_q, cq.data(), sizeof(int) * cq.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->p_chunk0, c0.data(), sizeof(int) * c0.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->p_nchunk, cn.data(), sizeof(int) * cn.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
   CK(launch_records(part_args(h, 0), h->stream));
   CK(cudaStreamSynchronize(h->stream));
   drop_graphs(h);
-  h->fused_valid = false;
+  h->moments_valid = false;
   return HLBM_OK;
 }
 
@@ -530,7 +611,7 @@ int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, con
   }
   CK(launch_records(part_args(h, 0), h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  h->fused_valid = false;
+  h->moments_valid = false;
   return HLBM_OK;
 }
 
@@ -543,9 +624,9 @@ int hlbm_step(hlbm_handle h, int nsteps) {
     if (rc != HLBM_OK) return rc;
   }
   for (int k = 0; k < nsteps; ++k) {
-    const int fused = (h->fused_valid && h->np > 0) ? 1 : 0;
-    CK(cudaGraphLaunch(h->exec[fused][(h->steps + k) & 1], h->stream));
-    h->fused_valid = true;
+    const int moments = (h->moments_valid && h->np > 0) ? 1 : 0;
+    CK(cudaGraphLaunch(h->exec[moments][(h->steps + k) & 1], h->stream));
+    h->moments_valid = h->mea_mode == HLBM_MEA_MOMENTS;
   }
   h->steps += nsteps;
   return HLBM_OK;
@@ -620,7 +701,7 @@ int hlbm_set_populations(hlbm_handle h, int box, const double* host_f) {
     CK(launch_scatter(la, h->prm.precision, parity, box, c0, n, h->stage, h->stream));
     CK(cudaStreamSynchronize(h->stream));
   }
-  h->fused_valid = false;
+  h->moments_valid = false;
   return HLBM_OK;
 }
 
@@ -636,6 +717,21 @@ int hlbm_set_launch(hlbm_handle h, int tile_y, int tile_z) {
   return HLBM_OK;
 }
 
+int hlbm_set_mea_mode(hlbm_handle h, int mode) {
+  if (!h) return HLBM_ERR_ARG;
+  if (mode != HLBM_MEA_KERNEL && mode != HLBM_MEA_MOMENTS) return fail(h, HLBM_ERR_ARG, "unknown momentum-exchange mode");
+  if (mode == HLBM_MEA_MOMENTS && !h->ilist_idx) return fail(h, HLBM_ERR_STATE, "no particle capacity");
+  if (mode != h->mea_mode) {
+    CK(cudaStreamSynchronize(h->stream));
+    h->mea_mode = mode;
+    h->moments_valid = false;
+    drop_graphs(h);
+  }
+  return HLBM_OK;
+}
+
+int hlbm_get_mea_mode(hlbm_handle h) { return h ? h->mea_mode : HLBM_ERR_ARG; }
+
 int hlbm_get_launch(hlbm_handle h, int* tile_y, int* tile_z) {
   if (!h) return HLBM_ERR_ARG;
   if (tile_y) *tile_y = h->sub_y;
@@ -650,12 +746,14 @@ int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, float* ms
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int by = h->sub_y, bz = h->sub_z;
+  int by = h->sub_y, bz = h->sub_z, bm = h->mea_mode;
   const int vals[4] = {1, 2, 4, 8};
   int rc = HLBM_OK;
-  for (int iy = 0; iy < 4 && rc == HLBM_OK; ++iy)
-    for (int iz = 0; iz < 4 && rc == HLBM_OK; ++iz) {
-      rc = hlbm_set_launch(h, vals[iy], vals[iz]);
+  const int nmodes = h->np > 0 ? 2 : 1;
+  for (int im = 0; im < nmodes * 16 && rc == HLBM_OK; ++im) {
+      const int mode = im / 16, iy = (im / 4) % 4, iz = im % 4;
+      rc = hlbm_set_mea_mode(h, mode);
+      if (rc == HLBM_OK) rc = hlbm_set_launch(h, vals[iy], vals[iz]);
       if (rc == HLBM_OK) rc = hlbm_step(h, 2);  // warm-up and graph build
       if (rc != HLBM_OK) break;
       cudaEventRecord(e0, h->stream);
@@ -665,12 +763,13 @@ int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, float* ms
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= nsteps;
-      if (ms < best) { best = ms; by = vals[iy]; bz = vals[iz]; }
-    }
+      if (ms < best) { best = ms; by = vals[iy]; bz = vals[iz]; bm = mode; }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != HLBM_OK) return rc;
-  rc = hlbm_set_launch(h, by, bz);
+  rc = hlbm_set_mea_mode(h, bm);
+  if (rc == HLBM_OK) rc = hlbm_set_launch(h, by, bz);
   if (tile_y) *tile_y = by;
   if (tile_z) *tile_z = bz;
   if (ms_per_step) *ms_per_step = best;
@@ -688,10 +787,11 @@ int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]) {
   for (int s = 0; s < nsteps; ++s) {
     const int parity = (int)(h->steps & 1);
     PartArgs pa = part_args(h, parity);
-    const bool fused = h->fused_valid && h->np > 0;
-    pa.use_partials = fused ? 0 : 1;
+    const bool fused = h->moments_valid && h->np > 0;
+    pa.from_acc = fused ? 1 : 0;
     cudaEventRecord(ev[0], h->stream);
     if (h->np > 0 && !fused) launch_mea(pa, h->prm.precision, parity, h->stream);
+    if (h->np > 0 && fused) launch_mea_moments(lbm_args(h, parity), h->prm.precision, parity, h->walls, h->nsm, h->stream);
     cudaEventRecord(ev[1], h->stream);
     if (h->np > 0) launch_update(pa, h->stream);
     cudaEventRecord(ev[2], h->stream);
@@ -705,7 +805,7 @@ int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]) {
       acc[k] += t;
     }
     h->steps += 1;
-    h->fused_valid = true;
+    h->moments_valid = h->mea_mode == HLBM_MEA_MOMENTS;
   }
   for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
   if (rc != HLBM_OK) return rc;

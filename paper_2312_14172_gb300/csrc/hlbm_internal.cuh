@@ -60,10 +60,10 @@ enum {
   PF_COUNT = 37
 };
 
-// the momentum exchange of one particle is split over this many thread
-// blocks, each taking a slab of the bounding box's z-planes; their FP64
-// partial sums (6 per block) are added in a fixed order by the update
-constexpr int MEA_CHUNKS = 8;
+// the momentum-exchange kernel gives every z-plane of a particle's bounding
+// box its own thread block; a particle spans at most this many planes
+// (circumscribed radius <= 30 cells)
+constexpr int MAX_PLANES = 64;
 
 // FP32 coupling record of one particle (128 bytes)
 struct __align__(16) Rec {
@@ -131,7 +131,15 @@ struct LbmArgs {
   const int* bin_ids;
   int bin_cap;
   const Rec* rec;
-  double* acc;              // [cap][6] force/torque of the next step's momentum exchange
+  // list of the cells inside particles, appended by the collision for the
+  // next step's momentum exchange (nullptr: not recorded):
+  //   ilist_idx[k] = (global cell index, particle), ilist_mom[k] = mass and
+  //   momentum of the cell's post-collision deviations as stored
+  int* ilist_count;
+  int2* ilist_idx;
+  float4* ilist_mom;
+  long long ilist_cap;
+  double* acc;              // [cap][6] momentum exchange of a particle (FP64 sums)
   int* status;
 };
 
@@ -148,11 +156,18 @@ struct PartArgs {
   const void* f;
   long long plane;
   float scale, inv_scale;
-  // partial force/torque sums of the momentum-exchange kernel, [cap][MEA_CHUNKS][6]
-  double* partial;
+  // momentum-exchange kernel: one block per (particle, bounding-box plane)
+  const int* chunk_p;       // [chunks] particle of the block
+  const int* chunk_q;       // [chunks] plane of the block
+  const int* p_chunk0;      // [cap] first block of a particle
+  const int* p_nchunk;      // [cap] blocks of a particle
+  int nchunks;
+  double* partial;          // [chunks][6] FP64 partial force/torque sums
+  int* done;                // [cap] blocks finished per particle (reset to 0)
   // the same sums accumulated by the previous collision, [cap][6]
   double* acc;
-  int use_partials;         // 1: take the kernel's partials, 0: take acc
+  int from_acc;             // 1: the update takes acc, 0: the table's F and T
+  int* ilist_count;         // reset by the update for the next collision
   // bins written by the update (this step) and cleared (other parity)
   int* bin_count;
   int* bin_ids;
@@ -162,9 +177,67 @@ struct PartArgs {
   int* status;
 };
 
+// "Centre inside the particle" (Sec. 3.2, above Eq. hydrodynamicforce) in
+// FP32, every operation rounded on its own so that each kernel (and the
+// oracle) takes the same decision:
+//   r = (fp32(cell) - xh, minimum image) - xl
+//   sphere:    (r0 r0 + r1 r1) + r2 r2 < fp32(a^2)
+//   ellipsoid: e = (M^T r) * fp32(1/a) componentwise, (e0 e0 + e1 e1) + e2 e2 < 1
+//   cuboid:    |M^T r| < a componentwise
+// where (M^T r)_j = (M_0j r0 + M_1j r1) + M_2j r2.
+__device__ __forceinline__ float offset_fp32(int cell, int n, bool wall, float xh, float xl) {
+  float r0 = __fsub_rn((float)cell, xh);
+  if (!wall) {
+    const float L = (float)n;
+    const float half = __fmul_rn(0.5f, L);
+    if (r0 > half) r0 = __fsub_rn(r0, L);
+    else if (r0 < -half) r0 = __fadd_rn(r0, L);
+  }
+  return __fsub_rn(r0, xl);
+}
+
+__device__ __forceinline__ bool inside_from_offset(const Rec& R, const float r[3]) {
+  if (R.shape == 0) {
+    float s = __fmul_rn(r[0], r[0]);
+    s = __fadd_rn(s, __fmul_rn(r[1], r[1]));
+    s = __fadd_rn(s, __fmul_rn(r[2], r[2]));
+    return s < R.in2;
+  }
+  float b[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    float t = __fmul_rn(R.M[0 * 3 + j], r[0]);
+    t = __fadd_rn(t, __fmul_rn(R.M[1 * 3 + j], r[1]));
+    t = __fadd_rn(t, __fmul_rn(R.M[2 * 3 + j], r[2]));
+    b[j] = t;
+  }
+  if (R.shape == 1) {
+    const float e0 = __fmul_rn(b[0], R.ia[0]);
+    const float e1 = __fmul_rn(b[1], R.ia[1]);
+    const float e2 = __fmul_rn(b[2], R.ia[2]);
+    float s = __fmul_rn(e0, e0);
+    s = __fadd_rn(s, __fmul_rn(e1, e1));
+    s = __fadd_rn(s, __fmul_rn(e2, e2));
+    return s < 1.0f;
+  }
+  return fabsf(b[0]) < R.a[0] && fabsf(b[1]) < R.a[1] && fabsf(b[2]) < R.a[2];
+}
+
+__device__ __forceinline__ bool inside_fp32(const Rec& R, const BoxDesc& bd, int x, int y, int z,
+                                            float r[3]) {
+  r[0] = offset_fp32(x, bd.nx, bd.bc & 1, R.xh[0], R.xl[0]);
+  r[1] = offset_fp32(y, bd.ny, bd.bc & 2, R.xh[1], R.xl[1]);
+  r[2] = offset_fp32(z, bd.nz, bd.bc & 4, R.xh[2], R.xl[2]);
+  return inside_from_offset(R, r);
+}
+
 // launchers (stream-ordered, no synchronisation)
 cudaError_t launch_collide(const LbmArgs& a, int precision, int parity, bool walls, bool couple,
                            cudaStream_t s);
+// momentum exchange from the arrivals and the moments recorded in the list of
+// interior cells (a.rec must describe the particle state of this step)
+cudaError_t launch_mea_moments(const LbmArgs& a, int precision, int parity, bool walls, int nsm,
+                               cudaStream_t s);
 cudaError_t launch_mea(const PartArgs& a, int precision, int parity, cudaStream_t s);
 cudaError_t launch_update(const PartArgs& a, cudaStream_t s);
 cudaError_t launch_records(const PartArgs& a, cudaStream_t s);

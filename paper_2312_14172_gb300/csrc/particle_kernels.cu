@@ -79,50 +79,6 @@ __device__ void build_record(const double* P, int cap, int p, int shape, int box
   R.pid = p;
 }
 
-// "centre inside the particle" in FP32, each operation rounded on its own:
-//   r = (fp32(cell) - xh, minimum image) - xl;  sphere |r|^2 < fp32(a^2);
-//   ellipsoid |M^T r / a|^2 < 1;  cuboid |M^T r| < a componentwise
-__device__ __forceinline__ bool inside_fp32(const Rec& R, const BoxDesc& bd, int x, int y, int z,
-                                            float r[3]) {
-  const int cell[3] = {x, y, z};
-  const int n[3] = {bd.nx, bd.ny, bd.nz};
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    float r0 = __fsub_rn((float)cell[j], R.xh[j]);
-    if (!((bd.bc >> j) & 1)) {
-      const float L = (float)n[j];
-      const float half = __fmul_rn(0.5f, L);
-      if (r0 > half) r0 = __fsub_rn(r0, L);
-      else if (r0 < -half) r0 = __fadd_rn(r0, L);
-    }
-    r[j] = __fsub_rn(r0, R.xl[j]);
-  }
-  if (R.shape == 0) {
-    float s = __fmul_rn(r[0], r[0]);
-    s = __fadd_rn(s, __fmul_rn(r[1], r[1]));
-    s = __fadd_rn(s, __fmul_rn(r[2], r[2]));
-    return s < R.in2;
-  }
-  float b[3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    float t = __fmul_rn(R.M[0 * 3 + j], r[0]);
-    t = __fadd_rn(t, __fmul_rn(R.M[1 * 3 + j], r[1]));
-    t = __fadd_rn(t, __fmul_rn(R.M[2 * 3 + j], r[2]));
-    b[j] = t;
-  }
-  if (R.shape == 1) {
-    const float e0 = __fmul_rn(b[0], R.ia[0]);
-    const float e1 = __fmul_rn(b[1], R.ia[1]);
-    const float e2 = __fmul_rn(b[2], R.ia[2]);
-    float s = __fmul_rn(e0, e0);
-    s = __fadd_rn(s, __fmul_rn(e1, e1));
-    s = __fadd_rn(s, __fmul_rn(e2, e2));
-    return s < 1.0f;
-  }
-  return fabsf(b[0]) < R.a[0] && fabsf(b[1]) < R.a[1] && fabsf(b[2]) < R.a[2];
-}
-
 // force on the particle from cell x (used form of Eq. hlbm:mea):
 //   sum_i (c_i - u_p) f_i(x) + (c_i + u_p) f_ibar(x - c_i)
 // = sum_i c_i (in_i + out_i) - u_p sum_i (in_i - out_i), with in_i = f_i(x)
@@ -161,18 +117,35 @@ __device__ __forceinline__ void mea_cell(const S* f, long long P, const Nbr<true
   }
 }
 
-constexpr int MEA_LPR = 8;  // lanes per bounding-box row
+// x-range of the cells of bounding-box row iy (plane offset dz) that can lie
+// inside the circumscribed sphere (+-1 cell of margin); empty when the row
+// misses it
+__device__ __forceinline__ void row_range(int iy, int ext1, int lo0, int ext0, int lo1,
+                                          const double X[3], float dz, float rc2, int& xa, int& len) {
+  len = 0;
+  xa = 0;
+  if (iy >= ext1) return;
+  const float dy = (float)((double)(lo1 + iy) - X[1]);
+  const float d2 = dy * dy + dz * dz;
+  if (d2 >= rc2) return;
+  const float s = sqrtf(rc2 - d2);
+  xa = max(lo0, (int)floorf((float)X[0] - s) - 1);
+  const int xb = min(lo0 + ext0 - 1, (int)ceilf((float)X[0] + s) + 1);
+  len = max(xb - xa + 1, 0);
+}
 
 template <typename S, int PAR>
-__global__ void __launch_bounds__(128, 6) mea_kernel(PartArgs a) {
-  const int p = blockIdx.x;
-  const int chunk = blockIdx.y;
-  if (p >= a.np) return;
+__global__ void __launch_bounds__(128) mea_kernel(PartArgs a) {
+  const int chunk = blockIdx.x;
+  const int p = a.chunk_p[chunk], iz = a.chunk_q[chunk];
   __shared__ Rec R;
   __shared__ double wsum[4][6];
-  if (threadIdx.x < 32) reinterpret_cast<int*>(&R)[threadIdx.x] = reinterpret_cast<const int*>(&a.rec[p])[threadIdx.x];
+  __shared__ int s_start[MAX_PLANES + 1], s_xa[MAX_PLANES];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < 32) reinterpret_cast<int*>(&R)[tid] = reinterpret_cast<const int*>(&a.rec[p])[tid];
   __syncthreads();
-  double* out = a.partial + ((long long)p * MEA_CHUNKS + chunk) * 6;
+  double* out = a.partial + (long long)chunk * 6;
   const BoxDesc bd = a.boxes[R.box];
   const int n[3] = {bd.nx, bd.ny, bd.nz};
   const double rc = pget(a.P, a.cap, PF_RC, p);
@@ -185,65 +158,81 @@ __global__ void __launch_bounds__(128, 6) mea_kernel(PartArgs a) {
     X[j] = pget(a.P, a.cap, PF_X + j, p);
     ok = ok && (X[j] > -1.0e6 && X[j] < 1.0e6);
   }
-  if (!ok) {
-    if (threadIdx.x < 6) out[threadIdx.x] = 0.0;
-    if (threadIdx.x == 0) atomicOr(a.status, ST_UNSTABLE);
-    return;
-  }
   // cells that can be inside: [floor(X - r_c), ceil(X + r_c)] per axis
-  int lo[3], ext[3];
+  int lo[3] = {0, 0, 0}, ext[3] = {0, 0, 0};
+  if (ok) {
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    int l = (int)floor(X[j] - rc), h = (int)ceil(X[j] + rc);
-    if ((bd.bc >> j) & 1) {
-      l = max(l, 0);
-      h = min(h, n[j] - 1);
+    for (int j = 0; j < 3; ++j) {
+      int l = (int)floor(X[j] - rc), h = (int)ceil(X[j] + rc);
+      if ((bd.bc >> j) & 1) {
+        l = max(l, 0);
+        h = min(h, n[j] - 1);
+      }
+      lo[j] = l;
+      ext[j] = min(max(h - l + 1, 0), MAX_PLANES);
     }
-    lo[j] = l;
-    ext[j] = max(h - l + 1, 0);
+  } else if (tid == 0) {
+    atomicOr(a.status, ST_UNSTABLE);
   }
-  const int pz = (ext[2] + MEA_CHUNKS - 1) / MEA_CHUNKS;
-  const int z0 = chunk * pz, z1 = min(z0 + pz, ext[2]);
-  const int nrows = max(z1 - z0, 0) * ext[1];
-  const S* f = reinterpret_cast<const S*>(a.f) + bd.cell_off;
-  const float rc2 = (float)(rc * rc) * 1.0001f + 1e-3f;
   float Fx = 0.f, Fy = 0.f, Fz = 0.f, Tx = 0.f, Ty = 0.f, Tz = 0.f;
-  const int lane = threadIdx.x & 31;
-  const int rows_per_iter = blockDim.x / MEA_LPR;
-  for (int row = threadIdx.x / MEA_LPR; row < nrows; row += rows_per_iter) {
-    const int iz = z0 + row / ext[1], iy = row % ext[1];
-    const int zu = lo[2] + iz, yu = lo[1] + iy;  // unwrapped coordinates
-    const float dz = (float)((double)zu - X[2]), dy = (float)((double)yu - X[1]);
-    const float d2 = dy * dy + dz * dz;
-    if (d2 >= rc2) continue;  // the row misses the circumscribed sphere
-    const float sx = sqrtf(rc2 - d2);
-    const int xa = max(lo[0], (int)floorf((float)X[0] - sx) - 1);
-    const int xb = min(lo[0] + ext[0] - 1, (int)ceilf((float)X[0] + sx) + 1);
+  if (iz < ext[2]) {  // uniform over the block
+    const int zu = lo[2] + iz;
     const int z = zu < 0 ? zu + n[2] : (zu >= n[2] ? zu - n[2] : zu);
-    const int y = yu < 0 ? yu + n[1] : (yu >= n[1] ? yu - n[1] : yu);
-    for (int xu = xa + (lane % MEA_LPR); xu <= xb; xu += MEA_LPR) {
+    const float dz = (float)((double)zu - X[2]);
+    const float rc2 = (float)(rc * rc) * 1.0001f + 1e-3f;
+    // rows of this plane that meet the circumscribed sphere, flattened
+    if (warp == 0) {
+      int xa0, len0, xa1, len1;
+      row_range(lane, ext[1], lo[0], ext[0], lo[1], X, dz, rc2, xa0, len0);
+      row_range(lane + 32, ext[1], lo[0], ext[0], lo[1], X, dz, rc2, xa1, len1);
+      int s0 = len0, s1 = len1;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int t0 = __shfl_up_sync(0xffffffffu, s0, off);
+        const int t1 = __shfl_up_sync(0xffffffffu, s1, off);
+        if (lane >= off) { s0 += t0; s1 += t1; }
+      }
+      const int tot0 = __shfl_sync(0xffffffffu, s0, 31);
+      s1 += tot0;
+      s_start[lane] = s0 - len0;
+      s_start[lane + 32] = s1 - len1;
+      s_xa[lane] = xa0;
+      s_xa[lane + 32] = xa1;
+      if (lane == 31) s_start[MAX_PLANES] = s1;
+    }
+    __syncthreads();
+    const int total = s_start[MAX_PLANES];
+    const S* f = reinterpret_cast<const S*>(a.f) + bd.cell_off;
+    for (int q = tid; q < total; q += blockDim.x) {
+      // the row holding flat index q: the last row starting at or before q
+      int r = 0;
+#pragma unroll
+      for (int step = 32; step > 0; step >>= 1)
+        if (r + step < MAX_PLANES && s_start[r + step] <= q) r += step;
+      const int xu = s_xa[r] + (q - s_start[r]);
+      const int yu = lo[1] + r;
       const int x = xu < 0 ? xu + n[0] : (xu >= n[0] ? xu - n[0] : xu);
-      float r[3];
-      if (!inside_fp32(R, bd, x, y, z, r)) continue;
+      const int y = yu < 0 ? yu + n[1] : (yu >= n[1] ? yu - n[1] : yu);
+      float rr[3];
+      if (!inside_fp32(R, bd, x, y, z, rr)) continue;
       const Nbr<true> nb = make_nbr<true>(bd, x, y, z);
       const int c = (z * bd.ny + y) * bd.nx + x;
       float Fc[3], mg;
       mea_cell<S, PAR>(f, a.plane, nb, c, a.inv_scale, Fc, mg);
-      const float upx = R.u[0] + (R.w[1] * r[2] - R.w[2] * r[1]);
-      const float upy = R.u[1] + (R.w[2] * r[0] - R.w[0] * r[2]);
-      const float upz = R.u[2] + (R.w[0] * r[1] - R.w[1] * r[0]);
+      const float upx = R.u[0] + (R.w[1] * rr[2] - R.w[2] * rr[1]);
+      const float upy = R.u[1] + (R.w[2] * rr[0] - R.w[0] * rr[2]);
+      const float upz = R.u[2] + (R.w[0] * rr[1] - R.w[1] * rr[0]);
       Fc[0] -= upx * mg;
       Fc[1] -= upy * mg;
       Fc[2] -= upz * mg;
       Fx += Fc[0];
       Fy += Fc[1];
       Fz += Fc[2];
-      Tx += r[1] * Fc[2] - r[2] * Fc[1];
-      Ty += r[2] * Fc[0] - r[0] * Fc[2];
-      Tz += r[0] * Fc[1] - r[1] * Fc[0];
+      Tx += rr[1] * Fc[2] - rr[2] * Fc[1];
+      Ty += rr[2] * Fc[0] - rr[0] * Fc[2];
+      Tz += rr[0] * Fc[1] - rr[1] * Fc[0];
     }
   }
-  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   float v[6] = {Fx, Fy, Fz, Tx, Ty, Tz};
 #pragma unroll
   for (int k = 0; k < 6; ++k)
@@ -252,10 +241,26 @@ __global__ void __launch_bounds__(128, 6) mea_kernel(PartArgs a) {
   if (lane == 0)
     for (int k = 0; k < 6; ++k) wsum[warp][k] = (double)v[k];
   __syncthreads();
-  if (threadIdx.x < 6) {
+  if (tid < 6) {
     double s = 0.0;
-    for (int w = 0; w < nwarp; ++w) s += wsum[w][threadIdx.x];
-    out[threadIdx.x] = s;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += wsum[w][tid];
+    out[tid] = s;
+  }
+  // the last block of a particle adds its planes' partials in plane order
+  // (deterministic) and writes the particle's force and torque
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&a.done[p], 1) == a.p_nchunk[p] - 1);
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (tid < 6) {
+      const int c0 = a.p_chunk0[p], nc = a.p_nchunk[p];
+      double s = 0.0;
+      for (int k = 0; k < nc; ++k) s += __ldcg(a.partial + (long long)(c0 + k) * 6 + tid);
+      pset(a.P, a.cap, (tid < 3 ? PF_F : PF_T - 3) + tid, p, s);
+    }
+    if (tid == 0) a.done[p] = 0;
   }
 }
 
@@ -380,29 +385,22 @@ __global__ void __launch_bounds__(32) update_kernel(PartArgs a) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long t = tid; t < a.ntiles; t += stride) a.bin_count_clear[t] = 0;
+  if (tid == 0 && a.ilist_count) *a.ilist_count = 0;  // the collision appends anew
   if (tid >= a.np) return;
   const int p = (int)tid;
   const int shape = a.shape[p], box = a.box[p];
   const BoxDesc bd = a.boxes[box];
-  // force and torque of the momentum exchange: the kernel's partials in a
-  // fixed order, or the sums the previous collision accumulated; the
-  // accumulator is cleared for the collision of this step
-  double Fh[3] = {0, 0, 0}, Th[3] = {0, 0, 0};
+  // force and torque of the momentum exchange: written into the table by the
+  // momentum-exchange kernel, or accumulated by the previous collision (the
+  // accumulator is cleared for the collision of this step)
+  double Fh[3], Th[3];
   double* acc = a.acc + (long long)p * 6;
-  if (a.use_partials) {
-    const double* part = a.partial + (long long)p * MEA_CHUNKS * 6;
-    for (int k = 0; k < MEA_CHUNKS; ++k)
-      for (int j = 0; j < 3; ++j) {
-        Fh[j] += part[k * 6 + j];
-        Th[j] += part[k * 6 + 3 + j];
-      }
-  } else {
-    for (int j = 0; j < 3; ++j) {
-      Fh[j] = acc[j];
-      Th[j] = acc[3 + j];
-    }
+  for (int j = 0; j < 3; ++j) {
+    Fh[j] = a.from_acc ? acc[j] : pget(a.P, a.cap, PF_F + j, p);
+    Th[j] = a.from_acc ? acc[3 + j] : pget(a.P, a.cap, PF_T + j, p);
   }
-  for (int j = 0; j < 6; ++j) acc[j] = 0.0;
+  if (a.from_acc)
+    for (int j = 0; j < 6; ++j) acc[j] = 0.0;
   integrate(a, bd, p, shape, Fh, Th);
   Rec R;
   build_record(a.P, a.cap, p, shape, box, R);
@@ -454,8 +452,8 @@ __global__ void records_kernel(PartArgs a) {
 }
 
 cudaError_t launch_mea(const PartArgs& a, int precision, int parity, cudaStream_t s) {
-  if (a.np <= 0) return cudaSuccess;
-  const dim3 grid(a.np, MEA_CHUNKS);
+  if (a.np <= 0 || a.nchunks <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)a.nchunks;
   if (precision == 0) {
     if (parity == 0) mea_kernel<float, 0><<<grid, 128, 0, s>>>(a);
     else mea_kernel<float, 1><<<grid, 128, 0, s>>>(a);

@@ -19,6 +19,7 @@ HLBM_OK, HLBM_ERR_ARG, HLBM_ERR_CUDA, HLBM_ERR_UNSTABLE, HLBM_ERR_CAPACITY, HLBM
 HLBM_FP32, HLBM_FP16 = 0, 1
 HLBM_SPHERE, HLBM_ELLIPSOID, HLBM_CUBOID = 0, 1, 2
 HLBM_WALL_X, HLBM_WALL_Y, HLBM_WALL_Z = 1, 2, 4
+HLBM_MEA_KERNEL, HLBM_MEA_MOMENTS = 0, 1
 
 ERRORS = {HLBM_ERR_ARG: "HLBM_ERR_ARG", HLBM_ERR_CUDA: "HLBM_ERR_CUDA",
           HLBM_ERR_UNSTABLE: "HLBM_ERR_UNSTABLE", HLBM_ERR_CAPACITY: "HLBM_ERR_CAPACITY",
@@ -29,6 +30,7 @@ EXPORTS = ["hlbm_default_params", "hlbm_required_bytes", "hlbm_init_lattice", "h
            "hlbm_add_particles", "hlbm_set_particle_state", "hlbm_step", "hlbm_sync",
            "hlbm_particle_state", "hlbm_get_populations", "hlbm_set_populations",
            "hlbm_num_particles", "hlbm_steps_done", "hlbm_set_launch", "hlbm_get_launch",
+           "hlbm_set_mea_mode", "hlbm_get_mea_mode",
            "hlbm_autotune", "hlbm_kernel_times", "hlbm_last_error", "hlbm_destroy"]
 
 
@@ -86,6 +88,8 @@ def load(path=LIB_PATH):
     L.hlbm_steps_done.restype = ctypes.c_longlong
     L.hlbm_set_launch.argtypes = [_h, ctypes.c_int, ctypes.c_int]
     L.hlbm_get_launch.argtypes = [_h, _ip, _ip]
+    L.hlbm_set_mea_mode.argtypes = [_h, ctypes.c_int]
+    L.hlbm_get_mea_mode.argtypes = [_h]
     L.hlbm_autotune.argtypes = [_h, ctypes.c_int, _ip, _ip, _fp]
     L.hlbm_kernel_times.argtypes = [_h, ctypes.c_int, _fp]
     L.hlbm_last_error.argtypes = [_h]
@@ -255,6 +259,13 @@ class Lattice:
         ty, tz = ctypes.c_int(), ctypes.c_int()
         _check(self.h, load().hlbm_get_launch(self.h, ctypes.byref(ty), ctypes.byref(tz)))
         return ty.value, tz.value
+
+    def set_mea_mode(self, mode):
+        m = {"kernel": HLBM_MEA_KERNEL, "moments": HLBM_MEA_MOMENTS}.get(mode, mode)
+        _check(self.h, load().hlbm_set_mea_mode(self.h, int(m)))
+
+    def get_mea_mode(self):
+        return {HLBM_MEA_KERNEL: "kernel", HLBM_MEA_MOMENTS: "moments"}[load().hlbm_get_mea_mode(self.h)]
 
     def autotune(self, nsteps=10):
         ty, tz, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()

@@ -7,8 +7,9 @@ CUDA path and the FP64 oracle can both be fed from it without sharing code.
 Random numbers come from numpy's PCG64 generator (``numpy.random.default_rng``)
 seeded with 2312014172 + workload index.  Particles are placed by random
 sequential insertion: a candidate centre is drawn uniformly and accepted when
-its circumscribed sphere keeps a gap of at least ``eps + 1`` lattice units to
-every accepted particle (minimum image on periodic axes) and to every wall.
+its enclosing capsule (a sphere for spheres, a sphere-swept segment along the
+long axis otherwise) keeps a gap of at least ``eps + 1`` lattice units to every
+accepted particle (minimum image on periodic axes) and to every wall.
 
 The workloads stand in for the hindered-settling study of the paper (Sec. 5.1:
 random non-overlapping spheres in a periodic box, particles initially at rest,
@@ -51,29 +52,53 @@ def random_quaternions(rng, n):
                      s1 * np.cos(2 * np.pi * u2), s2 * np.sin(2 * np.pi * u3)], axis=1)
 
 
-def sequential_insertion(rng, n_box, radii, bc, gap, max_tries=200000):
-    """Random sequential insertion of circumscribed spheres of the given radii.
+def _segment_distance(p, u, hp, q, v, hq):
+    """Distance between the segments p +- hp u and q +- hq v (u, v unit)."""
+    w0 = p - q
+    b = float(u @ v)
+    d = float(u @ w0)
+    e = float(v @ w0)
+    den = 1.0 - b * b
+    if den > 1e-12:
+        s = np.clip((b * e - d) / den, -hp, hp)
+    else:
+        s = 0.0
+    t = np.clip(e + b * s, -hq, hq)
+    s = np.clip(b * t - d, -hp, hp)
+    return float(np.linalg.norm(w0 + s * u - t * v))
 
-    Returns centres (k, 3) for the first k radii that could be placed (k may be
-    below len(radii) when the box is too full).  Uses a uniform bucket grid so
-    that large particle counts stay fast.
+
+def sequential_insertion(rng, n_box, radii, bc, gap, max_tries=200000, axes=None, half_lengths=None):
+    """Random sequential insertion of capsules (sphere-swept segments).
+
+    Particle k occupies the points within radii[k] of the segment centre +-
+    half_lengths[k] * axes[k] (a sphere when the half-length is 0).  A
+    candidate centre is drawn uniformly and accepted when it keeps a gap to
+    every accepted capsule (minimum image on periodic axes) and to the walls.
+    Returns centres (k, 3) for the first k particles that could be placed.
+    Uses a uniform bucket grid so that large counts stay fast.
     """
     n_box = np.asarray(n_box, float)
-    rmax = float(np.max(radii)) if len(radii) else 1.0
+    radii = np.asarray(radii, float)
+    count = len(radii)
+    hl = np.zeros(count) if half_lengths is None else np.asarray(half_lengths, float)
+    ax = np.tile([0.0, 0.0, 1.0], (count, 1)) if axes is None else np.asarray(axes, float)
+    reach = radii + hl  # circumscribed radius of each capsule
+    rmax = float(np.max(reach)) if count else 1.0
     bucket = 2.0 * rmax + gap
     nb = np.maximum(1, np.floor(n_box / bucket).astype(int))
     bsize = n_box / nb
     buckets = {}
     centres = []
-    rad = []
     wall = [(bc >> a) & 1 for a in range(3)]
-    for r in radii:
+    for k in range(count):
+        r = reach[k]
         placed = False
+        lo = np.array([r + gap + 0.5 if wall[a] else 0.0 for a in range(3)])
+        hi = np.array([n_box[a] - 1.0 - r - gap + 0.5 if wall[a] else n_box[a] for a in range(3)])
+        if np.any(hi <= lo):
+            break
         for _ in range(max_tries):
-            lo = np.array([r + gap + 0.5 if wall[a] else 0.0 for a in range(3)])
-            hi = np.array([n_box[a] - 1.0 - r - gap + 0.5 if wall[a] else n_box[a] for a in range(3)])
-            if np.any(hi <= lo):
-                break
             c = lo + rng.random(3) * (hi - lo)
             b = np.floor(c / bsize).astype(int) % nb
             ok = True
@@ -86,8 +111,17 @@ def sequential_insertion(rng, n_box, radii, bc, gap, max_tries=200000):
                             for a in range(3):
                                 if not wall[a]:
                                     d[a] -= n_box[a] * np.round(d[a] / n_box[a])
-                            if np.dot(d, d) < (r + rad[j] + gap) ** 2:
+                            dd = float(np.dot(d, d))
+                            lim = reach[k] + reach[j] + gap
+                            if dd >= lim * lim:
+                                continue
+                            if hl[k] == 0.0 and hl[j] == 0.0:
                                 ok = False
+                            else:
+                                q = c - d  # image of particle j next to the candidate
+                                ok = _segment_distance(c, ax[k], hl[k], q, ax[j], hl[j]) >= \
+                                    radii[k] + radii[j] + gap
+                            if not ok:
                                 break
                         if not ok:
                             break
@@ -98,12 +132,17 @@ def sequential_insertion(rng, n_box, radii, bc, gap, max_tries=200000):
             if ok:
                 buckets.setdefault(tuple(b.tolist()), []).append(len(centres))
                 centres.append(c)
-                rad.append(r)
                 placed = True
                 break
         if not placed:
             break
     return np.array(centres).reshape(-1, 3)
+
+
+def body_axis_z(quat):
+    """World direction of the body z-axis of unit quaternions (w, x, y, z)."""
+    w, x, y, z = quat[:, 0], quat[:, 1], quat[:, 2], quat[:, 3]
+    return np.stack([2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y)], axis=1)
 
 
 def _particles(shape, a, X, rho_p, quat=None):
@@ -164,10 +203,15 @@ def nonspherical(n=(256, 256, 256), count=2000, r_eq=5.0, ar_range=(1.0, 4.0), t
             h = (vol / (8.0 * ar[k])) ** (1.0 / 3.0)        # 8 h^3 AR = volume
             shapes.append(CUBOID)
             axes.append([h, h, ar[k] * h])
-    radii = np.array([_circ_radius(s, a) for s, a in zip(shapes, axes)])
-    X = sequential_insertion(rng, n, radii, 0, eps + 1.0)
+    quat = random_quaternions(rng, count)
+    # enclosing capsules along the body z-axis (the long axis): an ellipsoid
+    # (a, a, c) lies within radius a of the segment +-(c - a); a cuboid
+    # (h, h, H) within radius sqrt(2) h of the segment +-H
+    cap_r = np.array([a[0] if s == ELLIPSOID else math.sqrt(2.0) * a[0] for s, a in zip(shapes, axes)])
+    cap_h = np.array([a[2] - a[0] if s == ELLIPSOID else a[2] for s, a in zip(shapes, axes)])
+    X = sequential_insertion(rng, n, cap_r, 0, eps + 1.0, axes=body_axis_z(quat), half_lengths=cap_h)
     k = len(X)
-    quat = random_quaternions(rng, k)
+    quat = quat[:k]
     P = _particles(shapes[:k], axes[:k], X, rho_ratio, quat)
     return _workload(f"nonspherical_{n[0]}x{n[1]}x{n[2]}_{k}", n, 0, tau, eps, P, steps, precision)
 

@@ -113,9 +113,10 @@ def test_set_get_roundtrip_both_parities(H, O):
 
 
 # ------------------------------------------------------------ with particles
-def _run_pair(H, O, w, steps, chunks=(1,), precision="fp32", check=True):
+def _run_pair(H, O, w, steps, chunks=(1,), precision="fp32", mode="kernel"):
     P = w["particles"]
     lat = H.from_workload(w, precision=precision)
+    lat.set_mea_mode(mode)
     orc = O.from_workload(w)
     X0, U0, W0 = P["X"].copy(), P["U"].copy(), P["omega"].copy()
     done = 0
@@ -135,12 +136,13 @@ def _run_pair(H, O, w, steps, chunks=(1,), precision="fp32", check=True):
     return sg, so, fg, fo, (X0, U0, W0)
 
 
-def test_single_sphere_settling_200_steps(H, O):
+@pytest.mark.parametrize("mode", ["kernel", "moments"])
+def test_single_sphere_settling_200_steps(H, O, mode):
     """The small benchmark configuration in full: 48^3 periodic, one sphere
     r = 6, tau 0.8, density ratio 2.5, g = 1e-5, 200 steps."""
     from paper_2312_14172_gb300 import workloads
     w = workloads.single_sphere()
-    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 200, chunks=(1, 1, 5))
+    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 200, chunks=(1, 1, 5), mode=mode)
     _pops_close(fg, fo)
     _motion_close(sg, so, X0, U0, W0)
     assert np.allclose(sg["F"], so["F"], rtol=1e-4, atol=1e-9)
@@ -167,13 +169,14 @@ def test_sphere_off_centre_rotating(H, O):
     lat.close()
 
 
-def test_hindered_settling_subbox_walls(H, O):
+@pytest.mark.parametrize("mode", ["kernel", "moments"])
+def test_hindered_settling_subbox_walls(H, O, mode):
     """Spheres between walls (the hindered-settling configuration) on a box
     the oracle finishes quickly, ragged in x and y."""
     from paper_2312_14172_gb300 import workloads
     w = workloads.hindered_settling(n=(70, 45, 48), count=14, steps=40)
     assert len(w["particles"]["shape"]) >= 8
-    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 40, chunks=(1,))
+    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 40, chunks=(1,), mode=mode)
     _pops_close(fg, fo)
     _motion_close(sg, so, X0, U0, W0)
 
@@ -186,7 +189,7 @@ def test_nonspherical_subbox(H, O):
     # give them some spin so that the rotation update is exercised
     rng = np.random.default_rng(1)
     w["particles"]["omega"] = rng.uniform(-3e-3, 3e-3, w["particles"]["omega"].shape)
-    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 40, chunks=(1,))
+    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 40, chunks=(1,), mode="moments")
     _pops_close(fg, fo)
     _motion_close(sg, so, X0, U0, W0)
     assert np.allclose(sg["quat"], so["quat"], atol=1e-9)
@@ -277,9 +280,9 @@ def test_launch_shapes_agree(H, O):
 
 
 @pytest.mark.parametrize("kind", ["spheres_walls", "nonspherical"])
-def test_fused_momentum_exchange_matches_kernel(H, O, kind):
-    """The collision accumulates the next step's momentum exchange from its
-    outgoing values; on the same state it equals the momentum-exchange kernel
+def test_moment_momentum_exchange_matches_kernel(H, O, kind):
+    """The momentum exchange from the arrivals and the moments the previous
+    collision recorded equals the bounding-box kernel's on the same state
     (which runs on the first step after any change of state)."""
     from paper_2312_14172_gb300 import workloads
     if kind == "spheres_walls":
@@ -290,6 +293,7 @@ def test_fused_momentum_exchange_matches_kernel(H, O, kind):
     w["particles"]["omega"] = rng.uniform(-4e-3, 4e-3, w["particles"]["omega"].shape)
     w["particles"]["U"] = rng.uniform(-2e-3, 2e-3, w["particles"]["U"].shape)
     lat = H.from_workload(w)
+    lat.set_mea_mode("moments")
     lat.step(7)
     s = lat.particle_state()
     f = lat.populations()
