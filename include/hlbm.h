@@ -13,7 +13,7 @@
  *             cells inside each particle (Eqs. hydrodynamicforce,
  *             hydrodynamictorque);
  *   Sec. 2.2  Newton-Euler motion (Eqs. particlemotiontrans, motionrot);
- *   Sec. 4.2.4 the order of one step (Algorithm 1).
+ *   Sec. 4.2.5 the order of one step (Algorithm 1).
  *
  * Conventions for every call:
  *   - Lattice units, dx = dt = 1, reference fluid density 1.  Cell (i, j, k)

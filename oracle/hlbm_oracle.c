@@ -18,7 +18,7 @@
  *              exact-difference source (Eq. kupershtokh), momentum exchange
  *              (Eq. hlbm:mea), force and torque sums (Eqs. hydrodynamicforce,
  *              hydrodynamictorque)
- *   Sec. 4.2.4 order of one time step (Algorithm 1)
+ *   Sec. 4.2.5 order of one time step (Algorithm 1)
  *   Sec. 5.1   external force on a particle, weight minus buoyancy
  */
 #include "hlbm_oracle.h"

@@ -9,7 +9,7 @@
  * decomposition scheme to improve parallel performance of fully resolved
  * particulate flow simulations", arXiv:2312.14172).
  *
- * What it computes (one time step, Algorithm 1 of Sec. 4.2.4 without its two
+ * What it computes (one time step, Algorithm 1 of Sec. 4.2.5 without its two
  * communication rows):
  *   1. momentum exchange (MEA, Eq. hlbm:mea) summed over the cells whose centre
  *      lies inside each particle (Eqs. hydrodynamicforce, hydrodynamictorque);

@@ -1,7 +1,7 @@
 // hlbm_api.cu -- the C-ABI of include/hlbm.h: handles, device memory layout,
 // particle set-up, CUDA-graph capture of the time step, data exchange.
 //
-// One time step (Algorithm 1 of arXiv:2312.14172, Sec. 4.2.4, without its
+// One time step (Algorithm 1 of arXiv:2312.14172, Sec. 4.2.5, without its
 // communication rows) is three launches on the handle's stream:
 //   1. momentum exchange per particle          (mea_kernel)
 //   2. external force, Newton-Euler, records,

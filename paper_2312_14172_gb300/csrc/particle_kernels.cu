@@ -11,7 +11,7 @@
 //                   (Eqs. particlemotiontrans, motionrot) in FP64, the FP32
 //                   coupling record of the new state, and the per-tile particle
 //                   lists (the single-GPU form of the paper's particle
-//                   assignment, Sec. 4.2.2) that the collision kernel reads.
+//                   assignment, Sec. 4.2.3) that the collision kernel reads.
 //   records_kernel  coupling records only (after particles are added or set).
 #include "hlbm_internal.cuh"
 
