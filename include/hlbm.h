@@ -196,6 +196,47 @@ int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, float* ms
  * and streaming.  Synchronises. */
 int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]);
 
+/* Momentum exchange without device allocation.
+ *
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory -- a particle code running inside another
+ * framework's memory pool or arena, or one whose device memory is all handed
+ * to it by its host application -- and still want the force and torque of
+ * Eqs. hlbm:mea / hydrodynamicforce / hydrodynamictorque on populations they
+ * own.  It computes what the momentum-exchange kernel of hlbm_step computes
+ * (bounding-box form, FP32 cell sums, FP64 partials added in plane order) for
+ * one lattice box, without a handle.
+ *
+ * Every intermediate lives in one file-scope device array of about 3.3 MB
+ * that every GPU loading the library holds until the process exits; the
+ * call allocates nothing (no cudaMalloc, no library allocator).  The first
+ * call on a device looks up that array's device address, so make it before
+ * any stream capture.  All calls on a device share the array: calls whose
+ * GPU work overlaps (other streams, other host threads) race; order them on
+ * one stream.  The array keeps the last call's contents; the call clears
+ * what must start at zero.
+ *
+ *   f            device: 19 planes of `plane` elements, FP32 (f - w) or FP16
+ *                (f - w) * 2^fp16_scale_log2, cell (x, y, z) of plane i at
+ *                i * plane + (z ny + y) nx + x, in the AA layout of `parity`
+ *                (0: slot i of x holds f_i(x); 1: slot ibar of x - c_i)
+ *   nx, ny, nz, bc_flags   the box as in hlbm_box
+ *   n            particles, 0 <= n <= HLBM_NOALLOC_MAX_PARTICLES
+ *   shape, shape_params, X, U, omega, quat   device arrays laid out as in
+ *                hlbm_add_particles (U, omega, quat may be NULL)
+ *   F, T         device outputs [3n]: hydrodynamic force and torque; NaN for
+ *                a particle with invalid data (sizes, orientation, centre) or
+ *                a circumscribed radius above 30 cells
+ *   cuda_stream  the stream all work is queued on; the call does not wait
+ * Returns HLBM_OK, HLBM_ERR_ARG (n out of range, bad lattice arguments, NULL
+ * pointer) or HLBM_ERR_CUDA. */
+#define HLBM_NOALLOC_MAX_PARTICLES 1024
+int hlbm_mea_noalloc(const void* f, long long plane, int nx, int ny, int nz, int bc_flags,
+                     int precision, int fp16_scale_log2, int parity, int n, const int* shape,
+                     const double* shape_params, const double* X, const double* U,
+                     const double* omega, const double* quat, double* F, double* T,
+                     void* cuda_stream);
+
 /* One-line description of the last error on this handle (or of the last
  * failed init when h is NULL). */
 const char* hlbm_last_error(hlbm_handle h);

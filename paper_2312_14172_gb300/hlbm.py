@@ -31,7 +31,9 @@ EXPORTS = ["hlbm_default_params", "hlbm_required_bytes", "hlbm_init_lattice", "h
            "hlbm_particle_state", "hlbm_get_populations", "hlbm_set_populations",
            "hlbm_num_particles", "hlbm_steps_done", "hlbm_set_launch", "hlbm_get_launch",
            "hlbm_set_mea_mode", "hlbm_get_mea_mode",
-           "hlbm_autotune", "hlbm_kernel_times", "hlbm_last_error", "hlbm_destroy"]
+           "hlbm_autotune", "hlbm_kernel_times", "hlbm_last_error", "hlbm_destroy",
+           "hlbm_mea_noalloc"]
+HLBM_NOALLOC_MAX_PARTICLES = 1024
 
 
 class hlbm_box(ctypes.Structure):
@@ -96,6 +98,8 @@ def load(path=LIB_PATH):
     L.hlbm_last_error.restype = ctypes.c_char_p
     L.hlbm_destroy.argtypes = [_h]
     L.hlbm_destroy.restype = None
+    L.hlbm_mea_noalloc.argtypes = [_vp, ctypes.c_longlong] + [ctypes.c_int] * 8 + [_vp] * 9
+    L.hlbm_mea_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -277,6 +281,16 @@ class Lattice:
         ms = (ctypes.c_float * 3)()
         _check(self.h, load().hlbm_kernel_times(self.h, int(nsteps), ms))
         return {"mea": ms[0], "update": ms[1], "collide_stream": ms[2]}
+
+
+def hlbm_mea_noalloc(f, plane, nx, ny, nz, bc_flags, precision, fp16_scale_log2, parity, n, shape,
+                     shape_params, X, U, omega, quat, F, T, stream):
+    """The allocation-free momentum exchange; every array argument is a
+    device address (int) or None, as in include/hlbm.h.  Returns the C code."""
+    vp = lambda v: _vp(v) if v else None
+    return load().hlbm_mea_noalloc(vp(f), ctypes.c_longlong(plane), nx, ny, nz, bc_flags, precision,
+                                   fp16_scale_log2, parity, n, vp(shape), vp(shape_params), vp(X), vp(U),
+                                   vp(omega), vp(quat), vp(F), vp(T), vp(stream))
 
 
 def from_workload(w, precision=None, stream=None, **kw):
