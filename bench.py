@@ -40,7 +40,13 @@ sys.path.insert(0, ROOT)
 BYTES_PER_CELL = {"fp32": 2 * 19 * 4, "fp16": 2 * 19 * 2}
 
 
+WORKLOADS = ("hindered_settling", "single_sphere", "nonspherical", "dense_batch", "fluid_256",
+             "dense_batch_256")
+
+
 def make_workload(name):
+    """The benchmark workloads; the two 256^3 ones are smaller stand-ins used
+    for profiling (no particles; the 50 000-sphere density on 256^3)."""
     from paper_2312_14172_gb300 import workloads
     if name == "hindered_settling":
         return workloads.hindered_settling()
@@ -50,6 +56,10 @@ def make_workload(name):
         return workloads.nonspherical()
     if name == "dense_batch":
         return workloads.dense_batch()
+    if name == "fluid_256":
+        return workloads.dense_batch(n=(256, 256, 256), count=0)
+    if name == "dense_batch_256":
+        return workloads.dense_batch(n=(256, 256, 256), count=50000 * 256 ** 3 // (512 * 512 * 1024))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -365,7 +375,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="hindered_settling")
+    ap.add_argument("--workload", default="hindered_settling", choices=WORKLOADS)
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp16"])
     ap.add_argument("--no-fp16", dest="fp16", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -56,6 +56,7 @@ bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& 
     if (B.nx < 1 || B.ny < 1 || B.nz < 1 || (B.bc_flags & ~7)) { err = "bad box dimensions or flags"; return false; }
     const long long n = (long long)B.nx * B.ny * B.nz;
     if (n >= (1LL << 31)) { err = "a box may hold at most 2^31 - 1 cells"; return false; }
+    if (cells + n >= (1LL << 31)) { err = "all boxes together may hold at most 2^31 - 1 cells"; return false; }
     BoxDesc& d = bd[b];
     d.nx = B.nx; d.ny = B.ny; d.nz = B.nz; d.bc = B.bc_flags;
     d.ntx = (B.nx + TILE_X - 1) / TILE_X;
@@ -171,6 +172,8 @@ static LbmArgs lbm_args(const hlbm_ctx* h, int parity) {
   LbmArgs a{};
   a.f = h->f;
   a.plane = h->L.plane;
+  const size_t es = h->prm.precision == HLBM_FP32 ? 4 : 2;
+  for (int i = 0; i < Q; ++i) a.pl[i] = (char*)h->f + (size_t)i * h->L.plane * es;
   a.boxes = h->d_boxes;
   a.nboxes = (int)h->boxes.size();
   a.sub_y = h->sub_y;

@@ -98,6 +98,21 @@ struct Nbr {
 };
 
 template <bool WALLS>
+__device__ __forceinline__ Nbr<WALLS> make_nbr(const BoxDesc& bd, int x, int y, int z);
+
+// neighbour offsets in global cell indices (the box's first cell added):
+// at() returns the global index, or a negative value beyond a wall
+template <bool WALLS>
+__device__ __forceinline__ Nbr<WALLS> make_nbr_global(const BoxDesc& bd, int x, int y, int z) {
+  Nbr<WALLS> n = make_nbr<WALLS>(bd, x, y, z);
+  const int off = (int)bd.cell_off;
+  n.z += off;
+  n.zm = n.zm < 0 ? n.zm : n.zm + off;
+  n.zp = n.zp < 0 ? n.zp : n.zp + off;
+  return n;
+}
+
+template <bool WALLS>
 __device__ __forceinline__ Nbr<WALLS> make_nbr(const BoxDesc& bd, int x, int y, int z) {
   Nbr<WALLS> n;
   const int nx = bd.nx, ny = bd.ny, nz = bd.nz, nxy = nx * ny;
@@ -118,6 +133,7 @@ __device__ __forceinline__ Nbr<WALLS> make_nbr(const BoxDesc& bd, int x, int y, 
 struct LbmArgs {
   void* f;                  // population planes (float* or __half*)
   long long plane;          // elements per plane
+  void* pl[Q];              // base of each plane (f + i * plane elements)
   const BoxDesc* boxes;
   int nboxes;
   int sub_y, sub_z;         // brick per block: 32 x sub_y x sub_z cells

@@ -19,19 +19,26 @@ namespace hlbm {
 
 constexpr int MAX_CAND = 64;  // particle records staged per block
 #ifndef HLBM_CS_MINBLOCKS
-#define HLBM_CS_MINBLOCKS 3
+#define HLBM_CS_MINBLOCKS 4
 #endif
 
 template <typename S> struct Pop;
 template <> struct Pop<float> {
+  static constexpr bool SCALED = false;
   static __device__ __forceinline__ float ld(const float* p, float) { return *p; }
   static __device__ __forceinline__ void st(float* p, float v, float) { *p = v; }
+  static __device__ __forceinline__ float ld_raw(const float* p) { return *p; }
+  static __device__ __forceinline__ void st_raw(float* p, float v) { *p = v; }
 };
 template <> struct Pop<__half> {
   static __device__ __forceinline__ float ld(const __half* p, float inv_s) {
     return __half2float(*p) * inv_s;
   }
   static __device__ __forceinline__ void st(__half* p, float v, float s) { *p = __float2half_rn(v * s); }
+  // the stored (scaled) value itself: the collision works in scaled units
+  static constexpr bool SCALED = true;
+  static __device__ __forceinline__ float ld_raw(const __half* p) { return __half2float(*p); }
+  static __device__ __forceinline__ void st_raw(__half* p, float v) { *p = __float2half_rn(v); }
 };
 // the value a store of v leaves in memory, read back as a deviation
 template <typename S>
@@ -95,9 +102,32 @@ __device__ __forceinline__ void load_arrivals(const S* f, long long P, const Nbr
   }
 }
 
+// plane i of the populations, from the kernel parameters
+template <typename S>
+__device__ __forceinline__ S* plane_of(const LbmArgs& a, int i) { return reinterpret_cast<S*>(a.pl[i]); }
+
+// the same accessor on global cell indices (g = this cell, nb from make_nbr_global)
+template <typename S, int PAR, bool WALLS>
+__device__ __forceinline__ void load_arrivals_raw(const LbmArgs& a, const Nbr<WALLS>& nb, unsigned g,
+                                                  float d[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (PAR == 0 || i == 0) {
+      d[i] = Pop<S>::ld_raw(plane_of<S>(a, i) + g);
+    } else {
+      const int src = nb.at(-cx(i), -cy(i), -cz(i));
+      d[i] = (src >= 0) ? Pop<S>::ld_raw(plane_of<S>(a, opp(i)) + (unsigned)src)
+                        : Pop<S>::ld_raw(plane_of<S>(a, i) + g);
+    }
+  }
+}
+
 template <typename S, int PAR, bool WALLS, bool COUPLE>
 __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(LbmArgs a) {
   __shared__ Rec srec[COUPLE ? MAX_CAND : 1];
+  // per row of the brick (local y + sub_y * local z): the candidates whose
+  // influence sphere meets the row
+  __shared__ unsigned long long s_rowmask[COUPLE ? TILE_Y * TILE_Z : 1];
   const long long brick = blockIdx.x;
   const long long tile = brick / a.nsub;
   const int sub = (int)(brick - tile * a.nsub);
@@ -122,6 +152,22 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
       reinterpret_cast<int*>(&srec[j])[e] = reinterpret_cast<const int*>(&a.rec[ids[j]])[e];
     }
     __syncthreads();
+    const float Ly = (float)bd.ny, Lz = (float)bd.nz;
+    for (int r = tid; r < a.sub_y * a.sub_z; r += nth) {
+      const int yy = ty * TILE_Y + sy * a.sub_y + r % a.sub_y;
+      const int zz = tz * TILE_Z + sz * a.sub_z + r / a.sub_y;
+      unsigned long long m = 0;
+      for (int k = 0; k < cnt; ++k) {
+        const Rec& R = srec[k];
+        float r0y = (float)yy - R.xh[1], r0z = (float)zz - R.xh[2];
+        if (!(bd.bc & 2)) { if (r0y > 0.5f * Ly) r0y -= Ly; else if (r0y < -0.5f * Ly) r0y += Ly; }
+        if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
+        const float ry = __fsub_rn(r0y, R.xl[1]), rz = __fsub_rn(r0z, R.xl[2]);
+        if (ry * ry + rz * rz < R.rinf2) m |= 1ull << k;
+      }
+      s_rowmask[r] = m;
+    }
+    __syncthreads();
   }
 
   const int x = tx * TILE_X + threadIdx.x;
@@ -129,16 +175,17 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
   if (x >= bd.nx || y >= bd.ny) return;
   const int z0 = tz * TILE_Z + sz * a.sub_z;
   const int z1 = min(z0 + a.sub_z, bd.nz);
-  S* __restrict__ f = reinterpret_cast<S*>(a.f) + bd.cell_off;
-  const long long P = a.plane;
   const float Lx = (float)bd.nx, Ly = (float)bd.ny, Lz = (float)bd.nz;
+  // storage scale: the collision runs on the stored (scaled) deviations
+  const float sc = Pop<S>::SCALED ? a.scale : 1.0f, isc = Pop<S>::SCALED ? a.inv_scale : 1.0f;
 
   for (int z = z0; z < z1; ++z) {
     const int c = (z * bd.ny + y) * bd.nx + x;
+    const unsigned g = (unsigned)(bd.cell_off + c);  // global cell index
     Nbr<WALLS> nb;
-    if (PAR == 1) nb = make_nbr<WALLS>(bd, x, y, z);
-    float d[Q];
-    load_arrivals<S, PAR, WALLS>(f, P, nb, c, a.inv_scale, d);
+    if (PAR == 1) nb = make_nbr_global<WALLS>(bd, x, y, z);
+    float d[Q];  // stored deviations (times the storage scale)
+    load_arrivals_raw<S, PAR, WALLS>(a, nb, g, d);
     float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -146,6 +193,12 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
       if (cx(i)) jx += (float)cx(i) * d[i];
       if (cy(i)) jy += (float)cy(i) * d[i];
       if (cz(i)) jz += (float)cz(i) * d[i];
+    }
+    if (Pop<S>::SCALED) {
+      drho *= isc;
+      jx *= isc;
+      jy *= isc;
+      jz *= isc;
     }
     const float rho = 1.0f + drho;
     if (!(rho > 0.0f && rho < 1e30f)) atomicOr(a.status, ST_UNSTABLE);
@@ -156,16 +209,17 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
     if (COUPLE) {
       float bestB = 0.0f, upx = 0.0f, upy = 0.0f, upz = 0.0f;
       int bestp = 0x7fffffff;
-      for (int k = 0; k < cnt; ++k) {
+      // only the candidates that meet this row (uniform over the warp)
+      unsigned long long rm = s_rowmask[threadIdx.y + a.sub_y * (z - z0)];
+      while (rm) {
+        const int k = __ffsll((long long)rm) - 1;
+        rm &= rm - 1;
         const Rec& R = srec[k];
-        // y and z offsets are the same for the whole warp (one row of x):
-        // most candidates miss the row and are rejected without divergence
         float r0y = (float)y - R.xh[1], r0z = (float)z - R.xh[2];
         if (!(bd.bc & 2)) { if (r0y > 0.5f * Ly) r0y -= Ly; else if (r0y < -0.5f * Ly) r0y += Ly; }
         if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
         const float ry = __fsub_rn(r0y, R.xl[1]), rz = __fsub_rn(r0z, R.xl[2]);
         const float d2 = ry * ry + rz * rz;
-        if (d2 >= R.rinf2) continue;
         float r0x = (float)x - R.xh[0];
         if (!(bd.bc & 1)) { if (r0x > 0.5f * Lx) r0x -= Lx; else if (r0x < -0.5f * Lx) r0x += Lx; }
         const float rx = __fsub_rn(r0x, R.xl[0]);
@@ -200,14 +254,15 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
     const float vx = ux + dux, vy = uy + duy, vz = uz + duz;
     const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
     const float vsq = 1.5f * (vx * vx + vy * vy + vz * vz);
-    float o[Q];
+    float o[Q];  // post-collision deviations (times the storage scale)
     {
-      constexpr float w0 = 1.0f / 3.0f;
+      const float w0 = sc * (1.0f / 3.0f);
       const float eu = w0 * drho - w0 * rho * usq, ev = w0 * drho - w0 * rho * vsq;
       o[0] = om1 * d[0] + (ev - om1 * eu);
     }
-    const float wr1 = rho * (1.0f / 18.0f), wd1 = drho * (1.0f / 18.0f);
-    const float wr2 = rho * (1.0f / 36.0f), wd2 = drho * (1.0f / 36.0f);
+    const float rs = rho * sc, ds = drho * sc;
+    const float wr1 = rs * (1.0f / 18.0f), wd1 = ds * (1.0f / 18.0f);
+    const float wr2 = rs * (1.0f / 36.0f), wd2 = ds * (1.0f / 36.0f);
 #define HLBM_PAIR(I, WR, WD, CU, CV)                                          \
     {                                                                         \
       const float cu_ = (CU), cv_ = (CV);                                     \
@@ -231,12 +286,12 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
     // store the post-collision deviations, streamed (AA pattern)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      if (PAR == 0) {
-        Pop<S>::st(f + opp(i) * P + c, o[i], a.scale);
+      if (PAR == 0 || i == 0) {
+        Pop<S>::st_raw(plane_of<S>(a, opp(i)) + g, o[i]);
       } else {
-        const int dst = (i == 0) ? c : nb.at(cx(i), cy(i), cz(i));
-        if (dst >= 0) Pop<S>::st(f + i * P + dst, o[i], a.scale);
-        else Pop<S>::st(f + opp(i) * P + c, o[i], a.scale);
+        const int dst = nb.at(cx(i), cy(i), cz(i));
+        if (dst >= 0) Pop<S>::st_raw(plane_of<S>(a, i) + (unsigned)dst, o[i]);
+        else Pop<S>::st_raw(plane_of<S>(a, opp(i)) + g, o[i]);
       }
     }
     // cells inside a particle record the mass and momentum they send out, as
@@ -250,7 +305,7 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
         if (nent) {
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
-            const float g = stored_value<S>(o[i], a.scale, a.inv_scale);
+            const float g = stored_value<S>(o[i], 1.0f, isc);
             mom.x += g;
             if (cx(i)) mom.y += (float)cx(i) * g;
             if (cy(i)) mom.z += (float)cy(i) * g;
@@ -271,7 +326,7 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
         if (lane == leader) base = atomicAdd(a.ilist_count, total);
         base = __shfl_sync(act, base, leader);
         const long long k0 = (long long)base + incl - nent;
-        const long long gcell = bd.cell_off + c;
+        const long long gcell = g;
         for (int e = 0; e < nent; ++e) {
           const long long k = k0 + e;
           if (k < a.ilist_cap) {
