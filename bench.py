@@ -230,6 +230,8 @@ def run_gpu(args, ws, rank, local):
         tune = lat.autotune(nsteps=5)
     if args.mea_mode:
         lat.set_mea_mode(args.mea_mode)
+    if args.launch:
+        lat.set_launch(*[int(v) for v in args.launch.split(",")])
     mea_mode = lat.get_mea_mode()
     lat.step(args.warmup)
     lat.sync()
@@ -298,6 +300,8 @@ def run_gpu(args, ws, rank, local):
             lat16.autotune(nsteps=5)
         if args.mea_mode:
             lat16.set_mea_mode(args.mea_mode)
+        if args.launch:
+            lat16.set_launch(*[int(v) for v in args.launch.split(",")])
         lat16.step(args.warmup)
         lat16.sync()
         flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -381,6 +385,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--mea-mode", default=None, choices=[None, "kernel", "moments"])
+    ap.add_argument("--launch", default=None, help="collision block shape TILE_Y,TILE_Z (skips tuning)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
