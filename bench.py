@@ -362,6 +362,7 @@ def run_gpu(args, ws, rank, local):
                    "l2": f"inputs larger than L2 ({BYTES_PER_CELL[prec] // 2 * cells / 1e6:.0f} MB "
                          "of populations); no flush between FP32 steps",
                    "launch": {"tile_y": lat_launch[0], "tile_z": lat_launch[1],
+                              "cells_per_thread": lat_launch[2],
                               "momentum_exchange": mea_mode,
                               "autotuned": bool(args.autotune)}},
         "roofline": roofline,
@@ -385,7 +386,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--mea-mode", default=None, choices=[None, "kernel", "moments"])
-    ap.add_argument("--launch", default=None, help="collision block shape TILE_Y,TILE_Z (skips tuning)")
+    ap.add_argument("--launch", default=None, help="collision launch shape TILE_Y,TILE_Z[,CELLS_X] (skips tuning)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

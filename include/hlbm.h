@@ -162,9 +162,13 @@ int hlbm_num_particles(hlbm_handle h);
 long long hlbm_steps_done(hlbm_handle h);
 
 /* Launch shape of the collision kernel: each thread block covers a brick of
- * 32 x tile_y x tile_z cells, tile_y and tile_z in {1, 2, 4, 8}. */
-int hlbm_set_launch(hlbm_handle h, int tile_y, int tile_z);
-int hlbm_get_launch(hlbm_handle h, int* tile_y, int* tile_z);
+ * 32 x tile_y x tile_z cells, tile_y and tile_z in {1, 2, 4, 8}, with
+ * cells_x = 1 or 2 x-adjacent cells per thread (32 x tile_y or 16 x tile_y
+ * threads).  cells_x = 2 needs an even nx in every box (HLBM_ERR_ARG
+ * otherwise) and is the default where allowed.  Both compute the same step;
+ * their results differ by FP32 rounding order only. */
+int hlbm_set_launch(hlbm_handle h, int tile_y, int tile_z, int cells_x);
+int hlbm_get_launch(hlbm_handle h, int* tile_y, int* tile_z, int* cells_x);
 
 /* How the momentum exchange (Eq. hlbm:mea) of a step is computed:
  *   HLBM_MEA_KERNEL   from the populations alone, by a kernel that walks the
@@ -184,11 +188,12 @@ int hlbm_get_launch(hlbm_handle h, int* tile_y, int* tile_z);
 int hlbm_set_mea_mode(hlbm_handle h, int mode);
 int hlbm_get_mea_mode(hlbm_handle h);
 
-/* Times every momentum-exchange mode and launch shape on nsteps steps of the
- * current state (the state advances by the steps taken) and keeps the
- * fastest; writes the chosen shape and its time per step in ms (any pointer
- * may be NULL). */
-int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, float* ms_per_step);
+/* Times every momentum-exchange mode and launch shape (tile_y, tile_z,
+ * cells_x; cells_x = 2 only with tile_y >= 2) on nsteps steps of the current
+ * state (the state advances by the steps taken) and keeps the fastest;
+ * writes the chosen shape and its time per step in ms (any pointer may be
+ * NULL). */
+int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, int* cells_x, float* ms_per_step);
 
 /* Runs nsteps steps with each kernel launched on its own, bracketed by CUDA
  * events on the handle's stream, and writes the mean time per launch in ms:

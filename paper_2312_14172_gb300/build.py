@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhlbm.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["hlbm_api.cu", "lbm_kernels.cu", "particle_kernels.cu", "noalloc.cu"]
+SOURCES = ["hlbm_api.cu", "lbm_kernels.cu", "lbm_pair_kernels.cu", "particle_kernels.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I", INCLUDE, "-I", CSRC]

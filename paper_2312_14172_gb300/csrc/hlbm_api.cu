@@ -145,6 +145,8 @@ struct hlbm_ctx {
   int np = 0;
   long long steps = 0;
   int sub_y = 4, sub_z = 2;
+  int cells_x = 1;       // cells per thread along x (2 needs an even nx in every box)
+  bool pair_ok = false;  // every box has an even nx
   // [0][parity]: step with the momentum-exchange kernel (after any change of
   // state); [1][parity]: step that takes the sums the previous collision made
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -178,6 +180,7 @@ static LbmArgs lbm_args(const hlbm_ctx* h, int parity) {
   a.nboxes = (int)h->boxes.size();
   a.sub_y = h->sub_y;
   a.sub_z = h->sub_z;
+  a.cells_x = h->cells_x;
   a.nsub = (TILE_Y / h->sub_y) * (TILE_Z / h->sub_z);
   a.nbricks = h->L.ntiles * a.nsub;
   a.omega = (float)(1.0 / h->prm.tau);
@@ -196,6 +199,7 @@ static LbmArgs lbm_args(const hlbm_ctx* h, int parity) {
   a.ilist_idx = rec ? h->ilist_idx : nullptr;
   a.ilist_mom = rec ? h->ilist_mom : nullptr;
   a.ilist_cap = h->L.ilist_cap;
+  a.np = h->np;
   a.acc = h->acc;
   a.status = h->status;
   return a;
@@ -297,6 +301,8 @@ static int read_status(hlbm_ctx* h) {
   CK(cudaStreamSynchronize(h->stream));
   if (st & ST_CAPACITY)
     return fail(h, HLBM_ERR_CAPACITY, "a 32x8x8 tile was touched by more particles than bin_capacity");
+  if (st & ST_INTERNAL)
+    return fail(h, HLBM_ERR_STATE, "the list of cells inside particles held an invalid entry");
   if (st & ST_LEFT_DOMAIN)
     return fail(h, HLBM_ERR_UNSTABLE, "a particle centre left the fluid domain through a wall");
   return fail(h, HLBM_ERR_UNSTABLE, "non-finite or non-positive density, or non-finite particle state");
@@ -335,7 +341,12 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
   h->prm = *prm;
   if (h->prm.bin_capacity == 0) h->prm.bin_capacity = DEFAULT_BIN_CAP;
   h->stream = (cudaStream_t)cuda_stream;
-  for (int b = 0; b < nboxes; ++b) h->walls |= boxes[b].bc_flags != 0;
+  h->pair_ok = true;
+  for (int b = 0; b < nboxes; ++b) {
+    h->walls |= boxes[b].bc_flags != 0;
+    h->pair_ok = h->pair_ok && boxes[b].nx % 2 == 0;
+  }
+  h->cells_x = h->pair_ok ? 2 : 1;
   cudaError_t e;
   if (device_buf) {
     if (((uintptr_t)device_buf % ALIGN) || device_buf_bytes < h->L.total) {
@@ -708,13 +719,16 @@ int hlbm_set_populations(hlbm_handle h, int box, const double* host_f) {
   return HLBM_OK;
 }
 
-int hlbm_set_launch(hlbm_handle h, int tile_y, int tile_z) {
+int hlbm_set_launch(hlbm_handle h, int tile_y, int tile_z, int cells_x) {
   if (!h) return HLBM_ERR_ARG;
   auto ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8; };
   if (!ok(tile_y) || !ok(tile_z)) return fail(h, HLBM_ERR_ARG, "tile_y and tile_z must be 1, 2, 4 or 8");
-  if (tile_y != h->sub_y || tile_z != h->sub_z) {
+  if (cells_x != 1 && cells_x != 2) return fail(h, HLBM_ERR_ARG, "cells_x must be 1 or 2");
+  if (cells_x == 2 && !h->pair_ok) return fail(h, HLBM_ERR_ARG, "cells_x = 2 needs an even nx in every box");
+  if (tile_y != h->sub_y || tile_z != h->sub_z || cells_x != h->cells_x) {
     h->sub_y = tile_y;
     h->sub_z = tile_z;
+    h->cells_x = cells_x;
     drop_graphs(h);
   }
   return HLBM_OK;
@@ -735,28 +749,31 @@ int hlbm_set_mea_mode(hlbm_handle h, int mode) {
 
 int hlbm_get_mea_mode(hlbm_handle h) { return h ? h->mea_mode : HLBM_ERR_ARG; }
 
-int hlbm_get_launch(hlbm_handle h, int* tile_y, int* tile_z) {
+int hlbm_get_launch(hlbm_handle h, int* tile_y, int* tile_z, int* cells_x) {
   if (!h) return HLBM_ERR_ARG;
   if (tile_y) *tile_y = h->sub_y;
   if (tile_z) *tile_z = h->sub_z;
+  if (cells_x) *cells_x = h->cells_x;
   return HLBM_OK;
 }
 
-int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, float* ms_per_step) {
+int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, int* cells_x, float* ms_per_step) {
   if (!h) return HLBM_ERR_ARG;
   if (nsteps < 1) return fail(h, HLBM_ERR_ARG, "nsteps < 1");
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int by = h->sub_y, bz = h->sub_z, bm = h->mea_mode;
+  int by = h->sub_y, bz = h->sub_z, bx = h->cells_x, bm = h->mea_mode;
   const int vals[4] = {1, 2, 4, 8};
   int rc = HLBM_OK;
   const int nmodes = h->np > 0 ? 2 : 1;
-  for (int im = 0; im < nmodes * 16 && rc == HLBM_OK; ++im) {
-      const int mode = im / 16, iy = (im / 4) % 4, iz = im % 4;
+  const int nkinds = h->pair_ok ? 2 : 1;
+  for (int im = 0; im < nkinds * nmodes * 16 && rc == HLBM_OK; ++im) {
+      const int kind = im / (nmodes * 16), mode = (im / 16) % nmodes, iy = (im / 4) % 4, iz = im % 4;
+      if (kind == 1 && vals[iy] == 1) continue;  // 16-thread blocks leave half of each warp idle
       rc = hlbm_set_mea_mode(h, mode);
-      if (rc == HLBM_OK) rc = hlbm_set_launch(h, vals[iy], vals[iz]);
+      if (rc == HLBM_OK) rc = hlbm_set_launch(h, vals[iy], vals[iz], kind + 1);
       if (rc == HLBM_OK) rc = hlbm_step(h, 2);  // warm-up and graph build
       if (rc != HLBM_OK) break;
       cudaEventRecord(e0, h->stream);
@@ -766,15 +783,16 @@ int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, float* ms
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= nsteps;
-      if (ms < best) { best = ms; by = vals[iy]; bz = vals[iz]; bm = mode; }
+      if (ms < best) { best = ms; by = vals[iy]; bz = vals[iz]; bx = kind + 1; bm = mode; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != HLBM_OK) return rc;
   rc = hlbm_set_mea_mode(h, bm);
-  if (rc == HLBM_OK) rc = hlbm_set_launch(h, by, bz);
+  if (rc == HLBM_OK) rc = hlbm_set_launch(h, by, bz, bx);
   if (tile_y) *tile_y = by;
   if (tile_z) *tile_z = bz;
+  if (cells_x) *cells_x = bx;
   if (ms_per_step) *ms_per_step = best;
   if (rc != HLBM_OK) return rc;
   return read_status(h);

@@ -80,7 +80,7 @@ struct __align__(16) Rec {
 };
 static_assert(sizeof(Rec) == 128, "record size");
 
-enum { ST_UNSTABLE = 1, ST_CAPACITY = 2, ST_LEFT_DOMAIN = 4 };
+enum { ST_UNSTABLE = 1, ST_CAPACITY = 2, ST_LEFT_DOMAIN = 4, ST_INTERNAL = 8 };
 
 // neighbour index helper: per-axis neighbour offsets; -1 marks a node beyond
 // a wall (only possible when WALLS)
@@ -137,6 +137,7 @@ struct LbmArgs {
   const BoxDesc* boxes;
   int nboxes;
   int sub_y, sub_z;         // brick per block: 32 x sub_y x sub_z cells
+  int cells_x;              // cells per thread along x: 1, or 2 (every box has an even nx)
   int nsub;                 // bricks per bin tile = (8/sub_y)*(8/sub_z)
   long long nbricks;        // total bricks (grid size)
   float omega;              // 1 / tau
@@ -155,6 +156,7 @@ struct LbmArgs {
   int2* ilist_idx;
   float4* ilist_mom;
   long long ilist_cap;
+  int np;                   // particles (list entries name 0 .. np-1)
   double* acc;              // [cap][6] momentum exchange of a particle (FP64 sums)
   int* status;
 };
@@ -250,6 +252,9 @@ __device__ __forceinline__ bool inside_fp32(const Rec& R, const BoxDesc& bd, int
 // launchers (stream-ordered, no synchronisation)
 cudaError_t launch_collide(const LbmArgs& a, int precision, int parity, bool walls, bool couple,
                            cudaStream_t s);
+// the collision with two x-adjacent cells per thread (a.cells_x == 2)
+cudaError_t launch_collide_pair(const LbmArgs& a, int precision, int parity, bool walls, bool couple,
+                                cudaStream_t s);
 // momentum exchange from the arrivals and the moments recorded in the list of
 // interior cells (a.rec must describe the particle state of this step)
 cudaError_t launch_mea_moments(const LbmArgs& a, int precision, int parity, bool walls, int nsm,

@@ -1,0 +1,266 @@
+// lbm_common.cuh -- device pieces shared by the collision kernels (one cell
+// per thread in lbm_kernels.cu, two x-adjacent cells per thread in
+// lbm_pair_kernels.cu): storage access, the indicator of Eq. B, the signed
+// distances of the three shapes, the per-tile particle candidates and the
+// per-cell coupling of Eq. hlbm:du (Sec. 3.2), and the list of cells inside
+// particles that the collision appends for the next momentum exchange.
+#pragma once
+#include "hlbm_internal.cuh"
+
+namespace hlbm {
+
+constexpr int MAX_CAND = 64;  // particle records staged per block
+
+template <typename S> struct Pop;
+template <> struct Pop<float> {
+  static constexpr bool SCALED = false;
+  static __device__ __forceinline__ float ld(const float* p, float) { return *p; }
+  static __device__ __forceinline__ void st(float* p, float v, float) { *p = v; }
+  static __device__ __forceinline__ float ld_raw(const float* p) { return *p; }
+  static __device__ __forceinline__ void st_raw(float* p, float v) { *p = v; }
+  // two adjacent cells (8-byte aligned)
+  static __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+  static __device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+};
+template <> struct Pop<__half> {
+  static __device__ __forceinline__ float ld(const __half* p, float inv_s) {
+    return __half2float(*p) * inv_s;
+  }
+  static __device__ __forceinline__ void st(__half* p, float v, float s) { *p = __float2half_rn(v * s); }
+  // the stored (scaled) value itself: the collision works in scaled units
+  static constexpr bool SCALED = true;
+  static __device__ __forceinline__ float ld_raw(const __half* p) { return __half2float(*p); }
+  static __device__ __forceinline__ void st_raw(__half* p, float v) { *p = __float2half_rn(v); }
+  // two adjacent cells (4-byte aligned)
+  static __device__ __forceinline__ float2 ld2(const __half* p) {
+    return __half22float2(*reinterpret_cast<const __half2*>(p));
+  }
+  static __device__ __forceinline__ void st2(__half* p, float2 v) {
+    *reinterpret_cast<__half2*>(p) = __float22half2_rn(v);
+  }
+};
+// the value a store of v leaves in memory, read back as a deviation
+template <typename S>
+__device__ __forceinline__ float stored_value(float v, float s, float inv_s) {
+  if (sizeof(S) == 4) return v;
+  return __half2float(__float2half_rn(v * s)) * inv_s;
+}
+
+// plane i of the populations, from the kernel parameters
+template <typename S>
+__device__ __forceinline__ S* plane_of(const LbmArgs& a, int i) { return reinterpret_cast<S*>(a.pl[i]); }
+
+// indicator of Eq. B written as (1 - sin(pi d / eps)) / 2 on the ramp, which
+// equals cos^2((pi/2)(d/eps + 1/2))
+__device__ __forceinline__ float indicator(float d, float eps, float inv_eps) {
+  if (d <= -0.5f * eps) return 1.0f;
+  if (d >= 0.5f * eps) return 0.0f;
+  return 0.5f - 0.5f * sinpif(d * inv_eps);
+}
+
+// signed distance of a particle at offset r (world frame), FP32
+__device__ __forceinline__ float sdf(const Rec& R, float rx, float ry, float rz, float r2) {
+  if (R.shape == 0) return sqrtf(r2) - R.a[0];
+  // body frame b = M^T r
+  const float b0 = R.M[0] * rx + R.M[3] * ry + R.M[6] * rz;
+  const float b1 = R.M[1] * rx + R.M[4] * ry + R.M[7] * rz;
+  const float b2 = R.M[2] * rx + R.M[5] * ry + R.M[8] * rz;
+  if (R.shape == 1) {
+    const float e0 = b0 * R.ia[0], e1 = b1 * R.ia[1], e2 = b2 * R.ia[2];
+    const float k2 = e0 * e0 + e1 * e1 + e2 * e2;
+    const float g0 = e0 * R.ia[0], g1 = e1 * R.ia[1], g2v = e2 * R.ia[2];
+    const float g2 = g0 * g0 + g1 * g1 + g2v * g2v;
+    if (g2 == 0.0f) return -fminf(R.a[0], fminf(R.a[1], R.a[2]));
+    const float k = sqrtf(k2);
+    return (k - 1.0f) * k * rsqrtf(g2);
+  }
+  const float q0 = fabsf(b0) - R.a[0], q1 = fabsf(b1) - R.a[1], q2 = fabsf(b2) - R.a[2];
+  const float o0 = fmaxf(q0, 0.0f), o1 = fmaxf(q1, 0.0f), o2 = fmaxf(q2, 0.0f);
+  return sqrtf(o0 * o0 + o1 * o1 + o2 * o2) + fminf(fmaxf(q0, fmaxf(q1, q2)), 0.0f);
+}
+
+__device__ __forceinline__ int find_box(const BoxDesc* boxes, int nboxes, long long tile) {
+  int lo = 0, hi = nboxes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (boxes[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// the brick of this block: 32 x sub_y x sub_z cells of one bin tile
+struct Brick {
+  BoxDesc bd;
+  long long tile;
+  int x0, y0, z0;  // first cell of the brick in its box
+};
+
+__device__ __forceinline__ Brick brick_of(const LbmArgs& a) {
+  Brick k;
+  const long long brick = blockIdx.x;
+  k.tile = brick / a.nsub;
+  const int sub = (int)(brick - k.tile * a.nsub);
+  const int b = a.nboxes > 1 ? find_box(a.boxes, a.nboxes, k.tile) : 0;
+  k.bd = a.boxes[b];
+  const long long lt = k.tile - k.bd.tile_off;
+  const int tx = (int)(lt % k.bd.ntx);
+  const long long t2 = lt / k.bd.ntx;
+  const int ty = (int)(t2 % k.bd.nty);
+  const int tz = (int)(t2 / k.bd.nty);
+  const int nsy = TILE_Y / a.sub_y;
+  k.x0 = tx * TILE_X;
+  k.y0 = ty * TILE_Y + (sub % nsy) * a.sub_y;
+  k.z0 = tz * TILE_Z + (sub / nsy) * a.sub_z;
+  return k;
+}
+
+// Stage the particle candidates of the brick's tile in shared memory and
+// mark, for each row (local y + sub_y * local z) of the brick, the
+// candidates whose influence sphere meets the row.  Called by every thread
+// of the block.
+__device__ __forceinline__ void load_candidates(const LbmArgs& a, const Brick& k, Rec* srec,
+                                                unsigned long long* s_rowmask) {
+  const int cnt = min(min(a.bin_count[k.tile], a.bin_cap), MAX_CAND);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nth = blockDim.x * blockDim.y;
+  const int* ids = a.bin_ids + k.tile * (long long)a.bin_cap;
+  for (int e = tid; e < cnt * 32; e += nth) {
+    const int j = e >> 5, w = e & 31;
+    reinterpret_cast<int*>(&srec[j])[w] = reinterpret_cast<const int*>(&a.rec[ids[j]])[w];
+  }
+  __syncthreads();
+  const BoxDesc& bd = k.bd;
+  const float Ly = (float)bd.ny, Lz = (float)bd.nz;
+  for (int r = tid; r < a.sub_y * a.sub_z; r += nth) {
+    const int yy = k.y0 + r % a.sub_y;
+    const int zz = k.z0 + r / a.sub_y;
+    unsigned long long m = 0;
+    for (int j = 0; j < cnt; ++j) {
+      const Rec& R = srec[j];
+      float r0y = (float)yy - R.xh[1], r0z = (float)zz - R.xh[2];
+      if (!(bd.bc & 2)) { if (r0y > 0.5f * Ly) r0y -= Ly; else if (r0y < -0.5f * Ly) r0y += Ly; }
+      if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
+      const float ry = __fsub_rn(r0y, R.xl[1]), rz = __fsub_rn(r0z, R.xl[2]);
+      if (ry * ry + rz * rz < R.rinf2) m |= 1ull << j;
+    }
+    s_rowmask[r] = m;
+  }
+  __syncthreads();
+}
+
+// Coupling of N consecutive cells x, x+1, .. of one row with the candidates
+// in rm: the largest indicator B (ties to the lowest particle id) with its
+// particle velocity u_p(x) = U + w x (x - X) (Eq. hlbm:du), and up to two
+// particles whose inside holds the cell's centre.
+template <int N>
+struct RowCoupling {
+  float B[N], upx[N], upy[N], upz[N];
+  int bestp[N], ip0[N], ip1[N];
+};
+
+template <int N>
+__device__ __forceinline__ void couple_row(const Rec* srec, unsigned long long rm, const BoxDesc& bd,
+                                           int x, int y, int z, float eps, float inv_eps, int* status,
+                                           RowCoupling<N>& cc) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    cc.B[j] = 0.0f;
+    cc.upx[j] = cc.upy[j] = cc.upz[j] = 0.0f;
+    cc.bestp[j] = 0x7fffffff;
+    cc.ip0[j] = cc.ip1[j] = -1;
+  }
+  const float Lx = (float)bd.nx, Ly = (float)bd.ny, Lz = (float)bd.nz;
+  while (rm) {
+    const int k = __ffsll((long long)rm) - 1;
+    rm &= rm - 1;
+    const Rec& R = srec[k];
+    float r0y = (float)y - R.xh[1], r0z = (float)z - R.xh[2];
+    if (!(bd.bc & 2)) { if (r0y > 0.5f * Ly) r0y -= Ly; else if (r0y < -0.5f * Ly) r0y += Ly; }
+    if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
+    const float ry = __fsub_rn(r0y, R.xl[1]), rz = __fsub_rn(r0z, R.xl[2]);
+    const float d2 = ry * ry + rz * rz;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float r0x = (float)(x + j) - R.xh[0];
+      if (!(bd.bc & 1)) { if (r0x > 0.5f * Lx) r0x -= Lx; else if (r0x < -0.5f * Lx) r0x += Lx; }
+      const float rx = __fsub_rn(r0x, R.xl[0]);
+      const float r2 = rx * rx + d2;
+      if (r2 < R.rinf2) {
+        const float rr[3] = {rx, ry, rz};
+        if (inside_from_offset(R, rr)) {
+          if (cc.ip0[j] < 0) cc.ip0[j] = R.pid;
+          else if (cc.ip1[j] < 0) cc.ip1[j] = R.pid;
+          else atomicOr(status, ST_CAPACITY);  // three overlapping particles
+        }
+        const float B = indicator(sdf(R, rx, ry, rz, r2), eps, inv_eps);
+        if (B > cc.B[j] || (B == cc.B[j] && B > 0.0f && R.pid < cc.bestp[j])) {
+          cc.B[j] = B;
+          cc.bestp[j] = R.pid;
+          cc.upx[j] = R.u[0] + (R.w[1] * rz - R.w[2] * ry);
+          cc.upy[j] = R.u[1] + (R.w[2] * rx - R.w[0] * rz);
+          cc.upz[j] = R.u[2] + (R.w[0] * ry - R.w[1] * rx);
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned lane_id() {
+  unsigned l;
+  asm("mov.u32 %0, %%laneid;" : "=r"(l));
+  return l;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Warp-aggregated append of the cells g, g+1, .. g+N-1 that lie inside a
+// particle to the list of interior cells: one entry (cell, particle) per
+// particle holding the cell, with the mass and momentum of the cell's
+// post-collision deviations as stored.  Called by all active lanes, which
+// may be any subset of the warp: a lane's offset among the warp's entries
+// is taken bit by bit of its entry count (one ballot per bit), so no lane
+// depends on a value passed through another.
+template <int N>
+__device__ __forceinline__ void append_interior(const LbmArgs& a, unsigned g, const RowCoupling<N>& cc,
+                                                const float4 (&mom)[N]) {
+  int nent = 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) nent += (cc.ip0[j] >= 0) + (cc.ip1[j] >= 0);
+  const unsigned act = __activemask();
+  if (!__ballot_sync(act, nent > 0)) return;
+  const unsigned lt = lanemask_lt();
+  int before = 0, total = 0;
+#pragma unroll
+  for (int b = 0; (1 << b) <= 2 * N; ++b) {
+    const unsigned m = __ballot_sync(act, (nent >> b) & 1);
+    before += __popc(m & lt) << b;
+    total += __popc(m) << b;
+  }
+  const int leader = __ffs(act) - 1;
+  int base = 0;
+  if ((int)lane_id() == leader) base = atomicAdd(a.ilist_count, total);
+  base = __shfl_sync(act, base, leader);
+  long long k = (long long)base + before;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int p = e == 0 ? cc.ip0[j] : cc.ip1[j];
+      if (p >= 0) {
+        if (k < a.ilist_cap) {
+          a.ilist_idx[k] = make_int2((int)(g + j), p);
+          a.ilist_mom[k] = mom[j];
+        } else {
+          atomicOr(a.status, ST_CAPACITY);
+        }
+        ++k;
+      }
+    }
+  }
+}
+
+}  // namespace hlbm

@@ -13,77 +13,13 @@
 // deviations d_i = f_i - w_i (float, or half scaled by 2^s); all arithmetic
 // is FP32 on deviations, which keeps the small non-equilibrium parts exact to
 // FP32 rounding instead of to the rounding of f ~ w_i.
-#include "hlbm_internal.cuh"
+#include "lbm_common.cuh"
 
 namespace hlbm {
 
-constexpr int MAX_CAND = 64;  // particle records staged per block
 #ifndef HLBM_CS_MINBLOCKS
 #define HLBM_CS_MINBLOCKS 4
 #endif
-
-template <typename S> struct Pop;
-template <> struct Pop<float> {
-  static constexpr bool SCALED = false;
-  static __device__ __forceinline__ float ld(const float* p, float) { return *p; }
-  static __device__ __forceinline__ void st(float* p, float v, float) { *p = v; }
-  static __device__ __forceinline__ float ld_raw(const float* p) { return *p; }
-  static __device__ __forceinline__ void st_raw(float* p, float v) { *p = v; }
-};
-template <> struct Pop<__half> {
-  static __device__ __forceinline__ float ld(const __half* p, float inv_s) {
-    return __half2float(*p) * inv_s;
-  }
-  static __device__ __forceinline__ void st(__half* p, float v, float s) { *p = __float2half_rn(v * s); }
-  // the stored (scaled) value itself: the collision works in scaled units
-  static constexpr bool SCALED = true;
-  static __device__ __forceinline__ float ld_raw(const __half* p) { return __half2float(*p); }
-  static __device__ __forceinline__ void st_raw(__half* p, float v) { *p = __float2half_rn(v); }
-};
-// the value a store of v leaves in memory, read back as a deviation
-template <typename S>
-__device__ __forceinline__ float stored_value(float v, float s, float inv_s) {
-  if (sizeof(S) == 4) return v;
-  return __half2float(__float2half_rn(v * s)) * inv_s;
-}
-
-// indicator of Eq. B written as (1 - sin(pi d / eps)) / 2 on the ramp, which
-// equals cos^2((pi/2)(d/eps + 1/2))
-__device__ __forceinline__ float indicator(float d, float eps, float inv_eps) {
-  if (d <= -0.5f * eps) return 1.0f;
-  if (d >= 0.5f * eps) return 0.0f;
-  return 0.5f - 0.5f * sinpif(d * inv_eps);
-}
-
-// signed distance of a particle at offset r (world frame), FP32
-__device__ __forceinline__ float sdf(const Rec& R, float rx, float ry, float rz, float r2) {
-  if (R.shape == 0) return sqrtf(r2) - R.a[0];
-  // body frame b = M^T r
-  const float b0 = R.M[0] * rx + R.M[3] * ry + R.M[6] * rz;
-  const float b1 = R.M[1] * rx + R.M[4] * ry + R.M[7] * rz;
-  const float b2 = R.M[2] * rx + R.M[5] * ry + R.M[8] * rz;
-  if (R.shape == 1) {
-    const float e0 = b0 * R.ia[0], e1 = b1 * R.ia[1], e2 = b2 * R.ia[2];
-    const float k2 = e0 * e0 + e1 * e1 + e2 * e2;
-    const float g0 = e0 * R.ia[0], g1 = e1 * R.ia[1], g2v = e2 * R.ia[2];
-    const float g2 = g0 * g0 + g1 * g1 + g2v * g2v;
-    if (g2 == 0.0f) return -fminf(R.a[0], fminf(R.a[1], R.a[2]));
-    const float k = sqrtf(k2);
-    return (k - 1.0f) * k * rsqrtf(g2);
-  }
-  const float q0 = fabsf(b0) - R.a[0], q1 = fabsf(b1) - R.a[1], q2 = fabsf(b2) - R.a[2];
-  const float o0 = fmaxf(q0, 0.0f), o1 = fmaxf(q1, 0.0f), o2 = fmaxf(q2, 0.0f);
-  return sqrtf(o0 * o0 + o1 * o1 + o2 * o2) + fminf(fmaxf(q0, fmaxf(q1, q2)), 0.0f);
-}
-
-__device__ __forceinline__ int find_box(const BoxDesc* boxes, int nboxes, long long tile) {
-  int lo = 0, hi = nboxes - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (boxes[mid].tile_off <= tile) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 // load of the post-streaming deviations f_i(x) - w_i of cell c (AA accessor):
 // even parity: slot i of x; odd parity: slot ibar of x - c_i, or slot i of x
@@ -97,14 +33,11 @@ __device__ __forceinline__ void load_arrivals(const S* f, long long P, const Nbr
       d[i] = Pop<S>::ld(f + i * P + c, inv_s);
     } else {
       const int src = (i == 0) ? c : nb.at(-cx(i), -cy(i), -cz(i));
-      d[i] = (src >= 0) ? Pop<S>::ld(f + opp(i) * P + src, inv_s) : Pop<S>::ld(f + i * P + c, inv_s);
+      const S* p = (!WALLS || src >= 0) ? f + opp(i) * P + src : f + i * P + c;
+      d[i] = Pop<S>::ld(p, inv_s);
     }
   }
 }
-
-// plane i of the populations, from the kernel parameters
-template <typename S>
-__device__ __forceinline__ S* plane_of(const LbmArgs& a, int i) { return reinterpret_cast<S*>(a.pl[i]); }
 
 // the same accessor on global cell indices (g = this cell, nb from make_nbr_global)
 template <typename S, int PAR, bool WALLS>
@@ -116,8 +49,8 @@ __device__ __forceinline__ void load_arrivals_raw(const LbmArgs& a, const Nbr<WA
       d[i] = Pop<S>::ld_raw(plane_of<S>(a, i) + g);
     } else {
       const int src = nb.at(-cx(i), -cy(i), -cz(i));
-      d[i] = (src >= 0) ? Pop<S>::ld_raw(plane_of<S>(a, opp(i)) + (unsigned)src)
-                        : Pop<S>::ld_raw(plane_of<S>(a, i) + g);
+      const S* p = (!WALLS || src >= 0) ? plane_of<S>(a, opp(i)) + (unsigned)src : plane_of<S>(a, i) + g;
+      d[i] = Pop<S>::ld_raw(p);
     }
   }
 }
@@ -128,54 +61,15 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
   // per row of the brick (local y + sub_y * local z): the candidates whose
   // influence sphere meets the row
   __shared__ unsigned long long s_rowmask[COUPLE ? TILE_Y * TILE_Z : 1];
-  const long long brick = blockIdx.x;
-  const long long tile = brick / a.nsub;
-  const int sub = (int)(brick - tile * a.nsub);
-  const int b = a.nboxes > 1 ? find_box(a.boxes, a.nboxes, tile) : 0;
-  const BoxDesc bd = a.boxes[b];
-  const long long lt = tile - bd.tile_off;
-  const int tx = (int)(lt % bd.ntx);
-  const long long t2 = lt / bd.ntx;
-  const int ty = (int)(t2 % bd.nty);
-  const int tz = (int)(t2 / bd.nty);
-  const int nsy = TILE_Y / a.sub_y;
-  const int sy = sub % nsy, sz = sub / nsy;
+  const Brick k = brick_of(a);
+  const BoxDesc& bd = k.bd;
+  if (COUPLE) load_candidates(a, k, srec, s_rowmask);
 
-  int cnt = 0;
-  if (COUPLE) {
-    cnt = min(min(a.bin_count[tile], a.bin_cap), MAX_CAND);
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nth = blockDim.x * blockDim.y;
-    const int* ids = a.bin_ids + tile * (long long)a.bin_cap;
-    for (int k = tid; k < cnt * 32; k += nth) {
-      const int j = k >> 5, e = k & 31;
-      reinterpret_cast<int*>(&srec[j])[e] = reinterpret_cast<const int*>(&a.rec[ids[j]])[e];
-    }
-    __syncthreads();
-    const float Ly = (float)bd.ny, Lz = (float)bd.nz;
-    for (int r = tid; r < a.sub_y * a.sub_z; r += nth) {
-      const int yy = ty * TILE_Y + sy * a.sub_y + r % a.sub_y;
-      const int zz = tz * TILE_Z + sz * a.sub_z + r / a.sub_y;
-      unsigned long long m = 0;
-      for (int k = 0; k < cnt; ++k) {
-        const Rec& R = srec[k];
-        float r0y = (float)yy - R.xh[1], r0z = (float)zz - R.xh[2];
-        if (!(bd.bc & 2)) { if (r0y > 0.5f * Ly) r0y -= Ly; else if (r0y < -0.5f * Ly) r0y += Ly; }
-        if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
-        const float ry = __fsub_rn(r0y, R.xl[1]), rz = __fsub_rn(r0z, R.xl[2]);
-        if (ry * ry + rz * rz < R.rinf2) m |= 1ull << k;
-      }
-      s_rowmask[r] = m;
-    }
-    __syncthreads();
-  }
-
-  const int x = tx * TILE_X + threadIdx.x;
-  const int y = ty * TILE_Y + sy * a.sub_y + threadIdx.y;
+  const int x = k.x0 + threadIdx.x;
+  const int y = k.y0 + threadIdx.y;
   if (x >= bd.nx || y >= bd.ny) return;
-  const int z0 = tz * TILE_Z + sz * a.sub_z;
+  const int z0 = k.z0;
   const int z1 = min(z0 + a.sub_z, bd.nz);
-  const float Lx = (float)bd.nx, Ly = (float)bd.ny, Lz = (float)bd.nz;
   // storage scale: the collision runs on the stored (scaled) deviations
   const float sc = Pop<S>::SCALED ? a.scale : 1.0f, isc = Pop<S>::SCALED ? a.inv_scale : 1.0f;
 
@@ -205,46 +99,15 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
     const float irho = 1.0f / rho;
     const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
     float dux = a.ff[0] * irho, duy = a.ff[1] * irho, duz = a.ff[2] * irho;
-    int ip0 = -1, ip1 = -1;  // particles whose inside holds the cell's centre
+    RowCoupling<1> cc;  // indicator, particle velocity, particles holding the cell
     if (COUPLE) {
-      float bestB = 0.0f, upx = 0.0f, upy = 0.0f, upz = 0.0f;
-      int bestp = 0x7fffffff;
       // only the candidates that meet this row (uniform over the warp)
-      unsigned long long rm = s_rowmask[threadIdx.y + a.sub_y * (z - z0)];
-      while (rm) {
-        const int k = __ffsll((long long)rm) - 1;
-        rm &= rm - 1;
-        const Rec& R = srec[k];
-        float r0y = (float)y - R.xh[1], r0z = (float)z - R.xh[2];
-        if (!(bd.bc & 2)) { if (r0y > 0.5f * Ly) r0y -= Ly; else if (r0y < -0.5f * Ly) r0y += Ly; }
-        if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
-        const float ry = __fsub_rn(r0y, R.xl[1]), rz = __fsub_rn(r0z, R.xl[2]);
-        const float d2 = ry * ry + rz * rz;
-        float r0x = (float)x - R.xh[0];
-        if (!(bd.bc & 1)) { if (r0x > 0.5f * Lx) r0x -= Lx; else if (r0x < -0.5f * Lx) r0x += Lx; }
-        const float rx = __fsub_rn(r0x, R.xl[0]);
-        const float r2 = rx * rx + d2;
-        if (r2 < R.rinf2) {
-          const float rr[3] = {rx, ry, rz};
-          if (inside_from_offset(R, rr)) {
-            if (ip0 < 0) ip0 = R.pid;
-            else if (ip1 < 0) ip1 = R.pid;
-            else atomicOr(a.status, ST_CAPACITY);  // three overlapping particles
-          }
-          const float B = indicator(sdf(R, rx, ry, rz, r2), a.eps, a.inv_eps);
-          if (B > bestB || (B == bestB && B > 0.0f && R.pid < bestp)) {
-            bestB = B;
-            bestp = R.pid;
-            upx = R.u[0] + (R.w[1] * rz - R.w[2] * ry);
-            upy = R.u[1] + (R.w[2] * rx - R.w[0] * rz);
-            upz = R.u[2] + (R.w[0] * ry - R.w[1] * rx);
-          }
-        }
-      }
-      if (bestB > 0.0f) {
-        dux += bestB * (upx - ux);
-        duy += bestB * (upy - uy);
-        duz += bestB * (upz - uz);
+      couple_row<1>(srec, s_rowmask[threadIdx.y + a.sub_y * (z - z0)], bd, x, y, z, a.eps, a.inv_eps,
+                    a.status, cc);
+      if (cc.B[0] > 0.0f) {
+        dux += cc.B[0] * (cc.upx[0] - ux);
+        duy += cc.B[0] * (cc.upy[0] - uy);
+        duz += cc.B[0] * (cc.upz[0] - uz);
       }
     }
     // f*_i - w_i = (1 - 1/tau) (d_i - E_i(u)) + E_i(u + Delta u), E = f^eq - w.
@@ -290,53 +153,25 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
         Pop<S>::st_raw(plane_of<S>(a, opp(i)) + g, o[i]);
       } else {
         const int dst = nb.at(cx(i), cy(i), cz(i));
-        if (dst >= 0) Pop<S>::st_raw(plane_of<S>(a, i) + (unsigned)dst, o[i]);
-        else Pop<S>::st_raw(plane_of<S>(a, opp(i)) + g, o[i]);
+        S* p = (!WALLS || dst >= 0) ? plane_of<S>(a, i) + (unsigned)dst : plane_of<S>(a, opp(i)) + g;
+        Pop<S>::st_raw(p, o[i]);
       }
     }
     // cells inside a particle record the mass and momentum they send out, as
     // stored, for the next step's momentum exchange (one entry per particle)
     if (COUPLE && a.ilist_idx) {
-      const int nent = (ip0 >= 0) + (ip1 >= 0);
-      const unsigned act = __activemask();
-      const unsigned want = __ballot_sync(act, nent > 0);
-      if (want) {
-        float4 mom = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (nent) {
+      float4 mom[1] = {make_float4(0.f, 0.f, 0.f, 0.f)};
+      if (cc.ip0[0] >= 0) {
 #pragma unroll
-          for (int i = 0; i < Q; ++i) {
-            const float g = stored_value<S>(o[i], 1.0f, isc);
-            mom.x += g;
-            if (cx(i)) mom.y += (float)cx(i) * g;
-            if (cy(i)) mom.z += (float)cy(i) * g;
-            if (cz(i)) mom.w += (float)cz(i) * g;
-          }
-        }
-        // warp-aggregated append
-        int incl = nent;
-        const int lane = threadIdx.x;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const int t = __shfl_up_sync(act, incl, off);
-          if (lane >= off && ((act >> (lane - off)) & 1u)) incl += t;
-        }
-        const int leader = 31 - __clz(act);
-        const int total = __shfl_sync(act, incl, leader);
-        int base = 0;
-        if (lane == leader) base = atomicAdd(a.ilist_count, total);
-        base = __shfl_sync(act, base, leader);
-        const long long k0 = (long long)base + incl - nent;
-        const long long gcell = g;
-        for (int e = 0; e < nent; ++e) {
-          const long long k = k0 + e;
-          if (k < a.ilist_cap) {
-            a.ilist_idx[k] = make_int2((int)gcell, e == 0 ? ip0 : ip1);
-            a.ilist_mom[k] = mom;
-          } else {
-            atomicOr(a.status, ST_CAPACITY);
-          }
+        for (int i = 0; i < Q; ++i) {
+          const float v = stored_value<S>(o[i], 1.0f, isc);
+          mom[0].x += v;
+          if (cx(i)) mom[0].y += (float)cx(i) * v;
+          if (cy(i)) mom[0].z += (float)cy(i) * v;
+          if (cz(i)) mom[0].w += (float)cz(i) * v;
         }
       }
+      append_interior<1>(a, g, cc, mom);
     }
   }
 }
@@ -362,17 +197,22 @@ __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
   const S* fbase = reinterpret_cast<const S*>(a.f);
   for (long long k0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); k0 < n; k0 += stride) {
     const long long k = k0 + lane;
-    const bool valid = k < n;
+    bool valid = k < n;
     int pid = -1;
     float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
+    const int2 e = valid ? a.ilist_idx[k] : make_int2(0, -1);
+    // an entry names a particle and a cell of that particle's box; anything
+    // else was never written by the collision and is skipped with a flag
+    if (valid && (e.y < 0 || e.y >= a.np)) valid = false;
+    const BoxDesc bd = a.boxes[valid ? a.rec[e.y].box : 0];
+    const long long cl = (long long)e.x - bd.cell_off;
+    if (valid && (cl < 0 || cl >= (long long)bd.nx * bd.ny * bd.nz)) valid = false;
+    if (k < n && !valid) atomicOr(a.status, ST_INTERNAL);
     if (valid) {
-      const int2 e = a.ilist_idx[k];
       const float4 sd = a.ilist_mom[k];
       pid = e.y;
       const Rec& R = a.rec[pid];
-      const int box = R.box;
-      const BoxDesc bd = a.boxes[box];
-      const int c = (int)((long long)e.x - bd.cell_off);
+      const int c = (int)cl;
       const int x = c % bd.nx, t = c / bd.nx, y = t % bd.ny, z = t / bd.ny;
       float r[3];
       r[0] = offset_fp32(x, bd.nx, bd.bc & 1, R.xh[0], R.xl[0]);
@@ -453,6 +293,7 @@ static cudaError_t launch_cs_prec(const LbmArgs& a, int parity, bool walls, bool
 cudaError_t launch_collide(const LbmArgs& a, int precision, int parity, bool walls, bool couple,
                            cudaStream_t s) {
   if (a.nbricks <= 0) return cudaSuccess;
+  if (a.cells_x == 2) return launch_collide_pair(a, precision, parity, walls, couple, s);
   return precision == 0 ? launch_cs_prec<float>(a, parity, walls, couple, s)
                         : launch_cs_prec<__half>(a, parity, walls, couple, s);
 }

@@ -1,0 +1,293 @@
+// lbm_pair_kernels.cu -- the fused collide-and-stream of lbm_kernels.cu
+// (Eqs. collide, bgk, maxbolt, kupershtokh, stream; coupling of Eqs. B and
+// hlbm:du) with two x-adjacent cells (x0, x0 + 1), x0 even, per thread.
+//
+// The two cells share every y/z offset, so a thread issues one 8-byte
+// (float) or 4-byte (half) access for both cells wherever their two slots
+// are adjacent in memory: all 19 loads and stores of an even step, and the 9
+// directions with c_x = 0 of an odd step.  The 10 directions with c_x != 0
+// of an odd step reach x0 - 1 .. x0 + 2 and take one access per cell.  All
+// FP32 arithmetic of the collision runs on float2 with the packed FP32x2
+// instructions of sm_100 and later (__ffma2_rn, __fadd2_rn, __fmul2_rn),
+// one instruction for both cells.  Requires an even nx in every box; a
+// block is 16 x sub_y threads over the same 32 x sub_y x sub_z brick as the
+// one-cell kernel.
+#include "lbm_common.cuh"
+
+namespace hlbm {
+
+#ifndef HLBM_CP_MINBLOCKS_F32
+#define HLBM_CP_MINBLOCKS_F32 4
+#endif
+#ifndef HLBM_CP_MINBLOCKS_F16
+#define HLBM_CP_MINBLOCKS_F16 4
+#endif
+
+namespace {
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b, rounded once: b * (-1) is exact
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// The two cells' values of one slot as held in registers between load and
+// store: float2 for float storage; for half storage the packed __half2
+// itself (one register), widened to float2 where the arithmetic reads it.
+template <typename S> struct Two;
+template <> struct Two<float> {
+  using raw = float2;
+  static __device__ __forceinline__ raw ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
+  static __device__ __forceinline__ raw ld(const float* pa, const float* pb) { return make_float2(*pa, *pb); }
+  static __device__ __forceinline__ float2 val(raw v) { return v; }
+  static __device__ __forceinline__ raw pack(float2 v) { return v; }
+  static __device__ __forceinline__ void st(float* p, raw v) { *reinterpret_cast<float2*>(p) = v; }
+  static __device__ __forceinline__ void st(float* pa, float* pb, raw v) { *pa = v.x; *pb = v.y; }
+};
+template <> struct Two<__half> {
+  using raw = __half2;
+  static __device__ __forceinline__ raw ld(const __half* p) { return *reinterpret_cast<const __half2*>(p); }
+  static __device__ __forceinline__ raw ld(const __half* pa, const __half* pb) { return __halves2half2(*pa, *pb); }
+  static __device__ __forceinline__ float2 val(raw v) { return __half22float2(v); }
+  static __device__ __forceinline__ raw pack(float2 v) { return __float22half2_rn(v); }
+  static __device__ __forceinline__ void st(__half* p, raw v) { *reinterpret_cast<__half2*>(p) = v; }
+  static __device__ __forceinline__ void st(__half* pa, __half* pb, raw v) {
+    *pa = __low2half(v);
+    *pb = __high2half(v);
+  }
+};
+
+}  // namespace
+
+// registers: the float kernel holds 38 FP32 arrivals, the half kernel 19
+// packed pairs
+template <typename S>
+struct PairBlocks { static constexpr int value = sizeof(S) == 4 ? HLBM_CP_MINBLOCKS_F32 : HLBM_CP_MINBLOCKS_F16; };
+
+template <typename S, int PAR, bool WALLS, bool COUPLE>
+__global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel(LbmArgs a) {
+  using T = Two<S>;
+  __shared__ Rec srec[COUPLE ? MAX_CAND : 1];
+  __shared__ unsigned long long s_rowmask[COUPLE ? TILE_Y * TILE_Z : 1];
+  const Brick k = brick_of(a);
+  const BoxDesc& bd = k.bd;
+  if (COUPLE) load_candidates(a, k, srec, s_rowmask);
+
+  const int x0 = k.x0 + 2 * threadIdx.x;
+  const int y = k.y0 + threadIdx.y;
+  if (x0 >= bd.nx || y >= bd.ny) return;
+  const int z0 = k.z0;
+  const int z1 = min(z0 + a.sub_z, bd.nz);
+  const int nx = bd.nx, ny = bd.ny, nz = bd.nz, nxy = nx * ny;
+  const int off = (int)bd.cell_off;
+  const bool wy = WALLS && (bd.bc & 2), wz = WALLS && (bd.bc & 4);
+  // x0 - 1 and x0 + 2 as offsets from x0 (periodic wrap), and whether they
+  // lie beyond an x wall
+  const int xm = x0 > 0 ? -1 : nx - 1;
+  const int xp = x0 + 2 < nx ? 2 : 2 - nx;
+  const bool wl = WALLS && (bd.bc & 1) && x0 == 0;
+  const bool wr = WALLS && (bd.bc & 1) && x0 + 2 == nx;
+  // offsets of the rows y - 1, y, y + 1 (negative beyond a wall)
+  int yo[3];
+  yo[1] = y * nx;
+  yo[0] = y > 0 ? (y - 1) * nx : (wy ? -1 : (ny - 1) * nx);
+  yo[2] = y < ny - 1 ? (y + 1) * nx : (wy ? -1 : 0);
+  const float sc = Pop<S>::SCALED ? a.scale : 1.0f, isc = Pop<S>::SCALED ? a.inv_scale : 1.0f;
+
+  // one z slice at a time: an unrolled loop would hold two slices' arrivals
+#pragma unroll 1
+  for (int z = z0; z < z1; ++z) {
+    const int g = off + z * nxy + yo[1] + x0;  // global index of cell x0
+    // global index of cell x0 of the row shifted by (dy - 1, dz - 1), or
+    // negative beyond a y or z wall
+    int r[3][3];
+    if (PAR == 1) {
+      int zo[3];
+      zo[1] = z * nxy;
+      zo[0] = z > 0 ? (z - 1) * nxy : (wz ? -1 : (nz - 1) * nxy);
+      zo[2] = z < nz - 1 ? (z + 1) * nxy : (wz ? -1 : 0);
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz)
+          r[dy][dz] = (WALLS && (yo[dy] < 0 || zo[dz] < 0)) ? -1 : off + zo[dz] + yo[dy] + x0;
+    }
+    // arrivals (stored units), both cells
+    typename T::raw d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (PAR == 0 || i == 0) {
+        d[i] = T::ld(plane_of<S>(a, i) + g);
+      } else {
+        // slot ibar of x - c_i, or slot i of x when x - c_i lies beyond a wall
+        const int rs = r[1 - cy(i)][1 - cz(i)];
+        const bool wall = WALLS && rs < 0;
+        const S* own = plane_of<S>(a, i) + g;
+        const S* src = plane_of<S>(a, opp(i)) + (wall ? g : rs);
+        if (cx(i) == 0) {
+          d[i] = T::ld(wall ? own : src);
+        } else if (cx(i) > 0) {  // sources x0 - 1, x0
+          const S* pa = (wall || wl) ? own : src + xm;
+          const S* pb = wall ? own + 1 : src;
+          d[i] = T::ld(pa, pb);
+        } else {  // sources x0 + 1, x0 + 2
+          const S* pa = wall ? own : src + 1;
+          const S* pb = (wall || wr) ? own + 1 : src + xp;
+          d[i] = T::ld(pa, pb);
+        }
+      }
+    }
+    // moments, opposite directions taken together: s = d_i + d_ibar, m = d_i - d_ibar
+    float2 drho = T::val(d[0]), m[Q];  // m[i]: d_i - d_(i+1), i odd
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+      const float2 di = T::val(d[i]), dj = T::val(d[i + 1]);
+      drho = add2(drho, add2(di, dj));
+      m[i] = sub2(di, dj);
+    }
+    const float2 m1 = m[1], m3 = m[3], m5 = m[5], m7 = m[7], m9 = m[9], m11 = m[11];
+    const float2 m13 = m[13], m15 = m[15], m17 = m[17];
+    float2 jx = add2(add2(add2(m1, m7), add2(m9, m11)), m13);
+    float2 jy = add2(add2(sub2(add2(m3, m7), m9), m15), m17);
+    float2 jz = sub2(add2(sub2(add2(m5, m11), m13), m15), m17);
+    if (Pop<S>::SCALED) {
+      drho = mul2(drho, f2(isc));
+      jx = mul2(jx, f2(isc));
+      jy = mul2(jy, f2(isc));
+      jz = mul2(jz, f2(isc));
+    }
+    const float2 rho = add2(f2(1.0f), drho);
+    if (!(rho.x > 0.0f && rho.x < 1e30f && rho.y > 0.0f && rho.y < 1e30f)) atomicOr(a.status, ST_UNSTABLE);
+    const float2 irho = make_float2(__fdividef(1.0f, rho.x), __fdividef(1.0f, rho.y));
+    const float2 ux = mul2(jx, irho), uy = mul2(jy, irho), uz = mul2(jz, irho);
+    float2 dux = mul2(f2(a.ff[0]), irho), duy = mul2(f2(a.ff[1]), irho), duz = mul2(f2(a.ff[2]), irho);
+    RowCoupling<2> cc;
+    if (COUPLE) {
+      couple_row<2>(srec, s_rowmask[threadIdx.y + a.sub_y * (z - z0)], bd, x0, y, z, a.eps, a.inv_eps,
+                    a.status, cc);
+      if (cc.B[0] > 0.0f) {
+        dux.x += cc.B[0] * (cc.upx[0] - ux.x);
+        duy.x += cc.B[0] * (cc.upy[0] - uy.x);
+        duz.x += cc.B[0] * (cc.upz[0] - uz.x);
+      }
+      if (cc.B[1] > 0.0f) {
+        dux.y += cc.B[1] * (cc.upx[1] - ux.y);
+        duy.y += cc.B[1] * (cc.upy[1] - uy.y);
+        duz.y += cc.B[1] * (cc.upz[1] - uz.y);
+      }
+    }
+    // f*_i - w_i = (1 - 1/tau) (d_i - E_i(u)) + E_i(u + Delta u), E = f^eq - w;
+    // E_i = w drho + w rho (4.5 (c.u)^2 - 1.5 u.u) +- 3 w rho (c.u)
+    const float2 vx = add2(ux, dux), vy = add2(uy, duy), vz = add2(uz, duz);
+    const float2 nusq = mul2(fma2(uz, uz, fma2(uy, uy, mul2(ux, ux))), f2(-1.5f));
+    const float2 nvsq = mul2(fma2(vz, vz, fma2(vy, vy, mul2(vx, vx))), f2(-1.5f));
+    const float om1s = 1.0f - a.omega;
+    const float2 om1 = f2(om1s), nom1 = f2(-om1s);
+    const float2 rs = mul2(rho, f2(sc)), ds = mul2(drho, f2(sc));
+    {
+      const float2 w0r = mul2(rs, f2(1.0f / 3.0f)), w0d = mul2(ds, f2(1.0f / 3.0f));
+      const float2 eu = fma2(w0r, nusq, w0d), ev = fma2(w0r, nvsq, w0d);
+      d[0] = T::pack(fma2(om1, T::val(d[0]), fma2(nom1, eu, ev)));
+    }
+    const float2 wr1 = mul2(rs, f2(1.0f / 18.0f)), wd1 = mul2(ds, f2(1.0f / 18.0f));
+    const float2 wr2 = mul2(rs, f2(1.0f / 36.0f)), wd2 = mul2(ds, f2(1.0f / 36.0f));
+    const float2 w3r1 = mul2(rs, f2(1.0f / 6.0f)), w3r2 = mul2(rs, f2(1.0f / 12.0f));
+    auto pair = [&](int I, float2 WR, float2 WD, float2 W3, float2 cu, float2 cv) {
+      const float2 eu = fma2(WR, fma2(f2(4.5f), mul2(cu, cu), nusq), WD);
+      const float2 ev = fma2(WR, fma2(f2(4.5f), mul2(cv, cv), nvsq), WD);
+      const float2 C = fma2(nom1, eu, ev);
+      const float2 A = mul2(W3, fma2(nom1, cu, cv));
+      d[I] = T::pack(fma2(om1, T::val(d[I]), add2(C, A)));
+      d[I + 1] = T::pack(fma2(om1, T::val(d[I + 1]), sub2(C, A)));
+    };
+    pair(1, wr1, wd1, w3r1, ux, vx);
+    pair(3, wr1, wd1, w3r1, uy, vy);
+    pair(5, wr1, wd1, w3r1, uz, vz);
+    pair(7, wr2, wd2, w3r2, add2(ux, uy), add2(vx, vy));
+    pair(9, wr2, wd2, w3r2, sub2(ux, uy), sub2(vx, vy));
+    pair(11, wr2, wd2, w3r2, add2(ux, uz), add2(vx, vz));
+    pair(13, wr2, wd2, w3r2, sub2(ux, uz), sub2(vx, vz));
+    pair(15, wr2, wd2, w3r2, add2(uy, uz), add2(vy, vz));
+    pair(17, wr2, wd2, w3r2, sub2(uy, uz), sub2(vy, vz));
+    // store the post-collision deviations (now in d), streamed (AA pattern).
+    // The empty asm makes the store addresses depend on values produced here,
+    // so that they are formed now instead of being held in registers through
+    // the collision.
+    int gs = g;
+    asm volatile("" : "+r"(gs));
+    if (PAR == 1) {
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz) asm volatile("" : "+r"(r[dy][dz]));
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (PAR == 0 || i == 0) {
+        T::st(plane_of<S>(a, opp(i)) + gs, d[i]);
+      } else {
+        // slot i of x + c_i, or slot ibar of x when x + c_i lies beyond a wall
+        const int rd = r[1 + cy(i)][1 + cz(i)];
+        const bool wall = WALLS && rd < 0;
+        S* own = plane_of<S>(a, opp(i)) + gs;
+        S* dst = plane_of<S>(a, i) + (wall ? gs : rd);
+        if (cx(i) == 0) {
+          T::st(wall ? own : dst, d[i]);
+        } else if (cx(i) > 0) {  // destinations x0 + 1, x0 + 2
+          S* pa = wall ? own : dst + 1;
+          S* pb = (wall || wr) ? own + 1 : dst + xp;
+          T::st(pa, pb, d[i]);
+        } else {  // destinations x0 - 1, x0
+          S* pa = (wall || wl) ? own : dst + xm;
+          S* pb = wall ? own + 1 : dst;
+          T::st(pa, pb, d[i]);
+        }
+      }
+    }
+    // cells inside a particle record the mass and momentum they send out, as
+    // stored, for the next step's momentum exchange
+    if (COUPLE && a.ilist_idx) {
+      float4 mom[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (cc.ip0[j] >= 0) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const float2 dv = T::val(d[i]);  // as stored
+            const float v = (j == 0 ? dv.x : dv.y) * isc;
+            mom[j].x += v;
+            if (cx(i)) mom[j].y += (float)cx(i) * v;
+            if (cy(i)) mom[j].z += (float)cy(i) * v;
+            if (cz(i)) mom[j].w += (float)cz(i) * v;
+          }
+        }
+      }
+      append_interior<2>(a, (unsigned)g, cc, mom);
+    }
+  }
+}
+
+template <typename S, int PAR, bool W, bool C>
+static cudaError_t launch_cp(const LbmArgs& a, cudaStream_t s) {
+  dim3 block(TILE_X / 2, a.sub_y);
+  collide_pair_kernel<S, PAR, W, C><<<(unsigned)a.nbricks, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t launch_cp_prec(const LbmArgs& a, int parity, bool walls, bool couple,
+                                  cudaStream_t s) {
+  if (parity == 0) return couple ? launch_cp<S, 0, false, true>(a, s) : launch_cp<S, 0, false, false>(a, s);
+  if (walls) return couple ? launch_cp<S, 1, true, true>(a, s) : launch_cp<S, 1, true, false>(a, s);
+  return couple ? launch_cp<S, 1, false, true>(a, s) : launch_cp<S, 1, false, false>(a, s);
+}
+
+cudaError_t launch_collide_pair(const LbmArgs& a, int precision, int parity, bool walls, bool couple,
+                                cudaStream_t s) {
+  if (a.nbricks <= 0) return cudaSuccess;
+  return precision == 0 ? launch_cp_prec<float>(a, parity, walls, couple, s)
+                        : launch_cp_prec<__half>(a, parity, walls, couple, s);
+}
+
+}  // namespace hlbm

@@ -88,11 +88,11 @@ def load(path=LIB_PATH):
     L.hlbm_num_particles.argtypes = [_h]
     L.hlbm_steps_done.argtypes = [_h]
     L.hlbm_steps_done.restype = ctypes.c_longlong
-    L.hlbm_set_launch.argtypes = [_h, ctypes.c_int, ctypes.c_int]
-    L.hlbm_get_launch.argtypes = [_h, _ip, _ip]
+    L.hlbm_set_launch.argtypes = [_h, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.hlbm_get_launch.argtypes = [_h, _ip, _ip, _ip]
     L.hlbm_set_mea_mode.argtypes = [_h, ctypes.c_int]
     L.hlbm_get_mea_mode.argtypes = [_h]
-    L.hlbm_autotune.argtypes = [_h, ctypes.c_int, _ip, _ip, _fp]
+    L.hlbm_autotune.argtypes = [_h, ctypes.c_int, _ip, _ip, _ip, _fp]
     L.hlbm_kernel_times.argtypes = [_h, ctypes.c_int, _fp]
     L.hlbm_last_error.argtypes = [_h]
     L.hlbm_last_error.restype = ctypes.c_char_p
@@ -256,13 +256,17 @@ class Lattice:
     def steps_done(self):
         return load().hlbm_steps_done(self.h)
 
-    def set_launch(self, tile_y, tile_z):
-        _check(self.h, load().hlbm_set_launch(self.h, int(tile_y), int(tile_z)))
+    def set_launch(self, tile_y, tile_z, cells_x=None):
+        """Collision launch shape: bricks of 32 x tile_y x tile_z cells and
+        cells_x (1 or 2) x-adjacent cells per thread (None keeps the current)."""
+        if cells_x is None:
+            cells_x = self.get_launch()[2]
+        _check(self.h, load().hlbm_set_launch(self.h, int(tile_y), int(tile_z), int(cells_x)))
 
     def get_launch(self):
-        ty, tz = ctypes.c_int(), ctypes.c_int()
-        _check(self.h, load().hlbm_get_launch(self.h, ctypes.byref(ty), ctypes.byref(tz)))
-        return ty.value, tz.value
+        ty, tz, cx = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.h, load().hlbm_get_launch(self.h, ctypes.byref(ty), ctypes.byref(tz), ctypes.byref(cx)))
+        return ty.value, tz.value, cx.value
 
     def set_mea_mode(self, mode):
         m = {"kernel": HLBM_MEA_KERNEL, "moments": HLBM_MEA_MOMENTS}.get(mode, mode)
@@ -272,10 +276,12 @@ class Lattice:
         return {HLBM_MEA_KERNEL: "kernel", HLBM_MEA_MOMENTS: "moments"}[load().hlbm_get_mea_mode(self.h)]
 
     def autotune(self, nsteps=10):
-        ty, tz, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        """Times every launch shape and momentum-exchange mode, keeps the
+        fastest; returns (tile_y, tile_z, cells_x, ms per step)."""
+        ty, tz, cx, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
         _check(self.h, load().hlbm_autotune(self.h, int(nsteps), ctypes.byref(ty), ctypes.byref(tz),
-                                            ctypes.byref(ms)))
-        return ty.value, tz.value, ms.value
+                                            ctypes.byref(cx), ctypes.byref(ms)))
+        return ty.value, tz.value, cx.value, ms.value
 
     def kernel_times(self, nsteps=5):
         ms = (ctypes.c_float * 3)()
