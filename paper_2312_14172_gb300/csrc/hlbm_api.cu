@@ -30,7 +30,7 @@ const double PI_D = 3.14159265358979323846;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  long long plane = 0, ncell = 0, ntiles = 0, stage_cells = 0;
+  long long nblocks = 0, ncell = 0, ntiles = 0, stage_cells = 0;
   int cap = 0, bin_cap = 0;
   size_t off_f, off_boxes, off_P, off_shape, off_box, off_rec, off_part, off_acc, off_chp, off_chq,
       off_pc0, off_pnc, off_done, off_lcnt, off_lidx, off_lmom, off_cnt[2], off_ids[2], off_status,
@@ -50,7 +50,7 @@ bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& 
   for (int j = 0; j < 3; ++j)
     if (!std::isfinite(prm->gravity[j]) || !std::isfinite(prm->fluid_force[j])) { err = "non-finite force"; return false; }
   bd.assign(nb, BoxDesc{});
-  long long cells = 0, tiles = 0, maxbox = 0;
+  long long cells = 0, tiles = 0, blocks = 0, maxbox = 0;
   for (int b = 0; b < nb; ++b) {
     const hlbm_box& B = boxes[b];
     if (B.nx < 1 || B.ny < 1 || B.nz < 1 || (B.bc_flags & ~7)) { err = "bad box dimensions or flags"; return false; }
@@ -64,11 +64,13 @@ bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& 
     d.ntz = (B.nz + TILE_Z - 1) / TILE_Z;
     d.cell_off = cells;
     d.tile_off = tiles;
-    cells += (n + 63) / 64 * 64;  // every box starts on a 64-cell boundary
+    d.blk_off = blocks;
+    cells += n;
     tiles += (long long)d.ntx * d.nty * d.ntz;
+    blocks += (long long)d.ntx * d.ny * d.nz;  // storage blocks: rows of 32 cells
     if (n > maxbox) maxbox = n;
   }
-  L.plane = cells;
+  L.nblocks = blocks;
   L.ncell = cells;
   L.ntiles = tiles;
   L.stage_cells = maxbox < STAGE_CELLS ? maxbox : STAGE_CELLS;
@@ -76,7 +78,7 @@ bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& 
   L.bin_cap = prm->bin_capacity ? prm->bin_capacity : DEFAULT_BIN_CAP;
   const size_t s = prm->precision == HLBM_FP32 ? 4 : 2;
   size_t o = 0;
-  L.off_f = o; o = align_up(o + (size_t)Q * L.plane * s);
+  L.off_f = o; o = align_up(o + (size_t)QVB * L.nblocks * s);
   L.off_boxes = o; o = align_up(o + sizeof(BoxDesc) * nb);
   L.off_P = o; o = align_up(o + sizeof(double) * PF_COUNT * (size_t)L.cap);
   L.off_shape = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
@@ -91,7 +93,7 @@ bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& 
   L.off_done = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
   // interior-cell list for the momentum exchange from moments: room for half
   // of all cells (more than any packing of non-overlapping particles needs)
-  L.ilist_cap = L.cap > 0 ? (L.plane + 1) / 2 : 0;
+  L.ilist_cap = L.cap > 0 ? (L.ncell + 1) / 2 : 0;
   L.off_lcnt = o; o = align_up(o + sizeof(int));
   L.off_lidx = o; o = align_up(o + sizeof(int2) * (size_t)L.ilist_cap);
   L.off_lmom = o; o = align_up(o + sizeof(float4) * (size_t)L.ilist_cap);
@@ -173,9 +175,7 @@ static int fail(hlbm_ctx* h, int code, const std::string& msg) {
 static LbmArgs lbm_args(const hlbm_ctx* h, int parity) {
   LbmArgs a{};
   a.f = h->f;
-  a.plane = h->L.plane;
-  const size_t es = h->prm.precision == HLBM_FP32 ? 4 : 2;
-  for (int i = 0; i < Q; ++i) a.pl[i] = (char*)h->f + (size_t)i * h->L.plane * es;
+  a.ncell = h->L.ncell;
   a.boxes = h->d_boxes;
   a.nboxes = (int)h->boxes.size();
   a.sub_y = h->sub_y;
@@ -217,7 +217,6 @@ static PartArgs part_args(const hlbm_ctx* h, int parity) {
   for (int j = 0; j < 3; ++j) a.g[j] = h->prm.gravity[j];
   a.eps = h->prm.eps;
   a.f = h->f;
-  a.plane = h->L.plane;
   const double sc = h->prm.precision == HLBM_FP16 ? std::ldexp(1.0, h->prm.fp16_scale_log2) : 1.0;
   a.scale = (float)sc;
   a.inv_scale = (float)(1.0 / sc);

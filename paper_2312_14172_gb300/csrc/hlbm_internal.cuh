@@ -1,13 +1,19 @@
 // hlbm_internal.cuh -- device data layout and kernel launchers of libhlbm.
 //
 // HBM layout of one handle (all arrays carved from one device buffer):
-//   populations   19 planes of `plane` elements (float or half), plane i holds
-//                 slot i of every cell of every box, box b at cell offset
-//                 box.cell_off, x fastest.  Storage is the deviation f_i - w_i
-//                 (times 2^s for half).  In-place AA pattern: after an even
-//                 number of steps slot i of cell x holds f_i(x); after an odd
-//                 number slot ibar of cell x - c_i holds f_i(x) (or slot i of
-//                 x when x - c_i lies beyond a wall).
+//   populations   blocked structure of arrays: the cells of every row are
+//                 grouped in blocks of VB = 32 consecutive x (the last block
+//                 of a row padded), and block B holds its Q slots one after
+//                 the other, VB values each: slot i of cell x of block B is
+//                 element B * Q * VB + i * VB + (x & 31).  Blocks run x-block
+//                 fastest, then y, then z, box after box (box b from block
+//                 box.blk_off).  All 19 slots of 32 cells are one contiguous
+//                 run of 19 * 32 values, and every slot of a cell is an
+//                 immediate offset from the cell's slot 0.  Storage is the
+//                 deviation f_i - w_i (times 2^s for half).  In-place AA
+//                 pattern: after an even number of steps slot i of cell x
+//                 holds f_i(x); after an odd number slot ibar of cell x - c_i
+//                 holds f_i(x) (or slot i of x when x - c_i lies beyond a wall).
 //   particles     FP64 structure of arrays, field-major (PF_* below).
 //   records       one 128-byte FP32 record per particle (Rec), rebuilt after
 //                 every Newton-Euler update, read by the collision and the
@@ -45,11 +51,24 @@ __host__ __device__ constexpr double wq(int i) {
 
 struct BoxDesc {
   int nx, ny, nz, bc;        // bc: bit a set = walls on axis a
-  int ntx, nty, ntz;         // bin tiles per axis
+  int ntx, nty, ntz;         // bin tiles per axis (ntx = storage blocks per row)
   int pad0;
-  long long cell_off;        // first cell of the box in every plane
+  long long cell_off;        // first cell of the box in the global cell numbering
   long long tile_off;        // first bin tile of the box
+  long long blk_off;         // first storage block of the box
 };
+
+// blocked population storage (layout above)
+constexpr int VB = 32;       // cells per storage block (= TILE_X)
+constexpr int QVB = Q * VB;  // values per storage block
+
+// storage block of cell (x, y, z) of a box, and the element of its slot 0
+__host__ __device__ __forceinline__ long long block_of(const BoxDesc& bd, int x, int y, int z) {
+  return bd.blk_off + ((long long)z * bd.ny + y) * bd.ntx + (x >> 5);
+}
+__host__ __device__ __forceinline__ long long elem_of(const BoxDesc& bd, int x, int y, int z) {
+  return block_of(bd, x, y, z) * QVB + (x & 31);
+}
 
 // FP64 particle table fields (each an array of `cap` doubles).  PF_IM and
 // PF_II hold 1/m and 1/I, PF_IA holds fp32(1/a_j) (exact in a double).
@@ -100,6 +119,39 @@ struct Nbr {
 template <bool WALLS>
 __device__ __forceinline__ Nbr<WALLS> make_nbr(const BoxDesc& bd, int x, int y, int z);
 
+// neighbours in the blocked storage: at() returns the element of slot 0 of
+// the neighbour (slot i is VB * i further), or -1 beyond a wall
+struct NbrB {
+  long long xm, xp, x;  // x terms: (x >> 5) * QVB + (x & 31)
+  long long ym, yp, y;  // y terms: y * ntx * QVB
+  long long zm, zp, z;  // z terms incl. the box's first block
+  __device__ __forceinline__ long long at(int dx, int dy, int dz) const {
+    const long long a = dx < 0 ? xm : (dx > 0 ? xp : x);
+    const long long b = dy < 0 ? ym : (dy > 0 ? yp : y);
+    const long long c = dz < 0 ? zm : (dz > 0 ? zp : z);
+    if (a < 0 || b < 0 || c < 0) return -1;
+    return a + b + c;
+  }
+};
+
+__device__ __forceinline__ NbrB make_nbr_blocked(const BoxDesc& bd, int x, int y, int z) {
+  NbrB n;
+  const int nx = bd.nx, ny = bd.ny, nz = bd.nz;
+  const bool wx = bd.bc & 1, wy = bd.bc & 2, wz = bd.bc & 4;
+  const long long row = (long long)bd.ntx * QVB, pln = row * ny, base = bd.blk_off * QVB;
+  auto xt = [](int v) { return (long long)(v >> 5) * QVB + (v & 31); };
+  n.x = xt(x);
+  n.xm = x > 0 ? xt(x - 1) : (wx ? -1 : xt(nx - 1));
+  n.xp = x < nx - 1 ? xt(x + 1) : (wx ? -1 : xt(0));
+  n.y = y * row;
+  n.ym = y > 0 ? (y - 1) * row : (wy ? -1 : (ny - 1) * row);
+  n.yp = y < ny - 1 ? (y + 1) * row : (wy ? -1 : 0);
+  n.z = base + z * pln;
+  n.zm = z > 0 ? base + (z - 1) * pln : (wz ? -1 : base + (nz - 1) * pln);
+  n.zp = z < nz - 1 ? base + (z + 1) * pln : (wz ? -1 : base);
+  return n;
+}
+
 // neighbour offsets in global cell indices (the box's first cell added):
 // at() returns the global index, or a negative value beyond a wall
 template <bool WALLS>
@@ -131,9 +183,8 @@ __device__ __forceinline__ Nbr<WALLS> make_nbr(const BoxDesc& bd, int x, int y, 
 
 
 struct LbmArgs {
-  void* f;                  // population planes (float* or __half*)
-  long long plane;          // elements per plane
-  void* pl[Q];              // base of each plane (f + i * plane elements)
+  void* f;                  // populations, blocked layout (float* or __half*)
+  long long ncell;          // cells of all boxes (global cell numbering)
   const BoxDesc* boxes;
   int nboxes;
   int sub_y, sub_z;         // brick per block: 32 x sub_y x sub_z cells
@@ -171,8 +222,7 @@ struct PartArgs {
   double g[3];
   double eps;
   // momentum exchange input
-  const void* f;
-  long long plane;
+  const void* f;            // populations, blocked layout
   float scale, inv_scale;
   // momentum-exchange kernel: one block per (particle, bounding-box plane)
   const int* chunk_p;       // [chunks] particle of the block

@@ -46,9 +46,51 @@ __device__ __forceinline__ float stored_value(float v, float s, float inv_s) {
   return __half2float(__float2half_rn(v * s)) * inv_s;
 }
 
-// plane i of the populations, from the kernel parameters
+// Addressing of a thread's cells x .. x + n - 1 (one row, one storage block)
+// for the collide-and-stream: the rows y - 1, y, y + 1 as block offsets, and
+// the x neighbours left of the first and right of the last cell as element
+// offsets from the first cell in the same row (periodic wrap), with flags
+// for an x wall there.
+struct RowBlocks {
+  int yb[3];   // (y + dy - 1) * ntx, or -1 beyond a y wall
+  int xb, xin; // x-block of the cells and x & 31 of the first
+  int dl, dr;  // element of x - 1 and of x + n, minus the element of x
+  bool wl, wr; // x - 1 / x + n lies beyond an x wall
+};
+
+__device__ __forceinline__ int x_term(int x) { return (x >> 5) * QVB + (x & 31); }
+
+template <bool WALLS>
+__device__ __forceinline__ RowBlocks row_blocks(const BoxDesc& bd, int x, int y, int n) {
+  RowBlocks r;
+  const int nx = bd.nx, ny = bd.ny, ntx = bd.ntx;
+  const bool wx = WALLS && (bd.bc & 1), wy = WALLS && (bd.bc & 2);
+  r.yb[1] = y * ntx;
+  r.yb[0] = y > 0 ? (y - 1) * ntx : (wy ? -1 : (ny - 1) * ntx);
+  r.yb[2] = y < ny - 1 ? (y + 1) * ntx : (wy ? -1 : 0);
+  r.xb = x >> 5;
+  r.xin = x & 31;
+  const int xl = x > 0 ? x - 1 : nx - 1, xr = x + n < nx ? x + n : x + n - nx;
+  r.dl = x_term(xl) - x_term(x);
+  r.dr = x_term(xr) - x_term(x);
+  r.wl = wx && x == 0;
+  r.wr = wx && x + n == nx;
+  return r;
+}
+
+// first block of slice z + dz - 1 of the box, or -1 beyond a z wall
+template <bool WALLS>
+__device__ __forceinline__ void slice_blocks(const BoxDesc& bd, int z, int zb[3]) {
+  const int nz = bd.nz, sl = bd.ny * bd.ntx, b0 = (int)bd.blk_off;
+  const bool wz = WALLS && (bd.bc & 4);
+  zb[1] = b0 + z * sl;
+  zb[0] = z > 0 ? b0 + (z - 1) * sl : (wz ? -1 : b0 + (nz - 1) * sl);
+  zb[2] = z < nz - 1 ? b0 + (z + 1) * sl : (wz ? -1 : b0);
+}
+
+// element of slot 0 of the first cell in storage block B
 template <typename S>
-__device__ __forceinline__ S* plane_of(const LbmArgs& a, int i) { return reinterpret_cast<S*>(a.pl[i]); }
+__device__ __forceinline__ S* cell_ptr(S* f, int B, int xin) { return f + ((long long)B * QVB + xin); }
 
 // indicator of Eq. B written as (1 - sin(pi d / eps)) / 2 on the ramp, which
 // equals cos^2((pi/2)(d/eps + 1/2))

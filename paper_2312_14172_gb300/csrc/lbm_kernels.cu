@@ -21,36 +21,19 @@ namespace hlbm {
 #define HLBM_CS_MINBLOCKS 4
 #endif
 
-// load of the post-streaming deviations f_i(x) - w_i of cell c (AA accessor):
-// even parity: slot i of x; odd parity: slot ibar of x - c_i, or slot i of x
-// when x - c_i lies beyond a wall
-template <typename S, int PAR, bool WALLS>
-__device__ __forceinline__ void load_arrivals(const S* f, long long P, const Nbr<WALLS>& nb, int c,
-                                              float inv_s, float d[Q]) {
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (PAR == 0) {
-      d[i] = Pop<S>::ld(f + i * P + c, inv_s);
-    } else {
-      const int src = (i == 0) ? c : nb.at(-cx(i), -cy(i), -cz(i));
-      const S* p = (!WALLS || src >= 0) ? f + opp(i) * P + src : f + i * P + c;
-      d[i] = Pop<S>::ld(p, inv_s);
-    }
-  }
-}
-
-// the same accessor on global cell indices (g = this cell, nb from make_nbr_global)
-template <typename S, int PAR, bool WALLS>
-__device__ __forceinline__ void load_arrivals_raw(const LbmArgs& a, const Nbr<WALLS>& nb, unsigned g,
-                                                  float d[Q]) {
+// load of the post-streaming deviations f_i(x) - w_i of the cell whose slot
+// 0 is element e (AA accessor): even parity: slot i of x; odd parity: slot
+// ibar of x - c_i, or slot i of x when x - c_i lies beyond a wall
+template <typename S, int PAR>
+__device__ __forceinline__ void load_arrivals(const S* f, const NbrB& nb, long long e, float inv_s,
+                                              float d[Q]) {
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (PAR == 0 || i == 0) {
-      d[i] = Pop<S>::ld_raw(plane_of<S>(a, i) + g);
+      d[i] = Pop<S>::ld(f + e + i * VB, inv_s);
     } else {
-      const int src = nb.at(-cx(i), -cy(i), -cz(i));
-      const S* p = (!WALLS || src >= 0) ? plane_of<S>(a, opp(i)) + (unsigned)src : plane_of<S>(a, i) + g;
-      d[i] = Pop<S>::ld_raw(p);
+      const long long src = nb.at(-cx(i), -cy(i), -cz(i));
+      d[i] = Pop<S>::ld(src >= 0 ? f + src + opp(i) * VB : f + e + i * VB, inv_s);
     }
   }
 }
@@ -70,16 +53,38 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
   if (x >= bd.nx || y >= bd.ny) return;
   const int z0 = k.z0;
   const int z1 = min(z0 + a.sub_z, bd.nz);
+  const RowBlocks rb = row_blocks<WALLS>(bd, x, y, 1);
+  S* const f = reinterpret_cast<S*>(a.f);
   // storage scale: the collision runs on the stored (scaled) deviations
   const float sc = Pop<S>::SCALED ? a.scale : 1.0f, isc = Pop<S>::SCALED ? a.inv_scale : 1.0f;
 
+#pragma unroll 1
   for (int z = z0; z < z1; ++z) {
-    const int c = (z * bd.ny + y) * bd.nx + x;
-    const unsigned g = (unsigned)(bd.cell_off + c);  // global cell index
-    Nbr<WALLS> nb;
-    if (PAR == 1) nb = make_nbr_global<WALLS>(bd, x, y, z);
+    const unsigned g = (unsigned)(bd.cell_off + (z * bd.ny + y) * bd.nx + x);  // global cell index
+    int zb[3];
+    slice_blocks<WALLS>(bd, z, zb);
+    S* const own = cell_ptr(f, zb[1] + rb.yb[1] + rb.xb, rb.xin);
     float d[Q];  // stored deviations (times the storage scale)
-    load_arrivals_raw<S, PAR, WALLS>(a, nb, g, d);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (PAR == 0 || i == 0) {
+        d[i] = Pop<S>::ld_raw(own + i * VB);
+      } else {
+        // slot ibar of x - c_i, or slot i of x when x - c_i lies beyond a wall
+        const int by = rb.yb[1 - cy(i)], bz = zb[1 - cz(i)];
+        const bool wall = WALLS && (by < 0 || bz < 0 || (cx(i) > 0 && rb.wl) || (cx(i) < 0 && rb.wr));
+        const int dx = cx(i) > 0 ? rb.dl : (cx(i) < 0 ? rb.dr : 0);
+        const S* p = wall ? own + i * VB : cell_ptr(f, bz + by + rb.xb, rb.xin) + (dx + opp(i) * VB);
+        d[i] = Pop<S>::ld_raw(p);
+      }
+    }
+    // indicator, particle velocity and particles holding the cell, from the
+    // candidates that meet this row (uniform over the warp); it needs
+    // positions only and runs while the loads above are in flight
+    RowCoupling<1> cc;
+    if (COUPLE)
+      couple_row<1>(srec, s_rowmask[threadIdx.y + a.sub_y * (z - z0)], bd, x, y, z, a.eps, a.inv_eps,
+                    a.status, cc);
     float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -99,11 +104,7 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
     const float irho = 1.0f / rho;
     const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
     float dux = a.ff[0] * irho, duy = a.ff[1] * irho, duz = a.ff[2] * irho;
-    RowCoupling<1> cc;  // indicator, particle velocity, particles holding the cell
     if (COUPLE) {
-      // only the candidates that meet this row (uniform over the warp)
-      couple_row<1>(srec, s_rowmask[threadIdx.y + a.sub_y * (z - z0)], bd, x, y, z, a.eps, a.inv_eps,
-                    a.status, cc);
       if (cc.B[0] > 0.0f) {
         dux += cc.B[0] * (cc.upx[0] - ux);
         duy += cc.B[0] * (cc.upy[0] - uy);
@@ -146,14 +147,17 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
     HLBM_PAIR(15, wr2, wd2, uy + uz, vy + vz)
     HLBM_PAIR(17, wr2, wd2, uy - uz, vy - vz)
 #undef HLBM_PAIR
-    // store the post-collision deviations, streamed (AA pattern)
+    // store the post-collision deviations, streamed (AA pattern): slot i of
+    // x + c_i, or slot ibar of x when x + c_i lies beyond a wall
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (PAR == 0 || i == 0) {
-        Pop<S>::st_raw(plane_of<S>(a, opp(i)) + g, o[i]);
+        Pop<S>::st_raw(own + opp(i) * VB, o[i]);
       } else {
-        const int dst = nb.at(cx(i), cy(i), cz(i));
-        S* p = (!WALLS || dst >= 0) ? plane_of<S>(a, i) + (unsigned)dst : plane_of<S>(a, opp(i)) + g;
+        const int by = rb.yb[1 + cy(i)], bz = zb[1 + cz(i)];
+        const bool wall = WALLS && (by < 0 || bz < 0 || (cx(i) > 0 && rb.wr) || (cx(i) < 0 && rb.wl));
+        const int dx = cx(i) > 0 ? rb.dr : (cx(i) < 0 ? rb.dl : 0);
+        S* p = wall ? own + opp(i) * VB : cell_ptr(f, bz + by + rb.xb, rb.xin) + (dx + i * VB);
         Pop<S>::st_raw(p, o[i]);
       }
     }
@@ -218,9 +222,9 @@ __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
       r[0] = offset_fp32(x, bd.nx, bd.bc & 1, R.xh[0], R.xl[0]);
       r[1] = offset_fp32(y, bd.ny, bd.bc & 2, R.xh[1], R.xl[1]);
       r[2] = offset_fp32(z, bd.nz, bd.bc & 4, R.xh[2], R.xl[2]);
-      const Nbr<WALLS> nb = make_nbr<WALLS>(bd, x, y, z);
+      const NbrB nb = make_nbr_blocked(bd, x, y, z);
       float d[Q];
-      load_arrivals<S, PAR, WALLS>(fbase + bd.cell_off, a.plane, nb, c, a.inv_scale, d);
+      load_arrivals<S, PAR>(fbase, nb, elem_of(bd, x, y, z), a.inv_scale, d);
       float ms = 0.f, px = 0.f, py = 0.f, pz = 0.f;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -323,18 +327,17 @@ __global__ void gather_scatter_kernel(LbmArgs a, int box, long long c0, long lon
   const long long t = cl / bd.nx;
   const int y = (int)(t % bd.ny);
   const int z = (int)(t / bd.ny);
-  const int c = (int)cl;
-  S* f = reinterpret_cast<S*>(a.f) + bd.cell_off;
-  const long long P = a.plane;
-  const Nbr<true> nb = make_nbr<true>(bd, x, y, z);
+  S* f = reinterpret_cast<S*>(a.f);
+  const NbrB nb = make_nbr_blocked(bd, x, y, z);
+  const long long e = elem_of(bd, x, y, z);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     S* slot;
     if (PAR == 0 || i == 0) {
-      slot = f + i * P + c;
+      slot = f + e + i * VB;
     } else {
-      const int src = nb.at(-cx(i), -cy(i), -cz(i));
-      slot = (src >= 0) ? f + opp(i) * P + src : f + i * P + c;
+      const long long src = nb.at(-cx(i), -cy(i), -cz(i));
+      slot = (src >= 0) ? f + src + opp(i) * VB : f + e + i * VB;
     }
     if (GATHER) stage[i * n + k] = Pop<S>::ld(slot, a.inv_scale);
     else Pop<S>::st(slot, stage[i * n + k], a.scale);

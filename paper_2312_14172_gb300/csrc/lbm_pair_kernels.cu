@@ -79,65 +79,47 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
   if (x0 >= bd.nx || y >= bd.ny) return;
   const int z0 = k.z0;
   const int z1 = min(z0 + a.sub_z, bd.nz);
-  const int nx = bd.nx, ny = bd.ny, nz = bd.nz, nxy = nx * ny;
-  const int off = (int)bd.cell_off;
-  const bool wy = WALLS && (bd.bc & 2), wz = WALLS && (bd.bc & 4);
-  // x0 - 1 and x0 + 2 as offsets from x0 (periodic wrap), and whether they
-  // lie beyond an x wall
-  const int xm = x0 > 0 ? -1 : nx - 1;
-  const int xp = x0 + 2 < nx ? 2 : 2 - nx;
-  const bool wl = WALLS && (bd.bc & 1) && x0 == 0;
-  const bool wr = WALLS && (bd.bc & 1) && x0 + 2 == nx;
-  // offsets of the rows y - 1, y, y + 1 (negative beyond a wall)
-  int yo[3];
-  yo[1] = y * nx;
-  yo[0] = y > 0 ? (y - 1) * nx : (wy ? -1 : (ny - 1) * nx);
-  yo[2] = y < ny - 1 ? (y + 1) * nx : (wy ? -1 : 0);
+  const RowBlocks rb = row_blocks<WALLS>(bd, x0, y, 2);
+  S* const f = reinterpret_cast<S*>(a.f);
   const float sc = Pop<S>::SCALED ? a.scale : 1.0f, isc = Pop<S>::SCALED ? a.inv_scale : 1.0f;
 
   // one z slice at a time: an unrolled loop would hold two slices' arrivals
 #pragma unroll 1
   for (int z = z0; z < z1; ++z) {
-    const int g = off + z * nxy + yo[1] + x0;  // global index of cell x0
-    // global index of cell x0 of the row shifted by (dy - 1, dz - 1), or
-    // negative beyond a y or z wall
-    int r[3][3];
-    if (PAR == 1) {
-      int zo[3];
-      zo[1] = z * nxy;
-      zo[0] = z > 0 ? (z - 1) * nxy : (wz ? -1 : (nz - 1) * nxy);
-      zo[2] = z < nz - 1 ? (z + 1) * nxy : (wz ? -1 : 0);
-#pragma unroll
-      for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-        for (int dz = 0; dz < 3; ++dz)
-          r[dy][dz] = (WALLS && (yo[dy] < 0 || zo[dz] < 0)) ? -1 : off + zo[dz] + yo[dy] + x0;
-    }
+    int zb[3];
+    slice_blocks<WALLS>(bd, z, zb);
+    S* const own = cell_ptr(f, zb[1] + rb.yb[1] + rb.xb, rb.xin);  // slot 0 of cell x0
     // arrivals (stored units), both cells
     typename T::raw d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (PAR == 0 || i == 0) {
-        d[i] = T::ld(plane_of<S>(a, i) + g);
+        d[i] = T::ld(own + i * VB);
       } else {
         // slot ibar of x - c_i, or slot i of x when x - c_i lies beyond a wall
-        const int rs = r[1 - cy(i)][1 - cz(i)];
-        const bool wall = WALLS && rs < 0;
-        const S* own = plane_of<S>(a, i) + g;
-        const S* src = plane_of<S>(a, opp(i)) + (wall ? g : rs);
+        const int by = rb.yb[1 - cy(i)], bz = zb[1 - cz(i)];
+        const bool wall = WALLS && (by < 0 || bz < 0);
+        const S* src = cell_ptr(f, wall ? 0 : bz + by + rb.xb, rb.xin) + opp(i) * VB;  // x0 of the source row
+        const S* mine = own + i * VB;
         if (cx(i) == 0) {
-          d[i] = T::ld(wall ? own : src);
+          d[i] = T::ld(wall ? mine : src);
         } else if (cx(i) > 0) {  // sources x0 - 1, x0
-          const S* pa = (wall || wl) ? own : src + xm;
-          const S* pb = wall ? own + 1 : src;
+          const S* pa = (wall || rb.wl) ? mine : src + rb.dl;
+          const S* pb = wall ? mine + 1 : src;
           d[i] = T::ld(pa, pb);
         } else {  // sources x0 + 1, x0 + 2
-          const S* pa = wall ? own : src + 1;
-          const S* pb = (wall || wr) ? own + 1 : src + xp;
+          const S* pa = wall ? mine : src + 1;
+          const S* pb = (wall || rb.wr) ? mine + 1 : src + rb.dr;
           d[i] = T::ld(pa, pb);
         }
       }
     }
+    // coupling of both cells; it needs positions only and runs while the
+    // loads above are in flight
+    RowCoupling<2> cc;
+    if (COUPLE)
+      couple_row<2>(srec, s_rowmask[threadIdx.y + a.sub_y * (z - z0)], bd, x0, y, z, a.eps, a.inv_eps,
+                    a.status, cc);
     // moments, opposite directions taken together: s = d_i + d_ibar, m = d_i - d_ibar
     float2 drho = T::val(d[0]), m[Q];  // m[i]: d_i - d_(i+1), i odd
 #pragma unroll
@@ -162,10 +144,7 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
     const float2 irho = make_float2(__fdividef(1.0f, rho.x), __fdividef(1.0f, rho.y));
     const float2 ux = mul2(jx, irho), uy = mul2(jy, irho), uz = mul2(jz, irho);
     float2 dux = mul2(f2(a.ff[0]), irho), duy = mul2(f2(a.ff[1]), irho), duz = mul2(f2(a.ff[2]), irho);
-    RowCoupling<2> cc;
     if (COUPLE) {
-      couple_row<2>(srec, s_rowmask[threadIdx.y + a.sub_y * (z - z0)], bd, x0, y, z, a.eps, a.inv_eps,
-                    a.status, cc);
       if (cc.B[0] > 0.0f) {
         dux.x += cc.B[0] * (cc.upx[0] - ux.x);
         duy.x += cc.B[0] * (cc.upy[0] - uy.x);
@@ -210,37 +189,26 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
     pair(13, wr2, wd2, w3r2, sub2(ux, uz), sub2(vx, vz));
     pair(15, wr2, wd2, w3r2, add2(uy, uz), add2(vy, vz));
     pair(17, wr2, wd2, w3r2, sub2(uy, uz), sub2(vy, vz));
-    // store the post-collision deviations (now in d), streamed (AA pattern).
-    // The empty asm makes the store addresses depend on values produced here,
-    // so that they are formed now instead of being held in registers through
-    // the collision.
-    int gs = g;
-    asm volatile("" : "+r"(gs));
-    if (PAR == 1) {
-#pragma unroll
-      for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-        for (int dz = 0; dz < 3; ++dz) asm volatile("" : "+r"(r[dy][dz]));
-    }
+    // store the post-collision deviations (now in d), streamed (AA pattern):
+    // slot i of x + c_i, or slot ibar of x when x + c_i lies beyond a wall
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (PAR == 0 || i == 0) {
-        T::st(plane_of<S>(a, opp(i)) + gs, d[i]);
+        T::st(own + opp(i) * VB, d[i]);
       } else {
-        // slot i of x + c_i, or slot ibar of x when x + c_i lies beyond a wall
-        const int rd = r[1 + cy(i)][1 + cz(i)];
-        const bool wall = WALLS && rd < 0;
-        S* own = plane_of<S>(a, opp(i)) + gs;
-        S* dst = plane_of<S>(a, i) + (wall ? gs : rd);
+        const int by = rb.yb[1 + cy(i)], bz = zb[1 + cz(i)];
+        const bool wall = WALLS && (by < 0 || bz < 0);
+        S* dst = cell_ptr(f, wall ? 0 : bz + by + rb.xb, rb.xin) + i * VB;  // x0 of the destination row
+        S* mine = own + opp(i) * VB;
         if (cx(i) == 0) {
-          T::st(wall ? own : dst, d[i]);
+          T::st(wall ? mine : dst, d[i]);
         } else if (cx(i) > 0) {  // destinations x0 + 1, x0 + 2
-          S* pa = wall ? own : dst + 1;
-          S* pb = (wall || wr) ? own + 1 : dst + xp;
+          S* pa = wall ? mine : dst + 1;
+          S* pb = (wall || rb.wr) ? mine + 1 : dst + rb.dr;
           T::st(pa, pb, d[i]);
         } else {  // destinations x0 - 1, x0
-          S* pa = (wall || wl) ? own : dst + xm;
-          S* pb = wall ? own + 1 : dst;
+          S* pa = (wall || rb.wl) ? mine : dst + rb.dl;
+          S* pb = wall ? mine + 1 : dst;
           T::st(pa, pb, d[i]);
         }
       }
@@ -263,7 +231,7 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
           }
         }
       }
-      append_interior<2>(a, (unsigned)g, cc, mom);
+      append_interior<2>(a, (unsigned)(bd.cell_off + (z * bd.ny + y) * bd.nx + x0), cc, mom);
     }
   }
 }

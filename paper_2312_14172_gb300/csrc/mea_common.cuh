@@ -42,15 +42,17 @@ __device__ __forceinline__ void rotation_rn(const double q[4], double R[9]) {
 // and are left out; on deviations d = f - w that leaves -2 c_i w_i per
 // omitted link, because the weights of all 18 links sum to zero.  In both AA
 // parities the pair of slots is {slot i of x, slot ibar of x - c_i}; only
-// which of the two is the arrival differs.
-template <typename S, int PAR>
-__device__ __forceinline__ void mea_cell(const S* f, long long P, const Nbr<true>& nb, int c,
+// which of the two is the arrival differs.  Slot i of the cell whose slot 0
+// is element e lies at f + i * P + e: P is the plane stride of a plain
+// structure of arrays, or VB in the blocked layout (nb from make_nbr_blocked).
+template <typename S, int PAR, typename NB>
+__device__ __forceinline__ void mea_cell(const S* f, long long P, const NB& nb, long long c,
                                          float inv_s, float F[3], float& mgain) {
   F[0] = F[1] = F[2] = 0.0f;
   mgain = 0.0f;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    const int s = nb.at(-cx(i), -cy(i), -cz(i));
+    const long long s = nb.at(-cx(i), -cy(i), -cz(i));
     if (s < 0) {
       const float w2 = 2.0f * (float)wq(i);
       if (cx(i)) F[0] -= (float)cx(i) * w2;
@@ -90,8 +92,11 @@ __device__ __forceinline__ void row_range(int iy, int ext1, int lo0, int ext0, i
 // Per-thread sums (F, T) over the cells of plane iz of the bounding box
 // [floor(X - r_c), ceil(X + r_c)] of one particle whose centre is finite.
 // All threads of the block call it (it synchronises); s_start holds
-// MAX_PLANES + 1 ints, s_xa MAX_PLANES.
-template <typename S, int PAR>
+// MAX_PLANES + 1 ints, s_xa MAX_PLANES.  BLOCKED: f is the library's
+// blocked storage (plane unused); otherwise f holds the box alone as a plain
+// structure of arrays with `plane` values per slot, cell (x, y, z) at
+// (z * ny + y) * nx + x.
+template <typename S, int PAR, bool BLOCKED>
 __device__ __forceinline__ void mea_plane_sums(const Rec& R, const BoxDesc& bd, const double X[3],
                                                double rc, int iz, const S* f, long long plane,
                                                float inv_scale, int* s_start, int* s_xa,
@@ -152,10 +157,14 @@ __device__ __forceinline__ void mea_plane_sums(const Rec& R, const BoxDesc& bd, 
       const int y = yu < 0 ? yu + n[1] : (yu >= n[1] ? yu - n[1] : yu);
       float rr[3];
       if (!inside_fp32(R, bd, x, y, z, rr)) continue;
-      const Nbr<true> nb = make_nbr<true>(bd, x, y, z);
-      const int c = (z * bd.ny + y) * bd.nx + x;
       float Fc[3], mg;
-      mea_cell<S, PAR>(f, plane, nb, c, inv_scale, Fc, mg);
+      if constexpr (BLOCKED) {
+        mea_cell<S, PAR>(f, (long long)VB, make_nbr_blocked(bd, x, y, z), elem_of(bd, x, y, z), inv_scale,
+                         Fc, mg);
+      } else {
+        mea_cell<S, PAR>(f, plane, make_nbr<true>(bd, x, y, z), (long long)((z * bd.ny + y) * bd.nx + x),
+                         inv_scale, Fc, mg);
+      }
       const float upx = R.u[0] + (R.w[1] * rr[2] - R.w[2] * rr[1]);
       const float upy = R.u[1] + (R.w[2] * rr[0] - R.w[0] * rr[2]);
       const float upz = R.u[2] + (R.w[0] * rr[1] - R.w[1] * rr[0]);

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(128) noalloc_mea_kernel(NoAllocArgs a) {
   double X[3];
   for (int j = 0; j < 3; ++j) X[j] = a.X[3 * p + j];
   float v[6];
-  mea_plane_sums<S, PAR>(R, a.bd, X, na_rc(a)[p], iz, reinterpret_cast<const S*>(a.f), a.plane,
+  mea_plane_sums<S, PAR, false>(R, a.bd, X, na_rc(a)[p], iz, reinterpret_cast<const S*>(a.f), a.plane,
                          a.inv_scale, s_start, s_xa, v);
 #pragma unroll
   for (int k = 0; k < 6; ++k)

@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(128) mea_kernel(PartArgs a) {
   }
   float sums[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (ok) {
-    const S* f = reinterpret_cast<const S*>(a.f) + bd.cell_off;
-    mea_plane_sums<S, PAR>(R, bd, X, rc, iz, f, a.plane, a.inv_scale, s_start, s_xa, sums);
+    mea_plane_sums<S, PAR, true>(R, bd, X, rc, iz, reinterpret_cast<const S*>(a.f), 0, a.inv_scale, s_start,
+                                 s_xa, sums);
   } else if (tid == 0) {
     atomicOr(a.status, ST_UNSTABLE);
   }
