@@ -92,17 +92,31 @@ __device__ __forceinline__ void slice_blocks(const BoxDesc& bd, int z, int zb[3]
 template <typename S>
 __device__ __forceinline__ S* cell_ptr(S* f, int B, int xin) { return f + ((long long)B * QVB + xin); }
 
+// sin(pi t) for |t| <= 1/2: the Taylor series of sin truncated after the
+// t^11 term, in Horner form in t^2; the remainder is below
+// (pi/2)^13 / 13! < 6e-8, and FP32 rounding keeps the total below 2e-7
+__device__ __forceinline__ float sinpi_ramp(float t) {
+  const float t2 = t * t;
+  float p = -7.3704309457143508e-3f;    // -pi^11 / 11!
+  p = fmaf(p, t2, 8.2145886611128229e-2f);  // pi^9 / 9!
+  p = fmaf(p, t2, -5.9926452932079208e-1f); // -pi^7 / 7!
+  p = fmaf(p, t2, 2.5501640398773455f);     // pi^5 / 5!
+  p = fmaf(p, t2, -5.1677127800499703f);    // -pi^3 / 3!
+  p = fmaf(p, t2, 3.1415926535897932f);     // pi
+  return p * t;
+}
+
 // indicator of Eq. B written as (1 - sin(pi d / eps)) / 2 on the ramp, which
 // equals cos^2((pi/2)(d/eps + 1/2))
 __device__ __forceinline__ float indicator(float d, float eps, float inv_eps) {
   if (d <= -0.5f * eps) return 1.0f;
   if (d >= 0.5f * eps) return 0.0f;
-  return 0.5f - 0.5f * sinpif(d * inv_eps);
+  return 0.5f - 0.5f * sinpi_ramp(d * inv_eps);
 }
 
 // signed distance of a particle at offset r (world frame), FP32
 __device__ __forceinline__ float sdf(const Rec& R, float rx, float ry, float rz, float r2) {
-  if (R.shape == 0) return sqrtf(r2) - R.a[0];
+  if (R.shape == 0) return (r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f) - R.a[0];
   // body frame b = M^T r
   const float b0 = R.M[0] * rx + R.M[3] * ry + R.M[6] * rz;
   const float b1 = R.M[1] * rx + R.M[4] * ry + R.M[7] * rz;

@@ -58,6 +58,24 @@ template <> struct Two<__half> {
   }
 };
 
+// mass and momentum of the two cells' values v_i (opposite directions taken
+// together: s = v_i + v_ibar, m = v_i - v_ibar)
+template <typename T>
+__device__ __forceinline__ void moments2(const typename T::raw (&d)[Q], float2& m0, float2& jx, float2& jy,
+                                         float2& jz) {
+  float2 m[Q];
+  m0 = T::val(d[0]);
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const float2 di = T::val(d[i]), dj = T::val(d[i + 1]);
+    m0 = add2(m0, add2(di, dj));
+    m[i] = sub2(di, dj);
+  }
+  jx = add2(add2(add2(m[1], m[7]), add2(m[9], m[11])), m[13]);
+  jy = add2(add2(sub2(add2(m[3], m[7]), m[9]), m[15]), m[17]);
+  jz = sub2(add2(sub2(add2(m[5], m[11]), m[13]), m[15]), m[17]);
+}
+
 }  // namespace
 
 // registers: the float kernel holds 38 FP32 arrivals, the half kernel 19
@@ -120,19 +138,9 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
     if (COUPLE)
       couple_row<2>(srec, s_rowmask[threadIdx.y + a.sub_y * (z - z0)], bd, x0, y, z, a.eps, a.inv_eps,
                     a.status, cc);
-    // moments, opposite directions taken together: s = d_i + d_ibar, m = d_i - d_ibar
-    float2 drho = T::val(d[0]), m[Q];  // m[i]: d_i - d_(i+1), i odd
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-      const float2 di = T::val(d[i]), dj = T::val(d[i + 1]);
-      drho = add2(drho, add2(di, dj));
-      m[i] = sub2(di, dj);
-    }
-    const float2 m1 = m[1], m3 = m[3], m5 = m[5], m7 = m[7], m9 = m[9], m11 = m[11];
-    const float2 m13 = m[13], m15 = m[15], m17 = m[17];
-    float2 jx = add2(add2(add2(m1, m7), add2(m9, m11)), m13);
-    float2 jy = add2(add2(sub2(add2(m3, m7), m9), m15), m17);
-    float2 jz = sub2(add2(sub2(add2(m5, m11), m13), m15), m17);
+    // mass and momentum of the arrivals
+    float2 drho, jx, jy, jz;
+    moments2<T>(d, drho, jx, jy, jz);
     if (Pop<S>::SCALED) {
       drho = mul2(drho, f2(isc));
       jx = mul2(jx, f2(isc));
@@ -217,19 +225,17 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
     // stored, for the next step's momentum exchange
     if (COUPLE && a.ilist_idx) {
       float4 mom[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        if (cc.ip0[j] >= 0) {
-#pragma unroll
-          for (int i = 0; i < Q; ++i) {
-            const float2 dv = T::val(d[i]);  // as stored
-            const float v = (j == 0 ? dv.x : dv.y) * isc;
-            mom[j].x += v;
-            if (cx(i)) mom[j].y += (float)cx(i) * v;
-            if (cy(i)) mom[j].z += (float)cy(i) * v;
-            if (cz(i)) mom[j].w += (float)cz(i) * v;
-          }
+      if (cc.ip0[0] >= 0 || cc.ip0[1] >= 0) {
+        float2 ms, mx, my, mz;  // of the values as stored
+        moments2<T>(d, ms, mx, my, mz);
+        if (Pop<S>::SCALED) {
+          ms = mul2(ms, f2(isc));
+          mx = mul2(mx, f2(isc));
+          my = mul2(my, f2(isc));
+          mz = mul2(mz, f2(isc));
         }
+        mom[0] = make_float4(ms.x, mx.x, my.x, mz.x);
+        mom[1] = make_float4(ms.y, mx.y, my.y, mz.y);
       }
       append_interior<2>(a, (unsigned)(bd.cell_off + (z * bd.ny + y) * bd.nx + x0), cc, mom);
     }
