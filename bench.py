@@ -18,7 +18,9 @@ timed one step at a time with a 512 MB L2 flush between steps.
 The JSON line adds: roofline (collision kernel, algorithmic bytes over its
 CUDA-event time), cpu_baseline (the FP64 oracle on the host), e2e (the same
 metric through the C-ABI with pinned host buffers copied every step), clocks,
-gpu_launches, and fp16 (the FP16-storage run and its error against FP32).
+gpu_launches, fp16 (the FP16-storage run and its error against FP32), and
+batched_fp16: the large dense batch (512 x 512 x 1024 cells, 50 000 spheres)
+with FP32 and with FP16 storage, its collision roofline and the FP16 error.
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 repository) on the same workload, rank 0 only.
@@ -350,6 +352,8 @@ def run_gpu(args, ws, rank, local):
                 "error_note": "max |fp16 - fp32| / max|fp32| after the same steps; X as displacement; "
                               "rho absolute; FP32 itself matches the FP64 oracle within 1e-5"}
 
+    batched = batched_fp16_leg(args, stream, peak, max_over_ranks) if args.batched else None
+
     launches_per_step = 3 if npart > 0 else 1
     line = {
         "metric": "MLUPS incl. particle coupling", "value": value, "unit": "MLUPS", "n_gpus": ws,
@@ -370,8 +374,69 @@ def run_gpu(args, ws, rank, local):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "fp16": fp16,
+        "batched_fp16": batched,
     }
     return line
+
+
+def batched_fp16_leg(args, stream, peak, max_over_ranks):
+    """The large dense batch (512 x 512 x 1024 cells, 50 000 lognormal
+    spheres, solid fraction 0.2) with FP32 and with FP16 storage of f - w:
+    step time, collision roofline and the FP16 error against FP32 after the
+    same number of steps.  Populations of 20 GB (FP32) / 10 GB (FP16) are far
+    larger than L2, so steps run back to back."""
+    import torch
+    from paper_2312_14172_gb300 import hlbm
+    w = make_workload("dense_batch")
+    cells = w["n"][0] * w["n"][1] * w["n"][2]
+    steps = max(1, min(args.steps, 40))
+    out, states = {}, {}
+    for prec in ("fp32", "fp16"):
+        lat = hlbm.from_workload(w, precision=prec, stream=stream)
+        if args.autotune:
+            lat.autotune(nsteps=3)
+        elif args.mea_mode:
+            lat.set_mea_mode(args.mea_mode)
+        lat.step(args.warmup)
+        lat.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat.sync()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        kt = lat.kernel_times(nsteps=4)
+        ach = BYTES_PER_CELL[prec] * cells / (kt["collide_stream"] / 1e3) / 1e9
+        out[prec] = {"value": cells * steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / steps,
+                     "steps": steps, "launch": list(lat.get_launch()), "momentum_exchange": lat.get_mea_mode(),
+                     "kernel_ms": kt,
+                     "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                  "frac": ach / peak, "kernel": "collide_stream"}}
+        states[prec] = (lat.steps_done, lat)
+    # error of FP16 against FP32 after the same number of steps
+    n32, lat32 = states["fp32"]
+    n16, lat16 = states["fp16"]
+    if n16 < n32:
+        lat16.step(n32 - n16)
+    elif n32 < n16:
+        lat32.step(n16 - n32)
+    s32, s16 = lat32.particle_state(), lat16.particle_state()
+    lat32.close()
+    lat16.close()
+    err = {}
+    X0 = w["particles"]["X"]
+    for key in ("X", "U", "F", "T"):
+        a32 = s32[key] - (X0 if key == "X" else 0)
+        a16 = s16[key] - (X0 if key == "X" else 0)
+        scale = float(np.abs(a32).max()) or 1.0
+        err[key] = float(np.abs(a16 - a32).max() / scale)
+    out["error_fp16_vs_fp32"] = err
+    out["workload"] = {"name": w["name"], "dims": list(w["n"]), "particles": len(w["particles"]["shape"]),
+                       "cells": cells}
+    out["speedup_fp16_over_fp32"] = out["fp16"]["value"] / out["fp32"]["value"]
+    return out
 
 
 def main():
@@ -383,6 +448,8 @@ def main():
     ap.add_argument("--workload", default="hindered_settling", choices=WORKLOADS)
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp16"])
     ap.add_argument("--no-fp16", dest="fp16", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the 512x512x1024 dense-batch FP32/FP16 leg")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--mea-mode", default=None, choices=[None, "kernel", "moments"])

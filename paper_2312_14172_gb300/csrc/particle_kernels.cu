@@ -24,33 +24,43 @@ __device__ __forceinline__ void pset(double* P, int cap, int field, int p, doubl
   P[(long long)field * cap + p] = v;
 }
 
-__device__ void build_record(const double* P, int cap, int p, int shape, int box, Rec& R) {
+// FP32 coupling record of a particle state (X, U, W, q; semi-axes A, their
+// FP32 inverses iA, radius r_inf beyond which B = 0)
+__device__ __forceinline__ void make_record(const double X[3], const double U[3], const double W[3],
+                                            const double q[4], const double A[3], const double iA[3],
+                                            double rinf, int p, int shape, int box, Rec& R) {
   double Rm[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // a sphere needs no orientation
-  if (shape != 0) {
-    double q[4];
-    for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
-    rotation_rn(q, Rm);
-  }
+  if (shape != 0) rotation_rn(q, Rm);
   for (int j = 0; j < 3; ++j) {
-    const double X = pget(P, cap, PF_X + j, p);
-    const float xh = __double2float_rn(X);
+    const float xh = __double2float_rn(X[j]);
     R.xh[j] = xh;
-    R.xl[j] = __double2float_rn(X - (double)xh);
-    R.u[j] = (float)pget(P, cap, PF_U + j, p);
-    R.w[j] = (float)pget(P, cap, PF_W + j, p);
-    const double aj = pget(P, cap, PF_A + j, p);
-    R.a[j] = __double2float_rn(aj);
-    R.ia[j] = (float)pget(P, cap, PF_IA + j, p);
+    R.xl[j] = __double2float_rn(X[j] - (double)xh);
+    R.u[j] = (float)U[j];
+    R.w[j] = (float)W[j];
+    R.a[j] = __double2float_rn(A[j]);
+    R.ia[j] = (float)iA[j];
   }
   for (int k = 0; k < 9; ++k) R.M[k] = __double2float_rn(Rm[k]);
-  const double a0 = pget(P, cap, PF_A, p);
-  R.in2 = __double2float_rn(a0 * a0);
+  R.in2 = __double2float_rn(A[0] * A[0]);
   // B vanishes beyond r_inf; a slightly larger FP32 bound keeps the test safe
-  const double rinf = pget(P, cap, PF_RINF, p) + 0.01;
-  R.rinf2 = (float)(rinf * rinf);
+  const double rb = rinf + 0.01;
+  R.rinf2 = (float)(rb * rb);
   R.shape = shape;
   R.box = box;
   R.pid = p;
+}
+
+__device__ void build_record(const double* P, int cap, int p, int shape, int box, Rec& R) {
+  double X[3], U[3], W[3], q[4], A[3], iA[3];
+  for (int j = 0; j < 3; ++j) {
+    X[j] = pget(P, cap, PF_X + j, p);
+    U[j] = pget(P, cap, PF_U + j, p);
+    W[j] = pget(P, cap, PF_W + j, p);
+    A[j] = pget(P, cap, PF_A + j, p);
+    iA[j] = pget(P, cap, PF_IA + j, p);
+  }
+  for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
+  make_record(X, U, W, q, A, iA, pget(P, cap, PF_RINF, p), p, shape, box, R);
 }
 
 template <typename S, int PAR>
@@ -164,20 +174,21 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 // Newton-Euler step of one particle: symplectic Euler for translation, the
 // body-frame Euler equations for rotation, and the quaternion update
 // q <- normalise(q + q (x) (0, omega_b) / 2)
-__device__ void integrate(const PartArgs& a, const BoxDesc& bd, int p, int shape, const double Fh[3],
-                          const double Th[3]) {
-  double* P = a.P;
-  const int cap = a.cap;
-  const double im = pget(P, cap, PF_IM, p), V = pget(P, cap, PF_V, p), rho = pget(P, cap, PF_RHO, p);
-  double X[3], U[3], W[3], iI[3], q[4];
+// Newton-Euler step of one particle in registers (Eqs. particlemotiontrans,
+// motionrot): U += F / m with F = F_h + (rho_p - rho_f) V g, X += U;
+// spheres: omega += T / I; other shapes: body-frame Euler equations
+// omega_b += (T_b - omega_b x (I omega_b)) / I with the rotation of the old
+// quaternion; q += q (x) (0, omega_b) / 2, normalised.  Returns false when
+// the new state is not finite.
+__device__ __forceinline__ bool newton_euler(const PartArgs& a, int shape, double im, double V, double rho,
+                                             const double I[3], const double iI[3], const double Fh[3],
+                                             const double Th[3], double X[3], double U[3], double W[3],
+                                             double q[4]) {
   for (int j = 0; j < 3; ++j) {
     const double F = Fh[j] + (rho - 1.0) * V * a.g[j];
-    U[j] = pget(P, cap, PF_U + j, p) + F * im;
-    X[j] = pget(P, cap, PF_X + j, p) + U[j];
-    W[j] = pget(P, cap, PF_W + j, p);
-    iI[j] = pget(P, cap, PF_II + j, p);
+    U[j] += F * im;
+    X[j] += U[j];
   }
-  for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
   double R[9], wb[3];
   rotation_rn(q, R);
   if (shape == 0) {
@@ -189,7 +200,7 @@ __device__ void integrate(const PartArgs& a, const BoxDesc& bd, int p, int shape
       wb[j] = R[0 * 3 + j] * W[0] + R[1 * 3 + j] * W[1] + R[2 * 3 + j] * W[2];
       Tb[j] = R[0 * 3 + j] * Th[0] + R[1 * 3 + j] * Th[1] + R[2 * 3 + j] * Th[2];
     }
-    for (int j = 0; j < 3; ++j) Lb[j] = wb[j] / iI[j];
+    for (int j = 0; j < 3; ++j) Lb[j] = I[j] * wb[j];
     cross3(wb, Lb, gy);
     for (int j = 0; j < 3; ++j) wb[j] += (Tb[j] - gy[j]) * iI[j];
     for (int j = 0; j < 3; ++j) W[j] = R[j * 3 + 0] * wb[0] + R[j * 3 + 1] * wb[1] + R[j * 3 + 2] * wb[2];
@@ -207,8 +218,44 @@ __device__ void integrate(const PartArgs& a, const BoxDesc& bd, int p, int shape
   }
   const double inq = 1.0 / sqrt(nq);
   for (int j = 0; j < 4; ++j) q[j] *= inq;
+  bool ok = true;
+  for (int j = 0; j < 3; ++j) ok = ok && isfinite(X[j]) && isfinite(U[j]) && isfinite(W[j]);
+  return ok;
+}
+
+// One particle per thread (GB300's FP64 units are few: the FP64 work of a
+// particle runs on one lane): the weight minus buoyancy, the Newton-Euler
+// step, the coupling record of the new state, then the per-tile lists.
+__device__ __forceinline__ void update_particle(const PartArgs& a, int p) {
+  const double* __restrict__ P = a.P;
+  const int cap = a.cap;
+  const int shape = a.shape[p], box = a.box[p];
+  const BoxDesc bd = a.boxes[box];
+  double X[3], U[3], W[3], q[4], I[3], iI[3], A[3], iA[3], Fh[3], Th[3];
+  for (int j = 0; j < 3; ++j) {
+    X[j] = pget(P, cap, PF_X + j, p);
+    U[j] = pget(P, cap, PF_U + j, p);
+    W[j] = pget(P, cap, PF_W + j, p);
+    I[j] = pget(P, cap, PF_I + j, p);
+    iI[j] = pget(P, cap, PF_II + j, p);
+    A[j] = pget(P, cap, PF_A + j, p);
+    iA[j] = pget(P, cap, PF_IA + j, p);
+  }
+  for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
+  const double im = pget(P, cap, PF_IM, p), V = pget(P, cap, PF_V, p), rho = pget(P, cap, PF_RHO, p);
+  const double rinf = pget(P, cap, PF_RINF, p), rc = pget(P, cap, PF_RC, p);
+  // force and torque of the momentum exchange: written into the table by the
+  // momentum-exchange kernel, or accumulated from the recorded moments (the
+  // accumulator is cleared for the next step)
+  double* acc = a.acc + (long long)p * 6;
+  for (int j = 0; j < 3; ++j) {
+    Fh[j] = a.from_acc ? acc[j] : pget(P, cap, PF_F + j, p);
+    Th[j] = a.from_acc ? acc[3 + j] : pget(P, cap, PF_T + j, p);
+  }
+  if (a.from_acc)
+    for (int j = 0; j < 6; ++j) acc[j] = 0.0;
+  if (!newton_euler(a, shape, im, V, rho, I, iI, Fh, Th, X, U, W, q)) atomicOr(a.status, ST_UNSTABLE);
   const int n[3] = {bd.nx, bd.ny, bd.nz};
-  bool bad = false;
   for (int j = 0; j < 3; ++j) {
     if ((bd.bc >> j) & 1) {
       if (!(X[j] > -0.5 && X[j] < n[j] - 0.5)) atomicOr(a.status, ST_LEFT_DOMAIN);
@@ -218,79 +265,58 @@ __device__ void integrate(const PartArgs& a, const BoxDesc& bd, int p, int shape
       if (X[j] >= L) X[j] -= L;
       else if (X[j] < 0.0) X[j] += L;
     }
-    bad |= !isfinite(X[j]) || !isfinite(U[j]) || !isfinite(W[j]);
   }
-  if (bad) atomicOr(a.status, ST_UNSTABLE);
   for (int j = 0; j < 3; ++j) {
-    pset(P, cap, PF_X + j, p, X[j]);
-    pset(P, cap, PF_U + j, p, U[j]);
-    pset(P, cap, PF_W + j, p, W[j]);
-    pset(P, cap, PF_F + j, p, Fh[j]);
-    pset(P, cap, PF_T + j, p, Th[j]);
+    pset(a.P, cap, PF_X + j, p, X[j]);
+    pset(a.P, cap, PF_U + j, p, U[j]);
+    pset(a.P, cap, PF_W + j, p, W[j]);
+    pset(a.P, cap, PF_F + j, p, Fh[j]);
+    pset(a.P, cap, PF_T + j, p, Th[j]);
   }
-  for (int j = 0; j < 4; ++j) pset(P, cap, PF_Q + j, p, q[j]);
-}
-
-__global__ void __launch_bounds__(32) update_kernel(PartArgs a) {
-  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long t = tid; t < a.ntiles; t += stride) a.bin_count_clear[t] = 0;
-  if (tid == 0 && a.ilist_count) *a.ilist_count = 0;  // the collision appends anew
-  if (tid >= a.np) return;
-  const int p = (int)tid;
-  const int shape = a.shape[p], box = a.box[p];
-  const BoxDesc bd = a.boxes[box];
-  // force and torque of the momentum exchange: written into the table by the
-  // momentum-exchange kernel, or accumulated by the previous collision (the
-  // accumulator is cleared for the collision of this step)
-  double Fh[3], Th[3];
-  double* acc = a.acc + (long long)p * 6;
-  for (int j = 0; j < 3; ++j) {
-    Fh[j] = a.from_acc ? acc[j] : pget(a.P, a.cap, PF_F + j, p);
-    Th[j] = a.from_acc ? acc[3 + j] : pget(a.P, a.cap, PF_T + j, p);
-  }
-  if (a.from_acc)
-    for (int j = 0; j < 6; ++j) acc[j] = 0.0;
-  integrate(a, bd, p, shape, Fh, Th);
+  for (int j = 0; j < 4; ++j) pset(a.P, cap, PF_Q + j, p, q[j]);
   Rec R;
-  build_record(a.P, a.cap, p, shape, box, R);
+  make_record(X, U, W, q, A, iA, rinf, p, shape, box, R);
   a.rec[p] = R;
   // bin tiles touched by the influence sphere, widened so that the cells next
   // to the particle's interior (which feed its momentum exchange) see it too
-  const double rbin = fmax(pget(a.P, a.cap, PF_RINF, p), pget(a.P, a.cap, PF_RC, p) + 1.5);
-  const int n[3] = {bd.nx, bd.ny, bd.nz};
+  const double rbin = fmax(rinf, rc + 1.5);
   AxisTiles at[3];
   const int T[3] = {TILE_X, TILE_Y, TILE_Z};
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    const double X = pget(a.P, a.cap, PF_X + j, p);
-    if (!(X > -1.0e6 && X < 1.0e6)) return;  // flagged by the update; not binned
-    const int lo = (int)floor(X - rbin) - 1, hi = (int)ceil(X + rbin) + 1;
+    if (!(X[j] > -1.0e6 && X[j] < 1.0e6)) return;  // flagged above; not binned
+    const int lo = (int)floor(X[j] - rbin) - 1, hi = (int)ceil(X[j] + rbin) + 1;
     at[j] = axis_tiles(lo, hi, n[j], T[j], (bd.bc >> j) & 1);
   }
+  // a row of tiles along x takes its atomics in flight together, up to
+  // MAXTX at a time (a radius of 30 cells spans at most 4 tiles of 32)
+  constexpr int MAXTX = 4;
   const int cx_ = at[0].count(), cy_ = at[1].count(), cz_ = at[2].count();
-  const int total = cx_ * cy_ * cz_;
-  // four atomics in flight per lane
-  for (int t = 0; t < total; t += 4) {
-    long long tile[4];
-    int slot[4];
+  for (int iz = 0; iz < cz_; ++iz) {
+    for (int iy = 0; iy < cy_; ++iy) {
+      const long long row = bd.tile_off + ((long long)at[2].at(iz) * bd.nty + at[1].at(iy)) * bd.ntx;
+      for (int ix0 = 0; ix0 < cx_; ix0 += MAXTX) {
+        int slot[MAXTX];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int q = t + u;
-      tile[u] = -1;
-      if (q < total) {
-        const int ix = q % cx_, r = q / cx_, iy = r % cy_, iz = r / cy_;
-        tile[u] = bd.tile_off + ((long long)at[2].at(iz) * bd.nty + at[1].at(iy)) * bd.ntx + at[0].at(ix);
-        slot[u] = atomicAdd(&a.bin_count[tile[u]], 1);
+        for (int u = 0; u < MAXTX; ++u)
+          if (ix0 + u < cx_) slot[u] = atomicAdd(&a.bin_count[row + at[0].at(ix0 + u)], 1);
+#pragma unroll
+        for (int u = 0; u < MAXTX; ++u) {
+          if (ix0 + u >= cx_) continue;
+          if (slot[u] < a.bin_cap) a.bin_ids[(row + at[0].at(ix0 + u)) * a.bin_cap + slot[u]] = p;
+          else atomicOr(a.status, ST_CAPACITY);
+        }
       }
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (tile[u] < 0) continue;
-      if (slot[u] < a.bin_cap) a.bin_ids[tile[u] * a.bin_cap + slot[u]] = p;
-      else atomicOr(a.status, ST_CAPACITY);
-    }
   }
+}
+
+__global__ void __launch_bounds__(32) update_kernel(PartArgs a) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  for (long long t = tid; t < a.ntiles; t += nthr) a.bin_count_clear[t] = 0;
+  if (tid == 0 && a.ilist_count) *a.ilist_count = 0;  // the collision appends anew
+  for (long long p = tid; p < a.np; p += nthr) update_particle(a, (int)p);
 }
 
 __global__ void records_kernel(PartArgs a) {
