@@ -302,11 +302,23 @@ cudaError_t launch_collide(const LbmArgs& a, int precision, int parity, bool wal
                         : launch_cs_prec<__half>(a, parity, walls, couple, s);
 }
 
+// one wave of resident blocks walks the whole list
+template <typename S, int PAR, bool W>
+static unsigned ml_blocks(int nsm) {
+  static int per_sm = 0;  // the same on every GPU of this architecture
+  if (per_sm == 0) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, mea_list_kernel<S, PAR, W>, 256, 0) != cudaSuccess || v < 1)
+      v = 1;
+    per_sm = v;
+  }
+  return (unsigned)((nsm > 0 ? nsm : 152) * per_sm);
+}
+
 template <typename S, int PAR>
 static cudaError_t launch_ml(const LbmArgs& a, bool walls, int nsm, cudaStream_t s) {
-  const unsigned blocks = (unsigned)(nsm > 0 ? nsm * 8 : 1216);
-  if (walls) mea_list_kernel<S, PAR, true><<<blocks, 256, 0, s>>>(a);
-  else mea_list_kernel<S, PAR, false><<<blocks, 256, 0, s>>>(a);
+  if (walls) mea_list_kernel<S, PAR, true><<<ml_blocks<S, PAR, true>(nsm), 256, 0, s>>>(a);
+  else mea_list_kernel<S, PAR, false><<<ml_blocks<S, PAR, false>(nsm), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

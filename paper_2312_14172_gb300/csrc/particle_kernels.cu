@@ -223,10 +223,20 @@ __device__ __forceinline__ bool newton_euler(const PartArgs& a, int shape, doubl
   return ok;
 }
 
+// Tiles of one particle's bin range, kept in shared memory between the
+// Newton-Euler step and the binning.
+struct BinRange {
+  AxisTiles at[3];
+  long long tile_off;
+  int ntx, nty;
+  int count;  // tiles; 0 when the particle is not binned
+};
+
 // One particle per thread (GB300's FP64 units are few: the FP64 work of a
 // particle runs on one lane): the weight minus buoyancy, the Newton-Euler
-// step, the coupling record of the new state, then the per-tile lists.
-__device__ __forceinline__ void update_particle(const PartArgs& a, int p) {
+// step and the coupling record of the new state; returns the tiles the
+// particle's bins cover.
+__device__ __forceinline__ BinRange update_particle(const PartArgs& a, int p) {
   const double* __restrict__ P = a.P;
   const int cap = a.cap;
   const int shape = a.shape[p], box = a.box[p];
@@ -279,44 +289,56 @@ __device__ __forceinline__ void update_particle(const PartArgs& a, int p) {
   a.rec[p] = R;
   // bin tiles touched by the influence sphere, widened so that the cells next
   // to the particle's interior (which feed its momentum exchange) see it too
+  BinRange br;
+  br.tile_off = bd.tile_off;
+  br.ntx = bd.ntx;
+  br.nty = bd.nty;
+  br.count = 0;
   const double rbin = fmax(rinf, rc + 1.5);
-  AxisTiles at[3];
   const int T[3] = {TILE_X, TILE_Y, TILE_Z};
-#pragma unroll
   for (int j = 0; j < 3; ++j) {
-    if (!(X[j] > -1.0e6 && X[j] < 1.0e6)) return;  // flagged above; not binned
+    if (!(X[j] > -1.0e6 && X[j] < 1.0e6)) return br;  // flagged above; not binned
     const int lo = (int)floor(X[j] - rbin) - 1, hi = (int)ceil(X[j] + rbin) + 1;
-    at[j] = axis_tiles(lo, hi, n[j], T[j], (bd.bc >> j) & 1);
+    br.at[j] = axis_tiles(lo, hi, n[j], T[j], (bd.bc >> j) & 1);
   }
-  // a row of tiles along x takes its atomics in flight together, up to
-  // MAXTX at a time (a radius of 30 cells spans at most 4 tiles of 32)
-  constexpr int MAXTX = 4;
-  const int cx_ = at[0].count(), cy_ = at[1].count(), cz_ = at[2].count();
-  for (int iz = 0; iz < cz_; ++iz) {
-    for (int iy = 0; iy < cy_; ++iy) {
-      const long long row = bd.tile_off + ((long long)at[2].at(iz) * bd.nty + at[1].at(iy)) * bd.ntx;
-      for (int ix0 = 0; ix0 < cx_; ix0 += MAXTX) {
-        int slot[MAXTX];
-#pragma unroll
-        for (int u = 0; u < MAXTX; ++u)
-          if (ix0 + u < cx_) slot[u] = atomicAdd(&a.bin_count[row + at[0].at(ix0 + u)], 1);
-#pragma unroll
-        for (int u = 0; u < MAXTX; ++u) {
-          if (ix0 + u >= cx_) continue;
-          if (slot[u] < a.bin_cap) a.bin_ids[(row + at[0].at(ix0 + u)) * a.bin_cap + slot[u]] = p;
-          else atomicOr(a.status, ST_CAPACITY);
-        }
-      }
-    }
-  }
+  br.count = br.at[0].count() * br.at[1].count() * br.at[2].count();
+  return br;
 }
 
-__global__ void __launch_bounds__(32) update_kernel(PartArgs a) {
+// UPD_P particles per block of UPD_T threads: the first UPD_P threads each
+// update one particle; then all threads add the block's particles to the
+// per-tile lists, UPD_T / UPD_P threads per particle taking its tiles in turn.
+constexpr int UPD_P = 32, UPD_T = 256;
+
+__global__ void __launch_bounds__(UPD_T) update_kernel(PartArgs a) {
+  __shared__ BinRange s_br[UPD_P];
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nthr = (long long)gridDim.x * blockDim.x;
   for (long long t = tid; t < a.ntiles; t += nthr) a.bin_count_clear[t] = 0;
   if (tid == 0 && a.ilist_count) *a.ilist_count = 0;  // the collision appends anew
-  for (long long p = tid; p < a.np; p += nthr) update_particle(a, (int)p);
+  for (long long base = blockIdx.x * (long long)UPD_P; base < a.np; base += (long long)gridDim.x * UPD_P) {
+    if (threadIdx.x < UPD_P) {
+      const long long p = base + threadIdx.x;
+      BinRange br;
+      br.count = 0;
+      if (p < a.np) br = update_particle(a, (int)p);
+      s_br[threadIdx.x] = br;
+    }
+    __syncthreads();
+    const int k = threadIdx.x % UPD_P, sub = threadIdx.x / UPD_P;
+    const BinRange& br = s_br[k];
+    const int cx_ = br.at[0].count(), cy_ = br.at[1].count();
+    const int p = (int)(base + k);
+    for (int t = sub; t < br.count; t += UPD_T / UPD_P) {
+      const int ix = t % cx_, r = t / cx_, iy = r % cy_, iz = r / cy_;
+      const long long tile = br.tile_off + ((long long)br.at[2].at(iz) * br.nty + br.at[1].at(iy)) * br.ntx +
+                             br.at[0].at(ix);
+      const int slot = atomicAdd(&a.bin_count[tile], 1);
+      if (slot < a.bin_cap) a.bin_ids[tile * a.bin_cap + slot] = p;
+      else atomicOr(a.status, ST_CAPACITY);
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void records_kernel(PartArgs a) {
@@ -341,13 +363,12 @@ cudaError_t launch_mea(const PartArgs& a, int precision, int parity, cudaStream_
 }
 
 cudaError_t launch_update(const PartArgs& a, cudaStream_t s) {
-  // one warp per block spreads the FP64 work of the particles over many SMs
-  long long blocks = (a.np + 31) / 32;
-  long long clear_blocks = (a.ntiles + 31) / 32;
-  if (clear_blocks > 8192) clear_blocks = 8192;
+  long long blocks = (a.np + UPD_P - 1) / UPD_P;
+  long long clear_blocks = (a.ntiles + UPD_T - 1) / UPD_T;
   if (clear_blocks > blocks) blocks = clear_blocks;
+  if (blocks > 65535) blocks = 65535;
   if (blocks < 1) blocks = 1;
-  update_kernel<<<(unsigned)blocks, 32, 0, s>>>(a);
+  update_kernel<<<(unsigned)blocks, UPD_T, 0, s>>>(a);
   return cudaGetLastError();
 }
 
