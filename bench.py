@@ -76,45 +76,53 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("lbm_kernels.cu", "hlbm_internal.cuh"):
+    for f in ("lbm_kernels.cu", "lbm_pair_kernels.cu", "lbm_common.cuh", "hlbm_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2312_14172_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload, precision, cells):
+def profiled_traffic(workload, precision, cells, cells_x):
     """DRAM bytes per collision launch from a committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+    taken on the current kernel source with the same cells per thread; else
+    None."""
     path = os.path.join(ROOT, "profiles", f"collide_stream_{workload}_{precision}.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("kernel_source_hash") != kernel_source_hash() or d.get("cells_per_thread", 1) != cells_x:
         return None
     per_cell = d.get("dram_bytes_per_cell")
     return None if per_cell is None else per_cell * cells
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+    """nvidia-smi samples (every 10 ms) of SM clock and throttle reasons; only
+    the samples stamped inside the timed window count (the nearest two when
+    the window is shorter than the sampling interval)."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device):
         self.device = device
         self.proc = None
+        self.window = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+
+    def mark(self, t0, t1):
+        """host wall-clock bounds of the timed region"""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -125,24 +133,30 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, smax, reasons = [], None, set()
+        import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in out.strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 7:
+            if len(parts) < 8:
                 continue
             try:
-                sm.append(float(parts[0]))
-                smax = float(parts[1])
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]),
+                             [nm for nm, v in zip(names, parts[4:8]) if v.lower().startswith("active")]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[3:7]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        sel = rows
+        if self.window is not None:
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            sel = inside if inside else sorted(rows, key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))[:2]
+        reasons = sorted({nm for r in sel for nm in r[3]})
+        return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": sel[0][2], "reasons": reasons,
+                "samples": len(sel), "in_window": bool(self.window and any(
+                    self.window[0] <= r[0] <= self.window[1] for r in rows))}
 
 
 def oracle_mlups(w, steps, warmup=0):
@@ -243,11 +257,14 @@ def run_gpu(args, ws, rank, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
+    t_host0 = time.time()
     e0.record(stream)
     lat.step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    t_host1 = time.time()
     barrier()
+    sampler.mark(t_host0, t_host1)
     clocks = sampler.stop()
     lat.sync()
     ms = e0.elapsed_time(e1)
@@ -261,10 +278,11 @@ def run_gpu(args, ws, rank, local):
     k1_ms = kt["collide_stream"]
     algo_bytes = BYTES_PER_CELL[prec] * cells
     achieved = algo_bytes / (k1_ms / 1e3) / 1e9
-    traffic = profiled_traffic(args.workload, prec, cells)
+    traffic = profiled_traffic(args.workload, prec, cells, lat_launch[2])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                "kernel": "collide_stream_kernel", "algorithmic_bytes": algo_bytes,
+                "kernel": "collide_pair_kernel" if lat_launch[2] == 2 else "collide_stream_kernel",
+                "algorithmic_bytes": algo_bytes,
                 "kernel_ms": k1_ms, "kernel_ms_mea": kt["mea"], "kernel_ms_update": kt["update"]}
 
     # ---- end to end through the C-ABI with pinned host buffers
@@ -319,6 +337,7 @@ def run_gpu(args, ws, rank, local):
         ms16 = sum(a.elapsed_time(b) for a, b in evs)
         ms16 = max_over_ranks(ms16)
         kt16 = lat16.kernel_times(nsteps=max(5, min(args.steps, 50)))
+        cx16 = lat16.get_launch()[2]
         ach16 = BYTES_PER_CELL["fp16"] * cells / (kt16["collide_stream"] / 1e3) / 1e9
         # error against FP32 after the same number of steps
         rest = fp32_steps - lat16.steps_done
@@ -347,7 +366,7 @@ def run_gpu(args, ws, rank, local):
                 "ms_per_step": ms16 / args.steps, "l2": "512 MB flush between steps",
                 "roofline": {"bound": "hbm", "achieved": ach16, "peak": peak, "unit": "GB/s",
                              "frac": ach16 / peak, "kernel_ms": kt16["collide_stream"],
-                             "traffic": profiled_traffic(args.workload, "fp16", cells)},
+                             "traffic": profiled_traffic(args.workload, "fp16", cells, cx16)},
                 "error_vs_fp32": err,
                 "error_note": "max |fp16 - fp32| / max|fp32| after the same steps; X as displacement; "
                               "rho absolute; FP32 itself matches the FP64 oracle within 1e-5"}
@@ -381,7 +400,7 @@ def run_gpu(args, ws, rank, local):
 
 def batched_fp16_leg(args, stream, peak, max_over_ranks):
     """The large dense batch (512 x 512 x 1024 cells, 50 000 lognormal
-    spheres, solid fraction 0.2) with FP32 and with FP16 storage of f - w:
+    spheres, realised solid fraction 0.075) with FP32 and with FP16 storage of f - w:
     step time, collision roofline and the FP16 error against FP32 after the
     same number of steps.  Populations of 20 GB (FP32) / 10 GB (FP16) are far
     larger than L2, so steps run back to back."""
