@@ -12,6 +12,8 @@
 // one instruction for both cells.  Requires an even nx in every box; a
 // block is 16 x sub_y threads over the same 32 x sub_y x sub_z brick as the
 // one-cell kernel.
+#include <type_traits>
+
 #include "lbm_common.cuh"
 
 namespace hlbm {
@@ -101,11 +103,14 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
   S* const f = reinterpret_cast<S*>(a.f);
   const float sc = Pop<S>::SCALED ? a.scale : 1.0f, isc = Pop<S>::SCALED ? a.inv_scale : 1.0f;
 
-  // one z slice at a time: an unrolled loop would hold two slices' arrivals
-#pragma unroll 1
-  for (int z = z0; z < z1; ++z) {
+  // Walls need selects in every direction, but only the slices and rows next
+  // to a wall and the lanes at an x wall meet one; everything else runs the
+  // slice without them.
+  const bool row_free = !WALLS || (!((bd.bc & 2) && (y == 0 || y == bd.ny - 1)) && !rb.wl && !rb.wr);
+  auto slice = [&](auto wtag, int z) {
+    constexpr bool W = decltype(wtag)::value;
     int zb[3];
-    slice_blocks<WALLS>(bd, z, zb);
+    slice_blocks<W>(bd, z, zb);
     S* const own = cell_ptr(f, zb[1] + rb.yb[1] + rb.xb, rb.xin);  // slot 0 of cell x0
     // arrivals (stored units), both cells
     typename T::raw d[Q];
@@ -116,7 +121,7 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
       } else {
         // slot ibar of x - c_i, or slot i of x when x - c_i lies beyond a wall
         const int by = rb.yb[1 - cy(i)], bz = zb[1 - cz(i)];
-        const bool wall = WALLS && (by < 0 || bz < 0);
+        const bool wall = W && (by < 0 || bz < 0);
         const S* src = cell_ptr(f, wall ? 0 : bz + by + rb.xb, rb.xin) + opp(i) * VB;  // x0 of the source row
         const S* mine = own + i * VB;
         if (cx(i) == 0) {
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
         T::st(own + opp(i) * VB, d[i]);
       } else {
         const int by = rb.yb[1 + cy(i)], bz = zb[1 + cz(i)];
-        const bool wall = WALLS && (by < 0 || bz < 0);
+        const bool wall = W && (by < 0 || bz < 0);
         S* dst = cell_ptr(f, wall ? 0 : bz + by + rb.xb, rb.xin) + i * VB;  // x0 of the destination row
         S* mine = own + opp(i) * VB;
         if (cx(i) == 0) {
@@ -239,6 +244,14 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
       }
       append_interior<2>(a, (unsigned)(bd.cell_off + (z * bd.ny + y) * bd.nx + x0), cc, mom);
     }
+  };
+  // one z slice at a time: an unrolled loop would hold two slices' arrivals
+#pragma unroll 1
+  for (int z = z0; z < z1; ++z) {
+    if (WALLS && !(row_free && !((bd.bc & 4) && (z == 0 || z == bd.nz - 1))))
+      slice(std::integral_constant<bool, WALLS>{}, z);
+    else
+      slice(std::integral_constant<bool, false>{}, z);
   }
 }
 
