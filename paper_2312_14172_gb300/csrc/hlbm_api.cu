@@ -152,6 +152,8 @@ struct hlbm_ctx {
   // [0][parity]: step with the momentum-exchange kernel (after any change of
   // state); [1][parity]: step that takes the sums the previous collision made
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  // two steps in one graph: [m][parity] = step(parity, m) then step(1 - parity)
+  cudaGraphExec_t exec2[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool graphs_ok = false;
   bool moments_valid = false;  // the accumulator holds this state's momentum exchange
   std::vector<int> h_shape, h_box;  // host copies
@@ -243,46 +245,53 @@ static PartArgs part_args(const hlbm_ctx* h, int parity) {
 // moments of the cells inside particles, and the momentum exchange of this
 // step runs from them; otherwise the bounding-box kernel computes it from
 // the populations alone (always on the first step after a change of state).
+// Kernels captured into a step's graph use programmatic dependent launch.
 static cudaError_t enqueue_step(hlbm_ctx* h, int parity, bool moments, cudaStream_t s) {
   cudaError_t e;
+  LbmArgs la = lbm_args(h, parity);
+  la.pdl = 1;
   if (h->np > 0) {
     PartArgs pa = part_args(h, parity);
+    pa.pdl = 1;
     pa.from_acc = moments ? 1 : 0;
     if (moments) {
-      if ((e = launch_mea_moments(lbm_args(h, parity), h->prm.precision, parity, h->walls, h->nsm, s)) != cudaSuccess)
-        return e;
+      if ((e = launch_mea_moments(la, h->prm.precision, parity, h->walls, h->nsm, s)) != cudaSuccess) return e;
     } else if ((e = launch_mea(pa, h->prm.precision, parity, s)) != cudaSuccess) {
       return e;
     }
     if ((e = launch_update(pa, s)) != cudaSuccess) return e;
   }
-  return launch_collide(lbm_args(h, parity), h->prm.precision, parity, h->walls, h->np > 0, s);
+  return launch_collide(la, h->prm.precision, parity, h->walls, h->np > 0, s);
 }
 
 static void drop_graphs(hlbm_ctx* h) {
   for (int f = 0; f < 2; ++f)
     for (int k = 0; k < 2; ++k) {
       if (h->exec[f][k]) cudaGraphExecDestroy(h->exec[f][k]);
+      if (h->exec2[f][k]) cudaGraphExecDestroy(h->exec2[f][k]);
       h->exec[f][k] = nullptr;
+      h->exec2[f][k] = nullptr;
     }
   h->graphs_ok = false;
 }
 
 static int build_graphs(hlbm_ctx* h) {
   drop_graphs(h);
-  for (int gi = 0; gi < 4; ++gi) {
-    const int moments = gi >> 1, parity = gi & 1;
-    if (moments && h->mea_mode != HLBM_MEA_MOMENTS) continue;
+  const bool mom = h->mea_mode == HLBM_MEA_MOMENTS;
+  for (int gi = 0; gi < 8; ++gi) {
+    const int two = gi >> 2, moments = (gi >> 1) & 1, parity = gi & 1;
+    if (moments && !mom) continue;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_step(h, parity, moments != 0, h->cap_stream);
+    if (e == cudaSuccess && two) e = enqueue_step(h, 1 - parity, mom, h->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       return fail(h, HLBM_ERR_CUDA, std::string("graph capture: ") +
                                         cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&h->exec[moments][parity], g, 0);
+    e = cudaGraphInstantiate(two ? &h->exec2[moments][parity] : &h->exec[moments][parity], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, HLBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
@@ -636,9 +645,16 @@ int hlbm_step(hlbm_handle h, int nsteps) {
     const int rc = build_graphs(h);
     if (rc != HLBM_OK) return rc;
   }
-  for (int k = 0; k < nsteps; ++k) {
+  for (int k = 0; k < nsteps;) {
     const int moments = (h->moments_valid && h->np > 0) ? 1 : 0;
-    CK(cudaGraphLaunch(h->exec[moments][(h->steps + k) & 1], h->stream));
+    const int parity = (int)((h->steps + k) & 1);
+    if (nsteps - k >= 2) {
+      CK(cudaGraphLaunch(h->exec2[moments][parity], h->stream));
+      k += 2;
+    } else {
+      CK(cudaGraphLaunch(h->exec[moments][parity], h->stream));
+      k += 1;
+    }
     h->moments_valid = h->mea_mode == HLBM_MEA_MOMENTS;
   }
   h->steps += nsteps;

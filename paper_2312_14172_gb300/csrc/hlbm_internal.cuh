@@ -182,7 +182,30 @@ __device__ __forceinline__ Nbr<WALLS> make_nbr(const BoxDesc& bd, int x, int y, 
 }
 
 
+// Programmatic dependent launch: a step's kernels, captured in one graph,
+// are launched so that the next one is scheduled while the current one
+// runs; each waits for its predecessor's results before reading them.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 struct LbmArgs {
+  int pdl;                  // launch with programmatic dependent launch (host side only)
   void* f;                  // populations, blocked layout (float* or __half*)
   long long ncell;          // cells of all boxes (global cell numbering)
   const BoxDesc* boxes;
@@ -213,6 +236,7 @@ struct LbmArgs {
 };
 
 struct PartArgs {
+  int pdl;                  // launch with programmatic dependent launch (host side only)
   double* P;                // FP64 table, field-major with stride cap
   int cap, np;
   const int* shape;         // [np]

@@ -21,29 +21,14 @@ namespace hlbm {
 #define HLBM_CS_MINBLOCKS 4
 #endif
 
-// load of the post-streaming deviations f_i(x) - w_i of the cell whose slot
-// 0 is element e (AA accessor): even parity: slot i of x; odd parity: slot
-// ibar of x - c_i, or slot i of x when x - c_i lies beyond a wall
-template <typename S, int PAR>
-__device__ __forceinline__ void load_arrivals(const S* f, const NbrB& nb, long long e, float inv_s,
-                                              float d[Q]) {
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (PAR == 0 || i == 0) {
-      d[i] = Pop<S>::ld(f + e + i * VB, inv_s);
-    } else {
-      const long long src = nb.at(-cx(i), -cy(i), -cz(i));
-      d[i] = Pop<S>::ld(src >= 0 ? f + src + opp(i) * VB : f + e + i * VB, inv_s);
-    }
-  }
-}
-
 template <typename S, int PAR, bool WALLS, bool COUPLE>
 __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(LbmArgs a) {
   __shared__ Rec srec[COUPLE ? MAX_CAND : 1];
   // per row of the brick (local y + sub_y * local z): the candidates whose
   // influence sphere meets the row
   __shared__ unsigned long long s_rowmask[COUPLE ? TILE_Y * TILE_Z : 1];
+  pdl_trigger();
+  pdl_wait();
   const Brick k = brick_of(a);
   const BoxDesc& bd = k.bd;
   if (COUPLE) load_candidates(a, k, srec, s_rowmask);
@@ -195,6 +180,8 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
 
 template <typename S, int PAR, bool WALLS>
 __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
+  pdl_trigger();
+  pdl_wait();
   const int n = min(*a.ilist_count, (int)a.ilist_cap);
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -222,9 +209,28 @@ __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
       r[0] = offset_fp32(x, bd.nx, bd.bc & 1, R.xh[0], R.xl[0]);
       r[1] = offset_fp32(y, bd.ny, bd.bc & 2, R.xh[1], R.xl[1]);
       r[2] = offset_fp32(z, bd.nz, bd.bc & 4, R.xh[2], R.xl[2]);
-      const NbrB nb = make_nbr_blocked(bd, x, y, z);
+      // arrivals f_i(x) (AA accessor): slot i of x (even parity), slot ibar of
+      // x - c_i (odd parity), or slot i of x when x - c_i lies beyond a wall
+      const RowBlocks rb = row_blocks<WALLS>(bd, x, y, 1);
+      int zb[3];
+      slice_blocks<WALLS>(bd, z, zb);
+      const S* own = cell_ptr(fbase, zb[1] + rb.yb[1] + rb.xb, rb.xin);
       float d[Q];
-      load_arrivals<S, PAR>(fbase, nb, elem_of(bd, x, y, z), a.inv_scale, d);
+      unsigned walls = 0;  // bit i: x - c_i lies beyond a wall
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const int by = rb.yb[1 - cy(i)], bz = zb[1 - cz(i)];
+        const bool wall =
+            WALLS && i > 0 && (by < 0 || bz < 0 || (cx(i) > 0 && rb.wl) || (cx(i) < 0 && rb.wr));
+        if (wall) walls |= 1u << i;
+        if (PAR == 0 || i == 0) {
+          d[i] = Pop<S>::ld(own + i * VB, a.inv_scale);
+        } else {
+          const int dx = cx(i) > 0 ? rb.dl : (cx(i) < 0 ? rb.dr : 0);
+          const S* src = wall ? own + i * VB : cell_ptr(fbase, bz + by + rb.xb, rb.xin) + (dx + opp(i) * VB);
+          d[i] = Pop<S>::ld(src, a.inv_scale);
+        }
+      }
       float ms = 0.f, px = 0.f, py = 0.f, pz = 0.f;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
@@ -243,7 +249,7 @@ __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
       if (WALLS) {
 #pragma unroll
         for (int i = 1; i < Q; ++i)
-          if (nb.at(-cx(i), -cy(i), -cz(i)) < 0) {
+          if ((walls >> i) & 1u) {
             const float v = 2.0f * ((float)wq(i) + d[i]);
             if (cx(i)) F[0] -= (float)cx(i) * v;
             if (cy(i)) F[1] -= (float)cy(i) * v;
@@ -279,8 +285,7 @@ __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
 template <typename S, int PAR, bool W, bool C>
 static cudaError_t launch_cs(const LbmArgs& a, cudaStream_t s) {
   dim3 block(TILE_X, a.sub_y);
-  collide_stream_kernel<S, PAR, W, C><<<(unsigned)a.nbricks, block, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_k(collide_stream_kernel<S, PAR, W, C>, dim3((unsigned)a.nbricks), block, 0, s, a.pdl != 0, a);
 }
 
 template <typename S>
@@ -317,9 +322,9 @@ static unsigned ml_blocks(int nsm) {
 
 template <typename S, int PAR>
 static cudaError_t launch_ml(const LbmArgs& a, bool walls, int nsm, cudaStream_t s) {
-  if (walls) mea_list_kernel<S, PAR, true><<<ml_blocks<S, PAR, true>(nsm), 256, 0, s>>>(a);
-  else mea_list_kernel<S, PAR, false><<<ml_blocks<S, PAR, false>(nsm), 256, 0, s>>>(a);
-  return cudaGetLastError();
+  if (walls) return launch_k(mea_list_kernel<S, PAR, true>, dim3(ml_blocks<S, PAR, true>(nsm)), dim3(256), 0, s,
+                            a.pdl != 0, a);
+  return launch_k(mea_list_kernel<S, PAR, false>, dim3(ml_blocks<S, PAR, false>(nsm)), dim3(256), 0, s, a.pdl != 0, a);
 }
 
 cudaError_t launch_mea_moments(const LbmArgs& a, int precision, int parity, bool walls, int nsm,

@@ -90,6 +90,8 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
   using T = Two<S>;
   __shared__ Rec srec[COUPLE ? MAX_CAND : 1];
   __shared__ unsigned long long s_rowmask[COUPLE ? TILE_Y * TILE_Z : 1];
+  pdl_trigger();
+  pdl_wait();
   const Brick k = brick_of(a);
   const BoxDesc& bd = k.bd;
   if (COUPLE) load_candidates(a, k, srec, s_rowmask);
@@ -258,8 +260,7 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
 template <typename S, int PAR, bool W, bool C>
 static cudaError_t launch_cp(const LbmArgs& a, cudaStream_t s) {
   dim3 block(TILE_X / 2, a.sub_y);
-  collide_pair_kernel<S, PAR, W, C><<<(unsigned)a.nbricks, block, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_k(collide_pair_kernel<S, PAR, W, C>, dim3((unsigned)a.nbricks), block, 0, s, a.pdl != 0, a);
 }
 
 template <typename S>

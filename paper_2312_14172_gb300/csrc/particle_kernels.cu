@@ -65,6 +65,8 @@ __device__ void build_record(const double* P, int cap, int p, int shape, int box
 
 template <typename S, int PAR>
 __global__ void __launch_bounds__(128) mea_kernel(PartArgs a) {
+  pdl_trigger();
+  pdl_wait();
   const int chunk = blockIdx.x;
   const int p = a.chunk_p[chunk], iz = a.chunk_q[chunk];
   __shared__ Rec R;
@@ -312,6 +314,8 @@ constexpr int UPD_P = 32, UPD_T = 256;
 
 __global__ void __launch_bounds__(UPD_T) update_kernel(PartArgs a) {
   __shared__ BinRange s_br[UPD_P];
+  pdl_trigger();
+  pdl_wait();
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nthr = (long long)gridDim.x * blockDim.x;
   for (long long t = tid; t < a.ntiles; t += nthr) a.bin_count_clear[t] = 0;
@@ -352,14 +356,12 @@ __global__ void records_kernel(PartArgs a) {
 cudaError_t launch_mea(const PartArgs& a, int precision, int parity, cudaStream_t s) {
   if (a.np <= 0 || a.nchunks <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)a.nchunks;
-  if (precision == 0) {
-    if (parity == 0) mea_kernel<float, 0><<<grid, 128, 0, s>>>(a);
-    else mea_kernel<float, 1><<<grid, 128, 0, s>>>(a);
-  } else {
-    if (parity == 0) mea_kernel<__half, 0><<<grid, 128, 0, s>>>(a);
-    else mea_kernel<__half, 1><<<grid, 128, 0, s>>>(a);
-  }
-  return cudaGetLastError();
+  const bool pdl = a.pdl != 0;
+  if (precision == 0)
+    return parity == 0 ? launch_k(mea_kernel<float, 0>, dim3(grid), dim3(128), 0, s, pdl, a)
+                       : launch_k(mea_kernel<float, 1>, dim3(grid), dim3(128), 0, s, pdl, a);
+  return parity == 0 ? launch_k(mea_kernel<__half, 0>, dim3(grid), dim3(128), 0, s, pdl, a)
+                     : launch_k(mea_kernel<__half, 1>, dim3(grid), dim3(128), 0, s, pdl, a);
 }
 
 cudaError_t launch_update(const PartArgs& a, cudaStream_t s) {
@@ -368,8 +370,7 @@ cudaError_t launch_update(const PartArgs& a, cudaStream_t s) {
   if (clear_blocks > blocks) blocks = clear_blocks;
   if (blocks > 65535) blocks = 65535;
   if (blocks < 1) blocks = 1;
-  update_kernel<<<(unsigned)blocks, UPD_T, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_k(update_kernel, dim3((unsigned)blocks), dim3(UPD_T), 0, s, a.pdl != 0, a);
 }
 
 cudaError_t launch_records(const PartArgs& a, cudaStream_t s) {
