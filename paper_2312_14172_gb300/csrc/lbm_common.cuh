@@ -235,6 +235,11 @@ __device__ __forceinline__ void couple_row(const Rec* srec, unsigned long long r
     if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
     const float ry = __fsub_rn(r0y, R.xl[1]), rz = __fsub_rn(r0z, R.xl[2]);
     const float d2 = ry * ry + rz * rz;
+    // a sphere's indicator is 1 within r <= a - eps/2 and 0 beyond a + eps/2:
+    // only cells in that shell need the distance and the ramp
+    const bool sph = R.shape == 0;
+    const float a_in = R.a[0] - 0.5f * eps, a_out = R.a[0] + 0.5f * eps;
+    const float r2_in = a_in > 0.0f ? a_in * a_in : -1.0f, r2_out = a_out * a_out;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       float r0x = (float)(x + j) - R.xh[0];
@@ -248,7 +253,8 @@ __device__ __forceinline__ void couple_row(const Rec* srec, unsigned long long r
           else if (cc.ip1[j] < 0) cc.ip1[j] = R.pid;
           else atomicOr(status, ST_CAPACITY);  // three overlapping particles
         }
-        const float B = indicator(sdf(R, rx, ry, rz, r2), eps, inv_eps);
+        const float B = !sph ? indicator(sdf(R, rx, ry, rz, r2), eps, inv_eps)
+                        : (r2 <= r2_in ? 1.0f : (r2 >= r2_out ? 0.0f : indicator(sdf(R, rx, ry, rz, r2), eps, inv_eps)));
         if (B > cc.B[j] || (B == cc.B[j] && B > 0.0f && R.pid < cc.bestp[j])) {
           cc.B[j] = B;
           cc.bestp[j] = R.pid;
