@@ -180,8 +180,10 @@ int hlbm_get_launch(hlbm_handle h, int* tile_y, int* tile_z, int* cells_x);
  *                     minus u_p times the mass gained, from the arrivals alone.
  *                     The bounding-box kernel still runs on the first step
  *                     after any change of state.  Needs max_particles > 0; the
- *                     list holds up to half the lattice's cells
- *                     (HLBM_ERR_CAPACITY beyond).
+ *                     list is split into 64 stripes that the collision's
+ *                     blocks fill in turn, each holding 1/64 of half the
+ *                     lattice's cells (at least 4096 entries);
+ *                     HLBM_ERR_CAPACITY when one overflows.
  * Both give the same force and torque up to FP32 summation order. */
 #define HLBM_MEA_KERNEL 0
 #define HLBM_MEA_MOMENTS 1

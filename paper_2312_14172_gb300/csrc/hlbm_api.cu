@@ -9,6 +9,7 @@
 //   3. EDM coupling, collision and streaming   (collide_stream_kernel)
 // Steps alternate between the two AA parities, so each parity is captured
 // once as a CUDA graph and the graphs are launched alternately.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -91,12 +92,15 @@ bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& 
   L.off_pc0 = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
   L.off_pnc = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
   L.off_done = o; o = align_up(o + sizeof(int) * (size_t)L.cap);
-  // interior-cell list for the momentum exchange from moments: room for half
-  // of all cells (more than any packing of non-overlapping particles needs)
-  L.ilist_cap = L.cap > 0 ? (L.ncell + 1) / 2 : 0;
-  L.off_lcnt = o; o = align_up(o + sizeof(int));
-  L.off_lidx = o; o = align_up(o + sizeof(int2) * (size_t)L.ilist_cap);
-  L.off_lmom = o; o = align_up(o + sizeof(float4) * (size_t)L.ilist_cap);
+  // interior-cell list for the momentum exchange from moments, in
+  // ILIST_STRIPES stripes: together room for half of all cells (more than
+  // any packing of non-overlapping particles needs), and each stripe for two
+  // entries per cell of a whole brick
+  L.ilist_cap = L.cap > 0 ? std::max((L.ncell / 2 + ILIST_STRIPES - 1) / ILIST_STRIPES,
+                                     (long long)2 * TILE_X * TILE_Y * TILE_Z) : 0;
+  L.off_lcnt = o; o = align_up(o + sizeof(int) * ILIST_STRIPES);
+  L.off_lidx = o; o = align_up(o + sizeof(int2) * (size_t)L.ilist_cap * ILIST_STRIPES);
+  L.off_lmom = o; o = align_up(o + sizeof(float4) * (size_t)L.ilist_cap * ILIST_STRIPES);
   for (int k = 0; k < 2; ++k) {
     L.off_cnt[k] = o; o = align_up(o + sizeof(int) * (size_t)L.ntiles);
     L.off_ids[k] = o; o = align_up(o + sizeof(int) * (size_t)L.ntiles * L.bin_cap);

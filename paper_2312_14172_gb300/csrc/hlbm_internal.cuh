@@ -84,6 +84,9 @@ enum {
 // (circumscribed radius <= 30 cells)
 constexpr int MAX_PLANES = 64;
 
+// stripes of the list of interior cells (a power of two)
+constexpr int ILIST_STRIPES = 64;
+
 // FP32 coupling record of one particle (128 bytes)
 struct __align__(16) Rec {
   float xh[3], xl[3];  // centre as float pair: X = xh + xl
@@ -225,7 +228,11 @@ struct LbmArgs {
   // list of the cells inside particles, appended by the collision for the
   // next step's momentum exchange (nullptr: not recorded):
   //   ilist_idx[k] = (global cell index, particle), ilist_mom[k] = mass and
-  //   momentum of the cell's post-collision deviations as stored
+  //   momentum of the cell's post-collision deviations as stored.
+  // It is split into ILIST_STRIPES stripes of ilist_cap entries, stripe s at
+  // [s * ilist_cap, (s + 1) * ilist_cap) with its own count ilist_count[s];
+  // a collision block appends to stripe (block index mod ILIST_STRIPES), so
+  // the appends of the whole grid do not contend for one counter.
   int* ilist_count;
   int2* ilist_idx;
   float4* ilist_mom;
@@ -259,7 +266,7 @@ struct PartArgs {
   // the same sums accumulated by the previous collision, [cap][6]
   double* acc;
   int from_acc;             // 1: the update takes acc, 0: the table's F and T
-  int* ilist_count;         // reset by the update for the next collision
+  int* ilist_count;         // [ILIST_STRIPES], reset by the update for the next collision
   // bins written by the update (this step) and cleared (other parity)
   int* bin_count;
   int* bin_ids;

@@ -303,10 +303,12 @@ __device__ __forceinline__ void append_interior(const LbmArgs& a, unsigned g, co
     total += __popc(m) << b;
   }
   const int leader = __ffs(act) - 1;
+  const int stripe = (int)(blockIdx.x & (ILIST_STRIPES - 1));
   int base = 0;
-  if ((int)lane_id() == leader) base = atomicAdd(a.ilist_count, total);
+  if ((int)lane_id() == leader) base = atomicAdd(&a.ilist_count[stripe], total);
   base = __shfl_sync(act, base, leader);
-  long long k = (long long)base + before;
+  long long k = (long long)base + before;  // within the stripe
+  const long long k0 = (long long)stripe * a.ilist_cap;
 #pragma unroll
   for (int j = 0; j < N; ++j) {
 #pragma unroll
@@ -314,8 +316,8 @@ __device__ __forceinline__ void append_interior(const LbmArgs& a, unsigned g, co
       const int p = e == 0 ? cc.ip0[j] : cc.ip1[j];
       if (p >= 0) {
         if (k < a.ilist_cap) {
-          a.ilist_idx[k] = make_int2((int)(g + j), p);
-          a.ilist_mom[k] = mom[j];
+          a.ilist_idx[k0 + k] = make_int2((int)(g + j), p);
+          a.ilist_mom[k0 + k] = mom[j];
         } else {
           atomicOr(a.status, ST_CAPACITY);
         }

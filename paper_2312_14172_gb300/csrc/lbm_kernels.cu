@@ -182,15 +182,42 @@ template <typename S, int PAR, bool WALLS>
 __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
   pdl_trigger();
   pdl_wait();
-  const int n = min(*a.ilist_count, (int)a.ilist_cap);
+  // the stripes' entries numbered one after the other: s_first[s] is the
+  // number of entries in the stripes before s
+  __shared__ long long s_first[ILIST_STRIPES + 1];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    long long c0 = min((long long)a.ilist_count[lane], a.ilist_cap);
+    long long c1 = min((long long)a.ilist_count[lane + 32], a.ilist_cap);
+    long long s0 = c0, s1 = c1;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const long long t0 = __shfl_up_sync(0xffffffffu, s0, off), t1 = __shfl_up_sync(0xffffffffu, s1, off);
+      if (lane >= off) { s0 += t0; s1 += t1; }
+    }
+    const long long tot0 = __shfl_sync(0xffffffffu, s0, 31);
+    s_first[lane] = s0 - c0;
+    s_first[lane + 32] = tot0 + s1 - c1;
+    if (lane == 31) s_first[ILIST_STRIPES] = tot0 + s1;
+  }
+  __syncthreads();
+  const long long n = s_first[ILIST_STRIPES];
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const S* fbase = reinterpret_cast<const S*>(a.f);
   for (long long k0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); k0 < n; k0 += stride) {
-    const long long k = k0 + lane;
-    bool valid = k < n;
+    const long long kc = k0 + lane;  // compact index over all stripes
+    bool valid = kc < n;
     int pid = -1;
     float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
+    long long k = 0;  // entry index in the striped list
+    if (valid) {
+      int st = 0;  // the last stripe whose first entry is at or before kc
+#pragma unroll
+      for (int step = ILIST_STRIPES / 2; step > 0; step >>= 1)
+        if (s_first[st + step] <= kc) st += step;
+      k = (long long)st * a.ilist_cap + (kc - s_first[st]);
+    }
     const int2 e = valid ? a.ilist_idx[k] : make_int2(0, -1);
     // an entry names a particle and a cell of that particle's box; anything
     // else was never written by the collision and is skipped with a flag
@@ -198,7 +225,7 @@ __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
     const BoxDesc bd = a.boxes[valid ? a.rec[e.y].box : 0];
     const long long cl = (long long)e.x - bd.cell_off;
     if (valid && (cl < 0 || cl >= (long long)bd.nx * bd.ny * bd.nz)) valid = false;
-    if (k < n && !valid) atomicOr(a.status, ST_INTERNAL);
+    if (kc < n && !valid) atomicOr(a.status, ST_INTERNAL);
     if (valid) {
       const float4 sd = a.ilist_mom[k];
       pid = e.y;

@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(UPD_T) update_kernel(PartArgs a) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nthr = (long long)gridDim.x * blockDim.x;
   for (long long t = tid; t < a.ntiles; t += nthr) a.bin_count_clear[t] = 0;
-  if (tid == 0 && a.ilist_count) *a.ilist_count = 0;  // the collision appends anew
+  if (tid < ILIST_STRIPES && a.ilist_count) a.ilist_count[tid] = 0;  // the collision appends anew
   for (long long base = blockIdx.x * (long long)UPD_P; base < a.np; base += (long long)gridDim.x * UPD_P) {
     if (threadIdx.x < UPD_P) {
       const long long p = base + threadIdx.x;
