@@ -204,6 +204,22 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
     pair(13, wr2, wd2, w3r2, sub2(ux, uz), sub2(vx, vz));
     pair(15, wr2, wd2, w3r2, add2(uy, uz), add2(vy, vz));
     pair(17, wr2, wd2, w3r2, sub2(uy, uz), sub2(vy, vz));
+    // cells inside a particle record the mass and momentum they send out, as
+    // stored, for the next step's momentum exchange (taken before the stores,
+    // so that the values need not stay in registers through them)
+    float4 mom[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    if (COUPLE && a.ilist_idx && (cc.ip0[0] >= 0 || cc.ip0[1] >= 0)) {
+      float2 ms, mx, my, mz;  // of the values as stored
+      moments2<T>(d, ms, mx, my, mz);
+      if (Pop<S>::SCALED) {
+        ms = mul2(ms, f2(isc));
+        mx = mul2(mx, f2(isc));
+        my = mul2(my, f2(isc));
+        mz = mul2(mz, f2(isc));
+      }
+      mom[0] = make_float4(ms.x, mx.x, my.x, mz.x);
+      mom[1] = make_float4(ms.y, mx.y, my.y, mz.y);
+    }
     // store the post-collision deviations (now in d), streamed (AA pattern):
     // slot i of x + c_i, or slot ibar of x when x + c_i lies beyond a wall
 #pragma unroll
@@ -228,24 +244,8 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
         }
       }
     }
-    // cells inside a particle record the mass and momentum they send out, as
-    // stored, for the next step's momentum exchange
-    if (COUPLE && a.ilist_idx) {
-      float4 mom[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-      if (cc.ip0[0] >= 0 || cc.ip0[1] >= 0) {
-        float2 ms, mx, my, mz;  // of the values as stored
-        moments2<T>(d, ms, mx, my, mz);
-        if (Pop<S>::SCALED) {
-          ms = mul2(ms, f2(isc));
-          mx = mul2(mx, f2(isc));
-          my = mul2(my, f2(isc));
-          mz = mul2(mz, f2(isc));
-        }
-        mom[0] = make_float4(ms.x, mx.x, my.x, mz.x);
-        mom[1] = make_float4(ms.y, mx.y, my.y, mz.y);
-      }
+    if (COUPLE && a.ilist_idx)
       append_interior<2>(a, (unsigned)(bd.cell_off + (z * bd.ny + y) * bd.nx + x0), cc, mom);
-    }
   };
   // one z slice at a time: an unrolled loop would hold two slices' arrivals
 #pragma unroll 1
