@@ -139,6 +139,46 @@ def sequential_insertion(rng, n_box, radii, bc, gap, max_tries=200000, axes=None
     return np.array(centres).reshape(-1, 3)
 
 
+def sequential_insertion_spheres(rng, n_box, radii, bc, gap, batch=64, max_batches=400):
+    """Random sequential insertion of spheres for boxes of up to a few thousand
+    spheres: each round draws `batch` candidate centres uniformly and tests
+    them against every accepted sphere at once (minimum image on periodic
+    axes, the gap kept to walls); the first candidate that keeps the gap to
+    all is accepted.  Returns centres (k, 3) of the first k spheres that could
+    be placed within `max_batches` rounds each."""
+    n_box = np.asarray(n_box, float)
+    radii = np.asarray(radii, float)
+    count = len(radii)
+    wall = np.array([(bc >> a) & 1 for a in range(3)], bool)
+    centres = np.zeros((count, 3))
+    k = 0
+    for j in range(count):
+        r = radii[j]
+        lo = np.where(wall, r + gap + 0.5, 0.0)
+        hi = np.where(wall, n_box - 1.0 - r - gap + 0.5, n_box)
+        if np.any(hi <= lo):
+            break
+        placed = False
+        for _ in range(max_batches):
+            c = lo + rng.random((batch, 3)) * (hi - lo)
+            if k == 0:
+                ok = np.ones(batch, bool)
+            else:
+                d = c[:, None, :] - centres[None, :k, :]
+                per = ~wall
+                d[:, :, per] -= n_box[per] * np.round(d[:, :, per] / n_box[per])
+                lim = r + radii[:k] + gap
+                ok = np.all(np.einsum("bka,bka->bk", d, d) >= lim[None, :] ** 2, axis=1)
+            if ok.any():
+                centres[k] = c[int(np.argmax(ok))]
+                k += 1
+                placed = True
+                break
+        if not placed:
+            break
+    return centres[:k].copy()
+
+
 def body_axis_z(quat):
     """World direction of the body z-axis of unit quaternions (w, x, y, z)."""
     w, x, y, z = quat[:, 0], quat[:, 1], quat[:, 2], quat[:, 3]
@@ -241,7 +281,7 @@ def ensemble(nboxes=64, edge=(64, 96), count=(10, 200), r_range=(3.0, 7.0), phi_
         frac = np.cumsum(4.0 / 3.0 * math.pi * radii ** 3) / vol
         keep = int(np.searchsorted(frac, phi_max, side="right"))
         radii = radii[:max(1, keep)]
-        X = sequential_insertion(rng, n, radii, 0, eps + 1.0)
+        X = sequential_insertion_spheres(rng, n, radii, 0, eps + 1.0)
         k = len(X)
         P = _particles([SPHERE] * k, np.repeat(radii[:k, None], 3, axis=1), X, rho_ratio)
         boxes.append(_workload(f"box{b}", n, 0, tau, eps, P, steps, "fp32"))

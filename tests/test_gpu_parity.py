@@ -6,8 +6,9 @@ motion):
   populations       |f_gpu - f_ref| <= 1e-5 |f_ref| element by element
   particle motion   |dX_gpu - dX_ref| <= 1e-5 |dX_ref| + 1e-6 (dX = X - X0),
                     the same rule for U and omega against their own scale
-FP16 storage: errors against FP64 are measured and bounded loosely here; the
-stated per-quantity figures come from test_gpu_fp16_error.
+FP16 storage: errors against FP64 are bounded loosely here; the stated
+per-quantity figures against FP32 are the benchmark's (its fp16 and
+batched_fp16 entries).
 """
 import math
 
