@@ -20,7 +20,8 @@ CUDA-event time), cpu_baseline (the FP64 oracle on the host), e2e (the same
 metric through the C-ABI with pinned host buffers copied every step), clocks,
 gpu_launches, fp16 (the FP16-storage run and its error against FP32), and
 batched_fp16: the large dense batch (512 x 512 x 1024 cells, 50 000 spheres)
-with FP32 and with FP16 storage, its collision roofline and the FP16 error.
+with FP32 and with FP16 storage, its collision roofline and the FP16 error;
+ensemble: 64 independent boxes of 64..96^3 advanced together, FP32.
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 repository) on the same workload, rank 0 only.
@@ -372,6 +373,7 @@ def run_gpu(args, ws, rank, local):
                               "rho absolute; FP32 itself matches the FP64 oracle within 1e-5"}
 
     batched = batched_fp16_leg(args, stream, peak, max_over_ranks) if args.batched else None
+    ensemble = ensemble_leg(args, stream, peak, max_over_ranks) if args.ensemble else None
 
     launches_per_step = 3 if npart > 0 else 1
     line = {
@@ -394,8 +396,50 @@ def run_gpu(args, ws, rank, local):
         "clocks": clocks,
         "fp16": fp16,
         "batched_fp16": batched,
+        "ensemble": ensemble,
     }
     return line
+
+
+def ensemble_leg(args, stream, peak, max_over_ranks):
+    """The batched ensemble: 64 independent periodic boxes of 64..96^3 cells,
+    10..200 spheres each, all advanced by one captured graph per step with
+    the autotuned launch shape, FP32 storage."""
+    import torch
+    from paper_2312_14172_gb300 import hlbm, workloads
+    boxes = workloads.ensemble()
+    cells = sum(b["n"][0] * b["n"][1] * b["n"][2] for b in boxes)
+    npart = sum(len(b["particles"]["shape"]) for b in boxes)
+    params = hlbm.make_params(tau=boxes[0]["tau"], eps=boxes[0]["eps"], gravity=boxes[0]["gravity"],
+                              max_particles=npart)
+    lat = hlbm.Lattice([tuple(b["n"]) + (b["bc"],) for b in boxes], params, stream=stream)
+    for k, b in enumerate(boxes):
+        lat.add_workload_particles(b["particles"], box_id=[k] * len(b["particles"]["shape"]))
+    if args.autotune:
+        lat.autotune(nsteps=5)
+    elif args.mea_mode:
+        lat.set_mea_mode(args.mea_mode)
+    lat.step(args.warmup)
+    lat.sync()
+    steps = max(1, min(args.steps, 200))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lat.sync()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    kt = lat.kernel_times(nsteps=10)
+    ach = BYTES_PER_CELL["fp32"] * cells / (kt["collide_stream"] / 1e3) / 1e9
+    out = {"value": cells * steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / steps,
+           "steps": steps, "boxes": len(boxes), "cells": cells, "particles": npart,
+           "launch": list(lat.get_launch()), "momentum_exchange": lat.get_mea_mode(), "kernel_ms": kt,
+           "l2": f"inputs larger than L2 ({BYTES_PER_CELL['fp32'] // 2 * cells / 1e6:.0f} MB of populations)",
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "kernel": "collide_pair_kernel" if lat.get_launch()[2] == 2 else "collide_stream_kernel"}}
+    lat.close()
+    return out
 
 
 def batched_fp16_leg(args, stream, peak, max_over_ranks):
@@ -469,6 +513,8 @@ def main():
     ap.add_argument("--no-fp16", dest="fp16", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the 512x512x1024 dense-batch FP32/FP16 leg")
+    ap.add_argument("--no-ensemble", dest="ensemble", action="store_false",
+                    help="skip the 64-box ensemble leg")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--mea-mode", default=None, choices=[None, "kernel", "moments"])

@@ -191,10 +191,11 @@ int hlbm_set_mea_mode(hlbm_handle h, int mode);
 int hlbm_get_mea_mode(hlbm_handle h);
 
 /* Times every momentum-exchange mode and launch shape (tile_y, tile_z,
- * cells_x; cells_x = 2 only with tile_y >= 2) on nsteps steps of the current
- * state (the state advances by the steps taken) and keeps the fastest;
- * writes the chosen shape and its time per step in ms (any pointer may be
- * NULL). */
+ * cells_x; cells_x = 2 only with tile_y >= 2) on about 20 ms of steps
+ * (nsteps to 4 nsteps) of the current state (the state advances by the
+ * steps taken), times
+ * the three fastest once more and keeps the fastest; writes the chosen shape
+ * and its time per step in ms (any pointer may be NULL). */
 int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, int* cells_x, float* ms_per_step);
 
 /* Runs nsteps steps with each kernel launched on its own, bracketed by CUDA

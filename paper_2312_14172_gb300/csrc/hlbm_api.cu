@@ -782,37 +782,65 @@ int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, int* cell
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int by = h->sub_y, bz = h->sub_z, bx = h->cells_x, bm = h->mea_mode;
+  struct Cand { int ty, tz, cx, mode; float ms; };
+  std::vector<Cand> cand;
   const int vals[4] = {1, 2, 4, 8};
-  int rc = HLBM_OK;
   const int nmodes = h->np > 0 ? 2 : 1;
   const int nkinds = h->pair_ok ? 2 : 1;
-  for (int im = 0; im < nkinds * nmodes * 16 && rc == HLBM_OK; ++im) {
-      const int kind = im / (nmodes * 16), mode = (im / 16) % nmodes, iy = (im / 4) % 4, iz = im % 4;
-      if (kind == 1 && vals[iy] == 1) continue;  // 16-thread blocks leave half of each warp idle
-      rc = hlbm_set_mea_mode(h, mode);
-      if (rc == HLBM_OK) rc = hlbm_set_launch(h, vals[iy], vals[iz], kind + 1);
-      if (rc == HLBM_OK) rc = hlbm_step(h, 2);  // warm-up and graph build
-      if (rc != HLBM_OK) break;
-      cudaEventRecord(e0, h->stream);
-      rc = hlbm_step(h, nsteps);
-      cudaEventRecord(e1, h->stream);
-      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(h, HLBM_ERR_CUDA, "autotune timing failed"); break; }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= nsteps;
-      if (ms < best) { best = ms; by = vals[iy]; bz = vals[iz]; bx = kind + 1; bm = mode; }
+  for (int im = 0; im < nkinds * nmodes * 16; ++im) {
+    const int kind = im / (nmodes * 16), mode = (im / 16) % nmodes, iy = (im / 4) % 4, iz = im % 4;
+    if (kind == 1 && vals[iy] == 1) continue;  // 16-thread blocks leave half of each warp idle
+    cand.push_back({vals[iy], vals[iz], kind + 1, mode, 0.f});
+  }
+  int rc = HLBM_OK;
+  // steps per timing: about 20 ms, between nsteps and 4 nsteps (tuning
+  // advances the state; long runs would let particles settle and overlap)
+  int n = nsteps;
+  auto time_one = [&](Cand& c) -> int {
+    int r = hlbm_set_mea_mode(h, c.mode);
+    if (r == HLBM_OK) r = hlbm_set_launch(h, c.ty, c.tz, c.cx);
+    if (r == HLBM_OK) r = hlbm_step(h, 2);  // warm-up and graph build
+    if (r != HLBM_OK) return r;
+    cudaEventRecord(e0, h->stream);
+    r = hlbm_step(h, n);
+    cudaEventRecord(e1, h->stream);
+    if (r != HLBM_OK) return r;
+    if (cudaEventSynchronize(e1) != cudaSuccess) return fail(h, HLBM_ERR_CUDA, "autotune timing failed");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    c.ms = ms / n;
+    return HLBM_OK;
+  };
+  for (size_t k = 0; k < cand.size() && rc == HLBM_OK; ++k) {
+    rc = time_one(cand[k]);
+    if (rc == HLBM_OK && k == 0) {
+      n = std::min(4 * nsteps, std::max(nsteps, (int)std::ceil(20.0 / std::max(cand[0].ms, 1e-3f))));
+      rc = time_one(cand[0]);
+    }
+  }
+  if (rc == HLBM_OK) {
+    // time the three fastest once more and keep the faster of the two timings
+    std::vector<Cand> top = cand;
+    std::sort(top.begin(), top.end(), [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
+    top.resize(std::min<size_t>(3, top.size()));
+    for (auto& c : top) {
+      const float first = c.ms;
+      if ((rc = time_one(c)) != HLBM_OK) break;
+      c.ms = std::min(first, c.ms);
+    }
+    cand = top;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != HLBM_OK) return rc;
-  rc = hlbm_set_mea_mode(h, bm);
-  if (rc == HLBM_OK) rc = hlbm_set_launch(h, by, bz, bx);
-  if (tile_y) *tile_y = by;
-  if (tile_z) *tile_z = bz;
-  if (cells_x) *cells_x = bx;
-  if (ms_per_step) *ms_per_step = best;
+  const Cand best = *std::min_element(cand.begin(), cand.end(),
+                                      [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
+  rc = hlbm_set_mea_mode(h, best.mode);
+  if (rc == HLBM_OK) rc = hlbm_set_launch(h, best.ty, best.tz, best.cx);
+  if (tile_y) *tile_y = best.ty;
+  if (tile_z) *tile_z = best.tz;
+  if (cells_x) *cells_x = best.cx;
+  if (ms_per_step) *ms_per_step = best.ms;
   if (rc != HLBM_OK) return rc;
   return read_status(h);
 }
