@@ -164,9 +164,8 @@ long long hlbm_steps_done(hlbm_handle h);
 /* Launch shape of the collision kernel: each thread block covers a brick of
  * 32 x tile_y x tile_z cells, tile_y and tile_z in {1, 2, 4, 8}, with
  * cells_x = 1 or 2 x-adjacent cells per thread (32 x tile_y or 16 x tile_y
- * threads).  cells_x = 2 needs an even nx in every box (HLBM_ERR_ARG
- * otherwise) and is the default where allowed.  Both compute the same step;
- * their results differ by FP32 rounding order only. */
+ * threads); cells_x = 2 is the default.  Both compute the same step; their
+ * results differ by FP32 rounding order only. */
 int hlbm_set_launch(hlbm_handle h, int tile_y, int tile_z, int cells_x);
 int hlbm_get_launch(hlbm_handle h, int* tile_y, int* tile_z, int* cells_x);
 

@@ -151,8 +151,8 @@ struct hlbm_ctx {
   int np = 0;
   long long steps = 0;
   int sub_y = 4, sub_z = 2;
-  int cells_x = 1;       // cells per thread along x (2 needs an even nx in every box)
-  bool pair_ok = false;  // every box has an even nx
+  int cells_x = 1;       // cells per thread along x
+  bool pair_ok = false;  // the two-cell kernel may run
   // [0][parity]: step with the momentum-exchange kernel (after any change of
   // state); [1][parity]: step that takes the sums the previous collision made
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -353,12 +353,9 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
   h->prm = *prm;
   if (h->prm.bin_capacity == 0) h->prm.bin_capacity = DEFAULT_BIN_CAP;
   h->stream = (cudaStream_t)cuda_stream;
-  h->pair_ok = true;
-  for (int b = 0; b < nboxes; ++b) {
-    h->walls |= boxes[b].bc_flags != 0;
-    h->pair_ok = h->pair_ok && boxes[b].nx % 2 == 0;
-  }
-  h->cells_x = h->pair_ok ? 2 : 1;
+  h->pair_ok = true;  // any nx: an odd nx leaves one cell in a row's last pair
+  for (int b = 0; b < nboxes; ++b) h->walls |= boxes[b].bc_flags != 0;
+  h->cells_x = 2;
   cudaError_t e;
   if (device_buf) {
     if (((uintptr_t)device_buf % ALIGN) || device_buf_bytes < h->L.total) {
@@ -743,7 +740,7 @@ int hlbm_set_launch(hlbm_handle h, int tile_y, int tile_z, int cells_x) {
   auto ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8; };
   if (!ok(tile_y) || !ok(tile_z)) return fail(h, HLBM_ERR_ARG, "tile_y and tile_z must be 1, 2, 4 or 8");
   if (cells_x != 1 && cells_x != 2) return fail(h, HLBM_ERR_ARG, "cells_x must be 1 or 2");
-  if (cells_x == 2 && !h->pair_ok) return fail(h, HLBM_ERR_ARG, "cells_x = 2 needs an even nx in every box");
+  if (cells_x == 2 && !h->pair_ok) return fail(h, HLBM_ERR_ARG, "cells_x = 2 is not available");
   if (tile_y != h->sub_y || tile_z != h->sub_z || cells_x != h->cells_x) {
     h->sub_y = tile_y;
     h->sub_z = tile_z;

@@ -9,9 +9,8 @@
 // of an odd step reach x0 - 1 .. x0 + 2 and take one access per cell.  All
 // FP32 arithmetic of the collision runs on float2 with the packed FP32x2
 // instructions of sm_100 and later (__ffma2_rn, __fadd2_rn, __fmul2_rn),
-// one instruction for both cells.  Requires an even nx in every box; a
-// block is 16 x sub_y threads over the same 32 x sub_y x sub_z brick as the
-// one-cell kernel.
+// one instruction for both cells.  A block is 16 x sub_y threads over the
+// same 32 x sub_y x sub_z brick as the one-cell kernel.
 #include <type_traits>
 
 #include "lbm_common.cuh"
@@ -40,6 +39,8 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 template <typename S> struct Two;
 template <> struct Two<float> {
   using raw = float2;
+  static __device__ __forceinline__ float lo(raw v) { return v.x; }
+  static __device__ __forceinline__ void st1(float* p, float v) { *p = v; }
   static __device__ __forceinline__ raw ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
   static __device__ __forceinline__ raw ld(const float* pa, const float* pb) { return make_float2(*pa, *pb); }
   static __device__ __forceinline__ float2 val(raw v) { return v; }
@@ -49,6 +50,8 @@ template <> struct Two<float> {
 };
 template <> struct Two<__half> {
   using raw = __half2;
+  static __device__ __forceinline__ __half lo(raw v) { return __low2half(v); }
+  static __device__ __forceinline__ void st1(__half* p, __half v) { *p = v; }
   static __device__ __forceinline__ raw ld(const __half* p) { return *reinterpret_cast<const __half2*>(p); }
   static __device__ __forceinline__ raw ld(const __half* pa, const __half* pb) { return __halves2half2(*pa, *pb); }
   static __device__ __forceinline__ float2 val(raw v) { return __half22float2(v); }
@@ -99,9 +102,13 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
   const int x0 = k.x0 + 2 * threadIdx.x;
   const int y = k.y0 + threadIdx.y;
   if (x0 >= bd.nx || y >= bd.ny) return;
+  // an odd nx leaves one cell in a row's last pair: its second slot is the
+  // row's padding, computed but never stored, and the cell's right
+  // neighbour is x0 + 1 wrapped (rb.dr, rb.wr refer to x0 + 1 there)
+  const bool single = x0 + 1 == bd.nx;
   const int z0 = k.z0;
   const int z1 = min(z0 + a.sub_z, bd.nz);
-  const RowBlocks rb = row_blocks<WALLS>(bd, x0, y, 2);
+  const RowBlocks rb = row_blocks<WALLS>(bd, x0, y, single ? 1 : 2);
   S* const f = reinterpret_cast<S*>(a.f);
   const float sc = Pop<S>::SCALED ? a.scale : 1.0f, isc = Pop<S>::SCALED ? a.inv_scale : 1.0f;
 
@@ -132,9 +139,9 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
           const S* pa = (wall || rb.wl) ? mine : src + rb.dl;
           const S* pb = wall ? mine + 1 : src;
           d[i] = T::ld(pa, pb);
-        } else {  // sources x0 + 1, x0 + 2
-          const S* pa = wall ? mine : src + 1;
-          const S* pb = (wall || rb.wr) ? mine + 1 : src + rb.dr;
+        } else {  // sources x0 + 1, x0 + 2 (a single cell: x0 + 1 wrapped)
+          const S* pa = wall ? mine : (single ? (rb.wr ? mine : src + rb.dr) : src + 1);
+          const S* pb = (wall || rb.wr || single) ? mine + 1 : src + rb.dr;
           d[i] = T::ld(pa, pb);
         }
       }
@@ -142,9 +149,11 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
     // coupling of both cells; it needs positions only and runs while the
     // loads above are in flight
     RowCoupling<2> cc;
-    if (COUPLE)
+    if (COUPLE) {
       couple_row<2>(srec, s_rowmask[threadIdx.y + a.sub_y * (z - z0)], bd, x0, y, z, a.eps, a.inv_eps,
                     a.status, cc);
+      if (single) cc.ip0[1] = cc.ip1[1] = -1;
+    }
     // mass and momentum of the arrivals
     float2 drho, jx, jy, jz;
     moments2<T>(d, drho, jx, jy, jz);
@@ -155,7 +164,8 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
       jz = mul2(jz, f2(isc));
     }
     const float2 rho = add2(f2(1.0f), drho);
-    if (!(rho.x > 0.0f && rho.x < 1e30f && rho.y > 0.0f && rho.y < 1e30f)) atomicOr(a.status, ST_UNSTABLE);
+    if (!(rho.x > 0.0f && rho.x < 1e30f && (single || (rho.y > 0.0f && rho.y < 1e30f))))
+      atomicOr(a.status, ST_UNSTABLE);
     const float2 irho = make_float2(__fdividef(1.0f, rho.x), __fdividef(1.0f, rho.y));
     const float2 ux = mul2(jx, irho), uy = mul2(jy, irho), uz = mul2(jz, irho);
     float2 dux = mul2(f2(a.ff[0]), irho), duy = mul2(f2(a.ff[1]), irho), duz = mul2(f2(a.ff[2]), irho);
@@ -233,14 +243,22 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
         S* mine = own + opp(i) * VB;
         if (cx(i) == 0) {
           T::st(wall ? mine : dst, d[i]);
-        } else if (cx(i) > 0) {  // destinations x0 + 1, x0 + 2
-          S* pa = wall ? mine : dst + 1;
-          S* pb = (wall || rb.wr) ? mine + 1 : dst + rb.dr;
-          T::st(pa, pb, d[i]);
-        } else {  // destinations x0 - 1, x0
+        } else if (cx(i) > 0) {  // destinations x0 + 1, x0 + 2 (a single cell: x0 + 1 wrapped)
+          if (single) {
+            Two<S>::st1(wall || rb.wr ? mine : dst + rb.dr, Two<S>::lo(d[i]));
+          } else {
+            S* pa = wall ? mine : dst + 1;
+            S* pb = (wall || rb.wr) ? mine + 1 : dst + rb.dr;
+            T::st(pa, pb, d[i]);
+          }
+        } else {  // destinations x0 - 1, x0 (a single cell: x0 - 1 only)
           S* pa = (wall || rb.wl) ? mine : dst + rb.dl;
-          S* pb = wall ? mine + 1 : dst;
-          T::st(pa, pb, d[i]);
+          if (single) {
+            Two<S>::st1(pa, Two<S>::lo(d[i]));
+          } else {
+            S* pb = wall ? mine + 1 : dst;
+            T::st(pa, pb, d[i]);
+          }
         }
       }
     }

@@ -73,14 +73,16 @@ def _pair(H, O, n, bc, tau=0.7, eps=0.5, g=(0, 0, 0), ff=(0, 0, 0), precision="f
 
 
 # ------------------------------------------------------------ no particles
+@pytest.mark.parametrize("cells_x", [1, 2])
 @pytest.mark.parametrize("nx", [45, 46])
 @pytest.mark.parametrize("bc", [0, 4, 7, 3])
-def test_fluid_only_random_state(H, O, bc, nx):
+def test_fluid_only_random_state(H, O, bc, nx, cells_x):
     """Collision + streaming, ragged sizes spanning several tiles, every
-    parity; an odd nx runs the one-cell kernel, an even nx the two-cell one."""
+    parity, both kernels; with an odd nx the two-cell kernel's last pair of
+    a row holds one cell."""
     n = (nx, 19, 21)
     lat, orc = _pair(H, O, n, bc, tau=0.66, ff=(2e-6, -1e-6, 3e-6))
-    assert lat.get_launch()[2] == (2 if nx % 2 == 0 else 1)
+    lat.set_launch(4, 2, cells_x)
     f0 = _random_pops(O, n, 10 + bc)
     lat.set_populations(f0)
     orc.set_populations(f0)
@@ -92,10 +94,13 @@ def test_fluid_only_random_state(H, O, bc, nx):
     lat.close()
 
 
-def test_degenerate_thin_boxes(H, O):
+@pytest.mark.parametrize("cells_x", [1, 2])
+def test_degenerate_thin_boxes(H, O, cells_x):
     for n, bc in (((1, 1, 16), 4), ((1, 7, 5), 0), ((33, 1, 1), 0), ((2, 2, 2), 7), ((2, 1, 16), 4),
-                  ((2, 7, 5), 0), ((34, 1, 1), 1), ((4, 3, 3), 7)):
+                  ((2, 7, 5), 0), ((34, 1, 1), 1), ((4, 3, 3), 7), ((3, 2, 2), 7), ((33, 1, 1), 1),
+                  ((1, 3, 3), 1)):
         lat, orc = _pair(H, O, n, bc, tau=0.9, ff=(1e-5, 0, 0))
+        lat.set_launch(2, 2, cells_x)
         f0 = _random_pops(O, n, 3)
         lat.set_populations(f0)
         orc.set_populations(f0)
