@@ -188,6 +188,24 @@ def init_dist():
     return ws, rank, local
 
 
+def max_over_ranks(v):
+    """The largest of one value over all ranks (the value itself on one rank):
+    whole-job times are the slowest replica's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return v
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells, steps, ms, ws):
+    """MLUPS of ws replicas of `cells` cells that took `ms` (max over ranks)."""
+    return ws * cells * steps / (ms / 1e3) / 1e6
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return None
@@ -233,13 +251,6 @@ def run_gpu(args, ws, rank, local):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     # ---- main timed region: K graph-launched steps, inputs resident in HBM
     lat = hlbm.from_workload(w, precision=prec, stream=stream)
     tune = None
@@ -270,7 +281,7 @@ def run_gpu(args, ws, rank, local):
     lat.sync()
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(ms)
-    value = ws * cells * args.steps / (ms / 1e3) / 1e6
+    value = whole_job_mlups(cells, args.steps, ms, ws)
 
     lat_launch = lat.get_launch()
     # ---- per-kernel CUDA-event times on the same stream (roofline)
@@ -302,7 +313,7 @@ def run_gpu(args, ws, rank, local):
     torch.cuda.synchronize()
     t_e2e = max_over_ranks(time.perf_counter() - t0)
     barrier()
-    e2e = {"value": ws * cells * e2e_steps / t_e2e / 1e6, "unit": "MLUPS",
+    e2e = {"value": whole_job_mlups(cells, e2e_steps, t_e2e * 1e3, ws), "unit": "MLUPS",
            "h2d_bytes_per_step": npart * 13 * 8, "d2h_bytes_per_step": npart * 19 * 8,
            "steps": e2e_steps,
            "note": "per step: hlbm_set_particle_state (X, U, omega, q) + hlbm_step(1) + "
@@ -363,7 +374,7 @@ def run_gpu(args, ws, rank, local):
             err["rho"] = float(np.abs(r16 - r32).max())
             err["u"] = float(np.abs(u16 - u32).max() / max(np.abs(u32).max(), 1e-30))
         lat16.close()
-        fp16 = {"value": ws * cells * args.steps / (ms16 / 1e3) / 1e6, "unit": "MLUPS",
+        fp16 = {"value": whole_job_mlups(cells, args.steps, ms16, ws), "unit": "MLUPS",
                 "ms_per_step": ms16 / args.steps, "l2": "512 MB flush between steps",
                 "roofline": {"bound": "hbm", "achieved": ach16, "peak": peak, "unit": "GB/s",
                              "frac": ach16 / peak, "kernel_ms": kt16["collide_stream"],
@@ -372,8 +383,8 @@ def run_gpu(args, ws, rank, local):
                 "error_note": "max |fp16 - fp32| / max|fp32| after the same steps; X as displacement; "
                               "rho absolute; FP32 itself matches the FP64 oracle within 1e-5"}
 
-    batched = batched_fp16_leg(args, stream, peak, max_over_ranks) if args.batched else None
-    ensemble = ensemble_leg(args, stream, peak, max_over_ranks) if args.ensemble else None
+    batched = batched_fp16_leg(args, stream, peak, ws) if args.batched else None
+    ensemble = ensemble_leg(args, stream, peak, ws) if args.ensemble else None
 
     launches_per_step = 3 if npart > 0 else 1
     line = {
@@ -401,7 +412,7 @@ def run_gpu(args, ws, rank, local):
     return line
 
 
-def ensemble_leg(args, stream, peak, max_over_ranks):
+def ensemble_leg(args, stream, peak, ws):
     """The batched ensemble: 64 independent periodic boxes of 64..96^3 cells,
     10..200 spheres each, all advanced by one captured graph per step with
     the autotuned launch shape, FP32 storage."""
@@ -432,7 +443,7 @@ def ensemble_leg(args, stream, peak, max_over_ranks):
     ms = max_over_ranks(e0.elapsed_time(e1))
     kt = lat.kernel_times(nsteps=10)
     ach = BYTES_PER_CELL["fp32"] * cells / (kt["collide_stream"] / 1e3) / 1e9
-    out = {"value": cells * steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / steps,
+    out = {"value": whole_job_mlups(cells, steps, ms, ws), "unit": "MLUPS", "ms_per_step": ms / steps,
            "steps": steps, "boxes": len(boxes), "cells": cells, "particles": npart,
            "launch": list(lat.get_launch()), "momentum_exchange": lat.get_mea_mode(), "kernel_ms": kt,
            "l2": f"inputs larger than L2 ({BYTES_PER_CELL['fp32'] // 2 * cells / 1e6:.0f} MB of populations)",
@@ -442,7 +453,7 @@ def ensemble_leg(args, stream, peak, max_over_ranks):
     return out
 
 
-def batched_fp16_leg(args, stream, peak, max_over_ranks):
+def batched_fp16_leg(args, stream, peak, ws):
     """The large dense batch (512 x 512 x 1024 cells, 50 000 lognormal
     spheres, realised solid fraction 0.075) with FP32 and with FP16 storage of f - w:
     step time, collision roofline and the FP16 error against FP32 after the
@@ -472,7 +483,7 @@ def batched_fp16_leg(args, stream, peak, max_over_ranks):
         ms = max_over_ranks(e0.elapsed_time(e1))
         kt = lat.kernel_times(nsteps=4)
         ach = BYTES_PER_CELL[prec] * cells / (kt["collide_stream"] / 1e3) / 1e9
-        out[prec] = {"value": cells * steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / steps,
+        out[prec] = {"value": whole_job_mlups(cells, steps, ms, ws), "unit": "MLUPS", "ms_per_step": ms / steps,
                      "steps": steps, "launch": list(lat.get_launch()), "momentum_exchange": lat.get_mea_mode(),
                      "kernel_ms": kt,
                      "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
