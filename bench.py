@@ -314,7 +314,7 @@ def run_gpu(args, ws, rank, local):
     t_e2e = max_over_ranks(time.perf_counter() - t0)
     barrier()
     e2e = {"value": whole_job_mlups(cells, e2e_steps, t_e2e * 1e3, ws), "unit": "MLUPS",
-           "h2d_bytes_per_step": npart * 13 * 8, "d2h_bytes_per_step": npart * 19 * 8,
+           "h2d_bytes_per_step": npart * 13 * 8, "d2h_bytes_per_step": npart * 19 * 8 + 4,
            "steps": e2e_steps,
            "note": "per step: hlbm_set_particle_state (X, U, omega, q) + hlbm_step(1) + "
                    "hlbm_particle_state (X, U, omega, q, F, T), pinned host arrays"}

@@ -130,7 +130,11 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
                        const double* omega, const double* quat, const double* rho_p);
 
 /* Overwrites the motion state of all particles (any of the pointers may be
- * NULL to keep that field).  Arrays as in hlbm_add_particles. */
+ * NULL to keep that field).  Arrays as in hlbm_add_particles.  The values are
+ * checked and staged on the host, the upload is queued on the stream and the
+ * call returns without waiting for it: the arrays may be reused at once.
+ * HLBM_ERR_ARG (nothing changed) for a non-finite position or a zero or
+ * non-finite quaternion. */
 int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, const double* omega,
                             const double* quat);
 

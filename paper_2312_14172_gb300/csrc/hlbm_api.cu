@@ -147,6 +147,12 @@ struct hlbm_ctx {
   int* ids[2] = {nullptr, nullptr};
   int* status = nullptr;
   float* stage = nullptr;
+  // pinned host staging of the motion state (rows X, U, omega, q, F, T, each
+  // n doubles) and of the status word; hstage_ev marks the end of the last
+  // upload that reads it
+  double* hstage = nullptr;
+  int* hstatus = nullptr;
+  cudaEvent_t hstage_ev = nullptr;
   bool walls = false;
   int np = 0;
   long long steps = 0;
@@ -303,11 +309,9 @@ static int build_graphs(hlbm_ctx* h) {
   return HLBM_OK;
 }
 
-static int read_status(hlbm_ctx* h) {
-  int st = 0;
-  CK(cudaStreamSynchronize(h->stream));
-  CK(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+// the status word already copied to the host: HLBM_OK, or clears the device
+// flags and returns the error they name
+static int status_code(hlbm_ctx* h, int st) {
   if (st == 0) return HLBM_OK;
   CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -318,6 +322,12 @@ static int read_status(hlbm_ctx* h) {
   if (st & ST_LEFT_DOMAIN)
     return fail(h, HLBM_ERR_UNSTABLE, "a particle centre left the fluid domain through a wall");
   return fail(h, HLBM_ERR_UNSTABLE, "non-finite or non-positive density, or non-finite particle state");
+}
+
+static int read_status(hlbm_ctx* h) {
+  CK(cudaMemcpyAsync(h->hstatus, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return status_code(h, *h->hstatus);
 }
 
 extern "C" {
@@ -379,6 +389,17 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
     hlbm_destroy(h);
     return HLBM_ERR_CUDA;
   }
+  {
+    const size_t rows = sizeof(double) * 19 * (size_t)std::max(h->L.cap, 1);
+    e = cudaMallocHost((void**)&h->hstage, rows + sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->hstage_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      g_init_err = std::string("host staging: ") + cudaGetErrorString(e);
+      hlbm_destroy(h);
+      return HLBM_ERR_CUDA;
+    }
+    h->hstatus = (int*)((char*)h->hstage + rows);
+  }
   h->f = h->buf + h->L.off_f;
   h->d_boxes = (BoxDesc*)(h->buf + h->L.off_boxes);
   h->P = (double*)(h->buf + h->L.off_P);
@@ -432,6 +453,8 @@ void hlbm_destroy(hlbm_handle h) {
   drop_graphs(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->owns && h->buf) cudaFree(h->buf);
+  if (h->hstage_ev) cudaEventDestroy(h->hstage_ev);
+  if (h->hstage) cudaFreeHost(h->hstage);
   delete h;
 }
 
@@ -597,43 +620,50 @@ int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, con
   if (!h) return HLBM_ERR_ARG;
   const int n = h->np;
   if (n == 0) return HLBM_OK;
-  CK(cudaStreamSynchronize(h->stream));
-  std::vector<double> tmp((size_t)n * 4);
-  auto put = [&](int fld, int ncomp, const double* src, bool wrapX) -> int {
-    for (int j = 0; j < ncomp; ++j) {
-      for (int k = 0; k < n; ++k) tmp[k] = src[(size_t)ncomp * k + j];
-      CK(cudaMemcpy(h->P + (size_t)(fld + j) * h->L.cap, tmp.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-    }
-    (void)wrapX;
-    return HLBM_OK;
-  };
-  int rc;
-  if (X) {
-    std::vector<double> xw((size_t)3 * n);
+  for (int k = 0; X && k < n; ++k)
+    for (int j = 0; j < 3; ++j)
+      if (!std::isfinite(X[3 * k + j])) return fail(h, HLBM_ERR_ARG, "non-finite position");
+  for (int k = 0; quat && k < n; ++k) {
+    double nq = 0.0;
+    for (int j = 0; j < 4; ++j) nq += quat[4 * k + j] * quat[4 * k + j];
+    if (!(nq > 0.0) || !std::isfinite(nq)) return fail(h, HLBM_ERR_ARG, "quaternion must be finite and non-zero");
+  }
+  // the staging rows may still feed the previous upload
+  CK(cudaEventSynchronize(h->hstage_ev));
+  double* S = h->hstage;  // row r holds component r of the state, n doubles
+  if (X)
     for (int k = 0; k < n; ++k) {
       double x[3] = {X[3 * k], X[3 * k + 1], X[3 * k + 2]};
-      for (int j = 0; j < 3; ++j)
-        if (!std::isfinite(x[j])) return fail(h, HLBM_ERR_ARG, "non-finite position");
       wrap_host(h->boxes[h->h_box[k]], x);
-      for (int j = 0; j < 3; ++j) xw[3 * k + j] = x[j];
+      for (int j = 0; j < 3; ++j) S[(size_t)(PF_X + j) * n + k] = x[j];
     }
-    if ((rc = put(PF_X, 3, xw.data(), true)) != HLBM_OK) return rc;
-  }
-  if (U && (rc = put(PF_U, 3, U, false)) != HLBM_OK) return rc;
-  if (omega && (rc = put(PF_W, 3, omega, false)) != HLBM_OK) return rc;
-  if (quat) {
-    std::vector<double> qn((size_t)4 * n);
+  auto rows = [&](int fld, int ncomp, const double* src) {
+    for (int j = 0; j < ncomp; ++j)
+      for (int k = 0; k < n; ++k) S[(size_t)(fld + j) * n + k] = src[(size_t)ncomp * k + j];
+  };
+  if (U) rows(PF_U, 3, U);
+  if (omega) rows(PF_W, 3, omega);
+  if (quat)
     for (int k = 0; k < n; ++k) {
       double nq = 0.0;
       for (int j = 0; j < 4; ++j) nq += quat[4 * k + j] * quat[4 * k + j];
-      if (!(nq > 0.0) || !std::isfinite(nq)) return fail(h, HLBM_ERR_ARG, "quaternion must be finite and non-zero");
       nq = std::sqrt(nq);
-      for (int j = 0; j < 4; ++j) qn[4 * k + j] = quat[4 * k + j] / nq;
+      for (int j = 0; j < 4; ++j) S[(size_t)(PF_Q + j) * n + k] = quat[4 * k + j] / nq;
     }
-    if ((rc = put(PF_Q, 4, qn.data(), false)) != HLBM_OK) return rc;
+  // one strided copy per run of consecutive fields that were given
+  const bool given[4] = {X != nullptr, U != nullptr, omega != nullptr, quat != nullptr};
+  const int row0[5] = {PF_X, PF_U, PF_W, PF_Q, PF_F};
+  for (int f0 = 0; f0 < 4;) {
+    if (!given[f0]) { ++f0; continue; }
+    int f1 = f0;
+    while (f1 < 4 && given[f1]) ++f1;
+    const int r0 = row0[f0], nr = row0[f1] - r0;
+    CK(cudaMemcpy2DAsync(h->P + (size_t)r0 * h->L.cap, sizeof(double) * h->L.cap, S + (size_t)r0 * n,
+                         sizeof(double) * n, sizeof(double) * n, nr, cudaMemcpyHostToDevice, h->stream));
+    f0 = f1;
   }
+  CK(cudaEventRecord(h->hstage_ev, h->stream));
   CK(launch_records(part_args(h, 0), h->stream));
-  CK(cudaStreamSynchronize(h->stream));
   h->moments_valid = false;
   return HLBM_OK;
 }
@@ -670,25 +700,25 @@ int hlbm_sync(hlbm_handle h) {
 int hlbm_particle_state(hlbm_handle h, double* X, double* U, double* omega, double* quat, double* F,
                         double* T) {
   if (!h) return HLBM_ERR_ARG;
-  const int st = read_status(h);
   const int n = h->np;
-  if (n > 0) {
-    std::vector<double> tmp((size_t)n);
-    auto get = [&](int fld, int ncomp, double* dst) -> int {
-      for (int j = 0; j < ncomp; ++j) {
-        CK(cudaMemcpy(tmp.data(), h->P + (size_t)(fld + j) * h->L.cap, sizeof(double) * n, cudaMemcpyDeviceToHost));
-        for (int k = 0; k < n; ++k) dst[(size_t)ncomp * k + j] = tmp[k];
-      }
-      return HLBM_OK;
-    };
-    int rc;
-    if (X && (rc = get(PF_X, 3, X)) != HLBM_OK) return rc;
-    if (U && (rc = get(PF_U, 3, U)) != HLBM_OK) return rc;
-    if (omega && (rc = get(PF_W, 3, omega)) != HLBM_OK) return rc;
-    if (quat && (rc = get(PF_Q, 4, quat)) != HLBM_OK) return rc;
-    if (F && (rc = get(PF_F, 3, F)) != HLBM_OK) return rc;
-    if (T && (rc = get(PF_T, 3, T)) != HLBM_OK) return rc;
-  }
+  if (n == 0) return read_status(h);
+  // rows X, U, omega, q, F, T (19 components) in one strided copy, then the status word
+  double* S = h->hstage;
+  CK(cudaMemcpy2DAsync(S, sizeof(double) * n, h->P + (size_t)PF_X * h->L.cap, sizeof(double) * h->L.cap,
+                       sizeof(double) * n, PF_T + 3 - PF_X, cudaMemcpyDeviceToHost, h->stream));
+  const int st = read_status(h);
+  if (st == HLBM_ERR_CUDA) return st;
+  auto get = [&](int fld, int ncomp, double* dst) {
+    if (!dst) return;
+    for (int j = 0; j < ncomp; ++j)
+      for (int k = 0; k < n; ++k) dst[(size_t)ncomp * k + j] = S[(size_t)(fld + j) * n + k];
+  };
+  get(PF_X, 3, X);
+  get(PF_U, 3, U);
+  get(PF_W, 3, omega);
+  get(PF_Q, 4, quat);
+  get(PF_F, 3, F);
+  get(PF_T, 3, T);
   return st;
 }
 
