@@ -16,7 +16,11 @@ g = 1e-5, FP32 storage of f - w.  Its 19 FP32 planes (159 MB) exceed the
 timed one step at a time with a 512 MB L2 flush between steps.
 
 The JSON line adds: roofline (collision kernel, algorithmic bytes over its
-CUDA-event time), cpu_baseline (the FP64 oracle on the host), e2e (the same
+CUDA-event time), step_roofline (the whole step's bytes with and without the
+momentum exchange's per interior cell, against the step time, and the MLUPS
+rooflines they give), coupling (interior cells per step, momentum-exchange
+cell updates and particles per second), cpu_baseline (the FP64 oracle on
+the host), e2e (the same
 metric through the C-ABI with pinned host buffers copied every step), clocks,
 gpu_launches, fp16 (the FP16-storage run and its error against FP32), and
 batched_fp16: the large dense batch (512 x 512 x 1024 cells, 50 000 spheres)
@@ -297,6 +301,8 @@ def run_gpu(args, ws, rank, local):
                 "algorithmic_bytes": algo_bytes,
                 "kernel_ms": k1_ms, "kernel_ms_mea": kt["mea"], "kernel_ms_update": kt["update"]}
 
+    coupling, step_roofline = coupling_and_step_roofline(lat, cells, npart, args.steps, ms, ws, prec, peak)
+
     # ---- end to end through the C-ABI with pinned host buffers
     st0 = lat.particle_state()
     pin = {k: torch.empty(v.shape, dtype=torch.float64, pin_memory=True).numpy() for k, v in st0.items()}
@@ -385,6 +391,7 @@ def run_gpu(args, ws, rank, local):
 
     batched = batched_fp16_leg(args, stream, peak, ws) if args.batched else None
     ensemble = ensemble_leg(args, stream, peak, ws) if args.ensemble else None
+    phi = phi_matched_leg(args, stream, peak, ws) if args.phi_matched else None
 
     launches_per_step = 3 if npart > 0 else 1
     line = {
@@ -402,6 +409,8 @@ def run_gpu(args, ws, rank, local):
                               "momentum_exchange": mea_mode,
                               "autotuned": bool(args.autotune)}},
         "roofline": roofline,
+        "step_roofline": step_roofline,
+        "coupling": coupling,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -409,6 +418,8 @@ def run_gpu(args, ws, rank, local):
         "batched_fp16": batched,
         "ensemble": ensemble,
     }
+    if phi is not None:
+        line["phi_matched"] = phi
     return line
 
 
@@ -449,21 +460,61 @@ def ensemble_leg(args, stream, peak, ws):
            "l2": f"inputs larger than L2 ({BYTES_PER_CELL['fp32'] // 2 * cells / 1e6:.0f} MB of populations)",
            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                         "kernel": "collide_pair_kernel" if lat.get_launch()[2] == 2 else "collide_stream_kernel"}}
+    out["coupling"], out["step_roofline"] = coupling_and_step_roofline(lat, cells, npart, steps, ms, ws, "fp32", peak)
     lat.close()
     return out
 
 
-def batched_fp16_leg(args, stream, peak, ws):
-    """The large dense batch (512 x 512 x 1024 cells, 50 000 lognormal
-    spheres, realised solid fraction 0.075) with FP32 and with FP16 storage of f - w:
-    step time, collision roofline and the FP16 error against FP32 after the
-    same number of steps.  Populations of 20 GB (FP32) / 10 GB (FP16) are far
+def coupling_and_step_roofline(lat, cells, npart, steps, ms, ws, prec, peak):
+    """Particle-coupling throughput and the roofline of the whole step.
+
+    The interior cells (cell centre inside a particle) are the cells the
+    momentum exchange sums over; the library counts them in the moments
+    mode (the mode is switched for one step if another was in use).  Bytes
+    of a step: the collision's 2 * 19 * s per cell plus, per interior cell,
+    the momentum exchange's 19 arrivals (19 * s) and, in the moments mode,
+    the 24-byte list entry written by the collision and read back (in the
+    bounding-box mode the 19 departures instead)."""
+    mode = lat.get_mea_mode()
+    n_int = 0
+    if npart > 0:
+        if mode != "moments":
+            lat.set_mea_mode("moments")
+            lat.step(1)
+        n_int = lat.interior_cells()
+        if mode != "moments":
+            lat.set_mea_mode(mode)
+    s = BYTES_PER_CELL[prec] // 38
+    per_int = 19 * s + (48 if mode == "moments" else 19 * s)
+    bpc_mea = BYTES_PER_CELL[prec] + per_int * n_int / cells
+    sec = ms / steps / 1e3
+    coupling = {"interior_cells_per_step": n_int, "interior_fraction": n_int / cells,
+                "mea_cell_updates_per_s": ws * n_int / sec, "particles_per_s": ws * npart / sec,
+                "unit": "per second, whole job"}
+    step_roofline = {"bound": "hbm", "unit": "GB/s", "peak": peak,
+                     "bytes_per_cell_without_mea": BYTES_PER_CELL[prec],
+                     "bytes_per_cell_with_mea": bpc_mea,
+                     "achieved": bpc_mea * cells / sec / 1e9,
+                     "frac": bpc_mea * cells / sec / 1e9 / peak,
+                     "mlups_roofline_without_mea": peak * 1e3 / BYTES_PER_CELL[prec],
+                     "mlups_roofline_with_mea": peak * 1e3 / bpc_mea,
+                     "frac_of_mlups_roofline_without_mea": cells / sec / 1e6 / (peak * 1e3 / BYTES_PER_CELL[prec]),
+                     "frac_of_mlups_roofline_with_mea": cells / sec / 1e6 / (peak * 1e3 / bpc_mea),
+                     "note": "whole step (momentum exchange, update, collision) per GPU; per interior cell "
+                             f"{per_int} B of momentum exchange ({mode} mode)"}
+    return coupling, step_roofline
+
+
+def fp32_fp16_pair(w, args, stream, peak, ws, steps_max=40):
+    """One workload with FP32 and with FP16 storage of f - w: step time,
+    collision roofline, coupling throughput and whole-step roofline, and the
+    FP16 error against FP32 after the same number of steps.  Populations far
     larger than L2, so steps run back to back."""
     import torch
     from paper_2312_14172_gb300 import hlbm
-    w = make_workload("dense_batch")
     cells = w["n"][0] * w["n"][1] * w["n"][2]
-    steps = max(1, min(args.steps, 40))
+    npart = len(w["particles"]["shape"])
+    steps = max(1, min(args.steps, steps_max))
     out, states = {}, {}
     for prec in ("fp32", "fp16"):
         lat = hlbm.from_workload(w, precision=prec, stream=stream)
@@ -483,11 +534,13 @@ def batched_fp16_leg(args, stream, peak, ws):
         ms = max_over_ranks(e0.elapsed_time(e1))
         kt = lat.kernel_times(nsteps=4)
         ach = BYTES_PER_CELL[prec] * cells / (kt["collide_stream"] / 1e3) / 1e9
+        coupling, step_rl = coupling_and_step_roofline(lat, cells, npart, steps, ms, ws, prec, peak)
         out[prec] = {"value": whole_job_mlups(cells, steps, ms, ws), "unit": "MLUPS", "ms_per_step": ms / steps,
                      "steps": steps, "launch": list(lat.get_launch()), "momentum_exchange": lat.get_mea_mode(),
                      "kernel_ms": kt,
                      "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                                  "frac": ach / peak, "kernel": "collide_stream"}}
+                                  "frac": ach / peak, "kernel": "collide_stream"},
+                     "coupling": coupling, "step_roofline": step_rl}
         states[prec] = (lat.steps_done, lat)
     # error of FP16 against FP32 after the same number of steps
     n32, lat32 = states["fp32"]
@@ -504,13 +557,49 @@ def batched_fp16_leg(args, stream, peak, ws):
     for key in ("X", "U", "F", "T"):
         a32 = s32[key] - (X0 if key == "X" else 0)
         a16 = s16[key] - (X0 if key == "X" else 0)
+        if key == "X":  # displacement, periodic wrap of a centre next to a face
+            L = np.asarray(w["n"], float)
+            a32 -= L * np.round(a32 / L)
+            a16 -= L * np.round(a16 / L)
         scale = float(np.abs(a32).max()) or 1.0
         err[key] = float(np.abs(a16 - a32).max() / scale)
     out["error_fp16_vs_fp32"] = err
-    out["workload"] = {"name": w["name"], "dims": list(w["n"]), "particles": len(w["particles"]["shape"]),
-                       "cells": cells}
+    P = w["particles"]
+    out["workload"] = {"name": w["name"], "dims": list(w["n"]), "particles": npart, "cells": cells,
+                       "solid_fraction": solid_fraction(P, cells)}
     out["speedup_fp16_over_fp32"] = out["fp16"]["value"] / out["fp32"]["value"]
     return out
+
+
+def solid_fraction(P, cells):
+    """Total particle volume over the lattice volume."""
+    a = np.asarray(P["a"], float)
+    shp = np.asarray(P["shape"])
+    vol = np.where(shp == 2, 8.0 * a[:, 0] * a[:, 1] * a[:, 2], 4.0 / 3.0 * np.pi * a[:, 0] * a[:, 1] * a[:, 2])
+    return float(vol.sum() / cells)
+
+
+def batched_fp16_leg(args, stream, peak, ws):
+    """The large dense batch (512 x 512 x 1024 cells, 50 000 lognormal
+    spheres, realised solid fraction 0.075) with FP32 and with FP16 storage
+    (populations of 20 GB / 10 GB)."""
+    return fp32_fp16_pair(make_workload("dense_batch"), args, stream, peak, ws)
+
+
+def _generate(name):
+    from paper_2312_14172_gb300 import workloads
+    return getattr(workloads, name)()
+
+
+def phi_matched_leg(args, stream, peak, ws):
+    """The two workloads at the solid fractions their configurations name
+    (0.15: 4806 ellipsoids and cuboids in 256^3; 0.2: 50 000 spheres of
+    median diameter 11.1 in 512 x 512 x 1024), each with FP32 and FP16
+    storage.  Both are drawn in parallel host processes first."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(2) as pool:
+        ws_ = pool.map(_generate, ["nonspherical_phi_matched", "dense_batch_phi_matched"])
+    return {w["name"]: fp32_fp16_pair(w, args, stream, peak, ws) for w in ws_}
 
 
 def main():
@@ -526,6 +615,9 @@ def main():
                     help="skip the 512x512x1024 dense-batch FP32/FP16 leg")
     ap.add_argument("--no-ensemble", dest="ensemble", action="store_false",
                     help="skip the 64-box ensemble leg")
+    ap.add_argument("--phi-matched", action="store_true",
+                    help="add the solid-fraction-matched variants of the non-spherical and dense workloads "
+                         "(about two minutes of host time to draw them)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--mea-mode", default=None, choices=[None, "kernel", "moments"])

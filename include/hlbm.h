@@ -207,6 +207,15 @@ int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, int* cell
  * and streaming.  Synchronises. */
 int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]);
 
+/* Writes to *n the number of (cell, particle) pairs whose cell centre lies
+ * inside the particle (Sec. 3.2, the cells the sums of Eqs.
+ * hydrodynamicforce and hydrodynamictorque run over) at the current
+ * particle state: the entries the last collision listed in the moments
+ * mode, i.e. the work of the next step's momentum exchange.  A cell inside
+ * two particles counts twice.  Synchronises.  HLBM_ERR_STATE outside the
+ * moments mode or before the first step after a change of state. */
+int hlbm_interior_cells(hlbm_handle h, long long* n);
+
 /* Momentum exchange without device allocation.
  *
  * The paper has no counterpart to this call; it serves callers that cannot

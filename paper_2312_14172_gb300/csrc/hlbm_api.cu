@@ -241,6 +241,7 @@ static PartArgs part_args(const hlbm_ctx* h, int parity) {
   a.done = h->done;
   a.acc = h->acc;
   a.from_acc = 0;
+  a.nsm = h->nsm;
   a.ilist_count = h->ilist_count;
   a.bin_count = h->cnt[parity];
   a.bin_ids = h->ids[parity];
@@ -905,6 +906,21 @@ int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]) {
   for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
   if (rc != HLBM_OK) return rc;
   for (int k = 0; k < 3; ++k) ms[k] = (float)(acc[k] / nsteps);
+  return read_status(h);
+}
+
+int hlbm_interior_cells(hlbm_handle h, long long* n) {
+  if (!h || !n) return HLBM_ERR_ARG;
+  *n = 0;
+  if (h->np == 0) return HLBM_OK;
+  if (h->mea_mode != HLBM_MEA_MOMENTS || !h->moments_valid || !h->ilist_idx)
+    return fail(h, HLBM_ERR_STATE, "interior cells are counted by a collision in the moments mode");
+  int cnt[ILIST_STRIPES];
+  CK(cudaMemcpyAsync(cnt, h->ilist_count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  long long t = 0;
+  for (int k = 0; k < ILIST_STRIPES; ++k) t += std::min((long long)cnt[k], h->L.ilist_cap);
+  *n = t;
   return read_status(h);
 }
 

@@ -266,6 +266,8 @@ struct PartArgs {
   // the same sums accumulated by the previous collision, [cap][6]
   double* acc;
   int from_acc;             // 1: the update takes acc, 0: the table's F and T
+  int nsm;                  // SMs of the GPU (update grid size)
+  int ppb;                  // particles per update block (set by the launcher)
   int* ilist_count;         // [ILIST_STRIPES], reset by the update for the next collision
   // bins written by the update (this step) and cleared (other parity)
   int* bin_count;

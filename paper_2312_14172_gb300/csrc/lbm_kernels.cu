@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
     // an entry names a particle and a cell of that particle's box; anything
     // else was never written by the collision and is skipped with a flag
     if (valid && (e.y < 0 || e.y >= a.np)) valid = false;
-    const BoxDesc bd = a.boxes[valid ? a.rec[e.y].box : 0];
+    // one box: its descriptor does not wait for the particle's record
+    const BoxDesc bd = a.boxes[a.nboxes == 1 || !valid ? 0 : a.rec[e.y].box];
     const long long cl = (long long)e.x - bd.cell_off;
     if (valid && (cl < 0 || cl >= (long long)bd.nx * bd.ny * bd.nz)) valid = false;
     if (kc < n && !valid) atomicOr(a.status, ST_INTERNAL);

@@ -307,9 +307,12 @@ __device__ __forceinline__ BinRange update_particle(const PartArgs& a, int p) {
   return br;
 }
 
-// UPD_P particles per block of UPD_T threads: the first UPD_P threads each
-// update one particle; then all threads add the block's particles to the
-// per-tile lists, UPD_T / UPD_P threads per particle taking its tiles in turn.
+// a.ppb particles per block of UPD_T threads (ppb a power of two up to
+// UPD_P): the first ppb threads each update one particle; then all threads
+// add the block's particles to the per-tile lists, UPD_T / ppb threads per
+// particle taking its tiles in turn.  Few particles get small groups, so
+// that the blocks spread over the GPU and each particle's tiles take one
+// round of atomics.
 constexpr int UPD_P = 32, UPD_T = 256;
 
 __global__ void __launch_bounds__(UPD_T) update_kernel(PartArgs a) {
@@ -320,8 +323,9 @@ __global__ void __launch_bounds__(UPD_T) update_kernel(PartArgs a) {
   const long long nthr = (long long)gridDim.x * blockDim.x;
   for (long long t = tid; t < a.ntiles; t += nthr) a.bin_count_clear[t] = 0;
   if (tid < ILIST_STRIPES && a.ilist_count) a.ilist_count[tid] = 0;  // the collision appends anew
-  for (long long base = blockIdx.x * (long long)UPD_P; base < a.np; base += (long long)gridDim.x * UPD_P) {
-    if (threadIdx.x < UPD_P) {
+  const int ppb = a.ppb;
+  for (long long base = blockIdx.x * (long long)ppb; base < a.np; base += (long long)gridDim.x * ppb) {
+    if (threadIdx.x < ppb) {
       const long long p = base + threadIdx.x;
       BinRange br;
       br.count = 0;
@@ -329,11 +333,11 @@ __global__ void __launch_bounds__(UPD_T) update_kernel(PartArgs a) {
       s_br[threadIdx.x] = br;
     }
     __syncthreads();
-    const int k = threadIdx.x % UPD_P, sub = threadIdx.x / UPD_P;
+    const int k = threadIdx.x % ppb, sub = threadIdx.x / ppb;
     const BinRange& br = s_br[k];
     const int cx_ = br.at[0].count(), cy_ = br.at[1].count();
     const int p = (int)(base + k);
-    for (int t = sub; t < br.count; t += UPD_T / UPD_P) {
+    for (int t = sub; t < br.count; t += UPD_T / ppb) {
       const int ix = t % cx_, r = t / cx_, iy = r % cy_, iz = r / cy_;
       const long long tile = br.tile_off + ((long long)br.at[2].at(iz) * br.nty + br.at[1].at(iy)) * br.ntx +
                              br.at[0].at(ix);
@@ -364,8 +368,14 @@ cudaError_t launch_mea(const PartArgs& a, int precision, int parity, cudaStream_
                      : launch_k(mea_kernel<__half, 1>, dim3(grid), dim3(128), 0, s, pdl, a);
 }
 
-cudaError_t launch_update(const PartArgs& a, cudaStream_t s) {
-  long long blocks = (a.np + UPD_P - 1) / UPD_P;
+cudaError_t launch_update(const PartArgs& a_in, cudaStream_t s) {
+  PartArgs a = a_in;
+  // particles per block: the smallest power of two that keeps the blocks
+  // within about one per SM, at most UPD_P
+  const long long target = a.nsm > 0 ? a.nsm : 152;
+  a.ppb = 1;
+  while (a.ppb < UPD_P && (long long)a.ppb * target < a.np) a.ppb *= 2;
+  long long blocks = (a.np + a.ppb - 1) / a.ppb;
   long long clear_blocks = (a.ntiles + UPD_T - 1) / UPD_T;
   if (clear_blocks > blocks) blocks = clear_blocks;
   if (blocks > 65535) blocks = 65535;

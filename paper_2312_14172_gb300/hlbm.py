@@ -31,7 +31,7 @@ EXPORTS = ["hlbm_default_params", "hlbm_required_bytes", "hlbm_init_lattice", "h
            "hlbm_particle_state", "hlbm_get_populations", "hlbm_set_populations",
            "hlbm_num_particles", "hlbm_steps_done", "hlbm_set_launch", "hlbm_get_launch",
            "hlbm_set_mea_mode", "hlbm_get_mea_mode",
-           "hlbm_autotune", "hlbm_kernel_times", "hlbm_last_error", "hlbm_destroy",
+           "hlbm_autotune", "hlbm_kernel_times", "hlbm_interior_cells", "hlbm_last_error", "hlbm_destroy",
            "hlbm_mea_noalloc"]
 HLBM_NOALLOC_MAX_PARTICLES = 1024
 
@@ -94,6 +94,7 @@ def load(path=LIB_PATH):
     L.hlbm_get_mea_mode.argtypes = [_h]
     L.hlbm_autotune.argtypes = [_h, ctypes.c_int, _ip, _ip, _ip, _fp]
     L.hlbm_kernel_times.argtypes = [_h, ctypes.c_int, _fp]
+    L.hlbm_interior_cells.argtypes = [_h, ctypes.POINTER(ctypes.c_longlong)]
     L.hlbm_last_error.argtypes = [_h]
     L.hlbm_last_error.restype = ctypes.c_char_p
     L.hlbm_destroy.argtypes = [_h]
@@ -287,6 +288,13 @@ class Lattice:
         ms = (ctypes.c_float * 3)()
         _check(self.h, load().hlbm_kernel_times(self.h, int(nsteps), ms))
         return {"mea": ms[0], "update": ms[1], "collide_stream": ms[2]}
+
+    def interior_cells(self):
+        """(cell, particle) pairs with the cell centre inside the particle at
+        the current state (moments mode, after a step)."""
+        n = ctypes.c_longlong(0)
+        _check(self.h, load().hlbm_interior_cells(self.h, ctypes.byref(n)))
+        return n.value
 
 
 def hlbm_mea_noalloc(f, plane, nx, ny, nz, bc_flags, precision, fp16_scale_log2, parity, n, shape,

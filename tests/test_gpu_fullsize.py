@@ -6,9 +6,11 @@ against closed forms where it does not.
   hindered settling   128^3, walls at z, 200 spheres: three steps (both
                       parities, the bounding-box momentum exchange on the
                       first step and the moments form after it), every
-                      population and every particle
+                      population and every particle, and the number of
+                      cells inside particles (exact)
   non-spherical       256^3, 2000 ellipsoids and cuboids: two steps, every
-                      particle and every population
+                      particle and every population, and the number of
+                      cells inside particles (exact)
   dense batch         512 x 512 x 1024, 50 000 spheres, FP16 storage: the
                       first step from rest has a closed form for every
                       particle (the fluid at rest exerts no force, so
@@ -59,6 +61,14 @@ def _compare(lat, orc, w, steps):
     _pops_close(lat.populations(), orc.populations())
 
 
+def _interior_cells(lat, orc, n):
+    """The cells the next momentum exchange sums over: the collision's count
+    equals the oracle's (the same FP32 inside decision at the same state;
+    integers, so exactly)."""
+    want = sum(orc.mea(p)[2] for p in range(n))
+    assert want > 0 and lat.interior_cells() == want
+
+
 def test_hindered_settling_full_size(H, O):
     from paper_2312_14172_gb300 import workloads
     w = workloads.hindered_settling()
@@ -68,6 +78,7 @@ def test_hindered_settling_full_size(H, O):
     lat.set_launch(4, 4, 2)
     orc = O.from_workload(w)
     _compare(lat, orc, w, (1, 2))
+    _interior_cells(lat, orc, 200)
     lat.close()
 
 
@@ -80,6 +91,7 @@ def test_nonspherical_full_size(H, O):
     lat.set_launch(4, 8, 2)
     orc = O.from_workload(w)
     _compare(lat, orc, w, (1, 1))
+    _interior_cells(lat, orc, 2000)
     lat.close()
 
 

@@ -253,6 +253,14 @@ def test_errors_are_reported(H, O):
     with pytest.raises(H.HLBMError) as e:
         lat.add_particles([0], [[2.0] * 3], [[10, 10, 10]], rho_p=[2])
     assert e.value.code == H.HLBM_ERR_STATE
+    # the interior cells are counted by a collision in the moments mode only
+    with pytest.raises(H.HLBMError) as e:
+        lat.interior_cells()
+    assert e.value.code == H.HLBM_ERR_STATE
+    lat.set_mea_mode("moments")
+    with pytest.raises(H.HLBMError) as e:
+        lat.interior_cells()  # no step since the change of mode
+    assert e.value.code == H.HLBM_ERR_STATE
     lat.close()
     # a NaN population makes the density non-finite
     lat, _ = _pair(H, O, n, 0)

@@ -1,0 +1,64 @@
+"""The seeded input generators (no method arithmetic): random sequential
+insertion keeps the stated clearance between particles and to walls, and
+the workloads have the stated sizes."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2312_14172_gb300 import workloads as W
+
+
+def _segment_distance(p, u, hp, q, v, hq, n=401):
+    # brute force: closest points sampled along both segments
+    s = np.linspace(-hp, hp, n)[:, None, None] * u + p
+    t = np.linspace(-hq, hq, n)[None, :, None] * v + q
+    return float(np.sqrt(((s - t) ** 2).sum(-1)).min())
+
+
+@pytest.mark.parametrize("bc", [0, 4, 7])
+def test_grid_insertion_keeps_the_gap_between_spheres(bc):
+    rng = np.random.default_rng(7)
+    n = np.array([64, 48, 40])
+    r = rng.uniform(2.0, 5.0, 150)
+    gap = 1.5
+    X = W.sequential_insertion_grid(rng, n, r, bc, gap)
+    k = len(X)
+    assert k > 40
+    wall = np.array([(bc >> a) & 1 for a in range(3)], bool)
+    d = X[:, None, :] - X[None, :, :]
+    d[:, :, ~wall] -= n[~wall] * np.round(d[:, :, ~wall] / n[~wall])
+    D = np.sqrt((d ** 2).sum(-1)) - (r[:k, None] + r[None, :k])
+    np.fill_diagonal(D, np.inf)
+    assert D.min() >= gap
+    for a in np.nonzero(wall)[0]:
+        assert np.all(X[:, a] - r[:k] >= gap + 0.5 - 1e-12)
+        assert np.all(n[a] - 1.0 - X[:, a] - r[:k] >= gap - 0.5 - 1e-12)
+
+
+def test_grid_insertion_keeps_the_gap_between_capsules():
+    rng = np.random.default_rng(3)
+    n = np.array([48, 48, 48])
+    cnt = 40
+    r = rng.uniform(1.5, 2.5, cnt)
+    h = rng.uniform(0.0, 6.0, cnt)
+    ax = W.body_axis_z(W.random_quaternions(rng, cnt))
+    gap = 0.5
+    X = W.sequential_insertion_grid(rng, n, r, 0, gap, axes=ax, half_lengths=h)
+    k = len(X)
+    assert k == cnt
+    for i in range(k):
+        for j in range(i):
+            d = X[i] - X[j]
+            d -= n * np.round(d / n)
+            if np.linalg.norm(d) > r[i] + r[j] + h[i] + h[j] + gap:
+                continue
+            assert _segment_distance(X[i], ax[i], h[i], X[i] - d, ax[j], h[j]) >= r[i] + r[j] + gap - 0.05
+
+
+def test_phi_matched_variants_reach_the_named_fractions_on_a_small_box():
+    # the same laws on a box 1/64 of the volume: the fraction is what scales
+    w = W.dense_batch_phi_matched(n=(128, 128, 256), count=50000 // 32)
+    P = w["particles"]
+    phi = (4.0 / 3.0 * math.pi * P["a"][:, 0] ** 3).sum() / (128 * 128 * 256)
+    assert 0.17 < phi < 0.23
