@@ -23,7 +23,8 @@ cell updates and particles per second), cpu_baseline (the FP64 oracle on
 the host), e2e (the same
 metric through the C-ABI with pinned host buffers copied every step), clocks,
 gpu_launches, fp16 (the FP16-storage run and its error against FP32), and
-batched_fp16: the large dense batch (512 x 512 x 1024 cells, 50 000 spheres)
+nonspherical: the 256^3 box of 2000 ellipsoids and cuboids with FP32 and FP16
+storage; batched_fp16: the large dense batch (512 x 512 x 1024 cells, 50 000 spheres)
 with FP32 and with FP16 storage, its collision roofline and the FP16 error;
 ensemble: 64 independent boxes of 64..96^3 advanced together, FP32.
 
@@ -48,7 +49,7 @@ BYTES_PER_CELL = {"fp32": 2 * 19 * 4, "fp16": 2 * 19 * 2}
 
 
 WORKLOADS = ("hindered_settling", "single_sphere", "nonspherical", "dense_batch", "fluid_256",
-             "dense_batch_256")
+             "dense_batch_256", "nonspherical_phi", "dense_batch_phi")
 
 
 def make_workload(name):
@@ -67,6 +68,10 @@ def make_workload(name):
         return workloads.dense_batch(n=(256, 256, 256), count=0)
     if name == "dense_batch_256":
         return workloads.dense_batch(n=(256, 256, 256), count=50000 * 256 ** 3 // (512 * 512 * 1024))
+    if name == "nonspherical_phi":
+        return workloads.nonspherical_phi_matched()
+    if name == "dense_batch_phi":
+        return workloads.dense_batch_phi_matched()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -389,6 +394,7 @@ def run_gpu(args, ws, rank, local):
                 "error_note": "max |fp16 - fp32| / max|fp32| after the same steps; X as displacement; "
                               "rho absolute; FP32 itself matches the FP64 oracle within 1e-5"}
 
+    nonsph = nonspherical_leg(args, stream, peak, ws) if args.nonspherical else None
     batched = batched_fp16_leg(args, stream, peak, ws) if args.batched else None
     ensemble = ensemble_leg(args, stream, peak, ws) if args.ensemble else None
     phi = phi_matched_leg(args, stream, peak, ws) if args.phi_matched else None
@@ -415,6 +421,7 @@ def run_gpu(args, ws, rank, local):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "fp16": fp16,
+        "nonspherical": nonsph,
         "batched_fp16": batched,
         "ensemble": ensemble,
     }
@@ -579,6 +586,12 @@ def solid_fraction(P, cells):
     return float(vol.sum() / cells)
 
 
+def nonspherical_leg(args, stream, peak, ws):
+    """The non-spherical workload (256^3, 2000 ellipsoids and cuboids, eps =
+    1.5) with FP32 and with FP16 storage (populations of 1.27 GB / 0.64 GB)."""
+    return fp32_fp16_pair(make_workload("nonspherical"), args, stream, peak, ws, steps_max=100)
+
+
 def batched_fp16_leg(args, stream, peak, ws):
     """The large dense batch (512 x 512 x 1024 cells, 50 000 lognormal
     spheres, realised solid fraction 0.075) with FP32 and with FP16 storage
@@ -615,6 +628,8 @@ def main():
                     help="skip the 512x512x1024 dense-batch FP32/FP16 leg")
     ap.add_argument("--no-ensemble", dest="ensemble", action="store_false",
                     help="skip the 64-box ensemble leg")
+    ap.add_argument("--no-nonspherical", dest="nonspherical", action="store_false",
+                    help="skip the 256^3 non-spherical FP32/FP16 leg")
     ap.add_argument("--phi-matched", action="store_true",
                     help="add the solid-fraction-matched variants of the non-spherical and dense workloads "
                          "(about two minutes of host time to draw them)")

@@ -170,6 +170,66 @@ __device__ __forceinline__ Brick brick_of(const LbmArgs& a) {
   return k;
 }
 
+// A capsule (the points within sqrt(r2) of the segment c +- h u, u a unit
+// vector) that holds every cell a particle couples to (B > 0) and every cell
+// inside it, used to skip cells and rows far from elongated particles.
+//   sphere     radius a + eps/2, no segment
+//   ellipsoid  B > 0 only where |x / a| < s = 1 + eps / (2 a_min) (there the
+//              distance of Eq. B, (k - 1) k / |grad|, is at least (k - 1) a_min);
+//              the ellipsoid scaled by s lies in the capsule along its longest
+//              semi-axis a_k of radius s a_r and half-length s (a_k - a_r),
+//              a_r the larger of the two others
+//   cuboid     the box grown by eps/2 lies in the capsule along its longest
+//              half-extent h_k of radius |(h_i, h_j)| + eps/2 and half-length h_k
+// The radius carries a margin of 1e-3 relative + 0.01 cells over FP32 rounding.
+struct Capsule {
+  float u[3], h, r2;
+};
+
+__device__ __forceinline__ Capsule capsule_of(const Rec& R, float eps) {
+  Capsule c;
+  if (R.shape == 0) {
+    c.u[0] = 1.0f; c.u[1] = c.u[2] = 0.0f;
+    c.h = 0.0f;
+    const float r = R.a[0] + 0.5f * eps;
+    c.r2 = (r * 1.001f + 0.01f) * (r * 1.001f + 0.01f);
+    return c;
+  }
+  const int k = R.a[0] >= R.a[1] ? (R.a[0] >= R.a[2] ? 0 : 2) : (R.a[1] >= R.a[2] ? 1 : 2);
+  const int i = k == 0 ? 1 : 0, j = k == 2 ? 1 : 2;
+  // body axis k in world coordinates: column k of the body -> world rotation
+  c.u[0] = R.M[k]; c.u[1] = R.M[3 + k]; c.u[2] = R.M[6 + k];
+  float r;
+  if (R.shape == 1) {
+    const float s = 1.0f + 0.5f * eps / fminf(R.a[0], fminf(R.a[1], R.a[2]));
+    const float ar = fmaxf(R.a[i], R.a[j]);
+    r = s * ar;
+    c.h = s * (R.a[k] - ar);
+  } else {
+    r = sqrtf(R.a[i] * R.a[i] + R.a[j] * R.a[j]) + 0.5f * eps;
+    c.h = R.a[k];
+  }
+  r = r * 1.001f + 0.01f;
+  c.r2 = r * r;
+  return c;
+}
+
+// squared distance of offset r from the capsule's segment
+__device__ __forceinline__ float capsule_dist2(const Capsule& c, float rx, float ry, float rz) {
+  const float t = fminf(fmaxf(rx * c.u[0] + ry * c.u[1] + rz * c.u[2], -c.h), c.h);
+  const float qx = rx - t * c.u[0], qy = ry - t * c.u[1], qz = rz - t * c.u[2];
+  return qx * qx + qy * qy + qz * qz;
+}
+
+// squared distance of the x-parallel line through offset (., ry, rz) from
+// the capsule's segment
+__device__ __forceinline__ float capsule_row_dist2(const Capsule& c, float ry, float rz) {
+  const float uu = c.u[1] * c.u[1] + c.u[2] * c.u[2];
+  const float t = uu > 0.0f ? fminf(fmaxf((ry * c.u[1] + rz * c.u[2]) / uu, -c.h), c.h) : 0.0f;
+  const float qy = ry - t * c.u[1], qz = rz - t * c.u[2];
+  return qy * qy + qz * qz;
+}
+
 // Stage the particle candidates of the brick's tile in shared memory and
 // mark, for each row (local y + sub_y * local z) of the brick, the
 // candidates whose influence sphere meets the row.  Called by every thread
@@ -197,7 +257,14 @@ __device__ __forceinline__ void load_candidates(const LbmArgs& a, const Brick& k
       if (!(bd.bc & 2)) { if (r0y > 0.5f * Ly) r0y -= Ly; else if (r0y < -0.5f * Ly) r0y += Ly; }
       if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
       const float ry = __fsub_rn(r0y, R.xl[1]), rz = __fsub_rn(r0z, R.xl[2]);
-      if (ry * ry + rz * rz < R.rinf2) m |= 1ull << j;
+      if (ry * ry + rz * rz < R.rinf2) {
+        if (R.shape == 0) {
+          m |= 1ull << j;
+        } else {
+          const Capsule c = capsule_of(R, a.eps);
+          if (capsule_row_dist2(c, ry, rz) < c.r2) m |= 1ull << j;
+        }
+      }
     }
     s_rowmask[r] = m;
   }
@@ -235,32 +302,65 @@ __device__ __forceinline__ void couple_row(const Rec* srec, unsigned long long r
     if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
     const float ry = __fsub_rn(r0y, R.xl[1]), rz = __fsub_rn(r0z, R.xl[2]);
     const float d2 = ry * ry + rz * rz;
-    // a sphere's indicator is 1 within r <= a - eps/2 and 0 beyond a + eps/2:
-    // only cells in that shell need the distance and the ramp
-    const bool sph = R.shape == 0;
-    const float a_in = R.a[0] - 0.5f * eps, a_out = R.a[0] + 0.5f * eps;
-    const float r2_in = a_in > 0.0f ? a_in * a_in : -1.0f, r2_out = a_out * a_out;
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
+    // the cell's coupling to R: the particle id if its centre is inside, and
+    // the indicator with the particle velocity there when it is the largest
+    auto take = [&](int j, float rx, bool in, float B) {
+      if (in) {
+        if (cc.ip0[j] < 0) cc.ip0[j] = R.pid;
+        else if (cc.ip1[j] < 0) cc.ip1[j] = R.pid;
+        else atomicOr(status, ST_CAPACITY);  // three overlapping particles
+      }
+      if (B > cc.B[j] || (B == cc.B[j] && B > 0.0f && R.pid < cc.bestp[j])) {
+        cc.B[j] = B;
+        cc.bestp[j] = R.pid;
+        cc.upx[j] = R.u[0] + (R.w[1] * rz - R.w[2] * ry);
+        cc.upy[j] = R.u[1] + (R.w[2] * rx - R.w[0] * rz);
+        cc.upz[j] = R.u[2] + (R.w[0] * ry - R.w[1] * rx);
+      }
+    };
+    auto arm_x = [&](int j) {
       float r0x = (float)(x + j) - R.xh[0];
       if (!(bd.bc & 1)) { if (r0x > 0.5f * Lx) r0x -= Lx; else if (r0x < -0.5f * Lx) r0x += Lx; }
-      const float rx = __fsub_rn(r0x, R.xl[0]);
-      const float r2 = rx * rx + d2;
-      if (r2 < R.rinf2) {
-        const float rr[3] = {rx, ry, rz};
-        if (inside_from_offset(R, rr)) {
-          if (cc.ip0[j] < 0) cc.ip0[j] = R.pid;
-          else if (cc.ip1[j] < 0) cc.ip1[j] = R.pid;
-          else atomicOr(status, ST_CAPACITY);  // three overlapping particles
+      return __fsub_rn(r0x, R.xl[0]);
+    };
+    // The inside decision is the exactly rounded test of inside_from_offset;
+    // away from the surface the distance evaluated here (contracted
+    // arithmetic) has the same sign, and only cells within a margin far above
+    // the rounding difference of the two take the exact test (sphere: 1e-5
+    // relative in r^2; other shapes: 1e-3 cells).
+    if (R.shape == 0) {
+      // a sphere's indicator is 1 within r <= a - eps/2 and 0 beyond a + eps/2:
+      // only cells in that shell need the distance and the ramp
+      const float a_in = R.a[0] - 0.5f * eps, a_out = R.a[0] + 0.5f * eps;
+      const float r2_in = a_in > 0.0f ? a_in * a_in : -1.0f, r2_out = a_out * a_out;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const float rx = arm_x(j);
+        const float r2 = rx * rx + d2;
+        if (r2 < R.rinf2) {
+          bool in;
+          if (r2 < R.in2 * 0.99999f) in = true;
+          else if (r2 > R.in2 * 1.00001f) in = false;
+          else { const float rr[3] = {rx, ry, rz}; in = inside_from_offset(R, rr); }
+          const float B = r2 <= r2_in ? 1.0f : (r2 >= r2_out ? 0.0f : indicator(sdf(R, rx, ry, rz, r2), eps, inv_eps));
+          take(j, rx, in, B);
         }
-        const float B = !sph ? indicator(sdf(R, rx, ry, rz, r2), eps, inv_eps)
-                        : (r2 <= r2_in ? 1.0f : (r2 >= r2_out ? 0.0f : indicator(sdf(R, rx, ry, rz, r2), eps, inv_eps)));
-        if (B > cc.B[j] || (B == cc.B[j] && B > 0.0f && R.pid < cc.bestp[j])) {
-          cc.B[j] = B;
-          cc.bestp[j] = R.pid;
-          cc.upx[j] = R.u[0] + (R.w[1] * rz - R.w[2] * ry);
-          cc.upy[j] = R.u[1] + (R.w[2] * rx - R.w[0] * rz);
-          cc.upz[j] = R.u[2] + (R.w[0] * ry - R.w[1] * rx);
+      }
+    } else {
+      // elongated shapes: cells outside the enclosing capsule neither couple
+      // nor lie inside
+      const Capsule cap = capsule_of(R, eps);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const float rx = arm_x(j);
+        const float r2 = rx * rx + d2;
+        if (r2 < R.rinf2 && capsule_dist2(cap, rx, ry, rz) < cap.r2) {
+          const float d = sdf(R, rx, ry, rz, r2);
+          bool in;
+          if (d < -1e-3f) in = true;
+          else if (d > 1e-3f) in = false;
+          else { const float rr[3] = {rx, ry, rz}; in = inside_from_offset(R, rr); }
+          take(j, rx, in, indicator(d, eps, inv_eps));
         }
       }
     }

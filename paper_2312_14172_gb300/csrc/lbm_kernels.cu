@@ -205,20 +205,35 @@ __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const S* fbase = reinterpret_cast<const S*>(a.f);
-  for (long long k0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); k0 < n; k0 += stride) {
-    const long long kc = k0 + lane;  // compact index over all stripes
-    bool valid = kc < n;
-    int pid = -1;
-    float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
-    long long k = 0;  // entry index in the striped list
-    if (valid) {
+  // the entry with compact index kc (over all stripes) and its recorded
+  // moments; loaded one iteration ahead, so that the next entry is on its
+  // way while this one's arrivals are read
+  auto fetch = [&](long long kc, int2& e, float4& m) {
+    if (kc < n) {
       int st = 0;  // the last stripe whose first entry is at or before kc
 #pragma unroll
       for (int step = ILIST_STRIPES / 2; step > 0; step >>= 1)
         if (s_first[st + step] <= kc) st += step;
-      k = (long long)st * a.ilist_cap + (kc - s_first[st]);
+      const long long k = (long long)st * a.ilist_cap + (kc - s_first[st]);
+      e = a.ilist_idx[k];
+      m = a.ilist_mom[k];
+    } else {
+      e = make_int2(0, -1);
+      m = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const int2 e = valid ? a.ilist_idx[k] : make_int2(0, -1);
+  };
+  long long k0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane);
+  int2 e_next;
+  float4 m_next;
+  fetch(k0 + lane, e_next, m_next);
+  for (; k0 < n; k0 += stride) {
+    const long long kc = k0 + lane;
+    bool valid = kc < n;
+    int pid = -1;
+    float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
+    const int2 e = e_next;
+    const float4 sd = m_next;
+    fetch(kc + stride, e_next, m_next);
     // an entry names a particle and a cell of that particle's box; anything
     // else was never written by the collision and is skipped with a flag
     if (valid && (e.y < 0 || e.y >= a.np)) valid = false;
@@ -228,7 +243,6 @@ __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
     if (valid && (cl < 0 || cl >= (long long)bd.nx * bd.ny * bd.nz)) valid = false;
     if (kc < n && !valid) atomicOr(a.status, ST_INTERNAL);
     if (valid) {
-      const float4 sd = a.ilist_mom[k];
       pid = e.y;
       const Rec& R = a.rec[pid];
       const int c = (int)cl;
