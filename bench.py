@@ -169,11 +169,12 @@ class ClockSampler:
                     self.window[0] <= r[0] <= self.window[1] for r in rows))}
 
 
-def oracle_mlups(w, steps, warmup=0):
-    """FP64 oracle (single thread) on the workload: MLUPS and seconds."""
+def oracle_mlups(w, steps, warmup=0, omp=False):
+    """FP64 oracle on the workload (single thread, or its OpenMP build on all
+    host cores): MLUPS and seconds."""
     from oracle import oracle
-    oracle.build()
-    o = oracle.from_workload(w)
+    oracle.build(omp=omp)
+    o = oracle.from_workload(w, omp=omp)
     if warmup:
         o.step(warmup)
     t0 = time.perf_counter()
@@ -657,6 +658,15 @@ def main():
                 "value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                 "sample": f"{steps} steps of the full {w['n'][0]}x{w['n'][1]}x{w['n'][2]} workload, "
                           f"FP64, single thread, {dt:.1f} s"}
+            # the same oracle built with OpenMP: collision and streaming over z
+            # slices, momentum exchange over particles, on every host core
+            from oracle import oracle
+            probe, dt1 = oracle_mlups(w, 1, omp=True)
+            steps = max(1, min(100, int(15.0 / max(dt1, 1e-3))))
+            mlups, dt = oracle_mlups(w, steps, omp=True)
+            line["cpu_baseline"]["openmp"] = {
+                "value": mlups, "unit": "MLUPS", "cores": oracle.threads(omp=True), "kind": "oracle",
+                "sample": f"{steps} steps of the same workload, FP64, OpenMP, {dt:.1f} s"}
         else:
             line["cpu_baseline"] = None
         print(json.dumps(line), flush=True)

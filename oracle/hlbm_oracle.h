@@ -103,6 +103,9 @@ void oracle_collide_only(const oracle_sim* s, double* post);
 void oracle_stream_only(oracle_sim* s, const double* post);
 /* Newton-Euler with given total forces and torques (no MEA), for pins */
 void oracle_integrate_only(oracle_sim* s, const double* F, const double* T);
+/* threads the loops of a step use: omp_get_max_threads() in the -fopenmp
+ * build, else 1 */
+int oracle_threads(void);
 
 #ifdef __cplusplus
 }

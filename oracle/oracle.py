@@ -15,6 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "hlbm_oracle.c")
 HDR = os.path.join(HERE, "hlbm_oracle.h")
 LIB = os.path.join(HERE, "liboracle.so")
+# the same source built with -fopenmp (loops shared among the host cores;
+# identical results), for timing only
+LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
 
 SPHERE, ELLIPSOID, CUBOID = 0, 1, 2
 WALL_X, WALL_Y, WALL_Z = 1, 2, 4
@@ -23,32 +26,35 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
-def build(force=False):
-    """Compile the oracle with gcc (C99, -O2, no contraction, no fast-math)."""
+def _compile(out, extra, force):
     newest = max(os.path.getmtime(SRC), os.path.getmtime(HDR))
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
-        return LIB
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
+        return out
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=HERE)
     os.close(fd)
     cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", SRC, "-o", tmp, "-lm"]
+           "-fno-fast-math", *extra, SRC, "-o", tmp, "-lm"]
     try:
         subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
+        os.replace(tmp, out)
     finally:
         if os.path.exists(tmp):
             os.remove(tmp)
-    return LIB
+    return out
 
 
-_lib = None
+def build(force=False, omp=False):
+    """Compile the oracle with gcc (C99, -O2, no contraction, no fast-math);
+    omp: the -fopenmp build."""
+    return _compile(LIB_OMP, ["-fopenmp"], force) if omp else _compile(LIB, [], force)
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        build()
-        L = ctypes.CDLL(LIB)
+_libs = {}
+
+
+def lib(omp=False):
+    if omp not in _libs:
+        L = ctypes.CDLL(build(omp=omp))
         L.oracle_create.restype = ctypes.c_void_p
         L.oracle_create.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double, ctypes.c_double,
                                                          ctypes.c_int, _dp, _dp]
@@ -78,8 +84,14 @@ def lib():
         L.oracle_sdf_body.argtypes = [ctypes.c_int, _dp, _dp]
         L.oracle_rotation.argtypes = [_dp, _dp]
         L.oracle_inside_fp32.argtypes = [ctypes.c_int, _dp, _dp, _dp, _ip, _ip, ctypes.c_int]
-        _lib = L
-    return _lib
+        L.oracle_threads.restype = ctypes.c_int
+        _libs[omp] = L
+    return _libs[omp]
+
+
+def threads(omp=False):
+    """Threads the oracle's loops use (1 for the plain build)."""
+    return lib(omp).oracle_threads()
 
 
 def _d(a):
@@ -136,12 +148,13 @@ def inside_fp32(shape, a, q, X, cell, n, bc):
 class Oracle:
     """One FP64 HLBM lattice with its particles (two-lattice push streaming)."""
 
-    def __init__(self, n, tau, eps=0.5, bc=0, gravity=(0, 0, 0), fluid_force=(0, 0, 0)):
+    def __init__(self, n, tau, eps=0.5, bc=0, gravity=(0, 0, 0), fluid_force=(0, 0, 0), omp=False):
+        self._L = lib(omp)
         self.n = tuple(int(v) for v in n)
         g, gp = _d(gravity)
         ff, ffp = _d(fluid_force)
         self._keep = (g, ff)
-        self.h = lib().oracle_create(self.n[0], self.n[1], self.n[2], float(tau), float(eps),
+        self.h = self._L.oracle_create(self.n[0], self.n[1], self.n[2], float(tau), float(eps),
                                      int(bc), gp, ffp)
         if not self.h:
             raise ValueError("oracle_create rejected the lattice arguments")
@@ -149,7 +162,7 @@ class Oracle:
 
     def close(self):
         if self.h:
-            lib().oracle_destroy(self.h)
+            self._L.oracle_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -160,7 +173,7 @@ class Oracle:
 
     @property
     def num_particles(self):
-        return lib().oracle_num_particles(self.h)
+        return self._L.oracle_num_particles(self.h)
 
     def add_particles(self, shape, a, X, U=None, omega=None, quat=None, rho_p=None):
         shape, sp = _i(shape)
@@ -175,7 +188,7 @@ class Oracle:
             quat = np.tile([1.0, 0, 0, 0], (n, 1))
         qv, qp = _d(np.asarray(quat, float).reshape(n, 4))
         rho, rp = _d(np.asarray(rho_p, float).reshape(n))
-        rc = lib().oracle_add_particles(self.h, n, sp, ap, Xp, Up, Wp, qp, rp)
+        rc = self._L.oracle_add_particles(self.h, n, sp, ap, Xp, Up, Wp, qp, rp)
         if rc != 0:
             raise ValueError(f"oracle_add_particles failed ({rc})")
 
@@ -190,70 +203,71 @@ class Oracle:
                 arr, p = _d(np.asarray(v, float).reshape(n, k))
                 keep.append(arr)
                 args.append(p)
-        if lib().oracle_set_particle_state(self.h, *args) != 0:
+        if self._L.oracle_set_particle_state(self.h, *args) != 0:
             raise ValueError("oracle_set_particle_state failed")
 
     def particle_state(self):
         n = self.num_particles
         out = {k: np.zeros((n, 4 if k == "quat" else 3)) for k in ("X", "U", "omega", "quat", "F", "T")}
-        lib().oracle_particle_state(self.h, *[out[k].ctypes.data_as(_dp) for k in
+        self._L.oracle_particle_state(self.h, *[out[k].ctypes.data_as(_dp) for k in
                                               ("X", "U", "omega", "quat", "F", "T")])
         return out
 
     def populations(self):
         f = np.zeros((19, self.n[2], self.n[1], self.n[0]))
-        lib().oracle_get_populations(self.h, f.ctypes.data_as(_dp))
+        self._L.oracle_get_populations(self.h, f.ctypes.data_as(_dp))
         return f
 
     def set_populations(self, f):
         f, fp = _d(np.asarray(f, float).reshape(19, self.n[2], self.n[1], self.n[0]))
-        lib().oracle_set_populations(self.h, fp)
+        self._L.oracle_set_populations(self.h, fp)
 
     def step(self, nsteps=1):
-        lib().oracle_step(self.h, int(nsteps))
+        self._L.oracle_step(self.h, int(nsteps))
 
     @property
     def steps_done(self):
-        return lib().oracle_steps_done(self.h)
+        return self._L.oracle_steps_done(self.h)
 
     def mea(self, p):
         F = np.zeros(3)
         T = np.zeros(3)
-        cnt = lib().oracle_mea(self.h, int(p), F.ctypes.data_as(_dp), T.ctypes.data_as(_dp))
+        cnt = self._L.oracle_mea(self.h, int(p), F.ctypes.data_as(_dp), T.ctypes.data_as(_dp))
         return F, T, cnt
 
     def mea_printed_cell(self, x, up):
         x, xp = _i(x)
         up, upp = _d(up)
         Fh = np.zeros(3)
-        lib().oracle_mea_printed_cell(self.h, xp, upp, Fh.ctypes.data_as(_dp))
+        self._L.oracle_mea_printed_cell(self.h, xp, upp, Fh.ctypes.data_as(_dp))
         return Fh
 
     def indicator_field(self):
         B = np.zeros((self.n[2], self.n[1], self.n[0]))
         pid = np.zeros((self.n[2], self.n[1], self.n[0]), np.int32)
-        lib().oracle_indicator_field(self.h, B.ctypes.data_as(_dp), pid.ctypes.data_as(_ip))
+        self._L.oracle_indicator_field(self.h, B.ctypes.data_as(_dp), pid.ctypes.data_as(_ip))
         return B, pid
 
     def collide_only(self):
         post = np.zeros((19, self.n[2], self.n[1], self.n[0]))
-        lib().oracle_collide_only(self.h, post.ctypes.data_as(_dp))
+        self._L.oracle_collide_only(self.h, post.ctypes.data_as(_dp))
         return post
 
     def stream_only(self, post):
         post, pp = _d(post)
-        lib().oracle_stream_only(self.h, pp)
+        self._L.oracle_stream_only(self.h, pp)
 
     def integrate_only(self, F, T):
         n = self.num_particles
         F, Fp = _d(np.asarray(F, float).reshape(n, 3))
         T, Tp = _d(np.asarray(T, float).reshape(n, 3))
-        lib().oracle_integrate_only(self.h, Fp, Tp)
+        self._L.oracle_integrate_only(self.h, Fp, Tp)
 
 
-def from_workload(w):
-    """Build an oracle lattice from a workload description (see the workloads module)."""
-    o = Oracle(w["n"], w["tau"], w["eps"], w["bc"], w["gravity"], w.get("fluid_force", (0, 0, 0)))
+def from_workload(w, omp=False):
+    """Build an oracle lattice from a workload description (see the workloads
+    module); omp: on the -fopenmp build."""
+    o = Oracle(w["n"], w["tau"], w["eps"], w["bc"], w["gravity"], w.get("fluid_force", (0, 0, 0)), omp=omp)
     P = w["particles"]
     if len(P["shape"]):
         o.add_particles(P["shape"], P["a"], P["X"], P["U"], P["omega"], P["quat"], P["rho_p"])

@@ -221,3 +221,22 @@ def test_poiseuille_profile(O):
     assert _poiseuille_error(O, 0.8) < 1e-2
     # and the error grows away from the exact relaxation time
     assert _poiseuille_error(O, 1.5) > 10 * _poiseuille_error(O, tau_exact)
+
+
+def test_openmp_build_gives_identical_results():
+    """The oracle built with -fopenmp (used only to time it on every host
+    core) computes every cell and particle with the same operations as the
+    plain build: populations and particle states agree bit for bit."""
+    from oracle import oracle as O
+    from paper_2312_14172_gb300 import workloads as W
+    w = W.hindered_settling(n=(40, 36, 32), count=6, r_range=(3.0, 5.0), steps=3)
+    res = []
+    for omp in (False, True):
+        o = O.from_workload(w, omp=omp)
+        o.step(3)
+        res.append((o.populations(), o.particle_state()))
+        o.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    for k in res[0][1]:
+        assert np.array_equal(res[0][1][k], res[1][1][k]), k
+    assert O.threads(False) == 1 and O.threads(True) >= 1
