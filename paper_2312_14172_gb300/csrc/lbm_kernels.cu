@@ -182,58 +182,61 @@ template <typename S, int PAR, bool WALLS>
 __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
   pdl_trigger();
   pdl_wait();
-  // the stripes' entries numbered one after the other: s_first[s] is the
-  // number of entries in the stripes before s
-  __shared__ long long s_first[ILIST_STRIPES + 1];
+  // The list is walked in chunks of 32 entries, the stripes taken in turn
+  // and each stripe from its end: the first wave reads the arrivals the
+  // collision wrote last, which L2 still holds.  Chunk q covers entries
+  // [c_s - 32 (j + 1), c_s - 32 j) of stripe s = q mod 64, j = q / 64, c_s the
+  // stripe's count; the lanes take them in ascending order, so that a run of
+  // cells the collision appended together stays in one warp.
+  __shared__ int s_cnt[ILIST_STRIPES];
+  __shared__ int s_chunks;  // chunks per stripe
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    long long c0 = min((long long)a.ilist_count[lane], a.ilist_cap);
-    long long c1 = min((long long)a.ilist_count[lane + 32], a.ilist_cap);
-    long long s0 = c0, s1 = c1;
+    const int c0 = (int)min((long long)a.ilist_count[lane], a.ilist_cap);
+    const int c1 = (int)min((long long)a.ilist_count[lane + 32], a.ilist_cap);
+    s_cnt[lane] = c0;
+    s_cnt[lane + 32] = c1;
+    int m = max(c0, c1);
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const long long t0 = __shfl_up_sync(0xffffffffu, s0, off), t1 = __shfl_up_sync(0xffffffffu, s1, off);
-      if (lane >= off) { s0 += t0; s1 += t1; }
-    }
-    const long long tot0 = __shfl_sync(0xffffffffu, s0, 31);
-    s_first[lane] = s0 - c0;
-    s_first[lane + 32] = tot0 + s1 - c1;
-    if (lane == 31) s_first[ILIST_STRIPES] = tot0 + s1;
+    for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) s_chunks = (m + 31) / 32;
   }
   __syncthreads();
-  const long long n = s_first[ILIST_STRIPES];
+  const long long nq = (long long)ILIST_STRIPES * s_chunks;
   const int lane = threadIdx.x & 31;
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   const S* fbase = reinterpret_cast<const S*>(a.f);
-  // the entry with compact index kc (over all stripes) and its recorded
-  // moments; loaded one iteration ahead, so that the next entry is on its
-  // way while this one's arrivals are read
-  auto fetch = [&](long long kc, int2& e, float4& m) {
-    if (kc < n) {
-      int st = 0;  // the last stripe whose first entry is at or before kc
-#pragma unroll
-      for (int step = ILIST_STRIPES / 2; step > 0; step >>= 1)
-        if (s_first[st + step] <= kc) st += step;
-      const long long k = (long long)st * a.ilist_cap + (kc - s_first[st]);
-      e = a.ilist_idx[k];
-      m = a.ilist_mom[k];
-    } else {
-      e = make_int2(0, -1);
-      m = make_float4(0.f, 0.f, 0.f, 0.f);
+  // position of this lane's entry in chunk q (negative: none), its index in
+  // the striped list, and the entry with its recorded moments; loaded one
+  // chunk ahead, so that the next entry is on its way while this one's
+  // arrivals are read
+  auto fetch = [&](long long q, int& pos, int2& e, float4& m) {
+    pos = -1;
+    e = make_int2(0, -1);
+    m = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q < nq) {
+      const int st = (int)(q & (ILIST_STRIPES - 1)), j = (int)(q / ILIST_STRIPES);
+      pos = s_cnt[st] - 32 * (j + 1) + lane;
+      if (pos >= 0) {
+        const long long k = (long long)st * a.ilist_cap + pos;
+        e = a.ilist_idx[k];
+        m = a.ilist_mom[k];
+      }
     }
   };
-  long long k0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane);
+  long long q = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  int pos_next;
   int2 e_next;
   float4 m_next;
-  fetch(k0 + lane, e_next, m_next);
-  for (; k0 < n; k0 += stride) {
-    const long long kc = k0 + lane;
-    bool valid = kc < n;
+  fetch(q, pos_next, e_next, m_next);
+  for (; q < nq; q += nwarps) {
+    bool valid = pos_next >= 0;
+    const bool listed = valid;
     int pid = -1;
     float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
     const int2 e = e_next;
     const float4 sd = m_next;
-    fetch(kc + stride, e_next, m_next);
+    fetch(q + nwarps, pos_next, e_next, m_next);
     // an entry names a particle and a cell of that particle's box; anything
     // else was never written by the collision and is skipped with a flag
     if (valid && (e.y < 0 || e.y >= a.np)) valid = false;
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
     const BoxDesc bd = a.boxes[a.nboxes == 1 || !valid ? 0 : a.rec[e.y].box];
     const long long cl = (long long)e.x - bd.cell_off;
     if (valid && (cl < 0 || cl >= (long long)bd.nx * bd.ny * bd.nz)) valid = false;
-    if (kc < n && !valid) atomicOr(a.status, ST_INTERNAL);
+    if (listed && !valid) atomicOr(a.status, ST_INTERNAL);
     if (valid) {
       pid = e.y;
       const Rec& R = a.rec[pid];
