@@ -84,9 +84,12 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(cells_x=2):
+    """Hash of the sources that define the collision kernel with cells_x cells
+    per thread (a committed ncu figure holds only for the same source)."""
     h = hashlib.sha256()
-    for f in ("lbm_kernels.cu", "lbm_pair_kernels.cu", "lbm_common.cuh", "hlbm_internal.cuh"):
+    main = "lbm_pair_kernels.cu" if cells_x == 2 else "lbm_kernels.cu"
+    for f in (main, "lbm_common.cuh", "hlbm_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2312_14172_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -101,7 +104,7 @@ def profiled_traffic(workload, precision, cells, cells_x):
         return None
     with open(path) as fh:
         d = json.load(fh)
-    if d.get("kernel_source_hash") != kernel_source_hash() or d.get("cells_per_thread", 1) != cells_x:
+    if d.get("kernel_source_hash") != kernel_source_hash(cells_x) or d.get("cells_per_thread", 1) != cells_x:
         return None
     per_cell = d.get("dram_bytes_per_cell")
     return None if per_cell is None else per_cell * cells
