@@ -95,6 +95,48 @@ def test_fluid_only_random_state(H, O, bc, nx, cells_x):
 
 
 @pytest.mark.parametrize("cells_x", [1, 2])
+@pytest.mark.parametrize("bc", [0, 5])
+def test_fluid_only_fp16_both_kernels(H, O, bc, cells_x):
+    """FP16 storage of f - w (times 2^14) through both kernels, ragged odd
+    nx, every parity: within the storage error of the oracle."""
+    n = (45, 19, 21)
+    lat, orc = _pair(H, O, n, bc, tau=0.66, ff=(2e-6, -1e-6, 3e-6), precision="fp16")
+    lat.set_launch(4, 2, cells_x)
+    f0 = _random_pops(O, n, 20 + bc)
+    lat.set_populations(f0)
+    orc.set_populations(f0)
+    for steps in (1, 1, 3):
+        lat.step(steps)
+        orc.step(steps)
+        fg, fo = lat.populations(), orc.populations()
+        assert np.max(np.abs(fg - fo) / fo) < 1e-4
+    lat.sync()
+    lat.close()
+
+
+@pytest.mark.parametrize("cells_x", [1, 2])
+def test_particles_fp16_both_kernels(H, O, cells_x):
+    """Spheres between walls with FP16 storage through both kernels and the
+    moments form of the momentum exchange: populations within the storage
+    error, particle displacements within 2 % of the oracle's."""
+    from paper_2312_14172_gb300 import workloads
+    w = workloads.hindered_settling(n=(46, 40, 36), count=5, r_range=(3.0, 5.0), steps=10)
+    P = w["particles"]
+    lat = H.from_workload(w, precision="fp16")
+    lat.set_mea_mode("moments")
+    lat.set_launch(4, 4, cells_x)
+    orc = O.from_workload(w)
+    lat.step(10)
+    orc.step(10)
+    fg, fo = lat.populations(), orc.populations()
+    assert np.max(np.abs(fg - fo) / fo) < 1e-4
+    sg, so = lat.particle_state(), orc.particle_state()
+    dX = so["X"] - P["X"]
+    assert np.max(np.abs((sg["X"] - P["X"]) - dX)) <= 2e-2 * np.abs(dX).max() + 1e-6
+    lat.close()
+
+
+@pytest.mark.parametrize("cells_x", [1, 2])
 def test_degenerate_thin_boxes(H, O, cells_x):
     for n, bc in (((1, 1, 16), 4), ((1, 7, 5), 0), ((33, 1, 1), 0), ((2, 2, 2), 7), ((2, 1, 16), 4),
                   ((2, 7, 5), 0), ((34, 1, 1), 1), ((4, 3, 3), 7), ((3, 2, 2), 7), ((33, 1, 1), 1),
