@@ -63,8 +63,14 @@ __device__ void build_record(const double* P, int cap, int p, int shape, int box
   make_record(X, U, W, q, A, iA, pget(P, cap, PF_RINF, p), p, shape, box, R);
 }
 
+// six resident blocks per SM (80 registers): the bounding-box walk is
+// latency-bound, and more resident blocks beat the few spills this costs
+#ifndef HLBM_MEA_MINBLOCKS
+#define HLBM_MEA_MINBLOCKS 6
+#endif
+
 template <typename S, int PAR>
-__global__ void __launch_bounds__(128) mea_kernel(PartArgs a) {
+__global__ void __launch_bounds__(128, HLBM_MEA_MINBLOCKS) mea_kernel(PartArgs a) {
   pdl_trigger();
   pdl_wait();
   const int chunk = blockIdx.x;
