@@ -63,10 +63,10 @@ __device__ void build_record(const double* P, int cap, int p, int shape, int box
   make_record(X, U, W, q, A, iA, pget(P, cap, PF_RINF, p), p, shape, box, R);
 }
 
-// six resident blocks per SM (80 registers): the bounding-box walk is
-// latency-bound, and more resident blocks beat the few spills this costs
+// eight resident blocks per SM (64 registers): the bounding-box walk is
+// latency-bound, and more resident blocks beat the spills this costs
 #ifndef HLBM_MEA_MINBLOCKS
-#define HLBM_MEA_MINBLOCKS 6
+#define HLBM_MEA_MINBLOCKS 8
 #endif
 
 template <typename S, int PAR>
