@@ -112,7 +112,8 @@ __global__ void noalloc_setup_kernel(NoAllocArgs a) {
 // last block of a particle adds the planes' FP64 partials in plane order and
 // writes the caller's output
 template <typename S, int PAR>
-__global__ void __launch_bounds__(128) noalloc_mea_kernel(NoAllocArgs a) {
+// eight resident blocks per SM, as the bounding-box momentum exchange
+__global__ void __launch_bounds__(128, 8) noalloc_mea_kernel(NoAllocArgs a) {
   const int p = blockIdx.x, iz = blockIdx.y;
   const int npl = na_npl(a)[p];
   if (iz >= npl) return;
