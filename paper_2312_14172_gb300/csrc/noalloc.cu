@@ -110,9 +110,9 @@ __global__ void noalloc_setup_kernel(NoAllocArgs a) {
 
 // the bounding-box momentum exchange, one block per (particle, plane); the
 // last block of a particle adds the planes' FP64 partials in plane order and
-// writes the caller's output
+// writes the caller's output; eight resident blocks per SM, as the
+// bounding-box momentum exchange of the library
 template <typename S, int PAR>
-// eight resident blocks per SM, as the bounding-box momentum exchange
 __global__ void __launch_bounds__(128, 8) noalloc_mea_kernel(NoAllocArgs a) {
   const int p = blockIdx.x, iz = blockIdx.y;
   const int npl = na_npl(a)[p];
