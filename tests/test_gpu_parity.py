@@ -226,9 +226,9 @@ def test_hindered_settling_subbox_walls(H, O, mode):
     """Spheres between walls (the hindered-settling configuration) on a box
     the oracle finishes quickly, ragged in x and y."""
     from paper_2312_14172_gb300 import workloads
-    w = workloads.hindered_settling(n=(70, 45, 48), count=14, steps=40)
+    w = workloads.hindered_settling(n=(70, 45, 48), count=14, steps=50)
     assert len(w["particles"]["shape"]) >= 8
-    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 40, chunks=(1,), mode=mode)
+    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 50, chunks=(1,), mode=mode)
     _pops_close(fg, fo)
     _motion_close(sg, so, X0, U0, W0)
 
@@ -236,12 +236,12 @@ def test_hindered_settling_subbox_walls(H, O, mode):
 def test_nonspherical_subbox(H, O):
     """Ellipsoids and cuboids with random orientations, eps = 1.5."""
     from paper_2312_14172_gb300 import workloads
-    w = workloads.nonspherical(n=(64, 56, 60), count=16, steps=40)
+    w = workloads.nonspherical(n=(64, 56, 60), count=16, steps=50)
     assert len(w["particles"]["shape"]) >= 10
     # give them some spin so that the rotation update is exercised
     rng = np.random.default_rng(1)
     w["particles"]["omega"] = rng.uniform(-3e-3, 3e-3, w["particles"]["omega"].shape)
-    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 40, chunks=(1,), mode="moments")
+    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 50, chunks=(1,), mode="moments")
     _pops_close(fg, fo)
     _motion_close(sg, so, X0, U0, W0)
     assert np.allclose(sg["quat"], so["quat"], atol=1e-9)
