@@ -402,6 +402,7 @@ def run_gpu(args, ws, rank, local):
     batched = batched_fp16_leg(args, stream, peak, ws) if args.batched else None
     ensemble = ensemble_leg(args, stream, peak, ws) if args.ensemble else None
     phi = phi_matched_leg(args, stream, peak, ws) if args.phi_matched else None
+    settling = settling_validation_leg(args, stream) if args.settling_validation else None
 
     launches_per_step = 3 if npart > 0 else 1
     line = {
@@ -431,6 +432,8 @@ def run_gpu(args, ws, rank, local):
     }
     if phi is not None:
         line["phi_matched"] = phi
+    if settling is not None:
+        line["settling_validation"] = settling
     return line
 
 
@@ -596,6 +599,96 @@ def nonspherical_leg(args, stream, peak, ws):
     return fp32_fp16_pair(make_workload("nonspherical"), args, stream, peak, ws, steps_max=100)
 
 
+def settling_validation_leg(args, stream):
+    """Zero-net-flow hindered settling (the paper's Sec. 5.1 set-up with the
+    counter force of workloads.zero_net_flow) at solid fractions 0.05-0.2:
+    monodisperse spheres of 8 cells diameter in periodic cubes of 8
+    diameters, about 20 settling times each.  Reports the mean settling
+    velocity over the second half (relative to the volume-averaged velocity
+    of the lattice, the counter force held at zero net momentum by feedback)
+    against the terminal velocity u* of an
+    isolated sphere (Stokes with the Schiller-Naumann drag, solved for Re),
+    against one sphere in the same periodic box, and the Richardson-Zaki
+    law u / u* = (1 - phi)^n (n = 4.65 for Re < 0.2, 4.4 Re^-0.03 up to 1).
+    A qualitative check: the paper shows this comparison only as figures,
+    and 8 cells per diameter is below its converged resolution."""
+    import torch
+    from paper_2312_14172_gb300 import hlbm, workloads
+    d, tau, rho_p, g = 8, 0.6, 2.5, 1e-5
+    nu = (tau - 0.5) / 3.0
+    u_st = 2.0 / 9.0 * (rho_p - 1.0) * g * (d / 2) ** 2 / nu
+    u = u_st
+    for _ in range(50):  # Schiller-Naumann: C_d = 24/Re (1 + 0.15 Re^0.687)
+        re = u * d / nu
+        u = u_st / (1.0 + 0.15 * re ** 0.687)
+    re = u * d / nu
+    n_rz = 4.65 if re < 0.2 else 4.4 * re ** -0.03
+    t_star = d / u
+    steps = int(20 * t_star)
+    sample = max(1, int(t_star / 10))
+
+    cz = np.array([0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1], float)
+
+    def run(w):
+        # The momentum exchange does not see the EDM forcing of the smooth
+        # zone outside the interior cells (an O(eps / r) share of the
+        # coupling), so a constant counter force leaves a small net force and
+        # the whole suspension would drift.  The counter force is therefore
+        # reset every sample interval: it cancels the drift rate measured over
+        # the last interval and lets the accumulated momentum (lattice plus the
+        # particles' mass beyond the fluid's) decay over a few intervals.  The
+        # settling velocity is taken relative to the volume-averaged velocity
+        # of the lattice (the fluid inside a particle moves with it).
+        lat = hlbm.from_workload(w, stream=stream)
+        lat.set_mea_mode("moments")
+        lat.set_launch(4, 8, 2)
+        P = w["particles"]
+        extra = (np.asarray(P["rho_p"], float) - 1.0) * workloads.particle_volumes(P)
+        ncell = float(np.prod(w["n"]))
+        fz = float(w["fluid_force"][2])
+        p_prev = 0.0
+        vals, drift, stopped = [], [], None
+        t0 = time.perf_counter()
+        for k in range(0, steps, sample):
+            lat.step(sample)
+            try:
+                U = lat.particle_state()["U"]
+            except hlbm.HLBMError as e:  # e.g. particles overlapping (the paper has no contact model)
+                stopped = {"step": k + sample, "t_over_tstar": (k + sample) / t_star, "error": str(e)}
+                break
+            f = lat.populations()
+            jz = np.einsum("i,izyx->zyx", cz, f)
+            p_tot = float(jz.sum() + (extra * U[:, 2]).sum())
+            fz -= (p_tot - p_prev) / (ncell * sample) + p_tot / (ncell * 4 * sample)
+            p_prev = p_tot
+            lat.set_fluid_force((0.0, 0.0, fz))
+            if k >= steps // 2:
+                uz = float((jz / f.sum(axis=0)).mean())
+                vals.append(uz - float(U[:, 2].mean()))
+                drift.append(uz)
+        dt = time.perf_counter() - t0
+        lat.close()
+        mean = lambda v: float(np.mean(v)) if v else float("nan")
+        return mean(vals), dt, stopped, mean(drift)
+
+    one = workloads.hindered_settling_periodic(0.05, d=d)
+    one = dict(one)
+    one["particles"] = {k: v[:1] for k, v in one["particles"].items()}
+    one = workloads.zero_net_flow(one)
+    u1, _, _, _ = run(one)
+    rows = []
+    for phi in (0.05, 0.1, 0.15, 0.2):
+        w = workloads.hindered_settling_periodic(phi, d=d)
+        ub, dt, stopped, drift = run(w)
+        P = w["particles"]
+        rows.append({"phi": float(workloads.particle_volumes(P).sum() / np.prod(w["n"])),
+                     "particles": len(P["shape"]), "u_over_ustar": ub / u, "u_over_u_single": ub / u1,
+                     "richardson_zaki": (1.0 - phi) ** n_rz, "drift_over_ustar": drift / u,
+                     "seconds": dt, "stopped": stopped})
+    return {"d": d, "box": [8 * d] * 3, "tau": tau, "rho_p": rho_p, "g": g, "u_star": u, "re": re,
+            "n_rz": n_rz, "steps": steps, "t_star_steps": t_star, "u_single_over_ustar": u1 / u, "rows": rows}
+
+
 def batched_fp16_leg(args, stream, peak, ws):
     """The large dense batch (512 x 512 x 1024 cells, 50 000 lognormal
     spheres, realised solid fraction 0.075) with FP32 and with FP16 storage
@@ -634,6 +727,9 @@ def main():
                     help="skip the 64-box ensemble leg")
     ap.add_argument("--no-nonspherical", dest="nonspherical", action="store_false",
                     help="skip the 256^3 non-spherical FP32/FP16 leg")
+    ap.add_argument("--settling-validation", action="store_true",
+                    help="add the zero-net-flow hindered-settling check against Richardson-Zaki "
+                         "(about a minute)")
     ap.add_argument("--phi-matched", action="store_true",
                     help="add the solid-fraction-matched variants of the non-spherical and dense workloads "
                          "(about two minutes of host time to draw them)")

@@ -52,7 +52,9 @@ extern "C" {
 #define HLBM_ERR_ARG (-1)      /* invalid argument */
 #define HLBM_ERR_CUDA (-2)     /* a CUDA call failed */
 #define HLBM_ERR_UNSTABLE (-3) /* a non-finite or non-positive density or particle state */
-#define HLBM_ERR_CAPACITY (-4) /* a fixed-size work list overflowed */
+#define HLBM_ERR_CAPACITY (-4) /* a fixed-size work list overflowed: a tile's particle list
+                                  (bin_capacity), three particles overlapping at one cell, or
+                                  the list of interior cells; hlbm_last_error says which */
 #define HLBM_ERR_STATE (-5)    /* call not allowed in the current state */
 
 /* storage of the populations: the deviation f_i - w_i from the weights */
@@ -137,6 +139,13 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
  * non-finite quaternion. */
 int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, const double* omega,
                             const double* quat);
+
+/* Replaces the uniform body-force density on the fluid (hlbm_params
+ * fluid_force, f[3] in lattice units) from the next step on, e.g. to hold a
+ * periodic suspension at zero net flow while it settles.  Waits for the
+ * stream when the force changes.  HLBM_ERR_ARG for a NULL or non-finite f
+ * (nothing changed). */
+int hlbm_set_fluid_force(hlbm_handle h, const double f[3]);
 
 /* Queues nsteps >= 0 time steps (Algorithm 1: momentum exchange, external
  * force, Newton-Euler update, particle work lists, EDM coupling, collision

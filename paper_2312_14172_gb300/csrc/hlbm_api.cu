@@ -318,6 +318,10 @@ static int status_code(hlbm_ctx* h, int st) {
   CK(cudaStreamSynchronize(h->stream));
   if (st & ST_CAPACITY)
     return fail(h, HLBM_ERR_CAPACITY, "a 32x8x8 tile was touched by more particles than bin_capacity");
+  if (st & ST_OVERLAP)
+    return fail(h, HLBM_ERR_CAPACITY, "three particles overlap at one cell (the list of interior cells takes two)");
+  if (st & ST_LIST_FULL)
+    return fail(h, HLBM_ERR_CAPACITY, "the list of interior cells is full");
   if (st & ST_INTERNAL)
     return fail(h, HLBM_ERR_STATE, "the list of cells inside particles held an invalid entry");
   if (st & ST_LEFT_DOMAIN)
@@ -777,6 +781,18 @@ int hlbm_set_launch(hlbm_handle h, int tile_y, int tile_z, int cells_x) {
     h->sub_z = tile_z;
     h->cells_x = cells_x;
     drop_graphs(h);
+  }
+  return HLBM_OK;
+}
+
+int hlbm_set_fluid_force(hlbm_handle h, const double f[3]) {
+  if (!h || !f) return HLBM_ERR_ARG;
+  for (int j = 0; j < 3; ++j)
+    if (!std::isfinite(f[j])) return fail(h, HLBM_ERR_ARG, "non-finite fluid force");
+  if (f[0] != h->prm.fluid_force[0] || f[1] != h->prm.fluid_force[1] || f[2] != h->prm.fluid_force[2]) {
+    CK(cudaStreamSynchronize(h->stream));
+    for (int j = 0; j < 3; ++j) h->prm.fluid_force[j] = f[j];
+    drop_graphs(h);  // the captured steps hold the force by value
   }
   return HLBM_OK;
 }

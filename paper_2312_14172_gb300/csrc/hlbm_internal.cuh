@@ -102,7 +102,10 @@ struct __align__(16) Rec {
 };
 static_assert(sizeof(Rec) == 128, "record size");
 
-enum { ST_UNSTABLE = 1, ST_CAPACITY = 2, ST_LEFT_DOMAIN = 4, ST_INTERNAL = 8 };
+// status flags: ST_CAPACITY a tile's particle list is full; ST_OVERLAP three
+// particles hold one cell (the list of interior cells takes two per cell);
+// ST_LIST_FULL a stripe of the list of interior cells is full
+enum { ST_UNSTABLE = 1, ST_CAPACITY = 2, ST_LEFT_DOMAIN = 4, ST_INTERNAL = 8, ST_OVERLAP = 16, ST_LIST_FULL = 32 };
 
 // neighbour index helper: per-axis neighbour offsets; -1 marks a node beyond
 // a wall (only possible when WALLS)

@@ -308,7 +308,7 @@ __device__ __forceinline__ void couple_row(const Rec* srec, unsigned long long r
       if (in) {
         if (cc.ip0[j] < 0) cc.ip0[j] = R.pid;
         else if (cc.ip1[j] < 0) cc.ip1[j] = R.pid;
-        else atomicOr(status, ST_CAPACITY);  // three overlapping particles
+        else atomicOr(status, ST_OVERLAP);  // three overlapping particles
       }
       if (B > cc.B[j] || (B == cc.B[j] && B > 0.0f && R.pid < cc.bestp[j])) {
         cc.B[j] = B;
@@ -419,7 +419,7 @@ __device__ __forceinline__ void append_interior(const LbmArgs& a, unsigned g, co
           a.ilist_idx[k0 + k] = make_int2((int)(g + j), p);
           a.ilist_mom[k0 + k] = mom[j];
         } else {
-          atomicOr(a.status, ST_CAPACITY);
+          atomicOr(a.status, ST_LIST_FULL);
         }
         ++k;
       }

@@ -30,6 +30,7 @@ EXPORTS = ["hlbm_default_params", "hlbm_required_bytes", "hlbm_init_lattice", "h
            "hlbm_add_particles", "hlbm_set_particle_state", "hlbm_step", "hlbm_sync",
            "hlbm_particle_state", "hlbm_get_populations", "hlbm_set_populations",
            "hlbm_num_particles", "hlbm_steps_done", "hlbm_set_launch", "hlbm_get_launch",
+           "hlbm_set_fluid_force",
            "hlbm_set_mea_mode", "hlbm_get_mea_mode",
            "hlbm_autotune", "hlbm_kernel_times", "hlbm_interior_cells", "hlbm_last_error", "hlbm_destroy",
            "hlbm_mea_noalloc"]
@@ -91,6 +92,7 @@ def load(path=LIB_PATH):
     L.hlbm_set_launch.argtypes = [_h, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.hlbm_get_launch.argtypes = [_h, _ip, _ip, _ip]
     L.hlbm_set_mea_mode.argtypes = [_h, ctypes.c_int]
+    L.hlbm_set_fluid_force.argtypes = [_h, _dp]
     L.hlbm_get_mea_mode.argtypes = [_h]
     L.hlbm_autotune.argtypes = [_h, ctypes.c_int, _ip, _ip, _ip, _fp]
     L.hlbm_kernel_times.argtypes = [_h, ctypes.c_int, _fp]
@@ -268,6 +270,11 @@ class Lattice:
         ty, tz, cx = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(self.h, load().hlbm_get_launch(self.h, ctypes.byref(ty), ctypes.byref(tz), ctypes.byref(cx)))
         return ty.value, tz.value, cx.value
+
+    def set_fluid_force(self, f):
+        """Uniform body-force density on the fluid from the next step on."""
+        f = np.ascontiguousarray(np.asarray(f, np.float64).reshape(3))
+        _check(self.h, load().hlbm_set_fluid_force(self.h, f.ctypes.data_as(_dp)))
 
     def set_mea_mode(self, mode):
         m = {"kernel": HLBM_MEA_KERNEL, "moments": HLBM_MEA_MOMENTS}.get(mode, mode)

@@ -398,5 +398,46 @@ def ensemble(nboxes=64, edge=(64, 96), count=(10, 200), r_range=(3.0, 7.0), phi_
     return boxes
 
 
+def particle_volumes(P):
+    """Volumes of the particles of a workload: 4/3 pi abc (spheres and
+    ellipsoids), 8 abc (cuboids)."""
+    a = np.asarray(P["a"], float)
+    shp = np.asarray(P["shape"])
+    return np.where(shp == CUBOID, 8.0, 4.0 / 3.0 * math.pi) * a[:, 0] * a[:, 1] * a[:, 2]
+
+
+def zero_net_flow(w):
+    """The workload with a uniform body-force density on the fluid that
+    balances the particles' weight minus buoyancy, F_f = -sum_p (rho_p - 1)
+    V_p g / N_cells: the total momentum of fluid and particles then stays
+    zero in a periodic box.  It stands in for the counter pressure gradient
+    of the hindered-settling runs (Sec. 5.1), whose equation the paper does
+    not print."""
+    P = w["particles"]
+    n = w["n"]
+    weight = ((np.asarray(P["rho_p"], float) - 1.0) * particle_volumes(P)).sum()
+    g = np.asarray(w["gravity"], float)
+    out = dict(w)
+    out["fluid_force"] = tuple(float(v) for v in -weight * g / (n[0] * n[1] * n[2]))
+    out["name"] = w["name"] + "_zero_net_flow"
+    return out
+
+
+def hindered_settling_periodic(phi, d=8, box_d=8, tau=0.6, rho_ratio=2.5, eps=0.5, g=1e-5, seed_index=5):
+    """Hindered settling as in the paper's runs (Sec. 5.1): monodisperse
+    spheres of diameter d cells at solid fraction phi, at random without
+    overlap (half a cell of clearance), in a periodic cube of box_d
+    diameters, with the counter force of zero_net_flow."""
+    n = int(round(box_d * d))
+    r = 0.5 * d
+    count = int(round(phi * n ** 3 / (4.0 / 3.0 * math.pi * r ** 3)))
+    rng = np.random.default_rng(SEED0 + seed_index)
+    X = sequential_insertion_grid(rng, (n, n, n), np.full(count, r), 0, 0.5)
+    k = len(X)
+    P = _particles([SPHERE] * k, np.full((k, 3), r), X, rho_ratio)
+    w = _workload(f"hindered_periodic_{n}^3_phi{phi:g}_{k}", (n, n, n), 0, tau, eps, P, 0, "fp32", gravity=g)
+    return zero_net_flow(w)
+
+
 def by_index(i, **kw):
     return [single_sphere, hindered_settling, nonspherical, dense_batch, ensemble][i](**kw)

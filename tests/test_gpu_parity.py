@@ -256,6 +256,39 @@ def test_fp16_storage_error_is_small(H, O):
     assert np.max(np.abs((sg["X"] - X0) - dX)) <= 2e-2 * np.abs(dX).max() + 1e-6
 
 
+def test_set_fluid_force_equals_the_force_given_at_creation(H, O):
+    """hlbm_set_fluid_force before the first step gives the same run as the
+    same force in the parameters (bit for bit), and a later change takes
+    effect from the next step on (the oracle with the new force from the
+    same state agrees); a non-finite force is refused."""
+    n = (40, 18, 20)
+    ff = (3e-6, -2e-6, 4e-6)
+    f0 = _random_pops(O, n, 5)
+    lat_a, orc = _pair(H, O, n, 4, tau=0.7, ff=ff)
+    lat_b, _ = _pair(H, O, n, 4, tau=0.7)
+    lat_b.set_fluid_force(ff)
+    for lat in (lat_a, lat_b):
+        lat.set_populations(f0)
+        lat.step(3)
+    fa, fb = lat_a.populations(), lat_b.populations()
+    assert np.array_equal(fa, fb)
+    # change the force after three steps: the oracle with the new force
+    # continues from the same populations
+    ff2 = (-1e-6, 5e-6, 0.0)
+    lat_b.set_fluid_force(ff2)
+    lat_b.step(2)
+    orc2 = O.Oracle(n, 0.7, 0.5, 4, (0, 0, 0), ff2)
+    orc2.set_populations(fb)
+    # the oracle stores logical populations and can continue from any step
+    orc2.step(2)
+    _pops_close(lat_b.populations(), orc2.populations())
+    with pytest.raises(H.HLBMError) as e:
+        lat_b.set_fluid_force((0.0, float("nan"), 0.0))
+    assert e.value.code == H.HLBM_ERR_ARG
+    lat_a.close()
+    lat_b.close()
+
+
 # ------------------------------------------------------------ batch
 def test_batch_of_boxes_matches_separate_oracles(H, O):
     from paper_2312_14172_gb300 import workloads

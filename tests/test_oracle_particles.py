@@ -405,3 +405,42 @@ def test_stokes_drag_magnitude_quasi_steady(O):
     ratio = F[0] / (6 * math.pi * nu * r * ubar / K)
     assert 0.8 < ratio < 1.0
     assert abs(F[1]) < 1e-6 * F[0] and abs(F[2]) < 1e-6 * F[0]
+
+
+def test_zero_net_flow_counter_force_balances_the_weight(O):
+    """Hindered settling with the counter force of workloads.zero_net_flow:
+    a uniform force density on the fluid that balances the particles' weight
+    minus buoyancy (standing in for the counter pressure gradient of Sec. 5.1,
+    whose equation is not printed).  Without it the momentum of particles and
+    outside fluid grows by n F_g (plus the O(eps / r) share the momentum
+    exchange does not see); with it that momentum stays near zero: the same
+    share of the coupling, which the backflow enlarges, is what remains.  A
+    wrong sign would give about 2 n F_g, a force not applied about n F_g."""
+    from paper_2312_14172_gb300 import workloads as W
+    ratios = {}
+    for zero in (False, True):
+        w = W.hindered_settling_periodic(0.1, d=6, box_d=4)
+        if not zero:
+            w = dict(w)
+            w["fluid_force"] = (0.0, 0.0, 0.0)
+        else:
+            assert w["fluid_force"][2] > 0 and w["fluid_force"][0] == 0 == w["fluid_force"][1]
+        o = O.from_workload(w)
+        o.step(60)
+        s = o.particle_state()
+        P = w["particles"]
+        V = W.particle_volumes(P)
+        m = np.asarray(P["rho_p"]) * V
+        Fg = ((np.asarray(P["rho_p"]) - 1) * V).sum() * w["gravity"][2]
+        c, _, _ = O.velocity_set()
+        pz = np.einsum("i,izyx->zyx", c[:, 2].astype(float), o.populations())
+        n = w["n"][0]
+        zz, yy, xx = np.meshgrid(range(n), range(n), range(n), indexing="ij")
+        inside = np.zeros_like(pz, bool)
+        for X in s["X"]:
+            d = [np.minimum(np.abs(a - X[k]), n - np.abs(a - X[k])) for k, a in enumerate((xx, yy, zz))]
+            inside |= d[0] ** 2 + d[1] ** 2 + d[2] ** 2 < P["a"][0][0] ** 2
+        ratios[zero] = ((m * s["U"][:, 2]).sum() + pz[~inside].sum()) / (60 * Fg)
+        o.close()
+    assert 1.0 <= ratios[False] < 1.25
+    assert abs(ratios[True]) < 0.35
