@@ -103,10 +103,17 @@ double oracle_indicator(double d, double eps) {
  *   cuboid, half-extents a:     exact box distance
  *   ellipsoid, semi-axes a:     gradient-normalised algebraic distance
  *                               (k - 1) k / |r / a^2| with k = |r / a|, which
- *                               equals |r| - a for a sphere. */
+ *                               equals |r| - a for a sphere
+ *   capsule, radius a[0], half-length a[2] of its axis segment (body z):
+ *                               exact distance |r - clamp(r_z, -a[2], a[2]) e_z| - a[0] */
 double oracle_sdf_body(int shape, const double a[3], const double r[3]) {
   if (shape == ORACLE_SPHERE) {
     return sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) - a[0];
+  }
+  if (shape == ORACLE_CAPSULE) {
+    double c = r[2] < -a[2] ? -a[2] : (r[2] > a[2] ? a[2] : r[2]);
+    double t = r[2] - c;
+    return sqrt(r[0] * r[0] + r[1] * r[1] + t * t) - a[0];
   }
   if (shape == ORACLE_ELLIPSOID) {
     double k2 = 0.0, g2 = 0.0;
@@ -159,7 +166,9 @@ void oracle_rotation(const double q[4], double R[9]) {
  *   sphere:    (rx*rx + ry*ry) + rz*rz < fp32(a*a)
  *   ellipsoid: b = M^T r with M = fp32(R(q)), e_j = b_j * fp32(1/a_j),
  *              (e0*e0 + e1*e1) + e2*e2 < 1
- *   cuboid:    |b_j| < fp32(a_j) for all j                                  */
+ *   cuboid:    |b_j| < fp32(a_j) for all j
+ *   capsule:   t = b2 - clamp(b2, -fp32(a2), fp32(a2)),
+ *              (b0*b0 + b1*b1) + t*t < fp32(a0*a0)                          */
 int oracle_inside_fp32(int shape, const double a[3], const double q[4], const double X[3],
                        const int cell[3], const int n[3], int bc_flags) {
   float r[3];
@@ -192,6 +201,15 @@ int oracle_inside_fp32(int shape, const double a[3], const double q[4], const do
     t = t + M[1 * 3 + j] * r[1];
     t = t + M[2 * 3 + j] * r[2];
     b[j] = t;
+  }
+  if (shape == ORACLE_CAPSULE) {
+    float h = (float)a[2];
+    float c = b[2] < -h ? -h : (b[2] > h ? h : b[2]);
+    float t = b[2] - c;
+    float s = b[0] * b[0];
+    s = s + b[1] * b[1];
+    s = s + t * t;
+    return s < (float)(a[0] * a[0]);
   }
   if (shape == ORACLE_ELLIPSOID) {
     float e0 = b[0] * (float)(1.0 / a[0]);
@@ -320,6 +338,18 @@ static void shape_mass_properties(particle* P) {
     P->rc = a[0];
     if (a[1] > P->rc) P->rc = a[1];
     if (a[2] > P->rc) P->rc = a[2];
+  } else if (P->shape == ORACLE_CAPSULE) {
+    /* a cylinder of radius r and length 2h with two hemispherical caps; a
+     * cap's moment about a diameter of its flat face is 2/5 m r^2, moved to
+     * the centre through the cap's centroid (3r/8 from the face) */
+    const double r = a[0], h = a[2];
+    const double Vc = PI * r * r * 2.0 * h, Vs = 4.0 / 3.0 * PI * r * r * r;
+    P->V = Vc + Vs;
+    P->m = P->rho * P->V;
+    const double mc = P->rho * Vc, ms = P->rho * Vs;
+    P->I[0] = P->I[1] = mc * (r * r / 4.0 + h * h / 3.0) + ms * (0.4 * r * r + h * h + 0.75 * h * r);
+    P->I[2] = mc * r * r / 2.0 + ms * 0.4 * r * r;
+    P->rc = h + r;
   } else {
     P->V = 8.0 * a[0] * a[1] * a[2];
     P->m = P->rho * P->V;
@@ -356,9 +386,9 @@ int oracle_add_particles(oracle_sim* s, int n, const int* shape, const double* a
     particle P;
     memset(&P, 0, sizeof(P));
     P.shape = shape[k];
-    if (P.shape < 0 || P.shape > 2) return -1;
+    if (P.shape < 0 || P.shape > 3) return -1;
     for (int j = 0; j < 3; ++j) {
-      P.a[j] = (P.shape == ORACLE_SPHERE) ? a[3 * k] : a[3 * k + j];
+      P.a[j] = (P.shape == ORACLE_SPHERE || (P.shape == ORACLE_CAPSULE && j == 1)) ? a[3 * k] : a[3 * k + j];
       if (!(P.a[j] > 0.0)) return -1;
       P.X[j] = X[3 * k + j];
       P.U[j] = U ? U[3 * k + j] : 0.0;
@@ -511,8 +541,8 @@ long oracle_mea(const oracle_sim* s, int p, double F[3], double T[3]) {
  * wins and ties go to the lowest particle index; that particle also supplies
  * u_p(x).  B_p is evaluated only within the influence sphere |x - X_p| <
  * R_inf, outside of which d_s >= eps/2 and hence B_p = 0 exactly:
- *   sphere, cuboid (exact distances):  R_inf = r_c + eps/2, r_c the
- *                                      circumscribed radius;
+ *   sphere, cuboid, capsule (exact     R_inf = r_c + eps/2, r_c the
+ *   distances):                        circumscribed radius;
  *   ellipsoid (algebraic distance):    d_s >= (k - 1) a_min and |r| <= k a_max
  *                                      give R_inf = a_max (1 + eps / (2 a_min)). */
 static double influence_radius(const particle* P, double eps) {

@@ -48,6 +48,7 @@ extern "C" {
 #define ORACLE_SPHERE 0
 #define ORACLE_ELLIPSOID 1
 #define ORACLE_CUBOID 2
+#define ORACLE_CAPSULE 3 /* radius a[0], half-length a[2] of its axis segment (body z) */
 
 /* boundary flag bits: a set bit makes that axis bounded by two half-way
  * bounce-back walls; a clear bit makes it periodic. */

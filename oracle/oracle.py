@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 # identical results), for timing only
 LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
 
-SPHERE, ELLIPSOID, CUBOID = 0, 1, 2
+SPHERE, ELLIPSOID, CUBOID, CAPSULE = 0, 1, 2, 3
 WALL_X, WALL_Y, WALL_Z = 1, 2, 4
 
 _dp = ctypes.POINTER(ctypes.c_double)

@@ -68,8 +68,60 @@ def test_sdf_cuboid_exact(O):
         assert abs(O.sdf_body(2, a, r) - _box_distance_bruteforce(a, r)) < 1e-13
 
 
+def test_sdf_capsule_is_the_distance_to_its_segment(O):
+    """Capsule (shape 3): the points within a[0] of the segment +- a[2] e_z.
+    Its distance is the distance to the segment minus the radius, checked
+    against a brute-force minimum over points of the segment; with a
+    vanishing segment it is the sphere."""
+    a = np.array([1.7, 1.7, 3.2])
+    seg = np.linspace(-a[2], a[2], 200001)[:, None] * np.array([0.0, 0.0, 1.0])
+    rng = np.random.default_rng(17)
+    for _ in range(300):
+        r = rng.uniform(-7, 7, 3)
+        brute = np.sqrt(((seg - r) ** 2).sum(1)).min() - a[0]
+        assert abs(O.sdf_body(3, a, r) - brute) < 1e-9
+    for _ in range(50):
+        r = rng.uniform(-5, 5, 3)
+        assert abs(O.sdf_body(3, [2.0, 2.0, 1e-300], r) - O.sdf_body(0, [2.0] * 3, r)) < 1e-12
+
+
+def test_capsule_mass_and_inertia_against_integration(O):
+    """The capsule's mass and principal moments of inertia (the Newton-Euler
+    update of Sec. 2.2 divides by them): recovered from one update under a
+    known force and torque (dU = F / m, d omega = T / I for a body at rest
+    with the identity orientation) and checked against a sum over a fine grid
+    of the solid."""
+    r, h, rho = 1.5, 2.5, 2.0
+    o = O.Oracle((32, 32, 32), 0.8, 0.5, 0)
+    o.add_particles([3], [[r, r, h]], [[16.0, 16.0, 16.0]], rho_p=[rho])
+    F, T = np.array([[1e-3, 0.0, 0.0]]), np.array([[2e-3, 0.0, 3e-3]])
+    o.integrate_only(F, T)
+    s = o.particle_state()
+    m = F[0, 0] / s["U"][0, 0]
+    Ix, Iz = T[0, 0] / s["omega"][0, 0], T[0, 2] / s["omega"][0, 2]
+    # grid sum
+    k = 240
+    ax = np.linspace(-(h + r), h + r, 2 * k + 1)
+    dx = ax[1] - ax[0]
+    xs = np.linspace(-r, r, k + 1)
+    dxy = xs[1] - xs[0]
+    X, Y, Z = np.meshgrid(xs, xs, ax, indexing="ij")
+    t = Z - np.clip(Z, -h, h)
+    inside = X ** 2 + Y ** 2 + t ** 2 < r ** 2
+    dV = dxy * dxy * dx
+    m_grid = rho * inside.sum() * dV
+    Ix_grid = rho * ((Y ** 2 + Z ** 2) * inside).sum() * dV
+    Iz_grid = rho * ((X ** 2 + Y ** 2) * inside).sum() * dV
+    assert abs(m / m_grid - 1) < 5e-3
+    assert abs(Ix / Ix_grid - 1) < 5e-3
+    assert abs(Iz / Iz_grid - 1) < 5e-3
+    # the closed forms themselves
+    V = math.pi * r * r * 2 * h + 4 / 3 * math.pi * r ** 3
+    assert abs(m - rho * V) < 1e-12 * m
+
+
 @pytest.mark.parametrize("shape,a", [(0, [4, 4, 4]), (1, [2, 2, 8]), (1, [1.3, 2.1, 5.2]),
-                                     (2, [1.2, 1.2, 4.8]), (2, [1.0, 2.0, 3.0])])
+                                     (2, [1.2, 1.2, 4.8]), (2, [1.0, 2.0, 3.0]), (3, [1.5, 1.5, 4.0])])
 @pytest.mark.parametrize("eps", [0.5, 1.5])
 def test_indicator_vanishes_outside_influence_radius(O, shape, a, eps):
     """B is evaluated only inside |r| < R_inf; this holds exactly because d_s >=
@@ -78,7 +130,7 @@ def test_indicator_vanishes_outside_influence_radius(O, shape, a, eps):
     (2 a_min)) for the ellipsoid's algebraic distance."""
     a = np.array(a, float)
     rinf = {0: a[0] + eps / 2, 1: a.max() * (1 + eps / (2 * a.min())),
-            2: np.linalg.norm(a) + eps / 2}[shape]
+            2: np.linalg.norm(a) + eps / 2, 3: a[0] + a[2] + eps / 2}[shape]
     rng = np.random.default_rng(8)
     for _ in range(3000):
         v = rng.standard_normal(3)
@@ -116,7 +168,7 @@ def test_rotation_matches_quaternion_sandwich(O):
 def test_inside_fp32_agrees_with_fp64_away_from_surface(O):
     rng = np.random.default_rng(10)
     n = np.array([40, 40, 40])
-    for shape, a in ((0, [6, 6, 6]), (1, [3, 3, 9]), (2, [2, 2.5, 6])):
+    for shape, a in ((0, [6, 6, 6]), (1, [3, 3, 9]), (2, [2, 2.5, 6]), (3, [2.5, 2.5, 5])):
         a = np.array(a, float)
         for _ in range(300):
             q = rng.standard_normal(4)
@@ -148,6 +200,7 @@ def test_inside_is_strict_and_wraps(O):
     (0, [3.3, 3.3, 3.3], [1, 0, 0, 0]),
     (1, [2.0, 2.6, 4.1], [0.8, 0.2, -0.4, 0.4]),
     (2, [1.5, 2.0, 3.0], [0.6, -0.3, 0.7, 0.2]),
+    (3, [1.8, 1.8, 2.5], [0.7, 0.4, -0.2, 0.55]),
 ])
 def test_mea_equals_momentum_change_of_interior_cells(O, shape, a, q):
     """Summed over the cells inside a particle, the force of Eqs. hlbm:mea and
