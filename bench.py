@@ -27,6 +27,8 @@ nonspherical: the 256^3 box of 2000 ellipsoids and cuboids with FP32 and FP16
 storage; batched_fp16: the large dense batch (512 x 512 x 1024 cells, 50 000 spheres)
 with FP32 and with FP16 storage, its collision roofline and the FP16 error;
 ensemble: 64 independent boxes of 64..96^3 advanced together, FP32.
+Opt-in legs: --capsules (the non-spherical box with 2000 capsules),
+--phi-matched, --settling-validation.
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 repository) on the same workload, rank 0 only.
@@ -49,7 +51,7 @@ BYTES_PER_CELL = {"fp32": 2 * 19 * 4, "fp16": 2 * 19 * 2}
 
 
 WORKLOADS = ("hindered_settling", "single_sphere", "nonspherical", "dense_batch", "fluid_256",
-             "dense_batch_256", "nonspherical_phi", "dense_batch_phi")
+             "dense_batch_256", "nonspherical_phi", "dense_batch_phi", "capsules")
 
 
 def make_workload(name):
@@ -72,6 +74,8 @@ def make_workload(name):
         return workloads.nonspherical_phi_matched()
     if name == "dense_batch_phi":
         return workloads.dense_batch_phi_matched()
+    if name == "capsules":
+        return workloads.nonspherical(kinds=(workloads.CAPSULE,), name="capsules")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -403,6 +407,7 @@ def run_gpu(args, ws, rank, local):
     ensemble = ensemble_leg(args, stream, peak, ws) if args.ensemble else None
     phi = phi_matched_leg(args, stream, peak, ws) if args.phi_matched else None
     settling = settling_validation_leg(args, stream) if args.settling_validation else None
+    capsules = capsules_leg(args, stream, peak, ws) if args.capsules else None
 
     launches_per_step = 3 if npart > 0 else 1
     line = {
@@ -434,6 +439,8 @@ def run_gpu(args, ws, rank, local):
         line["phi_matched"] = phi
     if settling is not None:
         line["settling_validation"] = settling
+    if capsules is not None:
+        line["capsules"] = capsules
     return line
 
 
@@ -599,6 +606,13 @@ def nonspherical_leg(args, stream, peak, ws):
     return fp32_fp16_pair(make_workload("nonspherical"), args, stream, peak, ws, steps_max=100)
 
 
+def capsules_leg(args, stream, peak, ws):
+    """The non-spherical workload's box, counts and size laws with capsules
+    only (2000 sphere-swept segments of equal volume, aspect ratio
+    U(1, 4), eps = 1.5), FP32 and FP16 storage."""
+    return fp32_fp16_pair(make_workload("capsules"), args, stream, peak, ws, steps_max=100)
+
+
 def settling_validation_leg(args, stream):
     """Zero-net-flow hindered settling (the paper's Sec. 5.1 set-up with the
     counter force of workloads.zero_net_flow) at solid fractions 0.05-0.2:
@@ -730,6 +744,8 @@ def main():
     ap.add_argument("--settling-validation", action="store_true",
                     help="add the zero-net-flow hindered-settling check against Richardson-Zaki "
                          "(about a minute)")
+    ap.add_argument("--capsules", action="store_true",
+                    help="add the 256^3 box of 2000 capsules with FP32 and FP16 storage")
     ap.add_argument("--phi-matched", action="store_true",
                     help="add the solid-fraction-matched variants of the non-spherical and dense workloads "
                          "(about two minutes of host time to draw them)")

@@ -65,6 +65,8 @@ extern "C" {
 #define HLBM_SPHERE 0    /* radius r (the other two entries are ignored) */
 #define HLBM_ELLIPSOID 1 /* semi-axes a, b, c along the body axes */
 #define HLBM_CUBOID 2    /* half-extents a, b, c along the body axes */
+#define HLBM_CAPSULE 3   /* radius r, ignored, half-length h of the axis segment
+                            along the body z axis: the points within r of it */
 
 /* boundary flags: a set bit bounds that axis with two bounce-back walls */
 #define HLBM_WALL_X 1
@@ -116,7 +118,7 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
 /* Adds n particles (Sec. 2.2), allowed only before the first step
  * (HLBM_ERR_STATE afterwards).  Arrays (host, row-major):
  *   box_id[n]      box of each particle (NULL = box 0)
- *   shape[n]       HLBM_SPHERE / HLBM_ELLIPSOID / HLBM_CUBOID
+ *   shape[n]       HLBM_SPHERE / HLBM_ELLIPSOID / HLBM_CUBOID / HLBM_CAPSULE
  *   shape_params[3n], X[3n] centre of mass, U[3n] velocity (NULL = 0),
  *   omega[3n] angular velocity (NULL = 0), quat[4n] orientation (w,x,y,z,
  *   body -> world, normalised here; NULL = identity), rho_p[n] density.

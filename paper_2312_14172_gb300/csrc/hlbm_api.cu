@@ -489,6 +489,19 @@ static void mass_properties(int shape, const double a[3], double rho, double* V,
     *rc = amax;
     // algebraic distance: d >= (k - 1) a_min and |r| <= k a_max
     *rinf = amax * (1.0 + eps / (2.0 * amin));
+  } else if (shape == HLBM_CAPSULE) {
+    // a cylinder of radius r and length 2h with two hemispherical caps; a
+    // cap's moment about a diameter of its flat face, 2/5 m r^2, moves to the
+    // centre through the cap's centroid 3r/8 from that face
+    const double r = a[0], hh = a[2];
+    const double Vc = PI_D * r * r * 2.0 * hh, Vs = 4.0 / 3.0 * PI_D * r * r * r;
+    *V = Vc + Vs;
+    *m = rho * *V;
+    const double mc = rho * Vc, ms = rho * Vs;
+    I[0] = I[1] = mc * (r * r / 4.0 + hh * hh / 3.0) + ms * (0.4 * r * r + hh * hh + 0.75 * hh * r);
+    I[2] = mc * r * r / 2.0 + ms * 0.4 * r * r;
+    *rc = hh + r;
+    *rinf = *rc + eps / 2.0;
   } else {
     *V = 8.0 * a[0] * a[1] * a[2];
     *m = rho * *V;
@@ -535,10 +548,10 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
     if (b < 0 || b >= (int)h->boxes.size()) return fail(h, HLBM_ERR_ARG, "box_id out of range");
     const BoxDesc& bd = h->boxes[b];
     const int s = shape[k];
-    if (s < HLBM_SPHERE || s > HLBM_CUBOID) return fail(h, HLBM_ERR_ARG, "unknown shape");
+    if (s < HLBM_SPHERE || s > HLBM_CAPSULE) return fail(h, HLBM_ERR_ARG, "unknown shape");
     double a[3];
     for (int j = 0; j < 3; ++j) {
-      a[j] = (s == HLBM_SPHERE) ? shape_params[3 * k] : shape_params[3 * k + j];
+      a[j] = (s == HLBM_SPHERE || (s == HLBM_CAPSULE && j == 1)) ? shape_params[3 * k] : shape_params[3 * k + j];
       if (!(a[j] > 0.0) || !std::isfinite(a[j])) return fail(h, HLBM_ERR_ARG, "shape sizes must be finite and > 0");
     }
     const double rho = rho_p[k];

@@ -92,10 +92,10 @@ struct __align__(16) Rec {
   float xh[3], xl[3];  // centre as float pair: X = xh + xl
   float u[3], w[3];    // velocity, angular velocity
   float M[9];          // rotation body -> world, row-major (identity for spheres)
-  float a[3];          // radius / semi-axes / half-extents
+  float a[3];          // radius / semi-axes / half-extents / capsule (r, r, h)
   float ia[3];         // fp32(1 / a_j) (ellipsoid inside test)
   float rinf2;         // square of a radius beyond which B = 0
-  float in2;           // fp32(r * r) (sphere inside test)
+  float in2;           // fp32(r * r) (sphere and capsule inside tests)
   int shape;
   int box;
   int pid;
@@ -288,6 +288,7 @@ struct PartArgs {
 //   sphere:    (r0 r0 + r1 r1) + r2 r2 < fp32(a^2)
 //   ellipsoid: e = (M^T r) * fp32(1/a) componentwise, (e0 e0 + e1 e1) + e2 e2 < 1
 //   cuboid:    |M^T r| < a componentwise
+//   capsule:   b = M^T r, t = b2 - clamp(b2, -a2, a2), (b0 b0 + b1 b1) + t t < fp32(a0^2)
 // where (M^T r)_j = (M_0j r0 + M_1j r1) + M_2j r2.
 __device__ __forceinline__ float offset_fp32(int cell, int n, bool wall, float xh, float xl) {
   float r0 = __fsub_rn((float)cell, xh);
@@ -323,6 +324,14 @@ __device__ __forceinline__ bool inside_from_offset(const Rec& R, const float r[3
     s = __fadd_rn(s, __fmul_rn(e1, e1));
     s = __fadd_rn(s, __fmul_rn(e2, e2));
     return s < 1.0f;
+  }
+  if (R.shape == 3) {
+    const float c = b[2] < -R.a[2] ? -R.a[2] : (b[2] > R.a[2] ? R.a[2] : b[2]);
+    const float t = __fsub_rn(b[2], c);
+    float s = __fmul_rn(b[0], b[0]);
+    s = __fadd_rn(s, __fmul_rn(b[1], b[1]));
+    s = __fadd_rn(s, __fmul_rn(t, t));
+    return s < R.in2;
   }
   return fabsf(b[0]) < R.a[0] && fabsf(b[1]) < R.a[1] && fabsf(b[2]) < R.a[2];
 }

@@ -1,7 +1,7 @@
 // lbm_common.cuh -- device pieces shared by the collision kernels (one cell
 // per thread in lbm_kernels.cu, two x-adjacent cells per thread in
 // lbm_pair_kernels.cu): storage access, the indicator of Eq. B, the signed
-// distances of the three shapes, the per-tile particle candidates and the
+// distances of the four shapes, the per-tile particle candidates and the
 // per-cell coupling of Eq. hlbm:du (Sec. 3.2), and the list of cells inside
 // particles that the collision appends for the next momentum exchange.
 #pragma once
@@ -121,6 +121,10 @@ __device__ __forceinline__ float sdf(const Rec& R, float rx, float ry, float rz,
   const float b0 = R.M[0] * rx + R.M[3] * ry + R.M[6] * rz;
   const float b1 = R.M[1] * rx + R.M[4] * ry + R.M[7] * rz;
   const float b2 = R.M[2] * rx + R.M[5] * ry + R.M[8] * rz;
+  if (R.shape == 3) {
+    const float t = b2 - fminf(fmaxf(b2, -R.a[2]), R.a[2]);
+    return sqrtf(b0 * b0 + b1 * b1 + t * t) - R.a[0];
+  }
   if (R.shape == 1) {
     const float e0 = b0 * R.ia[0], e1 = b1 * R.ia[1], e2 = b2 * R.ia[2];
     const float k2 = e0 * e0 + e1 * e1 + e2 * e2;
@@ -181,6 +185,7 @@ __device__ __forceinline__ Brick brick_of(const LbmArgs& a) {
 //              a_r the larger of the two others
 //   cuboid     the box grown by eps/2 lies in the capsule along its longest
 //              half-extent h_k of radius |(h_i, h_j)| + eps/2 and half-length h_k
+//   capsule    itself grown by eps/2: radius a0 + eps/2 about its body-z segment
 // The radius carries a margin of 1e-3 relative + 0.01 cells over FP32 rounding.
 struct Capsule {
   float u[3], h, r2;
@@ -193,6 +198,13 @@ __device__ __forceinline__ Capsule capsule_of(const Rec& R, float eps) {
     c.h = 0.0f;
     const float r = R.a[0] + 0.5f * eps;
     c.r2 = (r * 1.001f + 0.01f) * (r * 1.001f + 0.01f);
+    return c;
+  }
+  if (R.shape == 3) {
+    c.u[0] = R.M[2]; c.u[1] = R.M[5]; c.u[2] = R.M[8];
+    c.h = R.a[2];
+    const float r = (R.a[0] + 0.5f * eps) * 1.001f + 0.01f;
+    c.r2 = r * r;
     return c;
   }
   const int k = R.a[0] >= R.a[1] ? (R.a[0] >= R.a[2] ? 0 : 2) : (R.a[1] >= R.a[2] ? 1 : 2);

@@ -59,9 +59,9 @@ __global__ void noalloc_setup_kernel(NoAllocArgs a) {
   if (p >= a.n) return;
   const int shape = a.shape[p];
   double s[3], X[3], q[4], nq = 0.0;
-  bool ok = shape >= 0 && shape <= 2;
+  bool ok = shape >= 0 && shape <= 3;
   for (int j = 0; j < 3; ++j) {
-    s[j] = a.params[3 * p + (shape == 0 ? 0 : j)];
+    s[j] = a.params[3 * p + ((shape == 0 || (shape == 3 && j == 1)) ? 0 : j)];
     X[j] = a.X[3 * p + j];
     ok = ok && s[j] > 0.0 && isfinite(s[j]) && X[j] > -1.0e6 && X[j] < 1.0e6;
   }
@@ -73,6 +73,7 @@ __global__ void noalloc_setup_kernel(NoAllocArgs a) {
   double rc = s[0];
   if (shape == 1) rc = fmax(s[0], fmax(s[1], s[2]));
   if (shape == 2) rc = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+  if (shape == 3) rc = s[0] + s[2];
   ok = ok && rc <= 30.0;
   na_done(a)[p] = 0;
   if (!ok) {

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libhlbm.so")
 
 HLBM_OK, HLBM_ERR_ARG, HLBM_ERR_CUDA, HLBM_ERR_UNSTABLE, HLBM_ERR_CAPACITY, HLBM_ERR_STATE = 0, -1, -2, -3, -4, -5
 HLBM_FP32, HLBM_FP16 = 0, 1
-HLBM_SPHERE, HLBM_ELLIPSOID, HLBM_CUBOID = 0, 1, 2
+HLBM_SPHERE, HLBM_ELLIPSOID, HLBM_CUBOID, HLBM_CAPSULE = 0, 1, 2, 3
 HLBM_WALL_X, HLBM_WALL_Y, HLBM_WALL_Z = 1, 2, 4
 HLBM_MEA_KERNEL, HLBM_MEA_MOMENTS = 0, 1
 

@@ -32,7 +32,7 @@ import math
 import numpy as np
 
 SEED0 = 2312014172
-SPHERE, ELLIPSOID, CUBOID = 0, 1, 2
+SPHERE, ELLIPSOID, CUBOID, CAPSULE = 0, 1, 2, 3
 WALL_Z = 4
 
 
@@ -41,6 +41,8 @@ def _circ_radius(shape, a):
         return float(a[0])
     if shape == ELLIPSOID:
         return float(max(a))
+    if shape == CAPSULE:
+        return float(a[0] + a[2])
     return float(math.sqrt(a[0] ** 2 + a[1] ** 2 + a[2] ** 2))
 
 
@@ -317,29 +319,37 @@ def hindered_settling(n=(128, 128, 128), count=200, r_range=(4.0, 8.0), tau=0.6,
 
 def nonspherical(n=(256, 256, 256), count=2000, r_eq=5.0, ar_range=(1.0, 4.0), tau=0.6,
                  rho_ratio=2.5, eps=1.5, steps=500, seed_index=2, precision="fp32", gap=None, grid=False,
-                 name="nonspherical"):
-    """Workload 2: prolate ellipsoids (even index) and elongated cuboids (odd
-    index) of equal volume 4/3 pi r_eq^3, aspect ratio AR ~ U(1, 4), uniform
-    random orientation, periodic box.  gap: clearance between the enclosing
-    capsules (default eps + 1); grid: the vectorised insertion."""
+                 name="nonspherical", kinds=(ELLIPSOID, CUBOID)):
+    """Workload 2: prolate ellipsoids and elongated cuboids (kinds cycles
+    through the shapes by index; capsules may join them) of equal volume
+    4/3 pi r_eq^3, aspect ratio AR ~ U(1, 4) (longest extent over the
+    width), uniform random orientation, periodic box.  gap: clearance
+    between the enclosing capsules (default eps + 1); grid: the vectorised
+    insertion."""
     rng = np.random.default_rng(SEED0 + seed_index)
     ar = rng.uniform(ar_range[0], ar_range[1], count)
     shapes, axes = [], []
     vol = 4.0 / 3.0 * math.pi * r_eq ** 3
     for k in range(count):
-        if k % 2 == 0:
+        kind = kinds[k % len(kinds)]
+        if kind == ELLIPSOID:
             a = (r_eq ** 3 / ar[k]) ** (1.0 / 3.0)          # a^3 AR = r_eq^3
-            shapes.append(ELLIPSOID)
             axes.append([a, a, ar[k] * a])
-        else:
+        elif kind == CUBOID:
             h = (vol / (8.0 * ar[k])) ** (1.0 / 3.0)        # 8 h^3 AR = volume
-            shapes.append(CUBOID)
             axes.append([h, h, ar[k] * h])
+        elif kind == CAPSULE:
+            # pi r^3 (2 (AR - 1) + 4/3) = volume, segment half-length (AR - 1) r
+            r = (vol / (math.pi * (2.0 * (ar[k] - 1.0) + 4.0 / 3.0))) ** (1.0 / 3.0)
+            axes.append([r, r, max((ar[k] - 1.0) * r, 1e-6)])
+        else:
+            raise ValueError(f"unknown shape {kind}")
+        shapes.append(kind)
     quat = random_quaternions(rng, count)
     # enclosing capsules along the body z-axis (the long axis): an ellipsoid
     # (a, a, c) lies within radius a of the segment +-(c - a); a cuboid
-    # (h, h, H) within radius sqrt(2) h of the segment +-H
-    cap_r = np.array([a[0] if s == ELLIPSOID else math.sqrt(2.0) * a[0] for s, a in zip(shapes, axes)])
+    # (h, h, H) within radius sqrt(2) h of the segment +-H; a capsule is one
+    cap_r = np.array([a[0] if s in (ELLIPSOID, CAPSULE) else math.sqrt(2.0) * a[0] for s, a in zip(shapes, axes)])
     cap_h = np.array([a[2] - a[0] if s == ELLIPSOID else a[2] for s, a in zip(shapes, axes)])
     g = eps + 1.0 if gap is None else gap
     insert = sequential_insertion_grid if grid else sequential_insertion
@@ -400,10 +410,12 @@ def ensemble(nboxes=64, edge=(64, 96), count=(10, 200), r_range=(3.0, 7.0), phi_
 
 def particle_volumes(P):
     """Volumes of the particles of a workload: 4/3 pi abc (spheres and
-    ellipsoids), 8 abc (cuboids)."""
+    ellipsoids), 8 abc (cuboids), 2 pi r^2 h + 4/3 pi r^3 (capsules)."""
     a = np.asarray(P["a"], float)
     shp = np.asarray(P["shape"])
-    return np.where(shp == CUBOID, 8.0, 4.0 / 3.0 * math.pi) * a[:, 0] * a[:, 1] * a[:, 2]
+    v = np.where(shp == CUBOID, 8.0, 4.0 / 3.0 * math.pi) * a[:, 0] * a[:, 1] * a[:, 2]
+    cap = 2.0 * math.pi * a[:, 0] ** 2 * a[:, 2] + 4.0 / 3.0 * math.pi * a[:, 0] ** 3
+    return np.where(shp == CAPSULE, cap, v)
 
 
 def zero_net_flow(w):

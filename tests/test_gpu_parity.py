@@ -247,6 +247,22 @@ def test_nonspherical_subbox(H, O):
     assert np.allclose(sg["quat"], so["quat"], atol=1e-9)
 
 
+@pytest.mark.parametrize("mode", ["kernel", "moments"])
+def test_capsules_subbox(H, O, mode):
+    """Capsules (sphere-swept segments) among ellipsoids and cuboids, with
+    random orientations and spin, eps = 1.5."""
+    from paper_2312_14172_gb300 import workloads
+    w = workloads.nonspherical(n=(62, 56, 60), count=18, steps=50,
+                               kinds=(workloads.CAPSULE, workloads.ELLIPSOID, workloads.CUBOID))
+    assert (w["particles"]["shape"] == workloads.CAPSULE).sum() >= 4
+    rng = np.random.default_rng(5)
+    w["particles"]["omega"] = rng.uniform(-3e-3, 3e-3, w["particles"]["omega"].shape)
+    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 50, chunks=(1,), mode=mode)
+    _pops_close(fg, fo)
+    _motion_close(sg, so, X0, U0, W0)
+    assert np.allclose(sg["quat"], so["quat"], atol=1e-9)
+
+
 def test_fp16_storage_error_is_small(H, O):
     from paper_2312_14172_gb300 import workloads
     w = workloads.single_sphere(n=40, radius=5.0, steps=100)

@@ -62,3 +62,32 @@ def test_phi_matched_variants_reach_the_named_fractions_on_a_small_box():
     P = w["particles"]
     phi = (4.0 / 3.0 * math.pi * P["a"][:, 0] ** 3).sum() / (128 * 128 * 256)
     assert 0.17 < phi < 0.23
+
+
+def test_nonspherical_with_capsules_keeps_the_volume_and_the_gap():
+    """Capsules in workload 2 have the equal volume 4/3 pi r_eq^3 and aspect
+    ratio (h + r) / r in the drawn range, and keep the clearance to the
+    ellipsoids' and cuboids' enclosing capsules."""
+    w = W.nonspherical(n=(48, 48, 48), count=24, steps=1, kinds=(W.CAPSULE, W.ELLIPSOID, W.CUBOID))
+    P = w["particles"]
+    shp, a = P["shape"], P["a"]
+    cap = shp == W.CAPSULE
+    assert cap.sum() >= 4
+    V = W.particle_volumes(P)
+    assert np.allclose(V, 4.0 / 3.0 * math.pi * 5.0 ** 3, rtol=1e-12)
+    ar = (a[cap, 2] + a[cap, 0]) / a[cap, 0]
+    assert np.all((ar >= 1.0) & (ar <= 4.0))
+    assert np.all(a[cap, 1] == a[cap, 0])
+    # brute-force clearance between the enclosing capsules
+    r = np.where(shp == W.CUBOID, math.sqrt(2.0) * a[:, 0], a[:, 0])
+    h = np.where(shp == W.ELLIPSOID, a[:, 2] - a[:, 0], a[:, 2])
+    ax = W.body_axis_z(P["quat"])
+    n = np.array(w["n"])
+    X = P["X"]
+    for i in range(len(X)):
+        for j in range(i):
+            d = X[i] - X[j]
+            d -= n * np.round(d / n)
+            if np.linalg.norm(d) > r[i] + r[j] + h[i] + h[j] + w["eps"] + 1.0:
+                continue
+            assert _segment_distance(X[i], ax[i], h[i], X[i] - d, ax[j], h[j]) >= r[i] + r[j] + w["eps"] + 1.0 - 0.05

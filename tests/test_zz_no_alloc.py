@@ -33,8 +33,8 @@ W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
 def _case(nx, ny, nz, bc, seed):
     rng = np.random.default_rng(seed)
     dev = (1e-3 * rng.standard_normal((19, nz, ny, nx)) * W[:, None, None, None]).astype(np.float32)
-    shape = np.array([0, 1, 2, 0], np.int32)
-    params = np.array([[5.2, 5.2, 5.2], [3.0, 4.0, 7.5], [2.0, 3.5, 4.5], [3.3, 3.3, 3.3]])
+    shape = np.array([0, 1, 2, 3], np.int32)
+    params = np.array([[5.2, 5.2, 5.2], [3.0, 4.0, 7.5], [2.0, 3.5, 4.5], [3.3, 0.0, 4.0]])
     X = np.array([[10.3, 11.7, 12.2], [nx - 9.6, 20.1, 14.8], [22.4, 6.2, nz - 11.3], [1.2, ny - 2.4, 20.5]])
     U = rng.uniform(-2e-3, 2e-3, (4, 3))
     omega = rng.uniform(-3e-3, 3e-3, (4, 3))
