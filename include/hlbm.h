@@ -227,6 +227,38 @@ int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]);
  * moments mode or before the first step after a change of state. */
 int hlbm_interior_cells(hlbm_handle h, long long* n);
 
+/* Snapshots (checkpoint and restart; not part of the paper's method).
+ *
+ * A snapshot holds the whole state the next step reads: the populations as
+ * stored (the handle's block layout and precision, bit for bit), the FP64
+ * particle table with shapes and box ids, the step count (hence the AA
+ * parity), the fluid force, the momentum-exchange mode and, when the next
+ * step takes its momentum exchange from the recorded moments, the list of
+ * interior cells the last collision wrote.  Launch shape and tuning are not
+ * part of it.  The layout is host byte order with fixed-width fields; it is
+ * meant for the same library on machines of the same byte order.
+ *
+ * hlbm_checkpoint_bytes: *bytes = the size of a snapshot of the current
+ * state.  Synchronises; returns the error the GPU flagged, if any (no
+ * snapshot of a failed state).
+ *
+ * hlbm_save: writes the snapshot into the caller's host buffer buf of
+ * `bytes` >= hlbm_checkpoint_bytes (pageable or pinned memory; the library
+ * keeps no reference).  Synchronises.  HLBM_ERR_ARG for a NULL or too small
+ * buffer.
+ *
+ * hlbm_load: restores a snapshot into a handle created with the same boxes,
+ * precision, fp16 scale, tau, eps and gravity and max_particles at least the
+ * snapshot's particle count, before its first step and before any particle
+ * is added (HLBM_ERR_STATE otherwise).  The next hlbm_step continues the
+ * saved run exactly as the saving handle would.  HLBM_ERR_ARG (nothing
+ * queued) for a NULL, truncated or foreign buffer or one that does not fit
+ * the handle; the particles go through hlbm_add_particles' checks.
+ * Synchronises. */
+int hlbm_checkpoint_bytes(hlbm_handle h, size_t* bytes);
+int hlbm_save(hlbm_handle h, void* buf, size_t bytes);
+int hlbm_load(hlbm_handle h, const void* buf, size_t bytes);
+
 /* Momentum exchange without device allocation.
  *
  * The paper has no counterpart to this call; it serves callers that cannot

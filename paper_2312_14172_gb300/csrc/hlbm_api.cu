@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -950,6 +951,219 @@ int hlbm_interior_cells(hlbm_handle h, long long* n) {
   long long t = 0;
   for (int k = 0; k < ILIST_STRIPES; ++k) t += std::min((long long)cnt[k], h->L.ilist_cap);
   *n = t;
+  return read_status(h);
+}
+
+}  // extern "C"
+// ---------------------------------------------------------------- snapshots
+// Layout (host byte order, no padding): the header below; per box nx, ny,
+// nz, bc (int64); shape and box id per particle (int32); the particle
+// table, PF_COUNT rows of np doubles; the interior-cell list when the next
+// step takes its momentum exchange from it (ILIST_STRIPES int32 counts,
+// then per stripe its int2 entries and its float4 moments); the populations
+// as stored (the handle's own block layout and precision).
+namespace {
+
+constexpr char CK_MAGIC[8] = {'H', 'L', 'B', 'M', 'C', 'K', 'P', '1'};
+
+struct CkHeader {
+  char magic[8];
+  int64_t nboxes, precision, fp16_scale_log2, np, pf_count, steps, mea_mode, has_list, pop_bytes;
+  double tau, eps, gravity[3], fluid_force[3];
+};
+
+size_t pop_bytes(const hlbm_ctx* h) {
+  return (size_t)QVB * h->L.nblocks * (h->prm.precision == HLBM_FP32 ? 4 : 2);
+}
+
+// the snapshot's size, with the interior-list counts it will hold (read
+// from the device when the next step uses the list)
+int snapshot_plan(hlbm_ctx* h, size_t* total, bool* has_list, int cnt[ILIST_STRIPES]) {
+  const int st = read_status(h);
+  if (st != HLBM_OK) return st;
+  *has_list = h->np > 0 && h->moments_valid && h->mea_mode == HLBM_MEA_MOMENTS && h->ilist_idx;
+  size_t t = sizeof(CkHeader) + sizeof(int64_t) * 4 * h->boxes.size() + sizeof(int32_t) * 2 * (size_t)h->np +
+             sizeof(double) * PF_COUNT * (size_t)h->np;
+  if (*has_list) {
+    CK(cudaMemcpyAsync(cnt, h->ilist_count, sizeof(int) * ILIST_STRIPES, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    t += sizeof(int32_t) * ILIST_STRIPES;
+    for (int k = 0; k < ILIST_STRIPES; ++k) {
+      if (cnt[k] < 0 || cnt[k] > h->L.ilist_cap) return fail(h, HLBM_ERR_STATE, "interior-cell list count out of range");
+      t += (sizeof(int2) + sizeof(float4)) * (size_t)cnt[k];
+    }
+  }
+  *total = t + pop_bytes(h);
+  return HLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hlbm_checkpoint_bytes(hlbm_handle h, size_t* bytes) {
+  if (!h || !bytes) return HLBM_ERR_ARG;
+  *bytes = 0;
+  bool has_list = false;
+  int cnt[ILIST_STRIPES];
+  return snapshot_plan(h, bytes, &has_list, cnt);
+}
+
+int hlbm_save(hlbm_handle h, void* buf, size_t bytes) {
+  if (!h) return HLBM_ERR_ARG;
+  if (!buf) return fail(h, HLBM_ERR_ARG, "NULL buffer");
+  size_t total = 0;
+  bool has_list = false;
+  int cnt[ILIST_STRIPES];
+  int rc = snapshot_plan(h, &total, &has_list, cnt);
+  if (rc != HLBM_OK) return rc;
+  if (bytes < total) return fail(h, HLBM_ERR_ARG, "buffer smaller than hlbm_checkpoint_bytes");
+  char* o = (char*)buf;
+  auto put = [&](const void* src, size_t n) { std::memcpy(o, src, n); o += n; };
+  CkHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, CK_MAGIC, 8);
+  hd.nboxes = (int64_t)h->boxes.size();
+  hd.precision = h->prm.precision;
+  hd.fp16_scale_log2 = h->prm.fp16_scale_log2;
+  hd.np = h->np;
+  hd.pf_count = PF_COUNT;
+  hd.steps = h->steps;
+  hd.mea_mode = h->mea_mode;
+  hd.has_list = has_list ? 1 : 0;
+  hd.pop_bytes = (int64_t)pop_bytes(h);
+  hd.tau = h->prm.tau;
+  hd.eps = h->prm.eps;
+  for (int j = 0; j < 3; ++j) {
+    hd.gravity[j] = h->prm.gravity[j];
+    hd.fluid_force[j] = h->prm.fluid_force[j];
+  }
+  put(&hd, sizeof(hd));
+  for (const BoxDesc& b : h->boxes) {
+    const int64_t d[4] = {b.nx, b.ny, b.nz, b.bc};
+    put(d, sizeof(d));
+  }
+  const size_t np = (size_t)h->np;
+  for (size_t k = 0; k < np; ++k) { const int32_t v = h->h_shape[k]; put(&v, sizeof(v)); }
+  for (size_t k = 0; k < np; ++k) { const int32_t v = h->h_box[k]; put(&v, sizeof(v)); }
+  if (np > 0) {
+    CK(cudaMemcpy2DAsync(o, sizeof(double) * np, h->P, sizeof(double) * h->L.cap, sizeof(double) * np, PF_COUNT,
+                         cudaMemcpyDeviceToHost, h->stream));
+    o += sizeof(double) * PF_COUNT * np;
+  }
+  if (has_list) {
+    put(cnt, sizeof(int32_t) * ILIST_STRIPES);
+    for (int k = 0; k < ILIST_STRIPES; ++k) {
+      if (cnt[k] == 0) continue;
+      const size_t k0 = (size_t)k * h->L.ilist_cap;
+      CK(cudaMemcpyAsync(o, h->ilist_idx + k0, sizeof(int2) * cnt[k], cudaMemcpyDeviceToHost, h->stream));
+      o += sizeof(int2) * cnt[k];
+      CK(cudaMemcpyAsync(o, h->ilist_mom + k0, sizeof(float4) * cnt[k], cudaMemcpyDeviceToHost, h->stream));
+      o += sizeof(float4) * cnt[k];
+    }
+  }
+  CK(cudaMemcpyAsync(o, h->f, pop_bytes(h), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return HLBM_OK;
+}
+
+int hlbm_load(hlbm_handle h, const void* buf, size_t bytes) {
+  if (!h) return HLBM_ERR_ARG;
+  if (!buf) return fail(h, HLBM_ERR_ARG, "NULL buffer");
+  if (h->steps != 0 || h->np != 0)
+    return fail(h, HLBM_ERR_STATE, "a snapshot loads into a new handle (no step taken, no particles added)");
+  const char* i = (const char*)buf;
+  const char* end = i + bytes;
+  auto get = [&](void* dst, size_t n) -> bool {
+    if ((size_t)(end - i) < n) return false;
+    std::memcpy(dst, i, n);
+    i += n;
+    return true;
+  };
+  CkHeader hd;
+  if (!get(&hd, sizeof(hd)) || std::memcmp(hd.magic, CK_MAGIC, 8) != 0)
+    return fail(h, HLBM_ERR_ARG, "not a snapshot of this library");
+  if (hd.pf_count != PF_COUNT) return fail(h, HLBM_ERR_ARG, "snapshot of another particle table layout");
+  if (hd.nboxes != (int64_t)h->boxes.size() || hd.precision != h->prm.precision ||
+      hd.fp16_scale_log2 != h->prm.fp16_scale_log2 || hd.pop_bytes != (int64_t)pop_bytes(h))
+    return fail(h, HLBM_ERR_ARG, "snapshot of other boxes or another storage precision");
+  bool same = hd.tau == h->prm.tau && hd.eps == h->prm.eps;
+  for (int j = 0; j < 3; ++j) same = same && hd.gravity[j] == h->prm.gravity[j];
+  if (!same) return fail(h, HLBM_ERR_ARG, "snapshot taken with another tau, eps or gravity");
+  if (hd.np < 0 || hd.np > h->L.cap) return fail(h, HLBM_ERR_ARG, "snapshot holds more particles than max_particles");
+  if (hd.steps < 0 || (hd.mea_mode != HLBM_MEA_KERNEL && hd.mea_mode != HLBM_MEA_MOMENTS))
+    return fail(h, HLBM_ERR_ARG, "corrupt snapshot header");
+  for (size_t b = 0; b < h->boxes.size(); ++b) {
+    int64_t d[4];
+    if (!get(d, sizeof(d))) return fail(h, HLBM_ERR_ARG, "truncated snapshot");
+    const BoxDesc& B = h->boxes[b];
+    if (d[0] != B.nx || d[1] != B.ny || d[2] != B.nz || d[3] != B.bc)
+      return fail(h, HLBM_ERR_ARG, "snapshot of other boxes or another storage precision");
+  }
+  const int n = (int)hd.np;
+  std::vector<int32_t> shp(n), bx(n);
+  std::vector<double> tab((size_t)PF_COUNT * n);
+  if (!get(shp.data(), sizeof(int32_t) * n) || !get(bx.data(), sizeof(int32_t) * n) ||
+      !get(tab.data(), sizeof(double) * tab.size()))
+    return fail(h, HLBM_ERR_ARG, "truncated snapshot");
+  int cnt[ILIST_STRIPES] = {0};
+  std::vector<const char*> lst(ILIST_STRIPES, nullptr);
+  if (hd.has_list) {
+    if (!get(cnt, sizeof(cnt))) return fail(h, HLBM_ERR_ARG, "truncated snapshot");
+    for (int k = 0; k < ILIST_STRIPES; ++k) {
+      if (cnt[k] < 0 || cnt[k] > h->L.ilist_cap || !h->ilist_idx)
+        return fail(h, HLBM_ERR_ARG, "snapshot's interior-cell list does not fit this handle");
+      const size_t nb = (sizeof(int2) + sizeof(float4)) * (size_t)cnt[k];
+      if ((size_t)(end - i) < nb) return fail(h, HLBM_ERR_ARG, "truncated snapshot");
+      lst[k] = i;
+      i += nb;
+    }
+  }
+  if ((size_t)(end - i) < pop_bytes(h)) return fail(h, HLBM_ERR_ARG, "truncated snapshot");
+  const char* pops = i;
+  // the particles through the regular path (validation, derived tables),
+  // then the table exactly as saved
+  if (n > 0) {
+    std::vector<double> a(3 * (size_t)n), X(3 * (size_t)n), U(3 * (size_t)n), W(3 * (size_t)n),
+        q(4 * (size_t)n), rho(n);
+    auto row = [&](int fld, int k) { return tab[(size_t)fld * n + k]; };
+    for (int k = 0; k < n; ++k) {
+      for (int j = 0; j < 3; ++j) {
+        a[3 * k + j] = row(PF_A + j, k);
+        X[3 * k + j] = row(PF_X + j, k);
+        U[3 * k + j] = row(PF_U + j, k);
+        W[3 * k + j] = row(PF_W + j, k);
+      }
+      for (int j = 0; j < 4; ++j) q[4 * k + j] = row(PF_Q + j, k);
+      rho[k] = row(PF_RHO, k);
+    }
+    const int rc = hlbm_add_particles(h, n, bx.data(), shp.data(), a.data(), X.data(), U.data(), W.data(),
+                                      q.data(), rho.data());
+    if (rc != HLBM_OK) return rc;
+    CK(cudaMemcpy2DAsync(h->P, sizeof(double) * h->L.cap, tab.data(), sizeof(double) * n, sizeof(double) * n,
+                         PF_COUNT, cudaMemcpyHostToDevice, h->stream));
+    CK(launch_records(part_args(h, 0), h->stream));
+  }
+  CK(cudaMemsetAsync(h->ilist_count, 0, sizeof(int) * ILIST_STRIPES, h->stream));
+  if (hd.has_list) {
+    CK(cudaMemcpyAsync(h->ilist_count, cnt, sizeof(cnt), cudaMemcpyHostToDevice, h->stream));
+    for (int k = 0; k < ILIST_STRIPES; ++k) {
+      if (cnt[k] == 0) continue;
+      const size_t k0 = (size_t)k * h->L.ilist_cap;
+      CK(cudaMemcpyAsync(h->ilist_idx + k0, lst[k], sizeof(int2) * cnt[k], cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(h->ilist_mom + k0, lst[k] + sizeof(int2) * cnt[k], sizeof(float4) * cnt[k],
+                         cudaMemcpyHostToDevice, h->stream));
+    }
+  }
+  for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(h->cnt[k], 0, sizeof(int) * (size_t)h->L.ntiles, h->stream));
+  CK(cudaMemcpyAsync(h->f, pops, pop_bytes(h), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int j = 0; j < 3; ++j) h->prm.fluid_force[j] = hd.fluid_force[j];
+  // the saver's momentum-exchange mode, where this handle can hold its list
+  if (hd.mea_mode == HLBM_MEA_KERNEL || h->ilist_idx) h->mea_mode = (int)hd.mea_mode;
+  h->steps = hd.steps;
+  h->moments_valid = hd.has_list != 0 && h->mea_mode == HLBM_MEA_MOMENTS;
+  drop_graphs(h);
   return read_status(h);
 }
 

@@ -32,7 +32,8 @@ EXPORTS = ["hlbm_default_params", "hlbm_required_bytes", "hlbm_init_lattice", "h
            "hlbm_num_particles", "hlbm_steps_done", "hlbm_set_launch", "hlbm_get_launch",
            "hlbm_set_fluid_force",
            "hlbm_set_mea_mode", "hlbm_get_mea_mode",
-           "hlbm_autotune", "hlbm_kernel_times", "hlbm_interior_cells", "hlbm_last_error", "hlbm_destroy",
+           "hlbm_autotune", "hlbm_kernel_times", "hlbm_interior_cells",
+           "hlbm_checkpoint_bytes", "hlbm_save", "hlbm_load", "hlbm_last_error", "hlbm_destroy",
            "hlbm_mea_noalloc"]
 HLBM_NOALLOC_MAX_PARTICLES = 1024
 
@@ -97,6 +98,9 @@ def load(path=LIB_PATH):
     L.hlbm_autotune.argtypes = [_h, ctypes.c_int, _ip, _ip, _ip, _fp]
     L.hlbm_kernel_times.argtypes = [_h, ctypes.c_int, _fp]
     L.hlbm_interior_cells.argtypes = [_h, ctypes.POINTER(ctypes.c_longlong)]
+    L.hlbm_checkpoint_bytes.argtypes = [_h, ctypes.POINTER(ctypes.c_size_t)]
+    L.hlbm_save.argtypes = [_h, _vp, ctypes.c_size_t]
+    L.hlbm_load.argtypes = [_h, _vp, ctypes.c_size_t]
     L.hlbm_last_error.argtypes = [_h]
     L.hlbm_last_error.restype = ctypes.c_char_p
     L.hlbm_destroy.argtypes = [_h]
@@ -302,6 +306,20 @@ class Lattice:
         n = ctypes.c_longlong(0)
         _check(self.h, load().hlbm_interior_cells(self.h, ctypes.byref(n)))
         return n.value
+
+    def save(self):
+        """Snapshot of the whole state the next step reads (bytes)."""
+        L = load()
+        n = ctypes.c_size_t(0)
+        _check(self.h, L.hlbm_checkpoint_bytes(self.h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self.h, L.hlbm_save(self.h, buf, n.value))
+        return buf.raw
+
+    def load_snapshot(self, data):
+        """Restore a snapshot (from save()) into this new handle."""
+        data = bytes(data)
+        _check(self.h, load().hlbm_load(self.h, data, len(data)))
 
 
 def hlbm_mea_noalloc(f, plane, nx, ny, nz, bc_flags, precision, fp16_scale_log2, parity, n, shape,
