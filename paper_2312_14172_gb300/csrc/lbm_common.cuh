@@ -248,13 +248,38 @@ __device__ __forceinline__ float capsule_row_dist2(const Capsule& c, float ry, f
 // of the block.
 __device__ __forceinline__ void load_candidates(const LbmArgs& a, const Brick& k, Rec* srec,
                                                 unsigned long long* s_rowmask) {
-  const int cnt = min(min(a.bin_count[k.tile], a.bin_cap), MAX_CAND);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int nth = blockDim.x * blockDim.y;
   const int* ids = a.bin_ids + k.tile * (long long)a.bin_cap;
-  for (int e = tid; e < cnt * 32; e += nth) {
-    const int j = e >> 5, w = e & 31;
-    reinterpret_cast<int*>(&srec[j])[w] = reinterpret_cast<const int*>(&a.rec[ids[j]])[w];
+  // the tile's first 64 ids are read together with its count: one round
+  // trip to L2 instead of two
+  const int lane = tid & 31;
+  const int id0 = lane < a.bin_cap ? ids[lane] : 0;
+  const int id1 = 32 + lane < a.bin_cap ? ids[32 + lane] : 0;
+  const int cnt = min(min(a.bin_count[k.tile], a.bin_cap), MAX_CAND);
+  if (nth % 32 == 0) {
+    // whole warps: a record is one word per lane; each warp copies up to
+    // four records with their loads in flight before the stores
+    const int wid = tid >> 5, nw = nth >> 5;
+    for (int j0 = wid; j0 < cnt; j0 += 4 * nw) {
+      int v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u * nw;
+        const int id = __shfl_sync(0xffffffffu, j < 32 ? id0 : id1, j & 31);
+        v[u] = j < cnt ? reinterpret_cast<const int*>(&a.rec[id])[lane] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + u * nw;
+        if (j < cnt) reinterpret_cast<int*>(&srec[j])[lane] = v[u];
+      }
+    }
+  } else {
+    for (int e = tid; e < cnt * 32; e += nth) {
+      const int j = e >> 5, w = e & 31;
+      reinterpret_cast<int*>(&srec[j])[w] = reinterpret_cast<const int*>(&a.rec[ids[j]])[w];
+    }
   }
   __syncthreads();
   const BoxDesc& bd = k.bd;

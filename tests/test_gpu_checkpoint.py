@@ -72,11 +72,12 @@ def test_snapshot_with_particles_restores_and_continues(H, precision, mode):
     if mode == "moments":
         assert b.interior_cells() == a.interior_cells() > 0
     assert b.save() == snap
-    # and the run continues as the saving handle's does.  The FP64 atomic
-    # sums of the momentum exchange may add in another order; with FP16
-    # storage such a last-bit difference can move a stored population to the
-    # neighbouring half value, so its bound is wider.
-    rtol = 1e-9 if precision == "fp32" else 1e-6
+    # and the run continues as the saving handle's does, within the
+    # run-to-run spread: the momentum exchange adds its FP32 per-cell terms
+    # in warp groups and FP64 atomics whose order follows the list's
+    # (atomically appended) order, and with FP16 storage a last-bit change
+    # can move a stored population to the neighbouring half value
+    rtol = 1e-6
     X0 = sa["X"].copy()
     a.step(6)
     b.step(6)
