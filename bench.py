@@ -594,10 +594,8 @@ def fp32_fp16_pair(w, args, stream, peak, ws, steps_max=40):
 
 def solid_fraction(P, cells):
     """Total particle volume over the lattice volume."""
-    a = np.asarray(P["a"], float)
-    shp = np.asarray(P["shape"])
-    vol = np.where(shp == 2, 8.0 * a[:, 0] * a[:, 1] * a[:, 2], 4.0 / 3.0 * np.pi * a[:, 0] * a[:, 1] * a[:, 2])
-    return float(vol.sum() / cells)
+    from paper_2312_14172_gb300 import workloads
+    return float(workloads.particle_volumes(P).sum() / cells)
 
 
 def nonspherical_leg(args, stream, peak, ws):
