@@ -183,38 +183,43 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
       }
     }
     // f*_i - w_i = (1 - 1/tau) (d_i - E_i(u)) + E_i(u + Delta u), E = f^eq - w;
-    // E_i = w drho + w rho (4.5 (c.u)^2 - 1.5 u.u) +- 3 w rho (c.u)
+    // E_i = w drho + w rho (4.5 (c.u)^2 - 1.5 u.u) +- 3 w rho (c.u).  With
+    // v = u + Delta u and o = 1 - 1/tau, a pair +-c_i takes
+    //   f*_+- = o d_+- + C +- A,  A = 3 w rho (c.v - o c.u),
+    //   C = 4.5 w rho ((c.v)^2 - o (c.u)^2) + w rho K + w drho / tau,
+    // K = -1.5 (v.v - o u.u) shared by all directions.
     const float2 vx = add2(ux, dux), vy = add2(uy, duy), vz = add2(uz, duz);
     const float2 nusq = mul2(fma2(uz, uz, fma2(uy, uy, mul2(ux, ux))), f2(-1.5f));
     const float2 nvsq = mul2(fma2(vz, vz, fma2(vy, vy, mul2(vx, vx))), f2(-1.5f));
     const float om1s = 1.0f - a.omega;
-    const float2 om1 = f2(om1s), nom1 = f2(-om1s);
-    const float2 rs = mul2(rho, f2(sc)), ds = mul2(drho, f2(sc));
+    const float2 om1 = f2(om1s), nom1 = f2(-om1s), omg = f2(a.omega);
+    const float2 K = fma2(nom1, nusq, nvsq);
+    const float2 rs = mul2(rho, f2(sc)), dso = mul2(mul2(drho, f2(sc)), omg);
     {
-      const float2 w0r = mul2(rs, f2(1.0f / 3.0f)), w0d = mul2(ds, f2(1.0f / 3.0f));
-      const float2 eu = fma2(w0r, nusq, w0d), ev = fma2(w0r, nvsq, w0d);
-      d[0] = T::pack(fma2(om1, T::val(d[0]), fma2(nom1, eu, ev)));
+      const float2 C0 = fma2(mul2(rs, f2(1.0f / 3.0f)), K, mul2(dso, f2(1.0f / 3.0f)));
+      d[0] = T::pack(fma2(om1, T::val(d[0]), C0));
     }
-    const float2 wr1 = mul2(rs, f2(1.0f / 18.0f)), wd1 = mul2(ds, f2(1.0f / 18.0f));
-    const float2 wr2 = mul2(rs, f2(1.0f / 36.0f)), wd2 = mul2(ds, f2(1.0f / 36.0f));
+    const float2 wr1 = mul2(rs, f2(1.0f / 18.0f)), wr2 = mul2(rs, f2(1.0f / 36.0f));
+    const float2 q1 = fma2(wr1, K, mul2(dso, f2(1.0f / 18.0f)));
+    const float2 q2 = fma2(wr2, K, mul2(dso, f2(1.0f / 36.0f)));
+    const float2 h1 = mul2(wr1, f2(4.5f)), h2 = mul2(wr2, f2(4.5f));
     const float2 w3r1 = mul2(rs, f2(1.0f / 6.0f)), w3r2 = mul2(rs, f2(1.0f / 12.0f));
-    auto pair = [&](int I, float2 WR, float2 WD, float2 W3, float2 cu, float2 cv) {
-      const float2 eu = fma2(WR, fma2(f2(4.5f), mul2(cu, cu), nusq), WD);
-      const float2 ev = fma2(WR, fma2(f2(4.5f), mul2(cv, cv), nvsq), WD);
-      const float2 C = fma2(nom1, eu, ev);
-      const float2 A = mul2(W3, fma2(nom1, cu, cv));
+    auto pair = [&](int I, float2 H, float2 Qc, float2 W3, float2 cu, float2 cv) {
+      const float2 p = mul2(nom1, cu);               // -o c.u
+      const float2 A = mul2(W3, add2(cv, p));
+      const float2 C = fma2(H, fma2(p, cu, mul2(cv, cv)), Qc);
       d[I] = T::pack(fma2(om1, T::val(d[I]), add2(C, A)));
       d[I + 1] = T::pack(fma2(om1, T::val(d[I + 1]), sub2(C, A)));
     };
-    pair(1, wr1, wd1, w3r1, ux, vx);
-    pair(3, wr1, wd1, w3r1, uy, vy);
-    pair(5, wr1, wd1, w3r1, uz, vz);
-    pair(7, wr2, wd2, w3r2, add2(ux, uy), add2(vx, vy));
-    pair(9, wr2, wd2, w3r2, sub2(ux, uy), sub2(vx, vy));
-    pair(11, wr2, wd2, w3r2, add2(ux, uz), add2(vx, vz));
-    pair(13, wr2, wd2, w3r2, sub2(ux, uz), sub2(vx, vz));
-    pair(15, wr2, wd2, w3r2, add2(uy, uz), add2(vy, vz));
-    pair(17, wr2, wd2, w3r2, sub2(uy, uz), sub2(vy, vz));
+    pair(1, h1, q1, w3r1, ux, vx);
+    pair(3, h1, q1, w3r1, uy, vy);
+    pair(5, h1, q1, w3r1, uz, vz);
+    pair(7, h2, q2, w3r2, add2(ux, uy), add2(vx, vy));
+    pair(9, h2, q2, w3r2, sub2(ux, uy), sub2(vx, vy));
+    pair(11, h2, q2, w3r2, add2(ux, uz), add2(vx, vz));
+    pair(13, h2, q2, w3r2, sub2(ux, uz), sub2(vx, vz));
+    pair(15, h2, q2, w3r2, add2(uy, uz), add2(vy, vz));
+    pair(17, h2, q2, w3r2, sub2(uy, uz), sub2(vy, vz));
     // cells inside a particle record the mass and momentum they send out, as
     // stored, for the next step's momentum exchange (taken before the stores,
     // so that the values need not stay in registers through them)
