@@ -187,6 +187,7 @@ static int fail(hlbm_ctx* h, int code, const std::string& msg) {
 
 static LbmArgs lbm_args(const hlbm_ctx* h, int parity) {
   LbmArgs a{};
+  a.nsm = h->nsm;
   a.f = h->f;
   a.ncell = h->L.ncell;
   a.boxes = h->d_boxes;

@@ -91,7 +91,8 @@ constexpr int ILIST_STRIPES = 64;
 struct __align__(16) Rec {
   float xh[3], xl[3];  // centre as float pair: X = xh + xl
   float u[3], w[3];    // velocity, angular velocity
-  float M[9];          // rotation body -> world, row-major (identity for spheres)
+  float M[9];          // rotation body -> world, row-major; a sphere's
+                       // first four: its collision bounds (SPH_* below)
   float a[3];          // radius / semi-axes / half-extents / capsule (r, r, h)
   float ia[3];         // fp32(1 / a_j) (ellipsoid inside test)
   float rinf2;         // square of a radius beyond which B = 0
@@ -101,6 +102,10 @@ struct __align__(16) Rec {
   int pid;
 };
 static_assert(sizeof(Rec) == 128, "record size");
+// a sphere's record: in2 * 0.99999 and in2 * 1.00001 (below / above them the
+// centre-inside decision needs no exact test), (a - eps/2)^2 (-1 when
+// a <= eps/2) and (a + eps/2)^2 (B is 1 within, 0 beyond), all FP32
+enum { SPH_IN_LO = 0, SPH_IN_HI = 1, SPH_R2_IN = 2, SPH_R2_OUT = 3 };
 
 // status flags: ST_CAPACITY a tile's particle list is full; ST_OVERLAP three
 // particles hold one cell (the list of interior cells takes two per cell);
@@ -212,6 +217,12 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
 
 struct LbmArgs {
   int pdl;                  // launch with programmatic dependent launch (host side only)
+  int nsm;                  // SMs of the device (host side only)
+  // blocks at the end of the grid (about its last wave) that let the next
+  // kernel launch as soon as they start; every earlier block does so when it
+  // ends, so that the next kernel's blocks, which wait for this grid to
+  // finish, take no SM room this grid's remaining blocks still need
+  long long pdl_tail;
   void* f;                  // populations, blocked layout (float* or __half*)
   long long ncell;          // cells of all boxes (global cell numbering)
   const BoxDesc* boxes;

@@ -281,29 +281,31 @@ __device__ __forceinline__ void load_candidates(const LbmArgs& a, const Brick& k
       reinterpret_cast<int*>(&srec[j])[w] = reinterpret_cast<const int*>(&a.rec[ids[j]])[w];
     }
   }
+  const int nrows = a.sub_y * a.sub_z;
+  for (int r = tid; r < nrows; r += nth) s_rowmask[r] = 0ull;
   __syncthreads();
+  // one (row, candidate) pair per thread: rows vary fastest, so a warp reads
+  // one record and sets bits of distinct rows
   const BoxDesc& bd = k.bd;
   const float Ly = (float)bd.ny, Lz = (float)bd.nz;
-  for (int r = tid; r < a.sub_y * a.sub_z; r += nth) {
-    const int yy = k.y0 + r % a.sub_y;
-    const int zz = k.z0 + r / a.sub_y;
-    unsigned long long m = 0;
-    for (int j = 0; j < cnt; ++j) {
-      const Rec& R = srec[j];
-      float r0y = (float)yy - R.xh[1], r0z = (float)zz - R.xh[2];
-      if (!(bd.bc & 2)) { if (r0y > 0.5f * Ly) r0y -= Ly; else if (r0y < -0.5f * Ly) r0y += Ly; }
-      if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
-      const float ry = __fsub_rn(r0y, R.xl[1]), rz = __fsub_rn(r0z, R.xl[2]);
-      if (ry * ry + rz * rz < R.rinf2) {
-        if (R.shape == 0) {
-          m |= 1ull << j;
-        } else {
-          const Capsule c = capsule_of(R, a.eps);
-          if (capsule_row_dist2(c, ry, rz) < c.r2) m |= 1ull << j;
-        }
+  const int lr = __ffs(nrows) - 1, ly = __ffs(a.sub_y) - 1;  // sub_y, sub_z are powers of two
+  for (int e = tid; e < (cnt << lr); e += nth) {
+    const int r = e & (nrows - 1), j = e >> lr;
+    const int yy = k.y0 + (r & (a.sub_y - 1));
+    const int zz = k.z0 + (r >> ly);
+    const Rec& R = srec[j];
+    float r0y = (float)yy - R.xh[1], r0z = (float)zz - R.xh[2];
+    if (!(bd.bc & 2)) { if (r0y > 0.5f * Ly) r0y -= Ly; else if (r0y < -0.5f * Ly) r0y += Ly; }
+    if (!(bd.bc & 4)) { if (r0z > 0.5f * Lz) r0z -= Lz; else if (r0z < -0.5f * Lz) r0z += Lz; }
+    const float ry = __fsub_rn(r0y, R.xl[1]), rz = __fsub_rn(r0z, R.xl[2]);
+    if (ry * ry + rz * rz < R.rinf2) {
+      bool hit = true;
+      if (R.shape != 0) {
+        const Capsule c = capsule_of(R, a.eps);
+        hit = capsule_row_dist2(c, ry, rz) < c.r2;
       }
+      if (hit) atomicOr(&s_rowmask[r], 1ull << j);
     }
-    s_rowmask[r] = m;
   }
   __syncthreads();
 }
@@ -367,17 +369,18 @@ __device__ __forceinline__ void couple_row(const Rec* srec, unsigned long long r
     // relative in r^2; other shapes: 1e-3 cells).
     if (R.shape == 0) {
       // a sphere's indicator is 1 within r <= a - eps/2 and 0 beyond a + eps/2:
-      // only cells in that shell need the distance and the ramp
-      const float a_in = R.a[0] - 0.5f * eps, a_out = R.a[0] + 0.5f * eps;
-      const float r2_in = a_in > 0.0f ? a_in * a_in : -1.0f, r2_out = a_out * a_out;
+      // only cells in that shell need the distance and the ramp (bounds
+      // precomputed in the record)
+      const float in_lo = R.M[SPH_IN_LO], in_hi = R.M[SPH_IN_HI];
+      const float r2_in = R.M[SPH_R2_IN], r2_out = R.M[SPH_R2_OUT];
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         const float rx = arm_x(j);
         const float r2 = rx * rx + d2;
         if (r2 < R.rinf2) {
           bool in;
-          if (r2 < R.in2 * 0.99999f) in = true;
-          else if (r2 > R.in2 * 1.00001f) in = false;
+          if (r2 < in_lo) in = true;
+          else if (r2 > in_hi) in = false;
           else { const float rr[3] = {rx, ry, rz}; in = inside_from_offset(R, rr); }
           const float B = r2 <= r2_in ? 1.0f : (r2 >= r2_out ? 0.0f : indicator(sdf(R, rx, ry, rz, r2), eps, inv_eps));
           take(j, rx, in, B);

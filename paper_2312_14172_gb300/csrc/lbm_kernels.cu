@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
   // per row of the brick (local y + sub_y * local z): the candidates whose
   // influence sphere meets the row
   __shared__ unsigned long long s_rowmask[COUPLE ? TILE_Y * TILE_Z : 1];
-  pdl_trigger();
+  const bool early = (long long)blockIdx.x + a.pdl_tail >= (long long)gridDim.x;
+  if (early) pdl_trigger();
   pdl_wait();
   const Brick k = brick_of(a);
   const BoxDesc& bd = k.bd;
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
       append_interior<1>(a, g, cc, mom);
     }
   }
+  if (!early) pdl_trigger();
 }
 
 // ---------------------------------------------------------------------------
@@ -330,7 +332,10 @@ __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
 template <typename S, int PAR, bool W, bool C>
 static cudaError_t launch_cs(const LbmArgs& a, cudaStream_t s) {
   dim3 block(TILE_X, a.sub_y);
-  return launch_k(collide_stream_kernel<S, PAR, W, C>, dim3((unsigned)a.nbricks), block, 0, s, a.pdl != 0, a);
+  LbmArgs b = a;
+  // resident blocks per SM as the launch bounds provide for (registers)
+  b.pdl_tail = a.nsm > 0 ? (long long)a.nsm * (HLBM_CS_MINBLOCKS * 256 / (int)(block.x * block.y)) : a.nbricks;
+  return launch_k(collide_stream_kernel<S, PAR, W, C>, dim3((unsigned)a.nbricks), block, 0, s, a.pdl != 0, b);
 }
 
 template <typename S>

@@ -94,7 +94,8 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
   using T = Two<S>;
   __shared__ Rec srec[COUPLE ? MAX_CAND : 1];
   __shared__ unsigned long long s_rowmask[COUPLE ? TILE_Y * TILE_Z : 1];
-  pdl_trigger();
+  const bool early = (long long)blockIdx.x + a.pdl_tail >= (long long)gridDim.x;
+  if (early) pdl_trigger();
   pdl_wait();
   const Brick k = brick_of(a);
   const BoxDesc& bd = k.bd;
@@ -279,12 +280,17 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
     else
       slice(std::integral_constant<bool, false>{}, z);
   }
+  if (!early) pdl_trigger();
 }
 
 template <typename S, int PAR, bool W, bool C>
 static cudaError_t launch_cp(const LbmArgs& a, cudaStream_t s) {
   dim3 block(TILE_X / 2, a.sub_y);
-  return launch_k(collide_pair_kernel<S, PAR, W, C>, dim3((unsigned)a.nbricks), block, 0, s, a.pdl != 0, a);
+  LbmArgs b = a;
+  // resident blocks per SM as the launch bounds provide for (registers)
+  b.pdl_tail = a.nsm > 0 ? (long long)a.nsm * (PairBlocks<S>::value * 128 / (int)(block.x * block.y))
+                         : a.nbricks;
+  return launch_k(collide_pair_kernel<S, PAR, W, C>, dim3((unsigned)a.nbricks), block, 0, s, a.pdl != 0, b);
 }
 
 template <typename S>

@@ -25,10 +25,10 @@ __device__ __forceinline__ void pset(double* P, int cap, int field, int p, doubl
 }
 
 // FP32 coupling record of a particle state (X, U, W, q; semi-axes A, their
-// FP32 inverses iA, radius r_inf beyond which B = 0)
+// FP32 inverses iA, radius r_inf beyond which B = 0; interface width eps)
 __device__ __forceinline__ void make_record(const double X[3], const double U[3], const double W[3],
                                             const double q[4], const double A[3], const double iA[3],
-                                            double rinf, int p, int shape, int box, Rec& R) {
+                                            double rinf, float eps, int p, int shape, int box, Rec& R) {
   double Rm[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // a sphere needs no orientation
   if (shape != 0) rotation_rn(q, Rm);
   for (int j = 0; j < 3; ++j) {
@@ -42,6 +42,16 @@ __device__ __forceinline__ void make_record(const double X[3], const double U[3]
   }
   for (int k = 0; k < 9; ++k) R.M[k] = __double2float_rn(Rm[k]);
   R.in2 = __double2float_rn(A[0] * A[0]);
+  if (shape == 0) {
+    // a sphere needs no rotation: its slots hold the FP32 bounds of the
+    // collision's per-cell tests (the same roundings as computed there)
+    const float a_in = __fsub_rn(R.a[0], __fmul_rn(0.5f, eps));
+    const float a_out = __fadd_rn(R.a[0], __fmul_rn(0.5f, eps));
+    R.M[SPH_IN_LO] = __fmul_rn(R.in2, 0.99999f);
+    R.M[SPH_IN_HI] = __fmul_rn(R.in2, 1.00001f);
+    R.M[SPH_R2_IN] = a_in > 0.0f ? __fmul_rn(a_in, a_in) : -1.0f;
+    R.M[SPH_R2_OUT] = __fmul_rn(a_out, a_out);
+  }
   // B vanishes beyond r_inf; a slightly larger FP32 bound keeps the test safe
   const double rb = rinf + 0.01;
   R.rinf2 = (float)(rb * rb);
@@ -50,7 +60,7 @@ __device__ __forceinline__ void make_record(const double X[3], const double U[3]
   R.pid = p;
 }
 
-__device__ void build_record(const double* P, int cap, int p, int shape, int box, Rec& R) {
+__device__ void build_record(const double* P, int cap, int p, int shape, int box, float eps, Rec& R) {
   double X[3], U[3], W[3], q[4], A[3], iA[3];
   for (int j = 0; j < 3; ++j) {
     X[j] = pget(P, cap, PF_X + j, p);
@@ -60,7 +70,7 @@ __device__ void build_record(const double* P, int cap, int p, int shape, int box
     iA[j] = pget(P, cap, PF_IA + j, p);
   }
   for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
-  make_record(X, U, W, q, A, iA, pget(P, cap, PF_RINF, p), p, shape, box, R);
+  make_record(X, U, W, q, A, iA, pget(P, cap, PF_RINF, p), eps, p, shape, box, R);
 }
 
 // eight resident blocks per SM (64 registers): the bounding-box walk is
@@ -293,7 +303,7 @@ __device__ __forceinline__ BinRange update_particle(const PartArgs& a, int p) {
   }
   for (int j = 0; j < 4; ++j) pset(a.P, cap, PF_Q + j, p, q[j]);
   Rec R;
-  make_record(X, U, W, q, A, iA, rinf, p, shape, box, R);
+  make_record(X, U, W, q, A, iA, rinf, (float)a.eps, p, shape, box, R);
   a.rec[p] = R;
   // bin tiles touched by the influence sphere, widened so that the cells next
   // to the particle's interior (which feed its momentum exchange) see it too
@@ -359,7 +369,7 @@ __global__ void records_kernel(PartArgs a) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.np) return;
   Rec R;
-  build_record(a.P, a.cap, p, a.shape[p], a.box[p], R);
+  build_record(a.P, a.cap, p, a.shape[p], a.box[p], (float)a.eps, R);
   a.rec[p] = R;
 }
 
