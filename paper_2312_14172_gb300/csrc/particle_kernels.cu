@@ -189,15 +189,14 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// Newton-Euler step of one particle: symplectic Euler for translation, the
-// body-frame Euler equations for rotation, and the quaternion update
-// q <- normalise(q + q (x) (0, omega_b) / 2)
 // Newton-Euler step of one particle in registers (Eqs. particlemotiontrans,
-// motionrot): U += F / m with F = F_h + (rho_p - rho_f) V g, X += U;
-// spheres: omega += T / I; other shapes: body-frame Euler equations
+// motionrot), symplectic Euler: U += F / m with F = F_h + (rho_p - rho_f) V g,
+// X += U; spheres: omega += T / I; other shapes: body-frame Euler equations
 // omega_b += (T_b - omega_b x (I omega_b)) / I with the rotation of the old
-// quaternion; q += q (x) (0, omega_b) / 2, normalised.  Returns false when
-// the new state is not finite.
+// quaternion; q += q (x) (0, omega_b) / 2, normalised (for a sphere in the
+// equal form (0, omega) (x) q / 2, which needs no rotation: GB300's FP64
+// pipe is narrow and this lane's FP64 chain bounds the kernel).  Returns
+// false when the new state is not finite.
 __device__ __forceinline__ bool newton_euler(const PartArgs& a, int shape, double im, double V, double rho,
                                              const double I[3], const double iI[3], const double Fh[3],
                                              const double Th[3], double X[3], double U[3], double W[3],
@@ -207,13 +206,18 @@ __device__ __forceinline__ bool newton_euler(const PartArgs& a, int shape, doubl
     U[j] += F * im;
     X[j] += U[j];
   }
-  double R[9], wb[3];
-  rotation_rn(q, R);
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  double dq[4];
   if (shape == 0) {
+    // q (x) (0, omega_b) equals (0, omega) (x) q: no rotation needed
     for (int j = 0; j < 3; ++j) W[j] += Th[j] * iI[j];
-    for (int j = 0; j < 3; ++j) wb[j] = R[0 * 3 + j] * W[0] + R[1 * 3 + j] * W[1] + R[2 * 3 + j] * W[2];
+    dq[0] = -0.5 * (W[0] * x + W[1] * y + W[2] * z);
+    dq[1] = 0.5 * (w * W[0] + W[1] * z - W[2] * y);
+    dq[2] = 0.5 * (w * W[1] + W[2] * x - W[0] * z);
+    dq[3] = 0.5 * (w * W[2] + W[0] * y - W[1] * x);
   } else {
-    double Tb[3], Lb[3], gy[3];
+    double R[9], wb[3], Tb[3], Lb[3], gy[3];
+    rotation_rn(q, R);
     for (int j = 0; j < 3; ++j) {
       wb[j] = R[0 * 3 + j] * W[0] + R[1 * 3 + j] * W[1] + R[2 * 3 + j] * W[2];
       Tb[j] = R[0 * 3 + j] * Th[0] + R[1 * 3 + j] * Th[1] + R[2 * 3 + j] * Th[2];
@@ -222,19 +226,17 @@ __device__ __forceinline__ bool newton_euler(const PartArgs& a, int shape, doubl
     cross3(wb, Lb, gy);
     for (int j = 0; j < 3; ++j) wb[j] += (Tb[j] - gy[j]) * iI[j];
     for (int j = 0; j < 3; ++j) W[j] = R[j * 3 + 0] * wb[0] + R[j * 3 + 1] * wb[1] + R[j * 3 + 2] * wb[2];
+    dq[0] = 0.5 * (-x * wb[0] - y * wb[1] - z * wb[2]);
+    dq[1] = 0.5 * (w * wb[0] + y * wb[2] - z * wb[1]);
+    dq[2] = 0.5 * (w * wb[1] + z * wb[0] - x * wb[2]);
+    dq[3] = 0.5 * (w * wb[2] + x * wb[1] - y * wb[0]);
   }
-  const double w = q[0], x = q[1], y = q[2], z = q[3];
-  double dq[4];
-  dq[0] = 0.5 * (-x * wb[0] - y * wb[1] - z * wb[2]);
-  dq[1] = 0.5 * (w * wb[0] + y * wb[2] - z * wb[1]);
-  dq[2] = 0.5 * (w * wb[1] + z * wb[0] - x * wb[2]);
-  dq[3] = 0.5 * (w * wb[2] + x * wb[1] - y * wb[0]);
   double nq = 0.0;
   for (int j = 0; j < 4; ++j) {
     q[j] += dq[j];
     nq += q[j] * q[j];
   }
-  const double inq = 1.0 / sqrt(nq);
+  const double inq = rsqrt(nq);
   for (int j = 0; j < 4; ++j) q[j] *= inq;
   bool ok = true;
   for (int j = 0; j < 3; ++j) ok = ok && isfinite(X[j]) && isfinite(U[j]) && isfinite(W[j]);

@@ -218,6 +218,10 @@ def test_sphere_off_centre_rotating(H, O):
     _pops_close(lat.populations(), orc.populations())
     _motion_close(sg, so, X0, U0, W0)
     assert np.allclose(sg["T"], so["T"], rtol=1e-3, atol=1e-8)
+    # the orientation of a spinning sphere (integrated in the world frame on
+    # the GPU, in the body frame by the oracle)
+    assert np.allclose(sg["quat"], so["quat"], atol=1e-9)
+    assert not np.allclose(sg["quat"][:, 0], 1.0)
     lat.close()
 
 
