@@ -131,7 +131,7 @@ struct hlbm_ctx {
   int* d_box = nullptr;
   Rec* rec = nullptr;
   double* partial = nullptr;
-  double* acc = nullptr;
+  long long* acc = nullptr;
   int* chunk_p = nullptr;
   int* chunk_q = nullptr;
   int* p_chunk0 = nullptr;
@@ -414,7 +414,7 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
   h->d_box = (int*)(h->buf + h->L.off_box);
   h->rec = (Rec*)(h->buf + h->L.off_rec);
   h->partial = (double*)(h->buf + h->L.off_part);
-  h->acc = (double*)(h->buf + h->L.off_acc);
+  h->acc = (long long*)(h->buf + h->L.off_acc);
   h->chunk_p = (int*)(h->buf + h->L.off_chp);
   h->chunk_q = (int*)(h->buf + h->L.off_chq);
   h->p_chunk0 = (int*)(h->buf + h->L.off_pc0);

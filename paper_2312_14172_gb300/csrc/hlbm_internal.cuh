@@ -107,6 +107,13 @@ static_assert(sizeof(Rec) == 128, "record size");
 // a <= eps/2) and (a + eps/2)^2 (B is 1 within, 0 beyond), all FP32
 enum { SPH_IN_LO = 0, SPH_IN_HI = 1, SPH_R2_IN = 2, SPH_R2_OUT = 3 };
 
+// The moments-mode momentum exchange adds its per-cell FP32 terms as 64-bit
+// integers in units of 2^-ACC_FRAC_BITS: integer sums do not depend on the
+// order in which the cells arrive, so a run is reproducible bit for bit.  A
+// term is rounded by at most 2^-45 and a particle's sum must stay below 2^19
+// in magnitude (forces and torques of lattice flows are many orders smaller).
+constexpr int ACC_FRAC_BITS = 44;
+
 // status flags: ST_CAPACITY a tile's particle list is full; ST_OVERLAP three
 // particles hold one cell (the list of interior cells takes two per cell);
 // ST_LIST_FULL a stripe of the list of interior cells is full
@@ -252,7 +259,7 @@ struct LbmArgs {
   float4* ilist_mom;
   long long ilist_cap;
   int np;                   // particles (list entries name 0 .. np-1)
-  double* acc;              // [cap][6] momentum exchange of a particle (FP64 sums)
+  long long* acc;           // [cap][6] momentum exchange of a particle, fixed point
   int* status;
 };
 
@@ -278,7 +285,7 @@ struct PartArgs {
   double* partial;          // [chunks][6] FP64 partial force/torque sums
   int* done;                // [cap] blocks finished per particle (reset to 0)
   // the same sums accumulated by the previous collision, [cap][6]
-  double* acc;
+  long long* acc;           // [cap][6] momentum exchange, fixed point (ACC_FRAC_BITS)
   int from_acc;             // 1: the update takes acc, 0: the table's F and T
   int nsm;                  // SMs of the GPU (update grid size)
   int ppb;                  // particles per update block (set by the launcher)

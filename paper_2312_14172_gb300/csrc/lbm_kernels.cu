@@ -177,11 +177,16 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
 // moments the previous collision recorded in the list of interior cells:
 //   F(x) = (j - j*) - u_p(x) (rho - rho*)  [links into a wall: - 2 c_i f_i(x)]
 // A persistent grid walks the list (one entry per thread, all 19 loads of a
-// cell in flight together); lanes of a warp that belong to the same particle
-// are summed with shuffles before one FP64 atomic per particle and warp.
+// cell in flight together); each cell's terms are rounded to fixed point
+// (ACC_FRAC_BITS), and the lanes of a warp that belong to the same particle
+// are summed with integer shuffles before one 64-bit integer atomic per
+// particle, component and warp: the sums do not depend on the list's order.
 
+// resident blocks per SM: four with walls (64 registers, a few spills; the
+// integer group sums otherwise take 88 registers and leave two blocks), five
+// without (48 registers)
 template <typename S, int PAR, bool WALLS>
-__global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
+__global__ void __launch_bounds__(256, WALLS ? 4 : 5) mea_list_kernel(LbmArgs a) {
   pdl_trigger();
   pdl_wait();
   // The list is walked in chunks of 32 entries, the stripes taken in turn
@@ -315,16 +320,15 @@ __global__ void __launch_bounds__(256) mea_list_kernel(LbmArgs a) {
       const bool mine = valid && pid == p;
       const unsigned grp = __ballot_sync(0xffffffffu, mine);
       todo &= ~grp;
-      float v[6];
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
-        v[q] = mine ? (q < 3 ? F[q] : T[q - 3]) : 0.0f;
+        const float t = q < 3 ? F[q] : T[q - 3];
+        long long v = mine ? __float2ll_rn(__fmul_rn(t, (float)(1LL << ACC_FRAC_BITS))) : 0LL;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == leader)
+          atomicAdd(reinterpret_cast<unsigned long long*>(&a.acc[(long long)p * 6 + q]), (unsigned long long)v);
       }
-      if (lane == leader)
-#pragma unroll
-        for (int q = 0; q < 6; ++q) atomicAdd(&a.acc[(long long)p * 6 + q], (double)v[q]);
     }
   }
 }

@@ -277,13 +277,14 @@ __device__ __forceinline__ BinRange update_particle(const PartArgs& a, int p) {
   // force and torque of the momentum exchange: written into the table by the
   // momentum-exchange kernel, or accumulated from the recorded moments (the
   // accumulator is cleared for the next step)
-  double* acc = a.acc + (long long)p * 6;
+  long long* acc = a.acc + (long long)p * 6;
+  const double unit = 1.0 / (double)(1LL << ACC_FRAC_BITS);  // fixed point -> force and torque
   for (int j = 0; j < 3; ++j) {
-    Fh[j] = a.from_acc ? acc[j] : pget(P, cap, PF_F + j, p);
-    Th[j] = a.from_acc ? acc[3 + j] : pget(P, cap, PF_T + j, p);
+    Fh[j] = a.from_acc ? (double)acc[j] * unit : pget(P, cap, PF_F + j, p);
+    Th[j] = a.from_acc ? (double)acc[3 + j] * unit : pget(P, cap, PF_T + j, p);
   }
   if (a.from_acc)
-    for (int j = 0; j < 6; ++j) acc[j] = 0.0;
+    for (int j = 0; j < 6; ++j) acc[j] = 0;
   if (!newton_euler(a, shape, im, V, rho, I, iI, Fh, Th, X, U, W, q)) atomicOr(a.status, ST_UNSTABLE);
   const int n[3] = {bd.nx, bd.ny, bd.nz};
   for (int j = 0; j < 3; ++j) {
