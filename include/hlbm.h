@@ -128,7 +128,8 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
  * radius beyond which B of Eq. B vanishes, plus 2 cells) spans half a
  * periodic axis or more.  The influence radius is r + eps/2 for spheres, the
  * circumscribed radius + eps/2 for cuboids and a_max (1 + eps / (2 a_min))
- * for ellipsoids.  The circumscribed radius may be at most 30 cells. */
+ * for ellipsoids, h + r + eps/2 for capsules.  The circumscribed radius may
+ * be at most 30 cells. */
 int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape,
                        const double* shape_params, const double* X, const double* U,
                        const double* omega, const double* quat, const double* rho_p);
@@ -137,8 +138,12 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
  * NULL to keep that field).  Arrays as in hlbm_add_particles.  The values are
  * checked and staged on the host, the upload is queued on the stream and the
  * call returns without waiting for it: the arrays may be reused at once.
- * HLBM_ERR_ARG (nothing changed) for a non-finite position or a zero or
- * non-finite quaternion. */
+ * A new position or orientation changes the cells inside the particles, so
+ * the next step takes the bounding-box momentum exchange; positions (and the
+ * orientations of non-spheres) that are not given, or that equal bit for bit
+ * the state hlbm_particle_state returned after the current step, keep the
+ * momentum exchange from the recorded moments.  HLBM_ERR_ARG (nothing
+ * changed) for a non-finite position or a zero or non-finite quaternion. */
 int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, const double* omega,
                             const double* quat);
 

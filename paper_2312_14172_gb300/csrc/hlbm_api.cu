@@ -167,6 +167,10 @@ struct hlbm_ctx {
   cudaGraphExec_t exec2[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool graphs_ok = false;
   bool moments_valid = false;  // the accumulator holds this state's momentum exchange
+  // hstage holds the device's particle rows X .. T as downloaded by
+  // hlbm_particle_state after step hst_steps (until an upload reuses it)
+  bool hst_valid = false;
+  long long hst_steps = -1;
   std::vector<int> h_shape, h_box;  // host copies
   std::string err;
 };
@@ -607,6 +611,7 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
   CK(cudaMemcpyAsync(h->d_shape + p0, sh.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->d_box + p0, bx.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
   h->np += n;
+  h->hst_valid = false;
   h->h_shape.insert(h->h_shape.end(), sh.begin(), sh.end());
   h->h_box.insert(h->h_box.end(), bx.begin(), bx.end());
   h->h_nchunk.insert(h->h_nchunk.end(), nch.begin(), nch.end());
@@ -651,11 +656,21 @@ int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, con
   // the staging rows may still feed the previous upload
   CK(cudaEventSynchronize(h->hstage_ev));
   double* S = h->hstage;  // row r holds component r of the state, n doubles
+  // The cells inside the particles (and so the list the last collision
+  // recorded) depend on positions and, for non-spheres, orientations only:
+  // when both come back as the state downloaded after this very step, bit
+  // for bit, the next step may still take the momentum exchange from the
+  // recorded moments.
+  const bool fresh = h->hst_valid && h->hst_steps == h->steps;
+  bool moved = false;
   if (X)
     for (int k = 0; k < n; ++k) {
       double x[3] = {X[3 * k], X[3 * k + 1], X[3 * k + 2]};
       wrap_host(h->boxes[h->h_box[k]], x);
-      for (int j = 0; j < 3; ++j) S[(size_t)(PF_X + j) * n + k] = x[j];
+      for (int j = 0; j < 3; ++j) {
+        moved = moved || !fresh || x[j] != S[(size_t)(PF_X + j) * n + k];
+        S[(size_t)(PF_X + j) * n + k] = x[j];
+      }
     }
   auto rows = [&](int fld, int ncomp, const double* src) {
     for (int j = 0; j < ncomp; ++j)
@@ -668,7 +683,11 @@ int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, con
       double nq = 0.0;
       for (int j = 0; j < 4; ++j) nq += quat[4 * k + j] * quat[4 * k + j];
       nq = std::sqrt(nq);
-      for (int j = 0; j < 4; ++j) S[(size_t)(PF_Q + j) * n + k] = quat[4 * k + j] / nq;
+      for (int j = 0; j < 4; ++j) {
+        const double v = quat[4 * k + j] / nq;
+        if (h->h_shape[k] != HLBM_SPHERE) moved = moved || !fresh || v != S[(size_t)(PF_Q + j) * n + k];
+        S[(size_t)(PF_Q + j) * n + k] = v;
+      }
     }
   // one strided copy per run of consecutive fields that were given
   const bool given[4] = {X != nullptr, U != nullptr, omega != nullptr, quat != nullptr};
@@ -684,7 +703,8 @@ int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, con
   }
   CK(cudaEventRecord(h->hstage_ev, h->stream));
   CK(launch_records(part_args(h, 0), h->stream));
-  h->moments_valid = false;
+  h->hst_valid = false;
+  if (moved) h->moments_valid = false;
   return HLBM_OK;
 }
 
@@ -728,6 +748,8 @@ int hlbm_particle_state(hlbm_handle h, double* X, double* U, double* omega, doub
                        sizeof(double) * n, PF_T + 3 - PF_X, cudaMemcpyDeviceToHost, h->stream));
   const int st = read_status(h);
   if (st == HLBM_ERR_CUDA) return st;
+  h->hst_valid = true;
+  h->hst_steps = h->steps;
   auto get = [&](int fld, int ncomp, double* dst) {
     if (!dst) return;
     for (int j = 0; j < ncomp; ++j)

@@ -310,6 +310,72 @@ def test_set_fluid_force_equals_the_force_given_at_creation(H, O):
 
 
 # ------------------------------------------------------------ batch
+@pytest.mark.parametrize("what", ["moved", "velocities"])
+def test_set_particle_state_then_steps_match_the_oracle(H, O, what):
+    """A state imposed between steps (hlbm_set_particle_state) on the GPU and
+    on the oracle, from the same populations, gives the same run: moved and
+    turned particles take the bounding-box momentum exchange on the new
+    interior cells; new velocities alone keep the recorded moments."""
+    from paper_2312_14172_gb300 import workloads
+    w = workloads.nonspherical(n=(62, 56, 60), count=12, steps=20,
+                               kinds=(workloads.CAPSULE, workloads.ELLIPSOID, workloads.CUBOID))
+    lat = H.from_workload(w)
+    lat.set_mea_mode("moments")
+    orc = O.from_workload(w)
+    lat.step(4)
+    s = lat.particle_state()
+    rng = np.random.default_rng(9)
+    n = np.array(w["n"], float)
+    U = rng.uniform(-1e-3, 1e-3, s["U"].shape)
+    Wv = rng.uniform(-2e-3, 2e-3, s["omega"].shape)
+    if what == "moved":
+        X = np.mod(s["X"] + rng.uniform(-0.4, 0.4, s["X"].shape), n)
+        # turned by about 0.1 rad: the clearance of the workload (eps + 1
+        # between enclosing capsules) keeps the particles apart
+        q = s["quat"] + 0.05 * rng.standard_normal(s["quat"].shape)
+        q /= np.linalg.norm(q, axis=1, keepdims=True)
+        lat.set_particle_state(X, U, Wv, q)
+        orc.set_particle_state(X, U, Wv, q)
+    else:
+        X, q = s["X"], s["quat"]
+        lat.set_particle_state(None, U, Wv, None)
+        orc.set_particle_state(X, U, Wv, q)
+    orc.set_populations(lat.populations())
+    X0, U0, W0 = lat.particle_state()["X"], U, Wv
+    lat.step(10)
+    orc.step(10)
+    sg, so = lat.particle_state(), orc.particle_state()
+    _pops_close(lat.populations(), orc.populations())
+    _motion_close(sg, so, X0, U0, W0)
+    assert np.allclose(sg["quat"], so["quat"], atol=1e-9)
+    lat.close()
+
+
+def test_unchanged_state_round_trip_keeps_the_run_bit_for_bit(H, O):
+    """Writing back the state just read (the end-to-end pattern) changes
+    nothing: the next step keeps the momentum exchange from the recorded
+    moments, and the run is the one without the round trip, bit for bit
+    (the orientation is normalised again on upload, to the last bit)."""
+    from paper_2312_14172_gb300 import workloads
+    w = workloads.hindered_settling(n=(70, 45, 48), count=14, steps=20)
+    a, b = H.from_workload(w), H.from_workload(w)
+    for lat in (a, b):
+        lat.set_mea_mode("moments")
+        lat.step(5)
+    for _ in range(4):
+        a.step(1)
+        s = b.particle_state()
+        b.set_particle_state(s["X"], s["U"], s["omega"], s["quat"])
+        b.step(1)
+    assert np.array_equal(a.populations(), b.populations())
+    sa, sb = a.particle_state(), b.particle_state()
+    for k in ("X", "U", "omega", "F", "T"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.allclose(sa["quat"], sb["quat"], rtol=0, atol=1e-15)
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 def test_reruns_are_bit_identical(H, O, precision):
     """Two runs of the same inputs agree bit for bit: the collision has no
