@@ -88,14 +88,24 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def _code_only(text):
+    """C++ source without its comments and blank lines (a comment does not
+    change the kernel)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def kernel_source_hash(cells_x=2):
-    """Hash of the sources that define the collision kernel with cells_x cells
-    per thread (a committed ncu figure holds only for the same source)."""
+    """Hash of the code (comments left out) that defines the collision kernel
+    with cells_x cells per thread (a committed ncu figure holds only for the
+    same code)."""
     h = hashlib.sha256()
     main = "lbm_pair_kernels.cu" if cells_x == 2 else "lbm_kernels.cu"
     for f in (main, "lbm_common.cuh", "hlbm_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2312_14172_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2312_14172_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -284,7 +284,8 @@ struct PartArgs {
   int nchunks;
   double* partial;          // [chunks][6] FP64 partial force/torque sums
   int* done;                // [cap] blocks finished per particle (reset to 0)
-  // the same sums accumulated by the previous collision, [cap][6]
+  // the same sums added up by the moments-mode momentum exchange from the
+  // moments the previous collision recorded
   long long* acc;           // [cap][6] momentum exchange, fixed point (ACC_FRAC_BITS)
   int from_acc;             // 1: the update takes acc, 0: the table's F and T
   int nsm;                  // SMs of the GPU (update grid size)
