@@ -26,7 +26,8 @@ gpu_launches, fp16 (the FP16-storage run and its error against FP32), and
 nonspherical: the 256^3 box of 2000 ellipsoids and cuboids with FP32 and FP16
 storage; batched_fp16: the large dense batch (512 x 512 x 1024 cells, 50 000 spheres)
 with FP32 and with FP16 storage, its collision roofline and the FP16 error;
-ensemble: 64 independent boxes of 64..96^3 advanced together, FP32.
+ensemble: 64 independent boxes of 64..96^3 advanced together, FP32 (its fp16
+entry: the same with FP16 storage).
 Opt-in legs: --capsules (the non-spherical box with 2000 capsules),
 --phi-matched, --settling-validation.
 
@@ -415,6 +416,8 @@ def run_gpu(args, ws, rank, local):
     nonsph = nonspherical_leg(args, stream, peak, ws) if args.nonspherical else None
     batched = batched_fp16_leg(args, stream, peak, ws) if args.batched else None
     ensemble = ensemble_leg(args, stream, peak, ws) if args.ensemble else None
+    if ensemble is not None and args.fp16:
+        ensemble["fp16"] = ensemble_leg(args, stream, peak, ws, "fp16")
     phi = phi_matched_leg(args, stream, peak, ws) if args.phi_matched else None
     settling = settling_validation_leg(args, stream) if args.settling_validation else None
     capsules = capsules_leg(args, stream, peak, ws) if args.capsules else None
@@ -454,17 +457,18 @@ def run_gpu(args, ws, rank, local):
     return line
 
 
-def ensemble_leg(args, stream, peak, ws):
+def ensemble_leg(args, stream, peak, ws, prec="fp32"):
     """The batched ensemble: 64 independent periodic boxes of 64..96^3 cells,
     10..200 spheres each, all advanced by one captured graph per step with
-    the autotuned launch shape, FP32 storage."""
+    the autotuned launch shape, FP32 or FP16 storage (2.4 GB / 1.2 GB of
+    populations)."""
     import torch
     from paper_2312_14172_gb300 import hlbm, workloads
     boxes = workloads.ensemble()
     cells = sum(b["n"][0] * b["n"][1] * b["n"][2] for b in boxes)
     npart = sum(len(b["particles"]["shape"]) for b in boxes)
     params = hlbm.make_params(tau=boxes[0]["tau"], eps=boxes[0]["eps"], gravity=boxes[0]["gravity"],
-                              max_particles=npart)
+                              max_particles=npart, precision=prec)
     lat = hlbm.Lattice([tuple(b["n"]) + (b["bc"],) for b in boxes], params, stream=stream)
     for k, b in enumerate(boxes):
         lat.add_workload_particles(b["particles"], box_id=[k] * len(b["particles"]["shape"]))
@@ -484,14 +488,14 @@ def ensemble_leg(args, stream, peak, ws):
     lat.sync()
     ms = max_over_ranks(e0.elapsed_time(e1))
     kt = lat.kernel_times(nsteps=10)
-    ach = BYTES_PER_CELL["fp32"] * cells / (kt["collide_stream"] / 1e3) / 1e9
+    ach = BYTES_PER_CELL[prec] * cells / (kt["collide_stream"] / 1e3) / 1e9
     out = {"value": whole_job_mlups(cells, steps, ms, ws), "unit": "MLUPS", "ms_per_step": ms / steps,
-           "steps": steps, "boxes": len(boxes), "cells": cells, "particles": npart,
+           "storage": prec, "steps": steps, "boxes": len(boxes), "cells": cells, "particles": npart,
            "launch": list(lat.get_launch()), "momentum_exchange": lat.get_mea_mode(), "kernel_ms": kt,
-           "l2": f"inputs larger than L2 ({BYTES_PER_CELL['fp32'] // 2 * cells / 1e6:.0f} MB of populations)",
+           "l2": f"inputs larger than L2 ({BYTES_PER_CELL[prec] // 2 * cells / 1e6:.0f} MB of populations)",
            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                         "kernel": "collide_pair_kernel" if lat.get_launch()[2] == 2 else "collide_stream_kernel"}}
-    out["coupling"], out["step_roofline"] = coupling_and_step_roofline(lat, cells, npart, steps, ms, ws, "fp32", peak)
+    out["coupling"], out["step_roofline"] = coupling_and_step_roofline(lat, cells, npart, steps, ms, ws, prec, peak)
     lat.close()
     return out
 
