@@ -91,3 +91,25 @@ def test_nonspherical_with_capsules_keeps_the_volume_and_the_gap():
             if np.linalg.norm(d) > r[i] + r[j] + h[i] + h[j] + w["eps"] + 1.0:
                 continue
             assert _segment_distance(X[i], ax[i], h[i], X[i] - d, ax[j], h[j]) >= r[i] + r[j] + w["eps"] + 1.0 - 0.05
+
+
+def test_workloads_are_seeded_and_in_the_box():
+    """The same call draws the same inputs (a fixed seed per workload), and
+    every centre lies in its box with its clearance to the walls."""
+    for make in (lambda: W.hindered_settling(n=(64, 48, 40), count=30, steps=1),
+                 lambda: W.nonspherical(n=(48, 48, 48), count=12, steps=1,
+                                        kinds=(W.CAPSULE, W.ELLIPSOID, W.CUBOID))):
+        a, b = make(), make()
+        for k in ("shape", "a", "X", "quat", "rho_p"):
+            assert np.array_equal(a["particles"][k], b["particles"][k]), k
+        n = np.array(a["n"], float)
+        X = a["particles"]["X"]
+        for ax in range(3):
+            if (a["bc"] >> ax) & 1:  # walls: centres strictly inside the fluid cells
+                assert np.all(X[:, ax] > -0.5) and np.all(X[:, ax] < n[ax] - 0.5)
+            else:                    # periodic: one image in [0, n)
+                assert np.all(X[:, ax] >= 0.0) and np.all(X[:, ax] < n[ax])
+        if a["bc"] & 4:
+            r = a["particles"]["a"][:, 0]
+            assert np.all(X[:, 2] - r >= a["eps"] + 1.0 - 0.5 - 1e-12)
+            assert np.all(n[2] - 1.0 - X[:, 2] - r >= a["eps"] + 1.0 - 0.5 - 1e-12)
