@@ -1114,7 +1114,9 @@ int hlbm_load(hlbm_handle h, const void* buf, size_t bytes) {
   for (int j = 0; j < 3; ++j) same = same && hd.gravity[j] == h->prm.gravity[j];
   if (!same) return fail(h, HLBM_ERR_ARG, "snapshot taken with another tau, eps or gravity");
   if (hd.np < 0 || hd.np > h->L.cap) return fail(h, HLBM_ERR_ARG, "snapshot holds more particles than max_particles");
-  if (hd.steps < 0 || (hd.mea_mode != HLBM_MEA_KERNEL && hd.mea_mode != HLBM_MEA_MOMENTS))
+  bool finite_force = true;
+  for (int j = 0; j < 3; ++j) finite_force = finite_force && std::isfinite(hd.fluid_force[j]);
+  if (hd.steps < 0 || (hd.mea_mode != HLBM_MEA_KERNEL && hd.mea_mode != HLBM_MEA_MOMENTS) || !finite_force)
     return fail(h, HLBM_ERR_ARG, "corrupt snapshot header");
   for (size_t b = 0; b < h->boxes.size(); ++b) {
     int64_t d[4];
