@@ -689,6 +689,9 @@ int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, con
         S[(size_t)(PF_Q + j) * n + k] = v;
       }
     }
+  // the staging rows now hold the upload, not the downloaded state
+  h->hst_valid = false;
+  if (moved) h->moments_valid = false;
   // one strided copy per run of consecutive fields that were given
   const bool given[4] = {X != nullptr, U != nullptr, omega != nullptr, quat != nullptr};
   const int row0[5] = {PF_X, PF_U, PF_W, PF_Q, PF_F};
@@ -703,8 +706,6 @@ int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, con
   }
   CK(cudaEventRecord(h->hstage_ev, h->stream));
   CK(launch_records(part_args(h, 0), h->stream));
-  h->hst_valid = false;
-  if (moved) h->moments_valid = false;
   return HLBM_OK;
 }
 
