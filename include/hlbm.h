@@ -278,11 +278,12 @@ int hlbm_load(hlbm_handle h, const void* buf, size_t bytes);
  * Every intermediate lives in one file-scope device array of about 3.3 MB
  * that every GPU loading the library holds until the process exits; the
  * call allocates nothing (no cudaMalloc, no library allocator).  The first
- * call on a device looks up that array's device address, so make it before
- * any stream capture.  All calls on a device share the array: calls whose
- * GPU work overlaps (other streams, other host threads) race; order them on
- * one stream.  The array keeps the last call's contents; the call clears
- * what must start at zero.
+ * call on a device (and the first in each new CUDA context on it, e.g.
+ * after cudaDeviceReset) looks up that array's device address, so make it
+ * before any stream capture.  All calls on a device share the array: calls
+ * whose GPU work overlaps (other streams, other host threads) race; order
+ * them on one stream.  The array keeps the last call's contents; the call
+ * clears what must start at zero.
  *
  *   f            device: 19 planes of `plane` elements, FP32 (f - w) or FP16
  *                (f - w) * 2^fp16_scale_log2, cell (x, y, z) of plane i at
@@ -292,9 +293,15 @@ int hlbm_load(hlbm_handle h, const void* buf, size_t bytes);
  *   n            particles, 0 <= n <= HLBM_NOALLOC_MAX_PARTICLES
  *   shape, shape_params, X, U, omega, quat   device arrays laid out as in
  *                hlbm_add_particles (U, omega, quat may be NULL)
- *   F, T         device outputs [3n]: hydrodynamic force and torque; NaN for
- *                a particle with invalid data (sizes, orientation, centre) or
- *                a circumscribed radius above 30 cells
+ *   F, T         device outputs [3n]: hydrodynamic force and torque.  A
+ *                particle is checked as hlbm_add_particles checks it and gets
+ *                NaN force and torque when its shape code is unknown, a size
+ *                is non-finite or <= 0, its quaternion is zero or non-finite,
+ *                a centre or velocity component is non-finite, its
+ *                circumscribed radius r_c exceeds 30 cells, its centre lies
+ *                outside (-1/2, n - 1/2) on a wall axis, or 2 (r_c + 2) >= n
+ *                on a periodic axis.  On a periodic axis any finite centre is
+ *                taken modulo n (the torque arm is the minimum image).
  *   cuda_stream  the stream all work is queued on; the call does not wait
  * Returns HLBM_OK, HLBM_ERR_ARG (n out of range, bad lattice arguments, NULL
  * pointer) or HLBM_ERR_CUDA. */

@@ -8,6 +8,8 @@
 // owns, with every intermediate held in one file-scope device array of fixed
 // size, declared below.  Every GPU that loads the library holds that array
 // until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "../../include/hlbm.h"
@@ -18,11 +20,13 @@ namespace {
 
 constexpr int NA_MAX = HLBM_NOALLOC_MAX_PARTICLES;
 
-// scratch layout (bytes): particle records, circumscribed radii, planes per
-// particle, finished-block counters, per-(particle, plane) FP64 partials
+// scratch layout (bytes): particle records, circumscribed radii, checked
+// centres (wrapped into the box on periodic axes), planes per particle,
+// finished-block counters, per-(particle, plane) FP64 partials
 constexpr size_t NA_REC = 0;
 constexpr size_t NA_RC = NA_REC + sizeof(Rec) * NA_MAX;
-constexpr size_t NA_NPL = NA_RC + sizeof(double) * NA_MAX;
+constexpr size_t NA_X = NA_RC + sizeof(double) * NA_MAX;
+constexpr size_t NA_NPL = NA_X + sizeof(double) * 3 * NA_MAX;
 constexpr size_t NA_DONE = NA_NPL + sizeof(int) * NA_MAX;
 constexpr size_t NA_PART = NA_DONE + sizeof(int) * NA_MAX;
 constexpr size_t NA_BYTES = NA_PART + sizeof(double) * 6 * MAX_PLANES * NA_MAX;
@@ -48,22 +52,33 @@ struct NoAllocArgs {
 
 __device__ __forceinline__ Rec* na_rec(const NoAllocArgs& a) { return reinterpret_cast<Rec*>(a.scratch + NA_REC); }
 __device__ __forceinline__ double* na_rc(const NoAllocArgs& a) { return reinterpret_cast<double*>(a.scratch + NA_RC); }
+__device__ __forceinline__ double* na_x(const NoAllocArgs& a) { return reinterpret_cast<double*>(a.scratch + NA_X); }
 __device__ __forceinline__ int* na_npl(const NoAllocArgs& a) { return reinterpret_cast<int*>(a.scratch + NA_NPL); }
 __device__ __forceinline__ int* na_done(const NoAllocArgs& a) { return reinterpret_cast<int*>(a.scratch + NA_DONE); }
 __device__ __forceinline__ double* na_part(const NoAllocArgs& a) { return reinterpret_cast<double*>(a.scratch + NA_PART); }
 
-// records of the caller's particles; clears the counters; a particle with
-// invalid data gets no planes and NaN force and torque
+// records of the caller's particles; clears the counters.  The checks are
+// those of hlbm_add_particles: a centre outside (-1/2, n - 1/2) on a wall
+// axis, or a particle whose circumscribed sphere plus two cells spans half a
+// periodic axis or more, is invalid, and so are non-finite or non-positive
+// sizes, a zero or non-finite quaternion and non-finite velocities.  On a
+// periodic axis the centre is wrapped into [0, n) and kept in the scratch
+// array, so that the exchange kernel walks a bounding box whose cells lie at
+// most one period outside the box.  An invalid particle gets no planes and
+// NaN force and torque.
 __global__ void noalloc_setup_kernel(NoAllocArgs a) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.n) return;
   const int shape = a.shape[p];
-  double s[3], X[3], q[4], nq = 0.0;
+  const int nn[3] = {a.bd.nx, a.bd.ny, a.bd.nz};
+  double s[3], X[3], U[3], W[3], q[4], nq = 0.0;
   bool ok = shape >= 0 && shape <= 3;
   for (int j = 0; j < 3; ++j) {
-    s[j] = a.params[3 * p + ((shape == 0 || (shape == 3 && j == 1)) ? 0 : j)];
+    s[j] = ok ? a.params[3 * p + ((shape == 0 || (shape == 3 && j == 1)) ? 0 : j)] : 1.0;
     X[j] = a.X[3 * p + j];
-    ok = ok && s[j] > 0.0 && isfinite(s[j]) && X[j] > -1.0e6 && X[j] < 1.0e6;
+    U[j] = a.U ? a.U[3 * p + j] : 0.0;
+    W[j] = a.W ? a.W[3 * p + j] : 0.0;
+    ok = ok && s[j] > 0.0 && isfinite(s[j]) && isfinite(X[j]) && isfinite(U[j]) && isfinite(W[j]);
   }
   for (int j = 0; j < 4; ++j) {
     q[j] = a.Q ? a.Q[4 * p + j] : (j == 0 ? 1.0 : 0.0);
@@ -75,6 +90,16 @@ __global__ void noalloc_setup_kernel(NoAllocArgs a) {
   if (shape == 2) rc = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
   if (shape == 3) rc = s[0] + s[2];
   ok = ok && rc <= 30.0;
+  for (int j = 0; j < 3 && ok; ++j) {
+    if ((a.bd.bc >> j) & 1) {
+      ok = X[j] > -0.5 && X[j] < nn[j] - 0.5;
+    } else {
+      const double L = (double)nn[j];
+      ok = 2.0 * (rc + 2.0) < L;
+      X[j] -= L * floor(X[j] / L);
+      if (X[j] >= L) X[j] -= L;
+    }
+  }
   na_done(a)[p] = 0;
   if (!ok) {
     na_npl(a)[p] = 0;
@@ -93,10 +118,11 @@ __global__ void noalloc_setup_kernel(NoAllocArgs a) {
     const float xh = __double2float_rn(X[j]);
     R.xh[j] = xh;
     R.xl[j] = __double2float_rn(X[j] - (double)xh);
-    R.u[j] = a.U ? (float)a.U[3 * p + j] : 0.0f;
-    R.w[j] = a.W ? (float)a.W[3 * p + j] : 0.0f;
+    R.u[j] = (float)U[j];
+    R.w[j] = (float)W[j];
     R.a[j] = __double2float_rn(s[j]);
     R.ia[j] = __double2float_rn(1.0 / s[j]);
+    na_x(a)[3 * p + j] = X[j];
   }
   for (int k = 0; k < 9; ++k) R.M[k] = __double2float_rn(M[k]);
   R.in2 = __double2float_rn(s[0] * s[0]);
@@ -125,8 +151,9 @@ __global__ void __launch_bounds__(128, 8) noalloc_mea_kernel(NoAllocArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid < 32) reinterpret_cast<int*>(&R)[tid] = reinterpret_cast<const int*>(&na_rec(a)[p])[tid];
   __syncthreads();
+  // the centre the set-up checked and wrapped, not the caller's array again
   double X[3];
-  for (int j = 0; j < 3; ++j) X[j] = a.X[3 * p + j];
+  for (int j = 0; j < 3; ++j) X[j] = na_x(a)[3 * p + j];
   float v[6];
   mea_plane_sums<S, PAR, false>(R, a.bd, X, na_rc(a)[p], iz, reinterpret_cast<const S*>(a.f), a.plane,
                          a.inv_scale, s_start, s_xa, v);
@@ -159,10 +186,46 @@ __global__ void __launch_bounds__(128, 8) noalloc_mea_kernel(NoAllocArgs a) {
   }
 }
 
-// device address of the scratch array, looked up once per device
+// Device address of the scratch array, looked up once per device and CUDA
+// context: the address belongs to the context that loaded the module, so a
+// new context on the device (after cudaDeviceReset, or a context the caller
+// made current) takes a fresh look-up.  The context's identity comes from
+// the driver's cuCtxGetCurrent / cuCtxGetId, reached through the runtime's
+// entry-point query (the library does not link the driver library itself);
+// where those are unavailable, or no context is current yet, the address is
+// looked up again on that call.
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mutex;
 unsigned char* g_na_ptr[NA_MAX_DEVICES] = {};
+unsigned long long g_na_ctx[NA_MAX_DEVICES] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// identity of the current context, or 0 when none is current or the driver
+// calls are unavailable (called with g_na_mutex held)
+unsigned long long current_context_id() {
+  static bool looked = false;
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!looked) {
+    looked = true;
+    void* f0 = nullptr;
+    void* f1 = nullptr;
+    cudaDriverEntryPointQueryResult q0 = cudaDriverEntryPointSymbolNotFound, q1 = q0;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q0 == cudaDriverEntryPointSuccess && q1 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+      get_id = reinterpret_cast<CtxGetIdFn>(f1);
+    }
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 }  // namespace
 }  // namespace hlbm
@@ -193,12 +256,17 @@ extern "C" int hlbm_mea_noalloc(const void* f, long long plane, int nx, int ny, 
   unsigned char* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_na_ptr[dev] || ctx == 0 || ctx != g_na_ctx[dev]) {
+      // set-up on this device and context (it is made current here if it
+      // was not): the device address of the file-scope scratch array
       void* ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+        g_na_ptr[dev] = nullptr;
         return HLBM_ERR_CUDA;
       }
       g_na_ptr[dev] = static_cast<unsigned char*>(ptr);
+      g_na_ctx[dev] = current_context_id();
     }
     scratch = g_na_ptr[dev];
   }

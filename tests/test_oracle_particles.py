@@ -120,6 +120,105 @@ def test_capsule_mass_and_inertia_against_integration(O):
     assert abs(m - rho * V) < 1e-12 * m
 
 
+def _grid_mass_properties(inside, R, rho, n=200):
+    """Mass and the three principal moments of a body given by a membership
+    test inside(x, y, z) (body frame, centred at the origin), by the
+    midpoint rule on an n^3 grid over the box [-R_j, R_j] (the body's
+    bounding box), summed slice by slice."""
+    h = 2.0 * np.asarray(R, float) / n
+    ax = [-R[j] + h[j] * (np.arange(n) + 0.5) for j in range(3)]
+    Xg, Yg = np.meshgrid(ax[0], ax[1], indexing="ij")
+    m = Ix = Iy = Iz = 0.0
+    for z in ax[2]:
+        ins = inside(Xg, Yg, z)
+        m += ins.sum()
+        Ix += ((Yg ** 2 + z * z) * ins).sum()
+        Iy += ((Xg ** 2 + z * z) * ins).sum()
+        Iz += ((Xg ** 2 + Yg ** 2) * ins).sum()
+    dV = rho * h.prod()
+    return m * dV, np.array([Ix, Iy, Iz]) * dV
+
+
+@pytest.mark.parametrize("shape,a", [(1, [1.3, 2.1, 5.2]), (1, [3.0, 3.0, 1.5]), (2, [1.0, 2.0, 3.0]),
+                                     (2, [2.5, 0.8, 1.7])])
+def test_ellipsoid_and_cuboid_mass_and_inertia_against_integration(O, shape, a):
+    """The mass and principal moments of inertia of the ellipsoid and the
+    cuboid (the Newton-Euler update of Sec. 2.2 divides by them), recovered
+    from one update under a known force and torque (dU = F / m and
+    d omega = T / I for a body at rest in the identity orientation), against
+    a midpoint-rule sum over a fine grid of the solid (0.5 %), and the volumes
+    against their closed forms 4/3 pi abc and 8 abc."""
+    rho = 1.7
+    o = O.Oracle((40, 40, 40), 0.8, 0.5, 0)
+    o.add_particles([shape], [a], [[20.0, 20.0, 20.0]], rho_p=[rho])
+    F, T = np.array([[1e-3, 0.0, 0.0]]), np.array([[2e-3, 3e-3, 5e-3]])
+    o.integrate_only(F, T)
+    s = o.particle_state()
+    m = F[0, 0] / s["U"][0, 0]
+    I = T[0] / s["omega"][0]
+    a = np.asarray(a, float)
+    if shape == 1:
+        inside = lambda x, y, z: (x / a[0]) ** 2 + (y / a[1]) ** 2 + (z / a[2]) ** 2 < 1.0
+        V = 4.0 / 3.0 * math.pi * a.prod()
+    else:
+        inside = lambda x, y, z: (np.abs(x) < a[0]) & (np.abs(y) < a[1]) & (abs(z) < a[2])
+        V = 8.0 * a.prod()
+    m_grid, I_grid = _grid_mass_properties(inside, a, rho)
+    assert abs(m / m_grid - 1) < 5e-3
+    assert np.all(np.abs(I / I_grid - 1) < 5e-3), (I, I_grid)
+    assert abs(m - rho * V) < 1e-12 * m
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_mea_at_a_wall_is_the_wall_pressure(O, axis):
+    """Eq. hlbm:mea next to a wall, on a fluid at rest (f = w): a link whose
+    far end lies beyond a bounce-back wall carries no fluid and is left out
+    (reading of Sec. 3.2 for walls), so an interior cell on the first plane
+    of a wall axis feels the pressure rho_f c_s^2 = 1/3 of the fluid on its
+    other side, pushing it into the wall; every other cell feels nothing,
+    whatever u_p.  F = 1/3 (n_upper - n_lower) e_axis and T = sum of the arms
+    times those forces, over the interior cells on the two wall planes (the
+    walls of one axis; the other two axes periodic)."""
+    n = [20, 22, 24]
+    bc = 1 << axis
+    rng = np.random.default_rng(40 + axis)
+    X = np.array([[9.6, 10.7, 11.8], [10.4, 11.2, 12.6]])
+    X[0, axis] = 3.3                 # sphere r = 4.6 crosses the lower wall plane
+    X[1, axis] = n[axis] - 1 - 1.4   # rotated cuboid crosses the upper one
+    q = rng.standard_normal(4)
+    q /= np.linalg.norm(q)
+    quat = np.array([[1.0, 0, 0, 0], q])
+    U = rng.uniform(-3e-2, 3e-2, (2, 3))
+    W = rng.uniform(-1e-2, 1e-2, (2, 3))
+    shapes, params = [0, 2], [[4.6] * 3, [2.5, 1.5, 3.0]]
+    o = O.Oracle(n, 0.8, 0.5, bc)
+    o.add_particles(shapes, params, X, U=U, omega=W, quat=quat, rho_p=[2.0, 2.0])
+    for p in range(2):
+        F, T, cnt = o.mea(p)
+        Fw, Tw = np.zeros(3), np.zeros(3)
+        walls = 0
+        for z in range(n[2]):
+            for y in range(n[1]):
+                for x in range(n[0]):
+                    cell = [x, y, z]
+                    if not O.inside_fp32(shapes[p], params[p], quat[p], X[p], cell, n, bc):
+                        continue
+                    if cell[axis] not in (0, n[axis] - 1):
+                        continue
+                    Fc = np.zeros(3)
+                    Fc[axis] = 1.0 / 3.0 if cell[axis] == n[axis] - 1 else -1.0 / 3.0
+                    r = np.array(cell, float) - X[p]
+                    for j in range(3):
+                        if j != axis:
+                            r[j] -= n[j] * round(r[j] / n[j])
+                    Fw += Fc
+                    Tw += np.cross(r, Fc)
+                    walls += 1
+        assert walls >= 6 and cnt > walls
+        assert np.allclose(F, Fw, rtol=0, atol=1e-14), (p, F, Fw)
+        assert np.allclose(T, Tw, rtol=0, atol=1e-13), (p, T, Tw)
+
+
 @pytest.mark.parametrize("shape,a", [(0, [4, 4, 4]), (1, [2, 2, 8]), (1, [1.3, 2.1, 5.2]),
                                      (2, [1.2, 1.2, 4.8]), (2, [1.0, 2.0, 3.0]), (3, [1.5, 1.5, 4.0])])
 @pytest.mark.parametrize("eps", [0.5, 1.5])
