@@ -187,9 +187,81 @@ class ClockSampler:
                     self.window[0] <= r[0] <= self.window[1] for r in rows))}
 
 
-def oracle_mlups(w, steps, warmup=0, omp=False):
+# D3Q19 velocities in the library's order (include/hlbm.h)
+C19 = np.array([[0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0],
+                [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1],
+                [0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1]], float)
+
+
+def _rel(got, ref, axis=None):
+    """max |got - ref| / max |ref| (vectors by their length when axis is
+    given) and the L2 relative error ||got - ref|| / ||ref||."""
+    d, r = np.asarray(got, float) - ref, np.asarray(ref, float)
+    if axis is not None:
+        d, r = np.linalg.norm(d, axis=axis), np.linalg.norm(r, axis=axis)
+    rmax, rl2 = float(np.abs(r).max()), float(np.sqrt((r * r).sum()))
+    return {"max": float(np.abs(d).max()) / rmax if rmax > 0 else float(np.abs(d).max()),
+            "l2": float(np.sqrt((d * d).sum())) / rl2 if rl2 > 0 else float(np.sqrt((d * d).sum()))}
+
+
+def state_errors(ref, got, n, bc, X0, coupling=None):
+    """Per-quantity error of a run `got` against a reference run `ref` after
+    the same steps, each a dict with populations f [19, nz, ny, nx] (FP64
+    values f_i) and the particle state of particle_state().  Returns for
+    each quantity {"max", "l2"} (see _rel):
+      rho    density, relative to rho itself;
+      p      density deviation rho - 1 (the pressure fluctuation over c_s^2),
+             relative to the reference's deviation;
+      u      fluid velocity sum_i c_i f_i / rho, relative to the largest speed;
+      u_out  the macroscopic velocity of the exact-difference forcing,
+             u + B (u_p - u) / 2 (when coupling = (B, pid) gives the
+             indicator field and its particle per cell; each run's own
+             particle state gives u_p(x) = U + omega x (x - X));
+      F, T   hydrodynamic force and torque per particle (vector lengths);
+      X      displacement X - X0 (minimum image on periodic axes);
+      U, omega  particle velocities.
+    Pure numpy: the callers supply both runs."""
+    L = np.asarray(n, float)
+    per = np.array([not (bc >> j) & 1 for j in range(3)])
+    out = {}
+    moments = {}
+    for key, run in (("ref", ref), ("got", got)):
+        f = run["f"]
+        rho = f.sum(0)
+        moments[key] = (rho, np.einsum("ai,izyx->azyx", C19, f) / rho)
+    (r_ref, u_ref), (r_got, u_got) = moments["ref"], moments["got"]
+    out["rho"] = _rel(r_got, r_ref)
+    out["p"] = _rel(r_got - 1.0, r_ref - 1.0)
+    out["u"] = _rel(u_got, u_ref, axis=0)
+    if coupling is not None:
+        B, pid = coupling
+        zz, yy, xx = np.nonzero(pid >= 0)
+        sh = {}
+        for key, run, u in (("ref", ref, u_ref), ("got", got, u_got)):
+            st = run["state"]
+            p = pid[zz, yy, xx]
+            r = np.stack([xx, yy, zz], 1) - st["X"][p]
+            r -= np.where(per, L * np.round(r / L), 0.0)
+            up = st["U"][p] + np.cross(st["omega"][p], r)
+            us = u.copy()
+            b = B[zz, yy, xx][:, None]
+            us[:, zz, yy, xx] = (u[:, zz, yy, xx].T + 0.5 * b * (up - u[:, zz, yy, xx].T)).T
+            sh[key] = us
+        out["u_out"] = _rel(sh["got"], sh["ref"], axis=0)
+    sr, sg = ref["state"], got["state"]
+    if len(sr["X"]):
+        for key in ("F", "T", "U", "omega"):
+            out[key] = _rel(sg[key], sr[key], axis=1)
+        dr, dg = sr["X"] - X0, sg["X"] - X0
+        dr -= np.where(per, L * np.round(dr / L), 0.0)
+        dg -= np.where(per, L * np.round(dg / L), 0.0)
+        out["X"] = _rel(dg, dr, axis=1)
+    return out
+
+
+def oracle_mlups(w, steps, warmup=0, omp=False, keep=False):
     """FP64 oracle on the workload (single thread, or its OpenMP build on all
-    host cores): MLUPS and seconds."""
+    host cores): MLUPS and seconds (and the oracle itself when keep)."""
     from oracle import oracle
     oracle.build(omp=omp)
     o = oracle.from_workload(w, omp=omp)
@@ -199,7 +271,28 @@ def oracle_mlups(w, steps, warmup=0, omp=False):
     o.step(steps)
     dt = time.perf_counter() - t0
     cells = w["n"][0] * w["n"][1] * w["n"][2]
+    if keep:
+        return cells * steps / dt / 1e6, dt, o
+    o.close()
     return cells * steps / dt / 1e6, dt
+
+
+def error_vs_fp64(w, o, steps):
+    """The full workload on the GPU with FP32 and with FP16 storage for the
+    same steps as the timed oracle o took from the same initial state: the
+    error of each quantity against that FP64 state (state_errors)."""
+    from paper_2312_14172_gb300 import hlbm
+    ref = {"f": o.populations(), "state": o.particle_state()}
+    coupling = o.indicator_field()
+    out = {"steps": steps, "mea_mode": "moments"}
+    for prec in ("fp32", "fp16"):
+        lat = hlbm.from_workload(w, precision=prec)
+        lat.set_mea_mode("moments")
+        lat.step(steps)
+        got = {"f": lat.populations(), "state": lat.particle_state()}
+        lat.close()
+        out[prec] = state_errors(ref, got, w["n"], w["bc"], w["particles"]["X"], coupling=coupling)
+    return out
 
 
 def init_dist():
@@ -738,6 +831,35 @@ def phi_matched_leg(args, stream, peak, ws):
     return {w["name"]: fp32_fp16_pair(w, args, stream, peak, ws) for w in ws_}
 
 
+def summary_of(line):
+    """Each leg's MLUPS, collision fraction of HBM and whole-step fraction of
+    the roofline MLUPS (without the momentum exchange's bytes), and the FP16
+    error against FP64, in one small object printed last on the line."""
+    def leg(d):
+        if not d:
+            return None
+        sr = d.get("step_roofline") or {}
+        return {"mlups": round(d["value"], 1), "collision_frac": round(d["roofline"]["frac"], 4),
+                "step_frac": round(sr["frac_of_mlups_roofline_without_mea"], 4) if sr else None}
+    out = {"headline": leg(line)}
+    out["headline"]["e2e_mlups"] = round(line["e2e"]["value"], 1) if line.get("e2e") else None
+    if line.get("fp16"):
+        out["headline_fp16"] = {"mlups": round(line["fp16"]["value"], 1),
+                                "collision_frac": round(line["fp16"]["roofline"]["frac"], 4)}
+    for key in ("nonspherical", "batched_fp16", "capsules", "phi_matched"):
+        d = line.get(key)
+        if d and "fp32" in d:
+            out[key] = {p: leg(d[p]) for p in ("fp32", "fp16")}
+            out[key]["fp16_over_fp32"] = round(d["speedup_fp16_over_fp32"], 3)
+    if line.get("ensemble"):
+        out["ensemble"] = {"fp32": leg(line["ensemble"]), "fp16": leg(line["ensemble"].get("fp16"))}
+    err = (line.get("cpu_baseline") or {}).get("error_vs_fp64")
+    if err:
+        out["error_vs_fp64_max"] = {p: {q: float(f"{v['max']:.3g}") for q, v in err[p].items()}
+                                    for p in ("fp32", "fp16")}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -780,11 +902,15 @@ def main():
             w = make_workload(args.workload)
             probe, dt1 = oracle_mlups(w, 1)
             steps = max(1, min(40, int(15.0 / max(dt1, 1e-3))))
-            mlups, dt = oracle_mlups(w, steps)
+            mlups, dt, o = oracle_mlups(w, steps, keep=True)
             line["cpu_baseline"] = {
                 "value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                 "sample": f"{steps} steps of the full {w['n'][0]}x{w['n'][1]}x{w['n'][2]} workload, "
                           f"FP64, single thread, {dt:.1f} s"}
+            # the GPU's FP32 and FP16 runs of the same steps against this
+            # FP64 state, per quantity
+            line["cpu_baseline"]["error_vs_fp64"] = error_vs_fp64(w, o, steps)
+            o.close()
             # the same oracle built with OpenMP: collision and streaming over z
             # slices, momentum exchange over particles, on every host core
             from oracle import oracle
@@ -796,6 +922,7 @@ def main():
                 "sample": f"{steps} steps of the same workload, FP64, OpenMP, {dt:.1f} s"}
         else:
             line["cpu_baseline"] = None
+        line["summary"] = summary_of(line)
         print(json.dumps(line), flush=True)
 
 

@@ -50,3 +50,44 @@ def test_solid_fraction_counts_every_shape():
     V = (4 / 3 * math.pi * 8 + 4 / 3 * math.pi * 6 + 8 * 6
          + math.pi * 1.5 ** 2 * 8 + 4 / 3 * math.pi * 1.5 ** 3)
     assert abs(bench.solid_fraction(P, 1000) - V / 1000) < 1e-12
+
+
+def test_state_errors_measures_each_quantity():
+    """The per-quantity error table of the FP16/FP32-against-FP64 entries:
+    a known perturbation of one quantity shows up in that quantity alone,
+    with the stated normalisations."""
+    rng = np.random.default_rng(3)
+    n = (6, 5, 4)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    f = w[:, None, None, None] * (1 + 1e-2 * rng.standard_normal((19, 4, 5, 6)))
+    st = {"X": np.array([[1.0, 2.0, 1.5], [5.5, 0.2, 2.0]]), "U": rng.standard_normal((2, 3)),
+          "omega": rng.standard_normal((2, 3)), "F": rng.standard_normal((2, 3)),
+          "T": rng.standard_normal((2, 3))}
+    X0 = st["X"] - np.array([[0.5, 0.0, 0.0], [0.0, -0.25, 0.0]])
+    ref = {"f": f, "state": st}
+    same = bench.state_errors(ref, {"f": f.copy(), "state": {k: v.copy() for k, v in st.items()}}, n, 4, X0)
+    assert all(v["max"] == 0 and v["l2"] == 0 for v in same.values())
+    g = {k: v.copy() for k, v in st.items()}
+    g["F"][1] += [0.0, 3e-3, 4e-3]  # |dF| = 5e-3 on one particle
+    g["X"][0, 0] += 0.5 - 6.0        # displacement 0.5 -> 1.0, seen through the periodic wrap
+    e = bench.state_errors(ref, {"f": f, "state": g}, n, 4, X0)
+    assert abs(e["F"]["max"] - 5e-3 / np.linalg.norm(st["F"], axis=1).max()) < 1e-12
+    assert abs(e["X"]["max"] - 0.5 / 0.5) < 1e-12
+    assert e["rho"]["max"] == 0 and e["T"]["max"] == 0 and e["U"]["l2"] == 0
+    # a uniform density change of 1e-6 relative
+    e = bench.state_errors(ref, {"f": f * (1 + 1e-6), "state": st}, n, 4, X0)
+    assert abs(e["rho"]["max"] - 1e-6) < 1e-12 and e["u"]["max"] < 1e-12
+    # the output velocity with the forcing shift: B = 1 at one cell owned by particle 0
+    B = np.zeros((4, 5, 6))
+    pid = -np.ones((4, 5, 6), int)
+    B[1, 2, 3], pid[1, 2, 3] = 1.0, 0
+    g = {k: v.copy() for k, v in st.items()}
+    g["U"][0] += [2e-3, 0, 0]
+    e = bench.state_errors(ref, {"f": f, "state": g}, n, 4, X0, coupling=(B, pid))
+    u = np.einsum("ai,izyx->azyx", bench.C19, f) / f.sum(0)
+    r = np.array([3.0, 2.0, 1.0]) - st["X"][0]
+    r[:2] -= np.array(n[:2]) * np.round(r[:2] / np.array(n[:2]))
+    up = st["U"][0] + np.cross(st["omega"][0], r)
+    us = u.copy()
+    us[:, 1, 2, 3] = u[:, 1, 2, 3] + 0.5 * (up - u[:, 1, 2, 3])
+    assert abs(e["u_out"]["max"] - 1e-3 / np.linalg.norm(us, axis=0).max()) < 1e-12

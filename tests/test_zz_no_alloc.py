@@ -222,10 +222,13 @@ def test_noalloc_wraps_centres_and_flags_invalid_particles(H):
                       [20.0, 18, 22], [20.0, 18, 20]])
     bad_q = np.tile([1.0, 0, 0, 0], (6, 1))
     bad_q[2] = 0.0  # zero quaternion
-    # 3: centre beyond the upper z wall (n - 1/2); 4: 2 (r + 2) >= nx; 5: unknown shape
+    bad_U = np.zeros((6, 3))
+    bad_U[0, 1] = np.nan  # non-finite velocity
+    # 1: negative size; 3: centre beyond the upper z wall (n - 1/2);
+    # 4: 2 (r + 2) >= nx; 5: unknown shape
     n = 4 + len(bad_shape)
     allp = (np.concatenate([shape, bad_shape]), np.concatenate([params, bad_params]),
-            np.concatenate([X, bad_X]), np.concatenate([U, np.zeros((6, 3))]),
+            np.concatenate([X, bad_X]), np.concatenate([U, bad_U]),
             np.concatenate([omega, np.zeros((6, 3))]), np.concatenate([quat, bad_q]))
 
     def flagged(F, T, call):
