@@ -154,6 +154,27 @@ int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, con
  * (nothing changed). */
 int hlbm_set_fluid_force(hlbm_handle h, const double f[3]);
 
+/* Contact between particles (an extension; the paper counts contact among
+ * the acting forces of Sec. 2.2 without stating a model, and its own runs
+ * have none, Sec. 3.2).  Each particle is enclosed by a capsule: a sphere and
+ * a capsule by themselves, an ellipsoid by the capsule along its longest
+ * semi-axis a_k with radius the larger other semi-axis r and half-length
+ * a_k - r, a cuboid by the capsule along its longest half-extent h_k with
+ * radius |(h_i, h_j)| and half-length h_k.  Two capsules of one box whose
+ * axis segments come closest at p_i, p_j (minimum image) with surface gap
+ * delta = |p_i - p_j| - r_i - r_j < zeta repel each other along p_i - p_j
+ * with the force k ((zeta - delta) / zeta)^2, particle i taking the torque
+ * (p_i - X_i) x F_i; a wall pushes the segment end nearest to it the same
+ * way (delta its distance to the wall minus r).  The forces enter the
+ * Newton-Euler update with the hydrodynamic force and the weight; the F and
+ * T that hlbm_particle_state reports stay the hydrodynamic ones.  k >= 0 in
+ * lattice force units (0, the default, switches contact off), zeta > 0
+ * cells; from the next step on (waits for the stream when they change).
+ * Each particle is tested against every other particle of the handle (one
+ * warp per particle): meant for boxes of up to a few thousand particles.
+ * HLBM_ERR_ARG for a negative or non-finite k or a zeta <= 0. */
+int hlbm_set_contact(hlbm_handle h, double k, double zeta);
+
 /* Queues nsteps >= 0 time steps (Algorithm 1: momentum exchange, external
  * force, Newton-Euler update, particle work lists, EDM coupling, collision
  * and streaming) on the stream and returns without waiting.  Errors found by
@@ -177,6 +198,13 @@ int hlbm_particle_state(hlbm_handle h, double* X, double* U, double* omega, doub
  * storage precision.  Both synchronise. */
 int hlbm_get_populations(hlbm_handle h, int box, double* host_f);
 int hlbm_set_populations(hlbm_handle h, int box, const double* host_f);
+
+/* Total mass deviation and momentum of box `box`, the moments of Sec. 3.1
+ * summed over its cells: out[0] = sum_x (rho(x) - 1), out[1..3] =
+ * sum_x sum_i c_i f_i(x), from the post-streaming populations as stored,
+ * summed in FP64 in a fixed order.  Synchronises.  HLBM_ERR_ARG for a bad
+ * box or a NULL out. */
+int hlbm_fluid_momentum(hlbm_handle h, int box, double out[4]);
 
 int hlbm_num_particles(hlbm_handle h);
 long long hlbm_steps_done(hlbm_handle h);
@@ -219,8 +247,8 @@ int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, int* cell
 
 /* Runs nsteps steps with each kernel launched on its own, bracketed by CUDA
  * events on the handle's stream, and writes the mean time per launch in ms:
- * ms[0] momentum exchange, ms[1] Newton-Euler and work lists, ms[2] collision
- * and streaming.  Synchronises. */
+ * ms[0] momentum exchange, ms[1] contact (when on), Newton-Euler and work
+ * lists, ms[2] collision and streaming.  Synchronises. */
 int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]);
 
 /* Writes to *n the number of (cell, particle) pairs whose cell centre lies
@@ -251,6 +279,8 @@ int hlbm_interior_cells(hlbm_handle h, long long* n);
  * `bytes` >= hlbm_checkpoint_bytes (pageable or pinned memory; the library
  * keeps no reference).  Synchronises.  HLBM_ERR_ARG for a NULL or too small
  * buffer.
+ *
+ * The contact parameters (hlbm_set_contact) travel with the snapshot.
  *
  * hlbm_load: restores a snapshot into a handle created with the same boxes,
  * precision, fp16 scale, tau, eps and gravity and max_particles at least the

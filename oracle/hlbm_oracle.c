@@ -244,6 +244,7 @@ struct oracle_sim {
   int np, cap;
   particle* p;
   long steps;
+  double contact_k, contact_zeta; /* contact stiffness and range (0: off) */
 };
 
 static double influence_radius(const particle* P, double eps);
@@ -731,6 +732,155 @@ void oracle_integrate_only(oracle_sim* s, const double* F, const double* T) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Contact (an extension).  The paper lists contact treatment among the forces
+ * on a particle (Sec. 2.2) and points to a published contact model for convex
+ * shapes without stating it; its own runs have none (Sec. 3.2), and it names
+ * the missing contact as the cause of the deviations at high solid fraction
+ * (Sec. 5.3).  The reading used here is a short-range repulsion of the
+ * quadratic-ramp kind used in resolved particle simulations:
+ *   - every particle's contact body is a capsule enclosing it: the points
+ *     within r_c of the segment X +- h_c e (sphere: r_c = a, h_c = 0;
+ *     capsule: itself; ellipsoid: e along its longest semi-axis a_k,
+ *     r_c = the larger of the two others, h_c = a_k - r_c; cuboid: e along
+ *     its longest half-extent h_k, r_c = |(h_i, h_j)|, h_c = h_k);
+ *   - two capsules whose segments come closest at points p_i, p_j (minimum
+ *     image), with gap delta = |p_i - p_j| - r_i - r_j < zeta, push each
+ *     other apart along n = (p_i - p_j) / |p_i - p_j| with the force
+ *     k ((zeta - delta) / zeta)^2, applied at the contact surface, so that
+ *     particle i receives the torque (p_i - X_i) x F_i;
+ *   - a wall of axis a (at -1/2 or n_a - 1/2) pushes the capsule's nearest
+ *     segment end the same way, with delta its distance to the wall minus r_c.
+ * The forces of a pair are equal and opposite and act on one line. */
+static void contact_capsule(const particle* P, double e[3], double* h, double* r) {
+  double R[9];
+  oracle_rotation(P->q, R);
+  int k = 2;
+  if (P->shape == ORACLE_SPHERE) {
+    *h = 0.0;
+    *r = P->a[0];
+  } else if (P->shape == ORACLE_CAPSULE) {
+    *h = P->a[2];
+    *r = P->a[0];
+  } else {
+    k = 0;
+    if (P->a[1] > P->a[k]) k = 1;
+    if (P->a[2] > P->a[k]) k = 2;
+    int i = (k + 1) % 3, j = (k + 2) % 3;
+    if (P->shape == ORACLE_ELLIPSOID) {
+      *r = P->a[i] > P->a[j] ? P->a[i] : P->a[j];
+      *h = P->a[k] - *r;
+    } else {
+      *r = sqrt(P->a[i] * P->a[i] + P->a[j] * P->a[j]);
+      *h = P->a[k];
+    }
+  }
+  /* body axis k in world coordinates: column k of the rotation */
+  for (int a = 0; a < 3; ++a) e[a] = R[a * 3 + k];
+}
+
+static double clamp(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* parameters s, t of the closest points P + s u and Q + t v of two segments,
+ * |s| <= hu, |t| <= hv, u and v unit vectors, Qp the second segment's centre
+ * (the classic method: the
+ * closest points of the two lines, s clamped, t from s and clamped, s again
+ * from t and clamped) */
+static void segment_closest(const double P[3], const double u[3], double hu, const double Qp[3],
+                            const double v[3], double hv, double* s, double* t) {
+  double w[3], b = 0.0, d = 0.0, f = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    w[a] = P[a] - Qp[a];
+    b += u[a] * v[a];
+    d += u[a] * w[a];
+    f += v[a] * w[a];
+  }
+  double den = 1.0 - b * b;
+  double ss = den > 1e-12 ? clamp((b * f - d) / den, -hu, hu) : 0.0;
+  double tt = clamp(b * ss + f, -hv, hv);
+  ss = clamp(b * tt - d, -hu, hu);
+  *s = ss;
+  *t = tt;
+}
+
+static double ramp_force(double k, double zeta, double gap) {
+  double x = (zeta - gap) / zeta;
+  return k * x * x;
+}
+
+int oracle_set_contact(oracle_sim* s, double k, double zeta) {
+  if (!(k >= 0.0) || !(zeta > 0.0)) return -1;
+  s->contact_k = k;
+  s->contact_zeta = zeta;
+  return 0;
+}
+
+void oracle_contact_forces(const oracle_sim* s, double* F, double* T) {
+  for (int p = 0; p < 3 * s->np; ++p) F[p] = T[p] = 0.0;
+  if (s->contact_k <= 0.0) return;
+  const double k = s->contact_k, zeta = s->contact_zeta;
+  for (int i = 0; i < s->np; ++i) {
+    const particle* Pi = &s->p[i];
+    double ei[3], hi, ri;
+    contact_capsule(Pi, ei, &hi, &ri);
+    /* walls */
+    for (int a = 0; a < 3; ++a) {
+      if (!is_wall(s, a)) continue;
+      for (int side = 0; side < 2; ++side) {
+        /* the segment end nearest to this wall */
+        double dir = side == 0 ? -1.0 : 1.0;
+        double t = ei[a] * dir > 0.0 ? hi : (ei[a] * dir < 0.0 ? -hi : 0.0);
+        double pt[3];
+        for (int c = 0; c < 3; ++c) pt[c] = Pi->X[c] + t * ei[c];
+        double gap = (side == 0 ? pt[a] + 0.5 : (s->n[a] - 0.5) - pt[a]) - ri;
+        if (gap >= zeta) continue;
+        double f[3] = {0.0, 0.0, 0.0}, arm[3], tq[3];
+        f[a] = -dir * ramp_force(k, zeta, gap);
+        for (int c = 0; c < 3; ++c) arm[c] = pt[c] - Pi->X[c];
+        cross(arm, f, tq);
+        for (int c = 0; c < 3; ++c) {
+          F[3 * i + c] += f[c];
+          T[3 * i + c] += tq[c];
+        }
+      }
+    }
+    /* pairs i < j */
+    for (int j = i + 1; j < s->np; ++j) {
+      const particle* Pj = &s->p[j];
+      double ej[3], hj, rj, Xj[3];
+      contact_capsule(Pj, ej, &hj, &rj);
+      for (int a = 0; a < 3; ++a) Xj[a] = Pi->X[a] + min_image(s, a, Pj->X[a] - Pi->X[a]);
+      double si, tj;
+      segment_closest(Pi->X, ei, hi, Xj, ej, hj, &si, &tj);
+      double pi_[3], pj_[3], dv[3], dist = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        pi_[a] = Pi->X[a] + si * ei[a];
+        pj_[a] = Xj[a] + tj * ej[a];
+        dv[a] = pi_[a] - pj_[a];
+        dist += dv[a] * dv[a];
+      }
+      dist = sqrt(dist);
+      double gap = dist - ri - rj;
+      if (gap >= zeta || !(dist > 0.0)) continue;
+      double fm = ramp_force(k, zeta, gap), f[3], ai[3], aj[3], ti[3], tj_[3], fn[3];
+      for (int a = 0; a < 3; ++a) {
+        f[a] = fm * dv[a] / dist;
+        fn[a] = -f[a];
+        ai[a] = pi_[a] - Pi->X[a];
+        aj[a] = pj_[a] - Xj[a];
+      }
+      cross(ai, f, ti);
+      cross(aj, fn, tj_);
+      for (int a = 0; a < 3; ++a) {
+        F[3 * i + a] += f[a];
+        T[3 * i + a] += ti[a];
+        F[3 * j + a] += fn[a];
+        T[3 * j + a] += tj_[a];
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* One time step in the order of Algorithm 1 (its communication rows have no
  * counterpart on one process). */
 void oracle_step(oracle_sim* s, int nsteps) {
@@ -742,14 +892,32 @@ void oracle_step(oracle_sim* s, int nsteps) {
     for (int p = 0; p < s->np; ++p) oracle_mea(s, p, s->p[p].F, s->p[p].T);
     /* apply external forces: weight minus buoyancy, (rho_p - rho_f) V g
      * (Sec. 5.1 prints (rho_f - rho_p) V g with "accelerated in z"; the
-     * reading is that heavier particles move along the gravity vector g) */
+     * reading is that heavier particles move along the gravity vector g),
+     * and the contact forces when switched on (an extension, see above),
+     * all taken at the state before this update */
+    double* Fc = NULL;
+    double* Tc = NULL;
+    if (s->contact_k > 0.0 && s->np > 0) {
+      Fc = (double*)malloc(sizeof(double) * 3 * s->np);
+      Tc = (double*)malloc(sizeof(double) * 3 * s->np);
+      oracle_contact_forces(s, Fc, Tc);
+    }
     for (int p = 0; p < s->np; ++p) {
       particle* P = &s->p[p];
-      double Ftot[3];
-      for (int a = 0; a < 3; ++a) Ftot[a] = P->F[a] + (P->rho - 1.0) * P->V * s->g[a];
+      double Ftot[3], Ttot[3];
+      for (int a = 0; a < 3; ++a) {
+        Ftot[a] = P->F[a] + (P->rho - 1.0) * P->V * s->g[a];
+        Ttot[a] = P->T[a];
+        if (Fc) {
+          Ftot[a] += Fc[3 * p + a];
+          Ttot[a] += Tc[3 * p + a];
+        }
+      }
       /* solve the equations of motion */
-      integrate_particle(s, P, Ftot, P->T);
+      integrate_particle(s, P, Ftot, Ttot);
     }
+    free(Fc);
+    free(Tc);
     /* couple particles to fluid (EDM), then collide and stream */
     oracle_indicator_field(s, s->B, s->pid);
     collide_into(s, s->B, s->pid, s->post);

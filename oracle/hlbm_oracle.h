@@ -108,6 +108,15 @@ void oracle_integrate_only(oracle_sim* s, const double* F, const double* T);
  * build, else 1 */
 int oracle_threads(void);
 
+/* --- contact (an extension: the paper refers to a contact model without
+ * stating one, Secs. 2.2 and 3.2; see hlbm_oracle.c) --- */
+/* stiffness k (force units) and range zeta (cells) of the repulsion between
+ * the enclosing capsules of two particles and between a capsule and a wall;
+ * k = 0 switches it off (the default).  Returns 0 or -1 (bad argument). */
+int oracle_set_contact(oracle_sim* s, double k, double zeta);
+/* contact force and torque on every particle at the current state */
+void oracle_contact_forces(const oracle_sim* s, double* F, double* T);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,8 @@ def lib(omp=False):
         L.oracle_rotation.argtypes = [_dp, _dp]
         L.oracle_inside_fp32.argtypes = [ctypes.c_int, _dp, _dp, _dp, _ip, _ip, ctypes.c_int]
         L.oracle_threads.restype = ctypes.c_int
+        L.oracle_set_contact.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+        L.oracle_contact_forces.argtypes = [ctypes.c_void_p, _dp, _dp]
         _libs[omp] = L
     return _libs[omp]
 
@@ -256,6 +258,18 @@ class Oracle:
     def stream_only(self, post):
         post, pp = _d(post)
         self._L.oracle_stream_only(self.h, pp)
+
+    def set_contact(self, k, zeta=1.0):
+        """Contact stiffness k (0: off) and range zeta of the repulsion
+        between the particles' enclosing capsules and with the walls."""
+        if self._L.oracle_set_contact(self.h, float(k), float(zeta)) != 0:
+            raise ValueError("oracle_set_contact: k must be >= 0 and zeta > 0")
+
+    def contact_forces(self):
+        n = self.num_particles
+        F, T = np.zeros((n, 3)), np.zeros((n, 3))
+        self._L.oracle_contact_forces(self.h, F.ctypes.data_as(_dp), T.ctypes.data_as(_dp))
+        return F, T
 
     def integrate_only(self, F, T):
         n = self.num_particles

@@ -4,7 +4,8 @@
 // One time step (Algorithm 1 of arXiv:2312.14172, Sec. 4.2.5, without its
 // communication rows) is three launches on the handle's stream:
 //   1. momentum exchange per particle          (mea_kernel)
-//   2. external force, Newton-Euler, records,
+//   2. contact forces, when switched on       (contact_kernel)
+//      external force, Newton-Euler, records,
 //      per-tile particle lists                 (update_kernel)
 //   3. EDM coupling, collision and streaming   (collide_stream_kernel)
 // Steps alternate between the two AA parities, so each parity is captured
@@ -155,6 +156,8 @@ struct hlbm_ctx {
   int* hstatus = nullptr;
   cudaEvent_t hstage_ev = nullptr;
   bool walls = false;
+  // contact stiffness and range (an extension; 0 = off)
+  double contact_k = 0.0, contact_zeta = 1.0;
   int np = 0;
   long long steps = 0;
   int sub_y = 4, sub_z = 2;
@@ -247,6 +250,8 @@ static PartArgs part_args(const hlbm_ctx* h, int parity) {
   a.done = h->done;
   a.acc = h->acc;
   a.from_acc = 0;
+  a.contact_k = h->contact_k;
+  a.contact_zeta = h->contact_zeta;
   a.nsm = h->nsm;
   a.ilist_count = h->ilist_count;
   a.bin_count = h->cnt[parity];
@@ -276,6 +281,7 @@ static cudaError_t enqueue_step(hlbm_ctx* h, int parity, bool moments, cudaStrea
     } else if ((e = launch_mea(pa, h->prm.precision, parity, s)) != cudaSuccess) {
       return e;
     }
+    if ((e = launch_contact(pa, s)) != cudaSuccess) return e;
     if ((e = launch_update(pa, s)) != cudaSuccess) return e;
   }
   return launch_collide(la, h->prm.precision, parity, h->walls, h->np > 0, s);
@@ -808,6 +814,26 @@ int hlbm_set_populations(hlbm_handle h, int box, const double* host_f) {
   return HLBM_OK;
 }
 
+int hlbm_fluid_momentum(hlbm_handle h, int box, double out[4]) {
+  if (!h) return HLBM_ERR_ARG;
+  if (box < 0 || box >= (int)h->boxes.size() || !out) return fail(h, HLBM_ERR_ARG, "bad box or NULL array");
+  const BoxDesc& bd = h->boxes[box];
+  const long long N = (long long)bd.nx * bd.ny * bd.nz;
+  // partial sums in the staging area (Q * stage_cells floats), four doubles per block
+  const long long room = (long long)Q * h->L.stage_cells / 8;
+  long long blocks = std::min<long long>(std::max(2 * h->nsm, 1), (N + 255) / 256);
+  blocks = std::max<long long>(1, std::min(blocks, room));
+  double* part = reinterpret_cast<double*>(h->stage);
+  CK(launch_fluid_moments(lbm_args(h, 0), h->prm.precision, (int)(h->steps & 1), box, (int)blocks, part, h->stream));
+  std::vector<double> hp(4 * (size_t)blocks);
+  CK(cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < 4; ++k) out[k] = 0.0;
+  for (long long b = 0; b < blocks; ++b)
+    for (int k = 0; k < 4; ++k) out[k] += hp[4 * b + k];
+  return HLBM_OK;
+}
+
 int hlbm_set_launch(hlbm_handle h, int tile_y, int tile_z, int cells_x) {
   if (!h) return HLBM_ERR_ARG;
   auto ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8; };
@@ -831,6 +857,19 @@ int hlbm_set_fluid_force(hlbm_handle h, const double f[3]) {
     CK(cudaStreamSynchronize(h->stream));
     for (int j = 0; j < 3; ++j) h->prm.fluid_force[j] = f[j];
     drop_graphs(h);  // the captured steps hold the force by value
+  }
+  return HLBM_OK;
+}
+
+int hlbm_set_contact(hlbm_handle h, double k, double zeta) {
+  if (!h) return HLBM_ERR_ARG;
+  if (!(k >= 0.0) || !std::isfinite(k) || !(zeta > 0.0) || !std::isfinite(zeta))
+    return fail(h, HLBM_ERR_ARG, "contact stiffness must be finite and >= 0, its range finite and > 0");
+  if (k != h->contact_k || zeta != h->contact_zeta) {
+    CK(cudaStreamSynchronize(h->stream));
+    h->contact_k = k;
+    h->contact_zeta = zeta;
+    drop_graphs(h);  // the captured steps hold the parameters by value
   }
   return HLBM_OK;
 }
@@ -943,6 +982,7 @@ int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]) {
     if (h->np > 0 && !fused) launch_mea(pa, h->prm.precision, parity, h->stream);
     if (h->np > 0 && fused) launch_mea_moments(lbm_args(h, parity), h->prm.precision, parity, h->walls, h->nsm, h->stream);
     cudaEventRecord(ev[1], h->stream);
+    if (h->np > 0) launch_contact(pa, h->stream);
     if (h->np > 0) launch_update(pa, h->stream);
     cudaEventRecord(ev[2], h->stream);
     launch_collide(lbm_args(h, parity), h->prm.precision, parity, h->walls, h->np > 0, h->stream);
@@ -988,12 +1028,12 @@ int hlbm_interior_cells(hlbm_handle h, long long* n) {
 // as stored (the handle's own block layout and precision).
 namespace {
 
-constexpr char CK_MAGIC[8] = {'H', 'L', 'B', 'M', 'C', 'K', 'P', '1'};
+constexpr char CK_MAGIC[8] = {'H', 'L', 'B', 'M', 'C', 'K', 'P', '2'};
 
 struct CkHeader {
   char magic[8];
   int64_t nboxes, precision, fp16_scale_log2, np, pf_count, steps, mea_mode, has_list, pop_bytes;
-  double tau, eps, gravity[3], fluid_force[3];
+  double tau, eps, gravity[3], fluid_force[3], contact_k, contact_zeta;
 };
 
 size_t pop_bytes(const hlbm_ctx* h) {
@@ -1058,6 +1098,8 @@ int hlbm_save(hlbm_handle h, void* buf, size_t bytes) {
   hd.pop_bytes = (int64_t)pop_bytes(h);
   hd.tau = h->prm.tau;
   hd.eps = h->prm.eps;
+  hd.contact_k = h->contact_k;
+  hd.contact_zeta = h->contact_zeta;
   for (int j = 0; j < 3; ++j) {
     hd.gravity[j] = h->prm.gravity[j];
     hd.fluid_force[j] = h->prm.fluid_force[j];
@@ -1117,7 +1159,9 @@ int hlbm_load(hlbm_handle h, const void* buf, size_t bytes) {
   if (hd.np < 0 || hd.np > h->L.cap) return fail(h, HLBM_ERR_ARG, "snapshot holds more particles than max_particles");
   bool finite_force = true;
   for (int j = 0; j < 3; ++j) finite_force = finite_force && std::isfinite(hd.fluid_force[j]);
-  if (hd.steps < 0 || (hd.mea_mode != HLBM_MEA_KERNEL && hd.mea_mode != HLBM_MEA_MOMENTS) || !finite_force)
+  if (hd.steps < 0 || (hd.mea_mode != HLBM_MEA_KERNEL && hd.mea_mode != HLBM_MEA_MOMENTS) || !finite_force ||
+      !(hd.contact_k >= 0.0) || !std::isfinite(hd.contact_k) || !(hd.contact_zeta > 0.0) ||
+      !std::isfinite(hd.contact_zeta))
     return fail(h, HLBM_ERR_ARG, "corrupt snapshot header");
   for (size_t b = 0; b < h->boxes.size(); ++b) {
     int64_t d[4];
@@ -1185,6 +1229,8 @@ int hlbm_load(hlbm_handle h, const void* buf, size_t bytes) {
   CK(cudaMemcpyAsync(h->f, pops, pop_bytes(h), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   for (int j = 0; j < 3; ++j) h->prm.fluid_force[j] = hd.fluid_force[j];
+  h->contact_k = hd.contact_k;
+  h->contact_zeta = hd.contact_zeta;
   // the saver's momentum-exchange mode, where this handle can hold its list
   if (hd.mea_mode == HLBM_MEA_KERNEL || h->ilist_idx) h->mea_mode = (int)hd.mea_mode;
   h->steps = hd.steps;

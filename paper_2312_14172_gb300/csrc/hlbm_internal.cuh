@@ -71,12 +71,14 @@ __host__ __device__ __forceinline__ long long elem_of(const BoxDesc& bd, int x, 
 }
 
 // FP64 particle table fields (each an array of `cap` doubles).  PF_IM and
-// PF_II hold 1/m and 1/I, PF_IA holds fp32(1/a_j) (exact in a double).
+// PF_II hold 1/m and 1/I, PF_IA holds fp32(1/a_j) (exact in a double);
+// PF_FC and PF_TC the contact force and torque of the step (when contact is
+// on).
 enum {
   PF_X = 0, PF_U = 3, PF_W = 6, PF_Q = 9, PF_F = 13, PF_T = 16,
   PF_M = 19, PF_V = 20, PF_I = 21, PF_RHO = 24, PF_A = 25, PF_RC = 28, PF_RINF = 29,
-  PF_IM = 30, PF_II = 31, PF_IA = 34,
-  PF_COUNT = 37
+  PF_IM = 30, PF_II = 31, PF_IA = 34, PF_FC = 37, PF_TC = 40,
+  PF_COUNT = 43
 };
 
 // the momentum-exchange kernel gives every z-plane of a particle's bounding
@@ -288,6 +290,9 @@ struct PartArgs {
   // moments the previous collision recorded
   long long* acc;           // [cap][6] momentum exchange, fixed point (ACC_FRAC_BITS)
   int from_acc;             // 1: the update takes acc, 0: the table's F and T
+  // contact between the particles' enclosing capsules and with the walls
+  // (an extension; off when contact_k == 0): stiffness and range
+  double contact_k, contact_zeta;
   int nsm;                  // SMs of the GPU (update grid size)
   int ppb;                  // particles per update block (set by the launcher)
   int* ilist_count;         // [ILIST_STRIPES], reset by the update for the next collision
@@ -375,6 +380,9 @@ cudaError_t launch_mea_moments(const LbmArgs& a, int precision, int parity, bool
                                cudaStream_t s);
 cudaError_t launch_mea(const PartArgs& a, int precision, int parity, cudaStream_t s);
 cudaError_t launch_update(const PartArgs& a, cudaStream_t s);
+// contact force and torque of every particle into PF_FC / PF_TC (only when
+// a.contact_k > 0)
+cudaError_t launch_contact(const PartArgs& a, cudaStream_t s);
 cudaError_t launch_records(const PartArgs& a, cudaStream_t s);
 // logical populations f_i - w_i of cells [c0, c0 + n) of one box, as float,
 // into/out of stage[i * n + k]
@@ -382,5 +390,9 @@ cudaError_t launch_gather(const LbmArgs& a, int precision, int parity, int box, 
                           long long n, float* stage, cudaStream_t s);
 cudaError_t launch_scatter(const LbmArgs& a, int precision, int parity, int box, long long c0,
                            long long n, const float* stage, cudaStream_t s);
+// FP64 mass deviation and momentum of one box: `blocks` partial sums of 4
+// values into out[4 * blocks]
+cudaError_t launch_fluid_moments(const LbmArgs& a, int precision, int parity, int box, int blocks,
+                                 double* out, cudaStream_t s);
 
 }  // namespace hlbm

@@ -415,6 +415,64 @@ __global__ void gather_scatter_kernel(LbmArgs a, int box, long long c0, long lon
   }
 }
 
+// mass deviation and momentum of one box, sum over its cells of the logical
+// f_i - w_i and c_i (f_i - w_i) (Sec. 3.1 moments; the weights carry no net
+// momentum), in FP64: each block writes its four sums (added in a fixed
+// order over its threads) to out[4 * blockIdx.x]
+template <typename S, int PAR>
+__global__ void __launch_bounds__(256) fluid_moments_kernel(LbmArgs a, int box, double* out) {
+  const BoxDesc bd = a.boxes[box];
+  const long long n = (long long)bd.nx * bd.ny * bd.nz;
+  const S* f = reinterpret_cast<const S*>(a.f);
+  double m[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long cl = blockIdx.x * (long long)blockDim.x + threadIdx.x; cl < n;
+       cl += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(cl % bd.nx);
+    const long long t = cl / bd.nx;
+    const int y = (int)(t % bd.ny);
+    const int z = (int)(t / bd.ny);
+    const NbrB nb = make_nbr_blocked(bd, x, y, z);
+    const long long e = elem_of(bd, x, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const S* slot;
+      if (PAR == 0 || i == 0) {
+        slot = f + e + i * VB;
+      } else {
+        const long long src = nb.at(-cx(i), -cy(i), -cz(i));
+        slot = (src >= 0) ? f + src + opp(i) * VB : f + e + i * VB;
+      }
+      const double d = (double)Pop<S>::ld(slot, a.inv_scale);
+      m[0] += d;
+      if (cx(i)) m[1] += cx(i) * d;
+      if (cy(i)) m[2] += cy(i) * d;
+      if (cz(i)) m[3] += cz(i) * d;
+    }
+  }
+  __shared__ double sm[4][256];
+  for (int k = 0; k < 4; ++k) sm[k][threadIdx.x] = m[k];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int k = 0; k < 4; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) out[4 * blockIdx.x + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+cudaError_t launch_fluid_moments(const LbmArgs& a, int precision, int parity, int box, int blocks,
+                                 double* out, cudaStream_t s) {
+  if (blocks < 1) return cudaErrorInvalidValue;
+  if (precision == 0) {
+    if (parity == 0) fluid_moments_kernel<float, 0><<<blocks, 256, 0, s>>>(a, box, out);
+    else fluid_moments_kernel<float, 1><<<blocks, 256, 0, s>>>(a, box, out);
+  } else {
+    if (parity == 0) fluid_moments_kernel<__half, 0><<<blocks, 256, 0, s>>>(a, box, out);
+    else fluid_moments_kernel<__half, 1><<<blocks, 256, 0, s>>>(a, box, out);
+  }
+  return cudaGetLastError();
+}
+
 template <typename S, bool G>
 static cudaError_t launch_gs(const LbmArgs& a, int parity, int box, long long c0, long long n,
                              float* stage, cudaStream_t s) {

@@ -202,7 +202,7 @@ __device__ __forceinline__ bool newton_euler(const PartArgs& a, int shape, doubl
                                              const double Th[3], double X[3], double U[3], double W[3],
                                              double q[4]) {
   for (int j = 0; j < 3; ++j) {
-    const double F = Fh[j] + (rho - 1.0) * V * a.g[j];
+    const double F = Fh[j] + (rho - 1.0) * V * a.g[j];  // Fh: hydrodynamic (and contact) force
     U[j] += F * im;
     X[j] += U[j];
   }
@@ -285,6 +285,17 @@ __device__ __forceinline__ BinRange update_particle(const PartArgs& a, int p) {
   }
   if (a.from_acc)
     for (int j = 0; j < 6; ++j) acc[j] = 0;
+  // the table keeps the hydrodynamic force and torque; the contact force
+  // and torque join them as acting forces
+  for (int j = 0; j < 3; ++j) {
+    pset(a.P, cap, PF_F + j, p, Fh[j]);
+    pset(a.P, cap, PF_T + j, p, Th[j]);
+  }
+  if (a.contact_k > 0.0)
+    for (int j = 0; j < 3; ++j) {
+      Fh[j] += pget(P, cap, PF_FC + j, p);
+      Th[j] += pget(P, cap, PF_TC + j, p);
+    }
   if (!newton_euler(a, shape, im, V, rho, I, iI, Fh, Th, X, U, W, q)) atomicOr(a.status, ST_UNSTABLE);
   const int n[3] = {bd.nx, bd.ny, bd.nz};
   for (int j = 0; j < 3; ++j) {
@@ -301,8 +312,6 @@ __device__ __forceinline__ BinRange update_particle(const PartArgs& a, int p) {
     pset(a.P, cap, PF_X + j, p, X[j]);
     pset(a.P, cap, PF_U + j, p, U[j]);
     pset(a.P, cap, PF_W + j, p, W[j]);
-    pset(a.P, cap, PF_F + j, p, Fh[j]);
-    pset(a.P, cap, PF_T + j, p, Th[j]);
   }
   for (int j = 0; j < 4; ++j) pset(a.P, cap, PF_Q + j, p, q[j]);
   Rec R;
@@ -368,6 +377,185 @@ __global__ void __launch_bounds__(UPD_T) update_kernel(PartArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- contact
+// Contact between particles (an extension: the paper counts contact among
+// the acting forces of Sec. 2.2 without stating a model, and its runs have
+// none).  Each particle is enclosed by a capsule, the points within r_c of
+// the segment X +- h_c e: a sphere by itself (h_c = 0), a capsule by itself,
+// an ellipsoid by the capsule along its longest semi-axis a_k with r_c the
+// larger other semi-axis and h_c = a_k - r_c, a cuboid by the capsule along
+// its longest half-extent h_k with r_c = |(h_i, h_j)| and h_c = h_k.  Two
+// capsules whose segments come closest at p_i, p_j (minimum image) with gap
+// delta = |p_i - p_j| - r_i - r_j < zeta repel along n = (p_i - p_j) / |.|
+// with k ((zeta - delta) / zeta)^2, and particle i takes the torque
+// (p_i - X_i) x F_i; a wall pushes the segment end nearest to it the same
+// way.  All in FP64 from the particle table at the state before the update.
+
+// enclosing capsule of particle p: unit axis e, half-length h, radius r
+__device__ __forceinline__ void contact_capsule(const double* P, int cap, int p, int shape, double e[3],
+                                                double& h, double& r) {
+  double A[3], q[4];
+  for (int j = 0; j < 3; ++j) A[j] = pget(P, cap, PF_A + j, p);
+  for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
+  int k = 2;
+  if (shape == 0) {
+    h = 0.0;
+    r = A[0];
+  } else if (shape == 3) {
+    h = A[2];
+    r = A[0];
+  } else {
+    k = A[1] > A[0] ? 1 : 0;
+    if (A[2] > A[k]) k = 2;
+    const int i = (k + 1) % 3, j = (k + 2) % 3;
+    if (shape == 1) {
+      r = fmax(A[i], A[j]);
+      h = A[k] - r;
+    } else {
+      r = sqrt(A[i] * A[i] + A[j] * A[j]);
+      h = A[k];
+    }
+  }
+  if (shape == 0) {
+    e[0] = 0.0; e[1] = 0.0; e[2] = 1.0;
+    return;
+  }
+  double R[9];
+  rotation_rn(q, R);
+  for (int j = 0; j < 3; ++j) e[j] = R[j * 3 + k];
+}
+
+// FP32 bound on the reach of a particle's contact capsule from its centre
+__device__ __forceinline__ float contact_reach(const Rec& R) {
+  if (R.shape == 0) return R.a[0];
+  if (R.shape == 3) return R.a[0] + R.a[2];
+  const float amax = fmaxf(R.a[0], fmaxf(R.a[1], R.a[2]));
+  if (R.shape == 1) return amax;
+  return sqrtf(R.a[0] * R.a[0] + R.a[1] * R.a[1] + R.a[2] * R.a[2]) + amax;  // >= h_k + |(h_i, h_j)|
+}
+
+// closest points P + s u, Q + t v of two segments (|s| <= hu, |t| <= hv,
+// unit u, v): the points of closest approach of the two lines, s clamped,
+// t taken from s and clamped, s taken again from t and clamped
+__device__ __forceinline__ void segment_closest(const double P[3], const double u[3], double hu,
+                                                const double Q[3], const double v[3], double hv,
+                                                double& s, double& t) {
+  double b = 0.0, d = 0.0, f = 0.0;
+  for (int j = 0; j < 3; ++j) {
+    const double w = P[j] - Q[j];
+    b += u[j] * v[j];
+    d += u[j] * w;
+    f += v[j] * w;
+  }
+  const double den = 1.0 - b * b;
+  s = den > 1e-12 ? fmin(fmax((b * f - d) / den, -hu), hu) : 0.0;
+  t = fmin(fmax(b * s + f, -hv), hv);
+  s = fmin(fmax(b * t - d, -hu), hu);
+}
+
+__device__ __forceinline__ double contact_ramp(double k, double zeta, double gap) {
+  const double x = (zeta - gap) / zeta;
+  return k * x * x;
+}
+
+// one warp per particle: the lanes take the other particles of its box in
+// turn (an FP32 test of the centre distance against the capsules' reach
+// first), lane 0 the walls; the warp's FP64 sums are added in a fixed order
+__global__ void __launch_bounds__(256) contact_kernel(PartArgs a) {
+  pdl_trigger();
+  pdl_wait();
+  const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= a.np) return;  // whole warps
+  const double* P = a.P;
+  const int cap = a.cap;
+  const Rec& Ri = a.rec[i];
+  const int si = a.shape[i], box = a.box[i];
+  const BoxDesc bd = a.boxes[box];
+  const int n[3] = {bd.nx, bd.ny, bd.nz};
+  double Xi[3], ei[3], hi, ri;
+  for (int j = 0; j < 3; ++j) Xi[j] = pget(P, cap, PF_X + j, i);
+  contact_capsule(P, cap, i, si, ei, hi, ri);
+  const float reach_i = contact_reach(Ri);
+  const double k = a.contact_k, zeta = a.contact_zeta;
+  double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+  auto add = [&](const double pt[3], const double f[3]) {
+    const double arm[3] = {pt[0] - Xi[0], pt[1] - Xi[1], pt[2] - Xi[2]};
+    double tq[3];
+    cross3(arm, f, tq);
+    for (int c = 0; c < 3; ++c) {
+      F[c] += f[c];
+      T[c] += tq[c];
+    }
+  };
+  for (int j = lane; j < a.np; j += 32) {
+    if (j == i || a.box[j] != box) continue;
+    const Rec& Rj = a.rec[j];
+    float d2 = 0.0f;
+    for (int c = 0; c < 3; ++c) {
+      float dc = Rj.xh[c] - Ri.xh[c];
+      if (!((bd.bc >> c) & 1)) {
+        const float L = (float)n[c];
+        if (dc > 0.5f * L) dc -= L;
+        else if (dc < -0.5f * L) dc += L;
+      }
+      d2 += dc * dc;
+    }
+    const float lim = reach_i + contact_reach(Rj) + (float)zeta + 0.05f;
+    if (d2 >= lim * lim) continue;
+    double Xj[3], ej[3], hj, rj;
+    for (int c = 0; c < 3; ++c) {
+      double dc = pget(P, cap, PF_X + c, j) - Xi[c];
+      if (!((bd.bc >> c) & 1)) {
+        const double L = (double)n[c];
+        if (dc > L / 2.0) dc -= L;
+        else if (dc < -L / 2.0) dc += L;
+      }
+      Xj[c] = Xi[c] + dc;
+    }
+    contact_capsule(P, cap, j, a.shape[j], ej, hj, rj);
+    double s, t;
+    segment_closest(Xi, ei, hi, Xj, ej, hj, s, t);
+    double pi[3], dv[3], dist = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      pi[c] = Xi[c] + s * ei[c];
+      dv[c] = pi[c] - (Xj[c] + t * ej[c]);
+      dist += dv[c] * dv[c];
+    }
+    dist = sqrt(dist);
+    const double gap = dist - ri - rj;
+    if (gap >= zeta || !(dist > 0.0)) continue;
+    const double fm = contact_ramp(k, zeta, gap);
+    const double f[3] = {fm * dv[0] / dist, fm * dv[1] / dist, fm * dv[2] / dist};
+    add(pi, f);
+  }
+  if (lane == 0) {
+    for (int c = 0; c < 3; ++c) {
+      if (!((bd.bc >> c) & 1)) continue;
+      for (int side = 0; side < 2; ++side) {
+        const double dir = side == 0 ? -1.0 : 1.0;
+        const double t = ei[c] * dir > 0.0 ? hi : (ei[c] * dir < 0.0 ? -hi : 0.0);
+        const double pt[3] = {Xi[0] + t * ei[0], Xi[1] + t * ei[1], Xi[2] + t * ei[2]};
+        const double gap = (side == 0 ? pt[c] + 0.5 : (n[c] - 0.5) - pt[c]) - ri;
+        if (gap >= zeta) continue;
+        double f[3] = {0.0, 0.0, 0.0};
+        f[c] = -dir * contact_ramp(k, zeta, gap);
+        add(pt, f);
+      }
+    }
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int o = 16; o > 0; o >>= 1) {
+      F[c] += __shfl_xor_sync(0xffffffffu, F[c], o);
+      T[c] += __shfl_xor_sync(0xffffffffu, T[c], o);
+    }
+  if (lane == 0)
+    for (int c = 0; c < 3; ++c) {
+      pset(a.P, cap, PF_FC + c, i, F[c]);
+      pset(a.P, cap, PF_TC + c, i, T[c]);
+    }
+}
+
 __global__ void records_kernel(PartArgs a) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.np) return;
@@ -400,6 +588,12 @@ cudaError_t launch_update(const PartArgs& a_in, cudaStream_t s) {
   if (blocks > 65535) blocks = 65535;
   if (blocks < 1) blocks = 1;
   return launch_k(update_kernel, dim3((unsigned)blocks), dim3(UPD_T), 0, s, a.pdl != 0, a);
+}
+
+cudaError_t launch_contact(const PartArgs& a, cudaStream_t s) {
+  if (a.np <= 0 || !(a.contact_k > 0.0)) return cudaSuccess;
+  const long long threads = (long long)a.np * 32;
+  return launch_k(contact_kernel, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, s, a.pdl != 0, a);
 }
 
 cudaError_t launch_records(const PartArgs& a, cudaStream_t s) {

@@ -30,7 +30,7 @@ EXPORTS = ["hlbm_default_params", "hlbm_required_bytes", "hlbm_init_lattice", "h
            "hlbm_add_particles", "hlbm_set_particle_state", "hlbm_step", "hlbm_sync",
            "hlbm_particle_state", "hlbm_get_populations", "hlbm_set_populations",
            "hlbm_num_particles", "hlbm_steps_done", "hlbm_set_launch", "hlbm_get_launch",
-           "hlbm_set_fluid_force",
+           "hlbm_set_fluid_force", "hlbm_set_contact", "hlbm_fluid_momentum",
            "hlbm_set_mea_mode", "hlbm_get_mea_mode",
            "hlbm_autotune", "hlbm_kernel_times", "hlbm_interior_cells",
            "hlbm_checkpoint_bytes", "hlbm_save", "hlbm_load", "hlbm_last_error", "hlbm_destroy",
@@ -94,6 +94,8 @@ def load(path=LIB_PATH):
     L.hlbm_get_launch.argtypes = [_h, _ip, _ip, _ip]
     L.hlbm_set_mea_mode.argtypes = [_h, ctypes.c_int]
     L.hlbm_set_fluid_force.argtypes = [_h, _dp]
+    L.hlbm_set_contact.argtypes = [_h, ctypes.c_double, ctypes.c_double]
+    L.hlbm_fluid_momentum.argtypes = [_h, ctypes.c_int, _dp]
     L.hlbm_get_mea_mode.argtypes = [_h]
     L.hlbm_autotune.argtypes = [_h, ctypes.c_int, _ip, _ip, _ip, _fp]
     L.hlbm_kernel_times.argtypes = [_h, ctypes.c_int, _fp]
@@ -279,6 +281,17 @@ class Lattice:
         """Uniform body-force density on the fluid from the next step on."""
         f = np.ascontiguousarray(np.asarray(f, np.float64).reshape(3))
         _check(self.h, load().hlbm_set_fluid_force(self.h, f.ctypes.data_as(_dp)))
+
+    def set_contact(self, k, zeta=1.0):
+        """Contact stiffness k (0: off) and range zeta (cells) between the
+        particles' enclosing capsules and with the walls."""
+        _check(self.h, load().hlbm_set_contact(self.h, float(k), float(zeta)))
+
+    def fluid_momentum(self, box=0):
+        """(sum of rho - 1, total momentum [3]) of one box, summed on the GPU."""
+        out = np.zeros(4)
+        _check(self.h, load().hlbm_fluid_momentum(self.h, int(box), out.ctypes.data_as(_dp)))
+        return out[0], out[1:].copy()
 
     def set_mea_mode(self, mode):
         m = {"kernel": HLBM_MEA_KERNEL, "moments": HLBM_MEA_MOMENTS}.get(mode, mode)

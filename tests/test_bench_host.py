@@ -91,3 +91,25 @@ def test_state_errors_measures_each_quantity():
     us = u.copy()
     us[:, 1, 2, 3] = u[:, 1, 2, 3] + 0.5 * (up - u[:, 1, 2, 3])
     assert abs(e["u_out"]["max"] - 1e-3 / np.linalg.norm(us, axis=0).max()) < 1e-12
+
+
+def test_settling_correlations_of_the_paper():
+    """The three correlations of Sec. 5 as written there: all give 1 at
+    phi = 0; Richardson-Zaki's index is 4.65 below Re = 0.2, 4.35 Re^-0.03
+    up to 1, 4.45 Re^-0.1 up to 500 and 2.39 beyond; Garside-Al-Dibouni's
+    tends to 5.1 for small Re and to 2.7 for large; Barnea-Mizrahi does not
+    depend on Re."""
+    c0 = bench.settling_correlations(0.0, 5.0)
+    assert c0["richardson_zaki"] == 1.0 and c0["garside_al_dibouni"] == 1.0 and c0["barnea_mizrahi"] == 1.0
+    assert bench.settling_correlations(0.1, 0.1)["n_rz"] == 4.65
+    assert abs(bench.settling_correlations(0.1, 0.5)["n_rz"] - 4.35 * 0.5 ** -0.03) < 1e-15
+    assert abs(bench.settling_correlations(0.1, 30.0)["n_rz"] - 4.45 * 30.0 ** -0.1) < 1e-15
+    assert bench.settling_correlations(0.1, 600.0)["n_rz"] == 2.39
+    assert abs(bench.settling_correlations(0.1, 1e-9)["n_gad"] - 5.1) < 1e-6
+    assert abs(bench.settling_correlations(0.1, 1e9)["n_gad"] - 2.7) < 1e-6
+    phi = 0.2
+    bm = (1 - phi) / ((1 + phi ** (1 / 3)) * math.exp(5 * phi / (3 * (1 - phi))))
+    for re in (0.1, 10.0, 100.0):
+        c = bench.settling_correlations(phi, re)
+        assert abs(c["barnea_mizrahi"] - bm) < 1e-15
+        assert abs(c["richardson_zaki"] - (1 - phi) ** c["n_rz"]) < 1e-15

@@ -267,6 +267,120 @@ def test_capsules_subbox(H, O, mode):
     assert np.allclose(sg["quat"], so["quat"], atol=1e-9)
 
 
+def _contact_workload():
+    """Particles set in contact with each other and with the lower z wall:
+    spheres, a capsule, an ellipsoid and a cuboid, pairs closing in."""
+    from paper_2312_14172_gb300 import workloads
+    rng = np.random.default_rng(17)
+    shapes = [0, 0, 3, 1, 2, 0]
+    a = [[4.0] * 3, [3.5] * 3, [2.0, 2.0, 3.0], [2.2, 2.5, 4.5], [1.8, 2.2, 3.4], [3.0] * 3]
+    X = np.array([[14.0, 14.0, 10.0], [14.0 + 4.0 + 3.5 + 0.4, 14.3, 10.5],  # gap 0.4
+                  [34.0, 20.0, 9.0], [34.5, 20.0, 19.0],    # capsule 0.5 below the ellipsoid's capsule
+                  [12.0, 32.0, 0.0], [20.3, 32.0, 3.2]])   # cuboid and sphere near the wall
+    quat = workloads.random_quaternions(rng, len(shapes))
+    quat[[0, 1, 2, 3, 5]] = [1, 0, 0, 0]  # capsule and ellipsoid axes along z
+    # the rotated cuboid's enclosing capsule (radius |(1.8, 2.2)|, segment
+    # +-3.4 along its long axis e) 0.3 above the wall at z = -1/2
+    q = quat[4]
+    ez = 1 - 2 * (q[1] ** 2 + q[2] ** 2)  # z component of the body z axis
+    X[4, 2] = 3.4 * abs(ez) + math.hypot(1.8, 2.2) - 0.5 + 0.3
+    P = workloads._particles(shapes, a, X, 2.5, quat)
+    P["U"][0] = [2e-4, 0, 0]
+    P["U"][1] = [-2e-4, 0, 0]
+    P["U"][3] = [0, 0, -2e-4]
+    P["omega"][4] = [0, 2e-3, 0]
+    w = workloads._workload("contact", (46, 44, 40), workloads.WALL_Z, 0.7, 0.5, P, 60, "fp32")
+    return w
+
+
+@pytest.mark.parametrize("mode", ["kernel", "moments"])
+def test_contact_subbox(H, O, mode):
+    """The contact extension (hlbm_set_contact; repulsion between enclosing
+    capsules and with the walls) against the oracle's: pairs closing in,
+    a sphere resting near the wall, rotated non-spheres, gravity, 60 steps."""
+    w = _contact_workload()
+    k, zeta = 2e-3, 1.0
+    P = w["particles"]
+    lat = H.from_workload(w)
+    lat.set_mea_mode(mode)
+    lat.set_contact(k, zeta)
+    orc = O.from_workload(w)
+    orc.set_contact(k, zeta)
+    Fc0, _ = orc.contact_forces()
+    assert np.count_nonzero(np.abs(Fc0).sum(1)) >= 4  # contacts engaged from the start
+    for c in (1, 59):
+        lat.step(c)
+        orc.step(c)
+    sg, so = lat.particle_state(), orc.particle_state()
+    _pops_close(lat.populations(), orc.populations())
+    _motion_close(sg, so, P["X"], P["U"], P["omega"])
+    assert np.allclose(sg["quat"], so["quat"], atol=1e-9)
+    # without contact the same run ends elsewhere
+    lat2 = H.from_workload(w)
+    lat2.set_mea_mode(mode)
+    lat2.step(60)
+    s2 = lat2.particle_state()
+    lat2.close()
+    lat.close()
+    dX = so["X"] - P["X"]
+    assert np.max(np.abs(s2["X"] - sg["X"])) > 0.05 * np.abs(dX).max()
+
+
+def test_contact_arguments_and_snapshot(H):
+    """hlbm_set_contact refuses a negative or non-finite stiffness and a
+    range <= 0; the parameters travel with a snapshot (the restored run
+    continues bit for bit)."""
+    w = _contact_workload()
+    lat = H.from_workload(w)
+    for bad in ((-1.0, 1.0), (float("nan"), 1.0), (1e-3, 0.0), (1e-3, float("inf"))):
+        with pytest.raises(H.HLBMError):
+            lat.set_contact(*bad)
+    lat.set_contact(2e-3, 1.0)
+    lat.step(5)
+    snap = lat.save()
+    lat.step(7)
+    ref = lat.particle_state()
+    P = w["particles"]
+    lat2 = H.Lattice([tuple(w["n"]) + (w["bc"],)],
+                     H.make_params(tau=w["tau"], eps=w["eps"], gravity=w["gravity"], max_particles=len(P["shape"])))
+    lat2.load_snapshot(snap)
+    lat2.step(7)
+    got = lat2.particle_state()
+    for key in ("X", "U", "omega", "quat", "F", "T"):
+        assert np.array_equal(got[key], ref[key]), key
+    lat.close()
+    lat2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_fluid_momentum_is_the_sum_of_the_moments(H, O, precision):
+    """hlbm_fluid_momentum: sum over the cells of rho - 1 and of the momentum
+    sum_i c_i f_i (Sec. 3.1), on the GPU, against the same sums of the
+    populations the handle returns, after even and odd step counts, with
+    walls and particles."""
+    from paper_2312_14172_gb300 import workloads
+    w = workloads.hindered_settling(n=(45, 38, 36), count=5, r_range=(3.0, 5.0), steps=10)
+    lat = H.from_workload(w, precision=precision)
+    lat.set_fluid_force((2e-6, -1e-6, 3e-6))
+    c = np.array(bench_C19())
+    for k in (3, 4):
+        lat.step(k)
+        f = lat.populations()
+        m, j = lat.fluid_momentum()
+        ref_m = (f.sum(0) - 1.0).sum()
+        ref_j = np.einsum("ai,izyx->a", c, f)
+        assert abs(m - ref_m) <= 1e-9, (m, ref_m)
+        assert np.allclose(j, ref_j, rtol=1e-6, atol=1e-9), (j, ref_j)
+        assert np.abs(ref_j).max() > 1e-4
+    lat.close()
+
+
+def bench_C19():
+    return [[0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0],
+            [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1],
+            [0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1]]
+
+
 def test_fp16_storage_error_is_small(H, O):
     from paper_2312_14172_gb300 import workloads
     w = workloads.single_sphere(n=40, radius=5.0, steps=100)

@@ -596,3 +596,128 @@ def test_zero_net_flow_counter_force_balances_the_weight(O):
         o.close()
     assert 1.0 <= ratios[False] < 1.25
     assert abs(ratios[True]) < 0.35
+
+
+# ------------------------------------------------ contact (an extension)
+def _contact_pair(O, shapes, params, X, quat=None, bc=0, n=(40, 40, 40), k=2e-3, zeta=1.5):
+    o = O.Oracle(n, 0.8, 0.5, bc)
+    o.add_particles(shapes, params, X, quat=quat, rho_p=[2.0] * len(shapes))
+    o.set_contact(k, zeta)
+    return o
+
+
+def test_contact_spheres_closed_form(O):
+    """Two spheres whose surfaces are delta apart (delta < zeta) push each
+    other apart along the line of centres with k ((zeta - delta) / zeta)^2,
+    equal and opposite, without torque; nothing at delta >= zeta; the
+    minimum image counts across a periodic face."""
+    k, zeta = 2e-3, 1.5
+    for delta, dx in ((0.4, 1.0), (-0.3, -1.0), (1.2, 1.0)):
+        r1, r2 = 4.0, 3.0
+        X = np.array([[20.0, 20.0, 20.0], [20.0 + dx * (r1 + r2 + delta), 20.0, 20.0]])
+        o = _contact_pair(O, [0, 0], [[r1] * 3, [r2] * 3], X, k=k, zeta=zeta)
+        F, T = o.contact_forces()
+        f = k * ((zeta - delta) / zeta) ** 2
+        assert np.allclose(F[0], [-dx * f, 0, 0], rtol=1e-13, atol=1e-18)
+        assert np.allclose(F[1], -F[0], rtol=0, atol=1e-18)
+        assert np.all(T == 0.0)
+    o = _contact_pair(O, [0, 0], [[4.0] * 3, [3.0] * 3], [[20, 20, 20], [20 + 7 + zeta, 20, 20]], k=k, zeta=zeta)
+    assert np.all(o.contact_forces()[0] == 0.0)
+    # across the periodic x face: centres at 1.0 and 32.5 of 40 cells, 8.5 apart
+    o = _contact_pair(O, [0, 0], [[4.0] * 3, [4.0] * 3], [[1.0, 20, 20], [32.5, 20, 20]], k=k, zeta=zeta)
+    F, _ = o.contact_forces()
+    assert np.allclose(F[0], [k * ((zeta - 0.5) / zeta) ** 2, 0, 0], rtol=1e-13)
+
+
+def test_contact_bodies_are_their_enclosing_capsules(O):
+    """The contact gap of a prolate ellipsoid (a, a, c) is measured from its
+    tips along the long axis (c) and from its side across it (a); of a
+    square cuboid (h, h, H) from the capsule of radius sqrt(2) h about its
+    axis segment +-H, which holds its corners: sqrt(2) h across and
+    H + sqrt(2) h along the axis (the capsule's cap reaches beyond the end
+    face); a capsule is itself."""
+    k, zeta, r = 1e-3, 2.0, 2.0
+    cases = [(1, [2.0, 2.0, 5.0], 2, 5.0), (1, [2.0, 2.0, 5.0], 0, 2.0),
+             (2, [1.5, 1.5, 4.0], 0, math.sqrt(2) * 1.5), (2, [1.5, 1.5, 4.0], 2, 4.0 + math.sqrt(2) * 1.5),
+             (3, [1.8, 1.8, 3.0], 2, 4.8), (3, [1.8, 1.8, 3.0], 1, 1.8)]
+    for shape, a, axis, reach in cases:
+        X = np.array([[20.0, 20.0, 20.0], [20.0, 20.0, 20.0]])
+        X[1, axis] += reach + r + 0.5  # gap 0.5 from the reach along this axis
+        o = _contact_pair(O, [shape, 0], [a, [r] * 3], X, k=k, zeta=zeta)
+        F, T = o.contact_forces()
+        f = k * ((zeta - 0.5) / zeta) ** 2
+        e = np.zeros(3)
+        e[axis] = 1.0
+        assert np.allclose(F[1], f * e, rtol=1e-12, atol=1e-18), (shape, axis, F)
+        assert np.allclose(F[0], -F[1], atol=1e-18)
+
+
+def test_contact_capsules_brute_force_and_balance(O):
+    """Random capsule pairs: the force has the magnitude the ramp gives for
+    the gap between their segments found by brute-force sampling, acts along
+    the line joining the closest points (equal and opposite forces, and the
+    torques about each centre balance the moment of the pair: the total
+    angular momentum change about the origin is zero)."""
+    rng = np.random.default_rng(7)
+    k, zeta = 1e-3, 1.5
+    done = 0
+    while done < 25:
+        q = rng.standard_normal((2, 4))
+        q /= np.linalg.norm(q, axis=1, keepdims=True)
+        h = rng.uniform(0.5, 4.0, 2)
+        rr = rng.uniform(1.0, 2.5, 2)
+        X = np.array([[20.0, 20.0, 20.0], 20.0 + rng.uniform(-6, 6, 3)])
+        segs = []
+        for p in range(2):
+            e = O.rotation(q[p])[:, 2]
+            t = np.linspace(-h[p], h[p], 801)
+            segs.append(X[p] + t[:, None] * e)
+        d = np.sqrt(((segs[0][:, None, :] - segs[1][None, :, :]) ** 2).sum(-1))
+        gap = d.min() - rr.sum()
+        if not (-0.8 < gap < zeta - 0.05):
+            continue
+        o = _contact_pair(O, [3, 3], [[rr[0], 0, h[0]], [rr[1], 0, h[1]]], X, quat=q, k=k, zeta=zeta)
+        F, T = o.contact_forces()
+        f = k * ((zeta - gap) / zeta) ** 2
+        assert abs(np.linalg.norm(F[0]) - f) <= 2 * k * 2e-2 / zeta, (gap, F)
+        assert np.allclose(F[0], -F[1], atol=1e-18)
+        L = np.cross(X[0], F[0]) + T[0] + np.cross(X[1], F[1]) + T[1]
+        assert np.all(np.abs(L) < 1e-15 * (1 + np.abs(X).max())), L
+        done += 1
+
+
+def test_contact_with_walls(O):
+    """A wall of a bounded axis pushes the nearest end of a capsule's segment:
+    a sphere at height z feels k ((zeta - (z + 1/2 - r)) / zeta)^2 upwards at
+    the lower wall; a tilted capsule near the upper wall is pushed down at
+    its upper segment end, with the torque of that lever."""
+    k, zeta = 1e-3, 1.0
+    n = (30, 30, 24)
+    o = _contact_pair(O, [0], [[3.0] * 3], [[15.0, 15.0, 3.1]], bc=4, n=n, k=k, zeta=zeta)
+    F, T = o.contact_forces()
+    assert np.allclose(F[0], [0, 0, k * ((zeta - (3.1 + 0.5 - 3.0)) / zeta) ** 2], rtol=1e-13)
+    assert np.all(T == 0)
+    th = 0.6  # capsule axis tilted in the x-z plane
+    q = [math.cos(th / 2), 0, math.sin(th / 2), 0]
+    h, r = 3.0, 1.5
+    e = np.array([math.sin(th), 0, math.cos(th)])
+    X = np.array([15.0, 15.0, n[2] - 0.5 - r - h * e[2] - 0.3])
+    o = _contact_pair(O, [3], [[r, 0, h]], [X], quat=[q], bc=4, n=n, k=k, zeta=zeta)
+    F, T = o.contact_forces()
+    f = k * ((zeta - 0.3) / zeta) ** 2
+    assert np.allclose(F[0], [0, 0, -f], rtol=1e-12)
+    assert np.allclose(T[0], np.cross(h * e, [0, 0, -f]), rtol=1e-12, atol=1e-20)
+
+
+def test_contact_force_enters_newton_euler(O):
+    """With the fluid at rest and no gravity, the first step's velocity of two
+    touching spheres is the contact force over the mass (Sec. 2.2 with the
+    contact force among the acting forces)."""
+    k, zeta = 5e-3, 1.0
+    o = _contact_pair(O, [0, 0], [[4.0] * 3, [3.0] * 3], [[20, 20, 20], [27.6, 20, 20]], k=k, zeta=zeta)
+    Fc, _ = o.contact_forces()
+    o.step(1)
+    s = o.particle_state()
+    m = 2.0 * 4 / 3 * math.pi * np.array([64.0, 27.0])
+    assert np.allclose(s["U"], Fc / m[:, None], rtol=1e-12, atol=1e-20)
+    assert abs(Fc[0, 0] + k * ((zeta - 0.6) / zeta) ** 2) < 1e-15
