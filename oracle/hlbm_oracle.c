@@ -154,6 +154,90 @@ void oracle_rotation(const double q[4], double R[9]) {
   R[8] = 1.0 - 2.0 * (x * x + y * y);
 }
 
+/* A signed-distance grid (shape ORACLE_GRID): FP32 samples of the signed
+ * distance on a regular body-frame grid, point (i, j, k) at
+ * ((i - (n0 - 1)/2) h, (j - (n1 - 1)/2) h, (k - (n2 - 1)/2) h), x fastest,
+ * with what the library derives from it at registration. */
+typedef struct {
+  int n[3];
+  double h;
+  float* v;
+  double V, I1[3]; /* volume and principal moments per unit density */
+  double rc;       /* radius of the cells holding any negative corner */
+  double rinf;     /* radius of the cells holding any corner below eps/2 */
+} grid_shape;
+
+/* Trilinear interpolation of a distance grid at the body-frame point r, in
+ * FP64; +infinity (no coupling) outside the grid's box.  The reading of a
+ * voxelised distance (the paper's outlook on arbitrary shapes, Sec. 6): the
+ * distance between samples is the trilinear blend of the eight corners of
+ * the grid cell that holds the point. */
+static double grid_value(const grid_shape* g, const double r[3]) {
+  double t[3];
+  int i0[3];
+  for (int j = 0; j < 3; ++j) {
+    double x = r[j] / g->h + 0.5 * (g->n[j] - 1);
+    if (!(x >= 0.0 && x <= (double)(g->n[j] - 1))) return INFINITY;
+    int i = (int)floor(x);
+    if (i > g->n[j] - 2) i = g->n[j] - 2;
+    i0[j] = i;
+    t[j] = x - i;
+  }
+  double c[2][2][2];
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx)
+        c[dz][dy][dx] = g->v[((long)(i0[2] + dz) * g->n[1] + (i0[1] + dy)) * g->n[0] + (i0[0] + dx)];
+  double e[2][2];
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy) e[dz][dy] = c[dz][dy][0] + t[0] * (c[dz][dy][1] - c[dz][dy][0]);
+  double f0 = e[0][0] + t[1] * (e[0][1] - e[0][0]);
+  double f1 = e[1][0] + t[1] * (e[1][1] - e[1][0]);
+  return f0 + t[2] * (f1 - f0);
+}
+
+/* The same blend in FP32, every operation rounded on its own in this order
+ * (the inside test of a grid particle; see oracle_inside_fp32):
+ *   x_j = b_j * fp32(1/h) + fp32((n_j - 1)/2); outside [0, n_j - 1]: not inside
+ *   i_j = min(floor(x_j), n_j - 2), t_j = x_j - i_j
+ *   lerp(a, b, t) = a + t * (b - a); along x (four), then y (two), then z */
+static float grid_value_fp32(const grid_shape* g, const float b[3]) {
+  float t[3];
+  int i0[3];
+  float ih = (float)(1.0 / g->h);
+  for (int j = 0; j < 3; ++j) {
+    float half = (float)(0.5 * (g->n[j] - 1));
+    float x = b[j] * ih;
+    x = x + half;
+    if (!(x >= 0.0f && x <= (float)(g->n[j] - 1))) return INFINITY;
+    int i = (int)floorf(x);
+    if (i > g->n[j] - 2) i = g->n[j] - 2;
+    i0[j] = i;
+    t[j] = x - (float)i;
+  }
+  float c[2][2][2];
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx)
+        c[dz][dy][dx] = g->v[((long)(i0[2] + dz) * g->n[1] + (i0[1] + dy)) * g->n[0] + (i0[0] + dx)];
+  float e[2][2];
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy) {
+      float d = c[dz][dy][1] - c[dz][dy][0];
+      d = t[0] * d;
+      e[dz][dy] = c[dz][dy][0] + d;
+    }
+  float d0 = e[0][1] - e[0][0];
+  d0 = t[1] * d0;
+  float f0 = e[0][0] + d0;
+  float d1 = e[1][1] - e[1][0];
+  d1 = t[1] * d1;
+  float f1 = e[1][0] + d1;
+  float d2 = f1 - f0;
+  d2 = t[2] * d2;
+  return f0 + d2;
+}
+
 /* "Cells whose centre is inside the particle" (Sec. 3.2, above Eq.
  * hydrodynamicforce).  Reading: strictly d_s < 0.  This yes/no decision is
  * taken in FP32, in the same precision and operation order as the GPU kernel,
@@ -223,10 +307,42 @@ int oracle_inside_fp32(int shape, const double a[3], const double q[4], const do
   return fabsf(b[0]) < (float)a[0] && fabsf(b[1]) < (float)a[1] && fabsf(b[2]) < (float)a[2];
 }
 
+/* The inside test of a grid particle: the FP32 offset r and body-frame
+ * offset b = M^T r exactly as in oracle_inside_fp32, then the FP32 blend of
+ * grid_value_fp32 strictly below zero. */
+static int inside_grid_fp32(const grid_shape* g, const double q[4], const double X[3], const int cell[3],
+                            const int n[3], int bc_flags) {
+  float r[3];
+  for (int j = 0; j < 3; ++j) {
+    float xh = (float)X[j];
+    float xl = (float)(X[j] - (double)xh);
+    float r0 = (float)cell[j] - xh;
+    if (!(bc_flags & (1 << j))) {
+      float L = (float)n[j];
+      float half = 0.5f * L;
+      if (r0 > half) r0 = r0 - L;
+      else if (r0 < -half) r0 = r0 + L;
+    }
+    r[j] = r0 - xl;
+  }
+  double Rd[9];
+  oracle_rotation(q, Rd);
+  float M[9], b[3];
+  for (int k = 0; k < 9; ++k) M[k] = (float)Rd[k];
+  for (int j = 0; j < 3; ++j) {
+    float t = M[0 * 3 + j] * r[0];
+    t = t + M[1 * 3 + j] * r[1];
+    t = t + M[2 * 3 + j] * r[2];
+    b[j] = t;
+  }
+  return grid_value_fp32(g, b) < 0.0f;
+}
+
 /* ------------------------------------------------------------------------ */
 typedef struct {
   int shape;
   double a[3];
+  const grid_shape* grid; /* ORACLE_GRID only */
   double X[3], U[3], W[3], q[4];
   double rho, V, m, I[3], rc;
   double F[3], T[3]; /* hydrodynamic force and torque of the last step */
@@ -245,6 +361,8 @@ struct oracle_sim {
   particle* p;
   long steps;
   double contact_k, contact_zeta; /* contact stiffness and range (0: off) */
+  int ngrid;
+  grid_shape* grids[ORACLE_MAX_GRIDS];
 };
 
 static double influence_radius(const particle* P, double eps);
@@ -316,16 +434,26 @@ void oracle_destroy(oracle_sim* s) {
   free(s->B);
   free(s->pid);
   free(s->p);
+  for (int g = 0; g < s->ngrid; ++g) {
+    free(s->grids[g]->v);
+    free(s->grids[g]);
+  }
   free(s);
 }
 
 long oracle_steps_done(const oracle_sim* s) { return s->steps; }
 int oracle_num_particles(const oracle_sim* s) { return s->np; }
 
-/* volume, mass and principal moments of inertia of the analytic shapes */
+/* volume, mass and principal moments of inertia of the analytic shapes and
+ * of registered grids */
 static void shape_mass_properties(particle* P) {
   const double* a = P->a;
-  if (P->shape == ORACLE_SPHERE) {
+  if (P->shape == ORACLE_GRID) {
+    P->V = P->grid->V;
+    P->m = P->rho * P->V;
+    for (int j = 0; j < 3; ++j) P->I[j] = P->rho * P->grid->I1[j];
+    P->rc = P->grid->rc;
+  } else if (P->shape == ORACLE_SPHERE) {
     P->V = 4.0 / 3.0 * PI * a[0] * a[0] * a[0];
     P->m = P->rho * P->V;
     for (int j = 0; j < 3; ++j) P->I[j] = 0.4 * P->m * a[0] * a[0];
@@ -387,10 +515,16 @@ int oracle_add_particles(oracle_sim* s, int n, const int* shape, const double* a
     particle P;
     memset(&P, 0, sizeof(P));
     P.shape = shape[k];
-    if (P.shape < 0 || P.shape > 3) return -1;
+    if (P.shape < 0 || P.shape > 4) return -1;
+    if (P.shape == ORACLE_GRID) {
+      double id = a[3 * k];
+      if (!(id >= 0.0 && id < s->ngrid && id == floor(id))) return -1;
+      P.grid = s->grids[(int)id];
+    }
     for (int j = 0; j < 3; ++j) {
-      P.a[j] = (P.shape == ORACLE_SPHERE || (P.shape == ORACLE_CAPSULE && j == 1)) ? a[3 * k] : a[3 * k + j];
-      if (!(P.a[j] > 0.0)) return -1;
+      P.a[j] = (P.shape == ORACLE_SPHERE || P.shape == ORACLE_GRID || (P.shape == ORACLE_CAPSULE && j == 1))
+                   ? a[3 * k] : a[3 * k + j];
+      if (!(P.a[j] > 0.0) && P.shape != ORACLE_GRID) return -1;
       P.X[j] = X[3 * k + j];
       P.U[j] = U ? U[3 * k + j] : 0.0;
       P.W[j] = omega ? omega[3 * k + j] : 0.0;
@@ -519,7 +653,9 @@ long oracle_mea(const oracle_sim* s, int p, double F[3], double T[3]) {
         int x[3];
         int k[3] = {kx, ky, kz};
         for (int a = 0; a < 3; ++a) x[a] = ((k[a] % s->n[a]) + s->n[a]) % s->n[a];
-        if (!oracle_inside_fp32(P->shape, P->a, P->q, P->X, x, s->n, s->bc)) continue;
+        if (P->shape == ORACLE_GRID ? !inside_grid_fp32(P->grid, P->q, P->X, x, s->n, s->bc)
+                                    : !oracle_inside_fp32(P->shape, P->a, P->q, P->X, x, s->n, s->bc))
+          continue;
         double r[3], wr[3], up[3], Fh[3], Fc[3], tc[3];
         for (int a = 0; a < 3; ++a) r[a] = min_image(s, a, (double)x[a] - P->X[a]);
         cross(P->W, r, wr);
@@ -547,6 +683,7 @@ long oracle_mea(const oracle_sim* s, int p, double F[3], double T[3]) {
  *   ellipsoid (algebraic distance):    d_s >= (k - 1) a_min and |r| <= k a_max
  *                                      give R_inf = a_max (1 + eps / (2 a_min)). */
 static double influence_radius(const particle* P, double eps) {
+  if (P->shape == ORACLE_GRID) return P->grid->rinf;
   if (P->shape == ORACLE_ELLIPSOID) {
     double amin = P->a[0], amax = P->a[0];
     for (int j = 1; j < 3; ++j) {
@@ -589,7 +726,8 @@ void oracle_indicator_field(const oracle_sim* s, double* B, int* pid) {
           if (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] >= rinf * rinf) continue;
           /* body-frame offset R^T r */
           for (int j = 0; j < 3; ++j) rb[j] = R[0 * 3 + j] * r[0] + R[1 * 3 + j] * r[1] + R[2 * 3 + j] * r[2];
-          double b = oracle_indicator(oracle_sdf_body(P->shape, P->a, rb), s->eps);
+          double d = P->shape == ORACLE_GRID ? grid_value(P->grid, rb) : oracle_sdf_body(P->shape, P->a, rb);
+          double b = oracle_indicator(d, s->eps);
           long c = cell_index(s, x[0], x[1], x[2]);
           if (b > B[c]) {
             B[c] = b;
@@ -732,6 +870,112 @@ void oracle_integrate_only(oracle_sim* s, const double* F, const double* T) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Signed-distance grids (the paper's outlook on shapes beyond spheres, Sec.
+ * 6, in the voxelised form).  Registration derives what the Newton-Euler
+ * update and the coupling need from the samples alone:
+ *   volume and second moments: midpoint rule over every grid cell split
+ *     into 4 x 4 x 4 sub-cells, a sub-cell counting when the FP64 blend at
+ *     its centre is negative;
+ *   rc: the largest |corner| of the grid cells with a negative corner (the
+ *     blend lies between the corner values, so the body is inside them);
+ *   rinf: the same for corners below eps/2 (B of Eq. B is zero elsewhere). */
+int oracle_add_grid(oracle_sim* s, int n0, int n1, int n2, double h, const float* values) {
+  if (s->ngrid >= ORACLE_MAX_GRIDS || n0 < 2 || n1 < 2 || n2 < 2 || !(h > 0.0) || !values) return -1;
+  const int n[3] = {n0, n1, n2};
+  long nv = (long)n0 * n1 * n2;
+  int neg = 0;
+  for (long k = 0; k < nv; ++k) {
+    if (!isfinite(values[k])) return -1;
+    if (values[k] < 0.0f) neg = 1;
+  }
+  if (!neg) return -1;
+  for (int k = 0; k < n2; ++k)
+    for (int j = 0; j < n1; ++j)
+      for (int i = 0; i < n0; ++i) {
+        int face = i == 0 || j == 0 || k == 0 || i == n0 - 1 || j == n1 - 1 || k == n2 - 1;
+        if (face && !((double)values[((long)k * n1 + j) * n0 + i] >= s->eps / 2.0)) return -1;
+      }
+  grid_shape* g = (grid_shape*)calloc(1, sizeof(grid_shape));
+  g->v = (float*)malloc(sizeof(float) * nv);
+  memcpy(g->v, values, sizeof(float) * nv);
+  for (int j = 0; j < 3; ++j) g->n[j] = n[j];
+  g->h = h;
+  /* radii from the cells' corners */
+  double rc = 0.0, rinf = 0.0;
+  for (int k = 0; k + 1 < n2; ++k)
+    for (int j = 0; j + 1 < n1; ++j)
+      for (int i = 0; i + 1 < n0; ++i) {
+        double vmin = INFINITY, cmax = 0.0;
+        for (int c = 0; c < 8; ++c) {
+          int ii = i + (c & 1), jj = j + ((c >> 1) & 1), kk = k + (c >> 2);
+          double v = values[((long)kk * n1 + jj) * n0 + ii];
+          if (v < vmin) vmin = v;
+          double x = (ii - 0.5 * (n0 - 1)) * h, y = (jj - 0.5 * (n1 - 1)) * h, z = (kk - 0.5 * (n2 - 1)) * h;
+          double d = sqrt(x * x + y * y + z * z);
+          if (d > cmax) cmax = d;
+        }
+        if (vmin < 0.0 && cmax > rc) rc = cmax;
+        if (vmin < s->eps / 2.0 && cmax > rinf) rinf = cmax;
+      }
+  g->rc = rc;
+  g->rinf = rinf;
+  /* volume, centroid and second moments over 4^3 sub-cells per cell */
+  const int sub = 4;
+  double V = 0.0, c1[3] = {0.0, 0.0, 0.0}, S[3][3] = {{0.0}};
+  const double dv = (h / sub) * (h / sub) * (h / sub);
+  for (int k = 0; k + 1 < n2; ++k)
+    for (int j = 0; j + 1 < n1; ++j)
+      for (int i = 0; i + 1 < n0; ++i)
+        for (int mz = 0; mz < sub; ++mz)
+          for (int my = 0; my < sub; ++my)
+            for (int mx = 0; mx < sub; ++mx) {
+              double r[3] = {(i + (mx + 0.5) / sub - 0.5 * (n0 - 1)) * h, (j + (my + 0.5) / sub - 0.5 * (n1 - 1)) * h,
+                             (k + (mz + 0.5) / sub - 0.5 * (n2 - 1)) * h};
+              if (!(grid_value(g, r) < 0.0)) continue;
+              V += dv;
+              for (int a = 0; a < 3; ++a) {
+                c1[a] += r[a] * dv;
+                for (int b = 0; b < 3; ++b) S[a][b] += r[a] * r[b] * dv;
+              }
+            }
+  g->V = V;
+  g->I1[0] = S[1][1] + S[2][2];
+  g->I1[1] = S[0][0] + S[2][2];
+  g->I1[2] = S[0][0] + S[1][1];
+  double imax = g->I1[0];
+  if (g->I1[1] > imax) imax = g->I1[1];
+  if (g->I1[2] > imax) imax = g->I1[2];
+  int ok = V > 0.0;
+  for (int a = 0; a < 3; ++a) ok = ok && fabs(c1[a] / V) <= h / 100.0;
+  ok = ok && fabs(S[0][1]) <= 1e-3 * imax && fabs(S[0][2]) <= 1e-3 * imax && fabs(S[1][2]) <= 1e-3 * imax;
+  if (!ok) {
+    free(g->v);
+    free(g);
+    return -2;
+  }
+  s->grids[s->ngrid] = g;
+  return s->ngrid++;
+}
+
+double oracle_grid_sdf(const oracle_sim* s, int grid, const double r_body[3]) {
+  if (grid < 0 || grid >= s->ngrid) return NAN;
+  return grid_value(s->grids[grid], r_body);
+}
+
+void oracle_grid_properties(const oracle_sim* s, int grid, double out[6]) {
+  const grid_shape* g = s->grids[grid];
+  out[0] = g->V;
+  for (int j = 0; j < 3; ++j) out[1 + j] = g->I1[j];
+  out[4] = g->rc;
+  out[5] = g->rinf;
+}
+
+int oracle_inside_grid_fp32(const oracle_sim* s, int grid, const double q[4], const double X[3],
+                            const int cell[3]) {
+  return inside_grid_fp32(s->grids[grid], q, X, cell, s->n, s->bc);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Contact (an extension).  The paper lists contact treatment among the forces
  * on a particle (Sec. 2.2) and points to a published contact model for convex
  * shapes without stating it; its own runs have none (Sec. 3.2), and it names
@@ -755,9 +999,9 @@ static void contact_capsule(const particle* P, double e[3], double* h, double* r
   double R[9];
   oracle_rotation(P->q, R);
   int k = 2;
-  if (P->shape == ORACLE_SPHERE) {
+  if (P->shape == ORACLE_SPHERE || P->shape == ORACLE_GRID) {
     *h = 0.0;
-    *r = P->a[0];
+    *r = P->shape == ORACLE_GRID ? P->rc : P->a[0];
   } else if (P->shape == ORACLE_CAPSULE) {
     *h = P->a[2];
     *r = P->a[0];

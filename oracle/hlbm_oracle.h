@@ -49,6 +49,8 @@ extern "C" {
 #define ORACLE_ELLIPSOID 1
 #define ORACLE_CUBOID 2
 #define ORACLE_CAPSULE 3 /* radius a[0], half-length a[2] of its axis segment (body z) */
+#define ORACLE_GRID 4    /* a registered signed-distance grid, its id in a[0] */
+#define ORACLE_MAX_GRIDS 64
 
 /* boundary flag bits: a set bit makes that axis bounded by two half-way
  * bounce-back walls; a clear bit makes it periodic. */
@@ -107,6 +109,25 @@ void oracle_integrate_only(oracle_sim* s, const double* F, const double* T);
 /* threads the loops of a step use: omp_get_max_threads() in the -fopenmp
  * build, else 1 */
 int oracle_threads(void);
+
+/* --- signed-distance grids (the paper's outlook on other shapes, Sec. 6) ---
+ * oracle_add_grid registers n0 x n1 x n2 FP32 samples of a signed distance
+ * (x fastest) with spacing h on a body-frame grid centred at the origin, the
+ * body's centre of mass, with its principal axes along the grid's.  Returns
+ * the grid id (>= 0), or -1 (bad sizes, a non-finite sample, no negative
+ * sample, or a boundary sample below eps/2: the indicator must vanish at the
+ * grid's faces), or -2 (centroid off the origin by more than h/100, or
+ * products of inertia above 1e-3 of the largest moment).  Particles of
+ * shape ORACLE_GRID name the id in their first size parameter. */
+int oracle_add_grid(oracle_sim* s, int n0, int n1, int n2, double h, const float* values);
+/* the grid's distance at a body-frame point (FP64 trilinear; +inf outside) */
+double oracle_grid_sdf(const oracle_sim* s, int grid, const double r_body[3]);
+/* volume and principal moments per unit density of a registered grid, and
+ * its circumscribed and influence radii (V, I0, I1, I2, rc, rinf) */
+void oracle_grid_properties(const oracle_sim* s, int grid, double out[6]);
+/* the FP32 inside test of a grid particle at a cell (as oracle_inside_fp32) */
+int oracle_inside_grid_fp32(const oracle_sim* s, int grid, const double q[4], const double X[3],
+                            const int cell[3]);
 
 /* --- contact (an extension: the paper refers to a contact model without
  * stating one, Secs. 2.2 and 3.2; see hlbm_oracle.c) --- */

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 # identical results), for timing only
 LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
 
-SPHERE, ELLIPSOID, CUBOID, CAPSULE = 0, 1, 2, 3
+SPHERE, ELLIPSOID, CUBOID, CAPSULE, GRID = 0, 1, 2, 3, 4
 WALL_X, WALL_Y, WALL_Z = 1, 2, 4
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -86,6 +86,12 @@ def lib(omp=False):
         L.oracle_inside_fp32.argtypes = [ctypes.c_int, _dp, _dp, _dp, _ip, _ip, ctypes.c_int]
         L.oracle_threads.restype = ctypes.c_int
         L.oracle_set_contact.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+        L.oracle_add_grid.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.POINTER(ctypes.c_float)]
+        L.oracle_grid_sdf.restype = ctypes.c_double
+        L.oracle_grid_sdf.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
+        L.oracle_grid_properties.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
+        L.oracle_inside_grid_fp32.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, _ip]
         L.oracle_contact_forces.argtypes = [ctypes.c_void_p, _dp, _dp]
         _libs[omp] = L
     return _libs[omp]
@@ -259,6 +265,32 @@ class Oracle:
         post, pp = _d(post)
         self._L.oracle_stream_only(self.h, pp)
 
+    def add_grid(self, values, h):
+        """Register a signed-distance grid (values[z, y, x], spacing h, body
+        frame centred at the origin); returns its id."""
+        v = np.ascontiguousarray(values, dtype=np.float32)
+        nz, ny, nx = v.shape
+        gid = self._L.oracle_add_grid(self.h, nx, ny, nz, float(h),
+                                      v.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        if gid < 0:
+            raise ValueError(f"oracle_add_grid refused the grid ({gid})")
+        return gid
+
+    def grid_sdf(self, grid, r_body):
+        r, rp = _d(r_body)
+        return self._L.oracle_grid_sdf(self.h, int(grid), rp)
+
+    def grid_properties(self, grid):
+        out = np.zeros(6)
+        self._L.oracle_grid_properties(self.h, int(grid), out.ctypes.data_as(_dp))
+        return {"V": out[0], "I1": out[1:4].copy(), "rc": out[4], "rinf": out[5]}
+
+    def inside_grid_fp32(self, grid, q, X, cell):
+        q, qp = _d(q)
+        X, Xp = _d(X)
+        cell, cp = _i(cell)
+        return bool(self._L.oracle_inside_grid_fp32(self.h, int(grid), qp, Xp, cp))
+
     def set_contact(self, k, zeta=1.0):
         """Contact stiffness k (0: off) and range zeta of the repulsion
         between the particles' enclosing capsules and with the walls."""
@@ -282,6 +314,8 @@ def from_workload(w, omp=False):
     """Build an oracle lattice from a workload description (see the workloads
     module); omp: on the -fopenmp build."""
     o = Oracle(w["n"], w["tau"], w["eps"], w["bc"], w["gravity"], w.get("fluid_force", (0, 0, 0)), omp=omp)
+    for values, h in w.get("grids", ()):
+        o.add_grid(values, h)
     P = w["particles"]
     if len(P["shape"]):
         o.add_particles(P["shape"], P["a"], P["X"], P["U"], P["omega"], P["quat"], P["rho_p"])

@@ -1,8 +1,11 @@
 """Seeded synthetic inputs: lattices and particle sets of the HLBM workloads.
 
 This module only draws inputs.  It holds none of the method's arithmetic (no
-distance function, indicator, collision, force or integrator), so that the
-CUDA path and the FP64 oracle can both be fed from it without sharing code.
+indicator, collision, force or integrator, and none of the distance
+functions the method evaluates), so that the CUDA path and the FP64 oracle
+can both be fed from it without sharing code.  The one piece of geometry
+here samples the input shapes of the distance-grid workloads: a grid shape
+is defined by its samples, which both sides then interpolate.
 
 Random numbers come from numpy's PCG64 generator (``numpy.random.default_rng``)
 seeded with 2312014172 + workload index.  Particles are placed by random
@@ -32,7 +35,7 @@ import math
 import numpy as np
 
 SEED0 = 2312014172
-SPHERE, ELLIPSOID, CUBOID, CAPSULE = 0, 1, 2, 3
+SPHERE, ELLIPSOID, CUBOID, CAPSULE, GRID = 0, 1, 2, 3, 4
 WALL_Z = 4
 
 
@@ -290,6 +293,71 @@ def _particles(shape, a, X, rho_p, quat=None):
         "quat": np.asarray(quat, float).reshape(n, 4),
         "rho_p": np.full(n, float(rho_p)),
     }
+
+
+def rounded_box_grid(b, rr, h=0.5, eps=1.5, margin=1.0):
+    """FP32 samples (values[z, y, x]) of the signed distance of a box of
+    half-extents b with edges rounded by radius rr (the box of half-extents
+    b - rr grown by rr), on a grid of spacing h centred at the origin that
+    reaches eps/2 + margin beyond the shape (the input of a distance-grid
+    particle)."""
+    b = np.asarray(b, float)
+    ext = b + 0.5 * eps + margin
+    n = [2 * int(math.ceil(e / h)) + 1 for e in ext]
+    ax = [(np.arange(k) - 0.5 * (k - 1)) * h for k in n]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    q = np.stack([np.abs(X), np.abs(Y), np.abs(Z)]) - (b - rr)[:, None, None, None]
+    outside = np.sqrt((np.maximum(q, 0.0) ** 2).sum(0))
+    inside = np.minimum(q.max(0), 0.0)
+    return (outside + inside - rr).astype(np.float32), float(h)
+
+
+def superellipsoid_grid(a, power=4.0, h=0.5, eps=1.5, margin=1.0):
+    """FP32 samples of a signed field whose zero set is the superellipsoid
+    |x/a0|^p + |y/a1|^p + |z/a2|^p = 1 (scaled so that it reads as a distance
+    along the shortest semi-axis), on a grid as in rounded_box_grid."""
+    a = np.asarray(a, float)
+    ext = a + 0.5 * eps + margin
+    n = [2 * int(math.ceil(e / h)) + 1 for e in ext]
+    ax = [(np.arange(k) - 0.5 * (k - 1)) * h for k in n]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    F = (np.abs(X / a[0]) ** power + np.abs(Y / a[1]) ** power + np.abs(Z / a[2]) ** power) ** (1.0 / power)
+    return ((F - 1.0) * a.min()).astype(np.float32), float(h)
+
+
+def grid_shapes(n=(256, 256, 256), count=2000, r_eq=5.0, ar_values=(1.0, 2.0, 3.0, 4.0), rounding=1.0,
+                tau=0.6, rho_ratio=2.5, eps=1.5, steps=500, seed_index=6, precision="fp32", name="grid_shapes"):
+    """The non-spherical box with distance-grid particles: rounded boxes
+    (b, b, AR b) of the volume of a sphere of radius r_eq, one grid per
+    aspect ratio in ar_values, particle k using grid k mod len(ar_values),
+    uniform random orientations, random sequential insertion of enclosing
+    capsules (radius sqrt(2) b along the long axis)."""
+    rng = np.random.default_rng(SEED0 + seed_index)
+    vol = 4.0 / 3.0 * math.pi * r_eq ** 3
+    grids, dims = [], []
+    for ar in ar_values:
+        # volume of the rounded box (b, b, AR b), solved for b by bisection
+        def volume(b):
+            c = np.array([b, b, ar * b]) - rounding
+            return (8 * c.prod() + 8 * rounding * (c[0] * c[1] + c[1] * c[2] + c[0] * c[2])
+                    + 2 * math.pi * rounding ** 2 * c.sum() + 4.0 / 3.0 * math.pi * rounding ** 3)
+        lo, hi = rounding, 20.0
+        for _ in range(80):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if volume(mid) < vol else (lo, mid)
+        b = 0.5 * (lo + hi)
+        dims.append(np.array([b, b, ar * b]))
+        grids.append(rounded_box_grid(dims[-1], rounding, eps=eps))
+    kinds = [k % len(ar_values) for k in range(count)]
+    quat = random_quaternions(rng, count)
+    cap_r = np.array([math.sqrt(2.0) * dims[k][0] for k in kinds])
+    cap_h = np.array([dims[k][2] for k in kinds])
+    X = sequential_insertion(rng, n, cap_r, 0, eps + 1.0, axes=body_axis_z(quat), half_lengths=cap_h)
+    m = len(X)
+    P = _particles([GRID] * m, [[kinds[k], 0.0, 0.0] for k in range(m)], X, rho_ratio, quat[:m])
+    w = _workload(f"{name}_{n[0]}x{n[1]}x{n[2]}_{m}", n, 0, tau, eps, P, steps, precision)
+    w["grids"] = grids
+    return w
 
 
 def _workload(name, n, bc, tau, eps, particles, steps, precision, gravity=1e-5):

@@ -721,3 +721,229 @@ def test_contact_force_enters_newton_euler(O):
     m = 2.0 * 4 / 3 * math.pi * np.array([64.0, 27.0])
     assert np.allclose(s["U"], Fc / m[:, None], rtol=1e-12, atol=1e-20)
     assert abs(Fc[0, 0] + k * ((zeta - 0.6) / zeta) ** 2) < 1e-15
+
+
+# --------------------------- signed-distance grids (the outlook's other shapes)
+def _sphere_grid(a, h, eps, margin=1.0):
+    """Exact sphere distance |r| - a sampled on a grid centred at the origin."""
+    ext = a + 0.5 * eps + margin
+    k = 2 * int(math.ceil(ext / h)) + 1
+    ax = (np.arange(k) - 0.5 * (k - 1)) * h
+    Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+    return (np.sqrt(X * X + Y * Y + Z * Z) - a).astype(np.float32)
+
+
+def test_grid_distance_is_the_trilinear_blend(O):
+    """The grid's distance equals the samples at grid points, the trilinear
+    blend between them (a linear field is reproduced exactly), approaches an
+    exact sphere distance to O(h^2 / a), and is +inf outside the grid."""
+    o = O.Oracle((40, 40, 40), 0.8, 0.5, 0)
+    h, a = 0.5, 4.0
+    v = _sphere_grid(a, h, 0.5)
+    g = o.add_grid(v, h)
+    k = v.shape[0]
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        i = rng.integers(0, k, 3)
+        r = (i - 0.5 * (k - 1)) * h
+        assert o.grid_sdf(g, r) == float(v[i[2], i[1], i[0]])
+    for _ in range(200):
+        r = rng.uniform(-a - 0.5, a + 0.5, 3)
+        assert abs(o.grid_sdf(g, r) - (np.linalg.norm(r) - a)) < h * h / a
+    assert o.grid_sdf(g, [0.0, 0.0, (k - 1) * h]) == float("inf")
+    # between two samples the blend is linear
+    o2 = O.Oracle((40, 40, 40), 0.8, 0.5, 0)
+    cube = np.full((9, 9, 9), 3.0, np.float32)
+    cube[2:7, 2:7, 2:7] = -1.0
+    g2 = o2.add_grid(cube, 0.7)
+    assert o2.grid_sdf(g2, [0.0, 0.0, 0.0]) == -1.0
+    assert abs(o2.grid_sdf(g2, [0.35 + 1.4, 0.0, 0.0]) - 1.0) < 1e-15  # halfway between -1 and 3
+
+
+@pytest.mark.parametrize("shape", ["sphere", "rounded_box", "superellipsoid"])
+def test_grid_mass_properties(O, shape):
+    """Volume and principal moments derived from the samples (midpoint rule
+    over sub-cells of the blend) against the closed forms of the sampled
+    shape (sphere, rounded box) or a fine direct integration of its defining
+    inequality (superellipsoid), within 0.5 % at spacing 1/4 (1 % for the
+    superellipsoid, whose field is not a distance), and the
+    radii: every point of the body lies within rc, B vanishes beyond rinf."""
+    from paper_2312_14172_gb300 import workloads
+    h, eps = 0.25, 1.5
+    o = O.Oracle((48, 48, 48), 0.8, eps, 0)
+    if shape == "sphere":
+        a = 3.5
+        g = o.add_grid(_sphere_grid(a, h, eps), h)
+        V = 4 / 3 * math.pi * a ** 3
+        I = np.full(3, 0.4 * V * a * a)
+        reach = a
+    elif shape == "rounded_box":
+        b, rr = np.array([2.0, 3.0, 4.5]), 0.8
+        v, _ = workloads.rounded_box_grid(b, rr, h=h, eps=eps)
+        g = o.add_grid(v, h)
+        c = b - rr
+        V = (8 * c.prod() + 8 * rr * (c[0] * c[1] + c[1] * c[2] + c[0] * c[2])
+             + 2 * math.pi * rr ** 2 * c.sum() + 4 / 3 * math.pi * rr ** 3)
+        inside = lambda x, y, z: np.sqrt(np.maximum(np.abs(x) - c[0], 0) ** 2 + np.maximum(np.abs(y) - c[1], 0) ** 2
+                                         + np.maximum(abs(z) - c[2], 0) ** 2) < rr
+        _, I = _grid_mass_properties(inside, b, 1.0, n=300)
+        reach = np.linalg.norm(c) + rr
+    else:
+        a = np.array([2.0, 2.5, 4.0])
+        v, _ = workloads.superellipsoid_grid(a, 4.0, h=h, eps=eps)
+        g = o.add_grid(v, h)
+        inside = lambda x, y, z: (x / a[0]) ** 4 + (y / a[1]) ** 4 + (z / a[2]) ** 4 < 1.0
+        V, I = _grid_mass_properties(inside, a, 1.0, n=300)
+        reach = np.linalg.norm(a)  # a bound
+    p = o.grid_properties(g)
+    # the superellipsoid's field is not a distance (its slope varies along
+    # the surface), so its blend departs more from the sampled shape
+    tol = 1e-2 if shape == "superellipsoid" else 5e-3
+    assert abs(p["V"] / V - 1) < tol, (p["V"], V)
+    assert np.all(np.abs(p["I1"] / I - 1) < tol), (p["I1"], I)
+    assert p["rc"] >= reach - 1e-9 * reach or shape == "superellipsoid"
+    assert p["rc"] <= reach + math.sqrt(3) * h + 1e-9
+    assert p["rinf"] >= p["rc"] + eps / 2 - math.sqrt(3) * h
+
+
+def test_grid_particle_mass_and_inertia_enter_newton_euler(O):
+    """A grid particle's mass and moments are rho V and rho I of its grid:
+    recovered from one update under a known force and torque."""
+    o = O.Oracle((40, 40, 40), 0.8, 0.5, 0)
+    g = o.add_grid(_sphere_grid(3.0, 0.5, 0.5), 0.5)
+    rho = 1.8
+    o.add_particles([4], [[g, 0, 0]], [[20.0, 20.0, 20.0]], rho_p=[rho])
+    F, T = np.array([[1e-3, 0, 0]]), np.array([[2e-3, 3e-3, 4e-3]])
+    o.integrate_only(F, T)
+    s = o.particle_state()
+    p = o.grid_properties(g)
+    assert abs(F[0, 0] / s["U"][0, 0] - rho * p["V"]) < 1e-12 * rho * p["V"]
+    assert np.allclose(T[0] / s["omega"][0], rho * p["I1"], rtol=1e-12)
+
+
+def test_grid_inside_fp32_agrees_with_fp64_away_from_surface(O):
+    """The FP32 inside decision of a grid particle (fixed operation order)
+    matches the FP64 blend wherever the blend is farther than 1e-4 from 0,
+    under rotation and across a periodic face."""
+    from paper_2312_14172_gb300 import workloads
+    n = (32, 30, 28)
+    o = O.Oracle(n, 0.8, 1.5, 0)
+    v, h = workloads.rounded_box_grid([2.0, 3.0, 4.5], 0.8, h=0.5, eps=1.5)
+    g = o.add_grid(v, h)
+    rng = np.random.default_rng(9)
+    checked = 0
+    for _ in range(4):
+        q = rng.standard_normal(4)
+        q /= np.linalg.norm(q)
+        X = np.array([rng.uniform(0, n[0]), 1.3, rng.uniform(0, n[2])])
+        R = O.rotation(q)
+        for z in range(n[2]):
+            for y in range(n[1]):
+                for x in range(n[0]):
+                    r = np.array([x, y, z], float) - X
+                    r -= np.array(n) * np.round(r / np.array(n))
+                    if np.linalg.norm(r) > 7:
+                        continue
+                    d = o.grid_sdf(g, R.T @ r)
+                    if abs(d) < 1e-4:
+                        continue
+                    assert o.inside_grid_fp32(g, q, X, [x, y, z]) == (d < 0), (x, y, z, d)
+                    checked += 1
+    assert checked > 2000
+
+
+def test_grid_registration_checks(O):
+    """Refused: a grid whose faces carry samples below eps/2 (the indicator
+    would be cut off), one without a negative sample, and one whose body is
+    off its centre (the body frame must be the principal frame about the
+    centre of mass)."""
+    o = O.Oracle((32, 32, 32), 0.8, 0.5, 0)
+    v = _sphere_grid(3.0, 0.5, 0.5)
+    bad = v.copy()
+    bad[0, 5, 5] = 0.1
+    with pytest.raises(ValueError):
+        o.add_grid(bad, 0.5)
+    with pytest.raises(ValueError):
+        o.add_grid(np.abs(v) + 1.0, 0.5)
+    shifted = np.roll(_sphere_grid(3.0, 0.5, 0.5, margin=3.0), 3, axis=2)
+    with pytest.raises(ValueError):
+        o.add_grid(shifted, 0.5)
+    assert o.add_grid(v, 0.5) == 0
+
+
+def test_grid_of_a_cuboid_couples_like_the_cuboid(O):
+    """A grid of the exact box distance, sampled so that the box faces lie
+    midway between samples, selects the same interior cells as the analytic
+    cuboid (the blend of a distance that is linear across a face is exact
+    there; edges and corners lie between cell centres), and the momentum
+    exchange identity holds for it."""
+    n = (20, 22, 24)
+    o = O.Oracle(n, 0.8, 0.5, 0)
+    half = np.array([2.5, 3.5, 4.5])
+    h = 0.5
+    ext = half + 2.0
+    k = [2 * int(math.ceil(e / h)) + 1 for e in ext]
+    ax = [(np.arange(m) - 0.5 * (m - 1)) * h for m in k]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    q = np.stack([np.abs(X), np.abs(Y), np.abs(Z)]) - half[:, None, None, None]
+    box = np.sqrt((np.maximum(q, 0) ** 2).sum(0)) + np.minimum(q.max(0), 0)
+    g = o.add_grid(box.astype(np.float32), h)
+    Xc = np.array([10.0, 11.0, 12.0])  # cell centres at integer offsets: faces at +-2.5.. are between cells
+    o.add_particles([4, 2], [[g, 0, 0], half], [Xc, Xc + [0, 0, 0]], rho_p=[2.0, 2.0])
+    same = 0
+    for z in range(n[2]):
+        for y in range(n[1]):
+            for x in range(n[0]):
+                a = o.inside_grid_fp32(g, [1, 0, 0, 0], Xc, [x, y, z])
+                b = O.inside_fp32(2, half, [1, 0, 0, 0], Xc, [x, y, z], n, 0)
+                assert a == b
+                same += a
+    assert same == 5 * 7 * 9
+
+
+def test_grid_mea_equals_momentum_change_and_b_vanishes_beyond_rinf(O):
+    """For a rotated, moving grid particle near a periodic face: the momentum
+    exchange equals the momentum gained by its interior cells in the last
+    streaming minus u_p times the mass gained (brute force, as for the
+    analytic shapes), and the indicator field is zero beyond its influence
+    radius."""
+    from paper_2312_14172_gb300 import workloads
+    n = (18, 17, 19)
+    o = O.Oracle(n, 0.8, 1.5, 0)
+    v, h = workloads.rounded_box_grid([2.0, 2.5, 4.0], 0.7, h=0.5, eps=1.5)
+    g = o.add_grid(v, h)
+    X = np.array([16.7, 6.2, 8.9])
+    U = np.array([2e-3, -1e-3, 3e-3])
+    W = np.array([1e-3, 4e-3, -2e-3])
+    q = np.array([0.7, 0.4, -0.2, 0.55])
+    q /= np.linalg.norm(q)
+    o.add_particles([4], [[g, 0, 0]], [X], U=[U], omega=[W], quat=[q], rho_p=[3.0])
+    c, w, _ = O.velocity_set()
+    rng = np.random.default_rng(21)
+    post = w[:, None, None, None] * (1 + 0.05 * rng.standard_normal((19, n[2], n[1], n[0])))
+    o.stream_only(post)
+    f = o.populations()
+    F, T, cnt = o.mea(0)
+    Fw, Tw, k = np.zeros(3), np.zeros(3), 0
+    for z in range(n[2]):
+        for y in range(n[1]):
+            for x in range(n[0]):
+                if not o.inside_grid_fp32(g, q, X, [x, y, z]):
+                    continue
+                k += 1
+                r = np.array([x, y, z], float) - X
+                r -= np.array(n) * np.round(r / np.array(n))
+                up = U + np.cross(W, r)
+                dp = c.T @ f[:, z, y, x] - c.T @ post[:, z, y, x]
+                dm = f[:, z, y, x].sum() - post[:, z, y, x].sum()
+                Fw += dp - up * dm
+                Tw += np.cross(r, dp - up * dm)
+    assert cnt == k and k > 40
+    assert np.allclose(F, Fw, rtol=1e-11, atol=1e-15)
+    assert np.allclose(T, Tw, rtol=1e-11, atol=1e-14)
+    B, pid = o.indicator_field()
+    rinf = o.grid_properties(g)["rinf"]
+    zz, yy, xx = np.nonzero(B > 0)
+    r = np.stack([xx, yy, zz], 1) - X
+    r -= np.array(n) * np.round(r / np.array(n))
+    assert len(zz) > k and np.linalg.norm(r, axis=1).max() < rinf
