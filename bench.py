@@ -29,6 +29,7 @@ with FP32 and with FP16 storage, its collision roofline and the FP16 error;
 ensemble: 64 independent boxes of 64..96^3 advanced together, FP32 (its fp16
 entry: the same with FP16 storage).
 Opt-in legs: --capsules (the non-spherical box with 2000 capsules),
+--grid-shapes (the same box with 2000 signed-distance grid particles),
 --phi-matched, --settling-validation.
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
@@ -53,7 +54,7 @@ BYTES_PER_CELL = {"fp32": 2 * 19 * 4, "fp16": 2 * 19 * 2}
 
 
 WORKLOADS = ("hindered_settling", "single_sphere", "nonspherical", "dense_batch", "fluid_256",
-             "dense_batch_256", "nonspherical_phi", "dense_batch_phi", "capsules")
+             "dense_batch_256", "nonspherical_phi", "dense_batch_phi", "capsules", "grid_shapes")
 
 
 def make_workload(name):
@@ -78,6 +79,8 @@ def make_workload(name):
         return workloads.dense_batch_phi_matched()
     if name == "capsules":
         return workloads.nonspherical(kinds=(workloads.CAPSULE,), name="capsules")
+    if name == "grid_shapes":
+        return workloads.grid_shapes()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -515,6 +518,7 @@ def run_gpu(args, ws, rank, local):
     phi = phi_matched_leg(args, stream, peak, ws) if args.phi_matched else None
     settling = settling_validation_leg(args, stream) if args.settling_validation else None
     capsules = capsules_leg(args, stream, peak, ws) if args.capsules else None
+    grids = grid_shapes_leg(args, stream, peak, ws) if args.grid_shapes else None
 
     launches_per_step = 3 if npart > 0 else 1
     line = {
@@ -548,6 +552,8 @@ def run_gpu(args, ws, rank, local):
         line["settling_validation"] = settling
     if capsules is not None:
         line["capsules"] = capsules
+    if grids is not None:
+        line["grid_shapes"] = grids
     return line
 
 
@@ -719,6 +725,14 @@ def capsules_leg(args, stream, peak, ws):
     return fp32_fp16_pair(make_workload("capsules"), args, stream, peak, ws, steps_max=100)
 
 
+def grid_shapes_leg(args, stream, peak, ws):
+    """The non-spherical workload's box and counts with signed-distance grid
+    particles (2000 rounded boxes of equal volume from four grids of aspect
+    ratio 1-4, spacing 1/2, random orientations, eps = 1.5), FP32 and FP16
+    storage."""
+    return fp32_fp16_pair(make_workload("grid_shapes"), args, stream, peak, ws, steps_max=100)
+
+
 def settling_correlations(phi, re):
     """The three hindered-settling correlations of the paper (Sec. 5) as
     u_bar / u*: Richardson-Zaki (1 - phi)^n with its piecewise expansion
@@ -874,7 +888,7 @@ def summary_of(line):
     if line.get("fp16"):
         out["headline_fp16"] = {"mlups": round(line["fp16"]["value"], 1),
                                 "collision_frac": round(line["fp16"]["roofline"]["frac"], 4)}
-    for key in ("nonspherical", "batched_fp16", "capsules", "phi_matched"):
+    for key in ("nonspherical", "batched_fp16", "capsules", "grid_shapes", "phi_matched"):
         d = line.get(key)
         if d and "fp32" in d:
             out[key] = {p: leg(d[p]) for p in ("fp32", "fp16")}
@@ -911,6 +925,8 @@ def main():
                     help="its duration in t* = D / u*_St (the paper: 300)")
     ap.add_argument("--capsules", action="store_true",
                     help="add the 256^3 box of 2000 capsules with FP32 and FP16 storage")
+    ap.add_argument("--grid-shapes", action="store_true",
+                    help="add the 256^3 box of 2000 signed-distance grid particles with FP32 and FP16 storage")
     ap.add_argument("--phi-matched", action="store_true",
                     help="add the solid-fraction-matched variants of the non-spherical and dense workloads "
                          "(about two minutes of host time to draw them)")

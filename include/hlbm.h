@@ -67,11 +67,19 @@ extern "C" {
 #define HLBM_CUBOID 2    /* half-extents a, b, c along the body axes */
 #define HLBM_CAPSULE 3   /* radius r, ignored, half-length h of the axis segment
                             along the body z axis: the points within r of it */
+#define HLBM_GRID 4      /* a signed-distance grid registered by hlbm_add_grid:
+                            its id, ignored, ignored */
+#define HLBM_MAX_GRIDS 64
 
 /* boundary flags: a set bit bounds that axis with two bounce-back walls */
 #define HLBM_WALL_X 1
 #define HLBM_WALL_Y 2
 #define HLBM_WALL_Z 4
+/* together with HLBM_WALL_Z: the box is one z slab of a larger lattice (see
+ * "Sub-domains" below): its z faces bound the lattice like walls, particle
+ * centres may lie beyond them, and only the owned planes enter the momentum
+ * exchange */
+#define HLBM_CUT_Z 8
 
 typedef struct hlbm_ctx* hlbm_handle;
 
@@ -91,10 +99,11 @@ typedef struct {
   int fp16_scale_log2;    /* HLBM_FP16 only: stored value (f_i - w_i) * 2^s, s in [0, 16] */
   int max_particles;      /* capacity of the particle table over all boxes, >= 0 */
   int bin_capacity;       /* particles per 32x8x8 cell tile seen by the collision; 0 = 64 */
+  long long grid_floats;  /* capacity for the samples of signed-distance grids, >= 0 */
 } hlbm_params;
 
 /* Fills p with the defaults: tau 0.6, eps 0.5 (Sec. 3.2), no forces, FP32,
- * s = 14, max_particles 0, bin_capacity 0. */
+ * s = 14, max_particles 0, bin_capacity 0, grid_floats 0. */
 void hlbm_default_params(hlbm_params* p);
 
 /* Device bytes that an init call with the same arguments needs; 0 if the
@@ -115,10 +124,32 @@ int hlbm_init_lattice(hlbm_handle* out, int nx, int ny, int nz, int bc_flags,
 int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const hlbm_params* prm,
                     void* cuda_stream, void* device_buf, size_t device_buf_bytes);
 
+/* Registers a signed-distance grid, the voxelised form of the paper's
+ * outlook on particle shapes beyond spheres (Sec. 6): values[(k ny + j) nx
+ * + i] (FP32, host) is the signed distance (negative inside) at the
+ * body-frame point ((i - (nx - 1)/2) h, (j - (ny - 1)/2) h, (k - (nz - 1)/2) h),
+ * nx, ny, nz >= 2, spacing h > 0.  Between samples the distance is the
+ * trilinear blend of the eight corners of the grid cell holding the point,
+ * and a cell centre is inside a grid particle when the FP32 blend (operation
+ * order as the library's inside test states) is negative.  The body frame
+ * must be the principal frame about the centre of mass: volume and second
+ * moments are summed over 4 x 4 x 4 sub-cells of every grid cell (midpoint
+ * rule on the blend), and a centroid off the origin by more than h/100 or
+ * products of inertia above 1e-3 of the largest moment are refused.  The
+ * samples on the grid's faces must be >= eps/2 (the indicator of Eq. B must
+ * vanish there), at least one must be negative, and the body's circumscribed
+ * radius (the farthest corner of the grid cells with a negative corner) may
+ * be at most 30 cells.  The samples are copied (the handle's grid_floats
+ * bounds their total).  Writes the grid id (0, 1, ...) to *grid_id.
+ * HLBM_ERR_ARG for refused grids, HLBM_ERR_CAPACITY when grid_floats or
+ * HLBM_MAX_GRIDS is exceeded. */
+int hlbm_add_grid(hlbm_handle h, int nx, int ny, int nz, double spacing, const float* values, int* grid_id);
+
 /* Adds n particles (Sec. 2.2), allowed only before the first step
  * (HLBM_ERR_STATE afterwards).  Arrays (host, row-major):
  *   box_id[n]      box of each particle (NULL = box 0)
- *   shape[n]       HLBM_SPHERE / HLBM_ELLIPSOID / HLBM_CUBOID / HLBM_CAPSULE
+ *   shape[n]       HLBM_SPHERE / HLBM_ELLIPSOID / HLBM_CUBOID / HLBM_CAPSULE /
+ *                  HLBM_GRID (shape_params: the grid id, then two ignored)
  *   shape_params[3n], X[3n] centre of mass, U[3n] velocity (NULL = 0),
  *   omega[3n] angular velocity (NULL = 0), quat[4n] orientation (w,x,y,z,
  *   body -> world, normalised here; NULL = identity), rho_p[n] density.
@@ -128,8 +159,9 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
  * radius beyond which B of Eq. B vanishes, plus 2 cells) spans half a
  * periodic axis or more.  The influence radius is r + eps/2 for spheres, the
  * circumscribed radius + eps/2 for cuboids and a_max (1 + eps / (2 a_min))
- * for ellipsoids, h + r + eps/2 for capsules.  The circumscribed radius may
- * be at most 30 cells. */
+ * for ellipsoids, h + r + eps/2 for capsules, and for grids the farthest
+ * corner of the grid cells with a corner below eps/2.  The circumscribed
+ * radius may be at most 30 cells. */
 int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape,
                        const double* shape_params, const double* X, const double* U,
                        const double* omega, const double* quat, const double* rho_p);
@@ -160,7 +192,8 @@ int hlbm_set_fluid_force(hlbm_handle h, const double f[3]);
  * a capsule by themselves, an ellipsoid by the capsule along its longest
  * semi-axis a_k with radius the larger other semi-axis r and half-length
  * a_k - r, a cuboid by the capsule along its longest half-extent h_k with
- * radius |(h_i, h_j)| and half-length h_k.  Two capsules of one box whose
+ * radius |(h_i, h_j)| and half-length h_k, a grid particle by the sphere of
+ * its circumscribed radius.  Two capsules of one box whose
  * axis segments come closest at p_i, p_j (minimum image) with surface gap
  * delta = |p_i - p_j| - r_i - r_j < zeta repel each other along p_i - p_j
  * with the force k ((zeta - delta) / zeta)^2, particle i taking the torque
@@ -262,7 +295,8 @@ int hlbm_interior_cells(hlbm_handle h, long long* n);
 
 /* Snapshots (checkpoint and restart; not part of the paper's method).
  *
- * A snapshot holds the whole state the next step reads: the populations as
+ * A snapshot holds the whole state the next step reads: the registered
+ * distance grids, the populations as
  * stored (the handle's block layout and precision, bit for bit), the FP64
  * particle table with shapes and box ids, the step count (hence the AA
  * parity), the fluid force, the momentum-exchange mode and, when the next
@@ -325,7 +359,8 @@ int hlbm_load(hlbm_handle h, const void* buf, size_t bytes);
  *                hlbm_add_particles (U, omega, quat may be NULL)
  *   F, T         device outputs [3n]: hydrodynamic force and torque.  A
  *                particle is checked as hlbm_add_particles checks it and gets
- *                NaN force and torque when its shape code is unknown, a size
+ *                NaN force and torque when its shape code is unknown or
+ *                HLBM_GRID (grids belong to a handle), a size
  *                is non-finite or <= 0, its quaternion is zero or non-finite,
  *                a centre or velocity component is non-finite, its
  *                circumscribed radius r_c exceeds 30 cells, its centre lies
@@ -341,6 +376,62 @@ int hlbm_mea_noalloc(const void* f, long long plane, int nx, int ny, int nz, int
                      const double* shape_params, const double* X, const double* U,
                      const double* omega, const double* quat, double* F, double* T,
                      void* cuda_stream);
+
+/* Sub-domains: z slabs of one lattice on several handles (one GPU each, or
+ * several on one GPU), the single-GPU building blocks of the paper's domain
+ * decomposition with its particle decomposition (Secs. 4.2.2-4.2.4).
+ *
+ * A slab of planes [z0, z1) of a global lattice is a box of z1 - z0 + 2
+ * planes with HLBM_WALL_Z | HLBM_CUT_Z: local plane 0 and the last plane are
+ * ghost copies of the neighbours' boundary planes, hlbm_set_owned_planes(h,
+ * box, 1, z1 - z0 + 1) marks the rest as owned.  Each slab holds copies of
+ * the particles whose influence reaches it (positions in its local frame,
+ * the periodic image nearest to it).  A step of the whole lattice is then:
+ *   1. before an odd step (steps done is odd), every ghost plane receives
+ *      the neighbour's boundary plane's slots that cross the face
+ *      (hlbm_plane_slots: the lower ghost the slots with c_z = -1 of the
+ *      lower neighbour's top owned plane, the upper ghost the slots with
+ *      c_z = +1 of the upper neighbour's bottom owned plane);
+ *   2. hlbm_step_forces on every slab: its partial momentum exchange
+ *      (Eq. hlbm:mea over its owned cells only) per particle copy;
+ *   3. the partial forces and torques of a particle are summed (in the paper
+ *      by the particle's owner, from the slabs its circumscribed sphere
+ *      reaches) and the totals are handed back to every slab holding it;
+ *   4. hlbm_step_with_forces on every slab: external force, Newton-Euler
+ *      update with those totals, coupling, collision and streaming;
+ *   5. after an odd step, every owned boundary plane takes back the slots
+ *      the neighbour's cells wrote into their ghost copy of it (the bottom
+ *      owned plane the slots with c_z = +1 of the lower neighbour's upper
+ *      ghost, the top owned plane the slots with c_z = -1 of the upper
+ *      neighbour's lower ghost).
+ * Every copy of a particle integrates the same totals, so the copies stay
+ * identical and the lattice evolves as one box would. */
+
+/* Owned planes [z_lo, z_hi) of a box with HLBM_CUT_Z; the other planes are
+ * ghosts whose cells the momentum exchange leaves out.  Synchronises.
+ * HLBM_ERR_ARG for a box without HLBM_CUT_Z or an empty or out-of-box
+ * range. */
+int hlbm_set_owned_planes(hlbm_handle h, int box, int z_lo, int z_hi);
+
+/* Copies the five stored slots {i : c_z of i = dir} (dir = +1 or -1; in
+ * increasing i) of every cell of plane z of box `box`, as stored (storage
+ * precision, FP32 or FP16 deviations), to (put = 0) or from (put = 1) the
+ * host buffer of 5 * nx * ny values laid out [slot][y][x].  These are the
+ * populations that cross a z face in the in-place (AA) storage.
+ * Synchronises.  HLBM_ERR_ARG for bad arguments. */
+int hlbm_plane_slots(hlbm_handle h, int box, int z, int dir, void* host, int put);
+
+/* A step split at the momentum exchange (Algorithm 1's "communicate surface
+ * forces" row).  hlbm_step_forces runs the momentum exchange of the next
+ * step and writes each particle's hydrodynamic force and torque [3n] (host)
+ * over the cells this handle owns; synchronises.  hlbm_step_with_forces
+ * takes the totals F, T [3n] (host) in their place and runs the rest of the
+ * step (contact when on, external force, Newton-Euler update, work lists,
+ * coupling, collision and streaming); synchronises.  hlbm_step refuses
+ * while a split step is open (HLBM_ERR_STATE), and so does a second
+ * hlbm_step_forces. */
+int hlbm_step_forces(hlbm_handle h, double* F, double* T);
+int hlbm_step_with_forces(hlbm_handle h, const double* F, const double* T);
 
 /* One-line description of the last error on this handle (or of the last
  * failed init when h is NULL). */

@@ -37,7 +37,8 @@ struct Layout {
   int cap = 0, bin_cap = 0;
   size_t off_f, off_boxes, off_P, off_shape, off_box, off_rec, off_part, off_acc, off_chp, off_chq,
       off_pc0, off_pnc, off_done, off_lcnt, off_lidx, off_lmom, off_cnt[2], off_ids[2], off_status,
-      off_stage, total;
+      off_stage, off_gdesc, off_gvals, total;
+  long long grid_floats = 0;
   long long ilist_cap = 0;
 };
 
@@ -50,18 +51,25 @@ bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& 
   if (prm->fp16_scale_log2 < 0 || prm->fp16_scale_log2 > 16) { err = "fp16_scale_log2 out of [0, 16]"; return false; }
   if (prm->max_particles < 0) { err = "max_particles < 0"; return false; }
   if (prm->bin_capacity < 0 || prm->bin_capacity > 64) { err = "bin_capacity out of [0, 64]"; return false; }
+  if (prm->grid_floats < 0 || prm->grid_floats > (1LL << 34)) { err = "grid_floats out of range"; return false; }
   for (int j = 0; j < 3; ++j)
     if (!std::isfinite(prm->gravity[j]) || !std::isfinite(prm->fluid_force[j])) { err = "non-finite force"; return false; }
   bd.assign(nb, BoxDesc{});
   long long cells = 0, tiles = 0, blocks = 0, maxbox = 0;
   for (int b = 0; b < nb; ++b) {
     const hlbm_box& B = boxes[b];
-    if (B.nx < 1 || B.ny < 1 || B.nz < 1 || (B.bc_flags & ~7)) { err = "bad box dimensions or flags"; return false; }
+    if (B.nx < 1 || B.ny < 1 || B.nz < 1 || (B.bc_flags & ~15) ||
+        ((B.bc_flags & HLBM_CUT_Z) && !(B.bc_flags & HLBM_WALL_Z))) {
+      err = "bad box dimensions or flags (HLBM_CUT_Z needs HLBM_WALL_Z)";
+      return false;
+    }
     const long long n = (long long)B.nx * B.ny * B.nz;
     if (n >= (1LL << 31)) { err = "a box may hold at most 2^31 - 1 cells"; return false; }
     if (cells + n >= (1LL << 31)) { err = "all boxes together may hold at most 2^31 - 1 cells"; return false; }
     BoxDesc& d = bd[b];
     d.nx = B.nx; d.ny = B.ny; d.nz = B.nz; d.bc = B.bc_flags;
+    d.own_lo = 0;
+    d.own_hi = B.nz;
     d.ntx = (B.nx + TILE_X - 1) / TILE_X;
     d.nty = (B.ny + TILE_Y - 1) / TILE_Y;
     d.ntz = (B.nz + TILE_Z - 1) / TILE_Z;
@@ -109,6 +117,9 @@ bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& 
   }
   L.off_status = o; o = align_up(o + sizeof(int));
   L.off_stage = o; o = align_up(o + sizeof(float) * Q * (size_t)L.stage_cells);
+  L.grid_floats = prm->grid_floats;
+  L.off_gdesc = o; o = align_up(o + (L.grid_floats > 0 ? sizeof(GridDesc) * MAX_GRIDS : 0));
+  L.off_gvals = o; o = align_up(o + sizeof(float) * (size_t)L.grid_floats);
   L.total = o;
   return true;
 }
@@ -170,11 +181,25 @@ struct hlbm_ctx {
   cudaGraphExec_t exec2[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool graphs_ok = false;
   bool moments_valid = false;  // the accumulator holds this state's momentum exchange
+  int split = 0;  // a split step is open: 1 after its bounding-box exchange, 2 after its moments one
   // hstage holds the device's particle rows X .. T as downloaded by
   // hlbm_particle_state after step hst_steps (until an upload reuses it)
   bool hst_valid = false;
   long long hst_steps = -1;
   std::vector<int> h_shape, h_box;  // host copies
+  // registered signed-distance grids: host copies of the samples and what
+  // was derived from them
+  struct HostGrid {
+    int n[3];
+    double h;
+    std::vector<float> v;
+    double V, I1[3], rc, rinf;
+    long long off;
+  };
+  std::vector<HostGrid> grids;
+  long long grid_used = 0;
+  GridDesc* d_gdesc = nullptr;
+  float* d_gvals = nullptr;
   std::string err;
 };
 
@@ -222,6 +247,7 @@ static LbmArgs lbm_args(const hlbm_ctx* h, int parity) {
   a.ilist_cap = h->L.ilist_cap;
   a.np = h->np;
   a.acc = h->acc;
+  a.grids = h->grids.empty() ? GridSet{} : GridSet{h->d_gdesc, h->d_gvals};
   a.status = h->status;
   return a;
 }
@@ -252,6 +278,7 @@ static PartArgs part_args(const hlbm_ctx* h, int parity) {
   a.from_acc = 0;
   a.contact_k = h->contact_k;
   a.contact_zeta = h->contact_zeta;
+  a.grids = h->grids.empty() ? GridSet{} : GridSet{h->d_gdesc, h->d_gvals};
   a.nsm = h->nsm;
   a.ilist_count = h->ilist_count;
   a.bin_count = h->cnt[parity];
@@ -444,6 +471,8 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
   }
   h->status = (int*)(h->buf + h->L.off_status);
   h->stage = (float*)(h->buf + h->L.off_stage);
+  h->d_gdesc = h->L.grid_floats > 0 ? (GridDesc*)(h->buf + h->L.off_gdesc) : nullptr;
+  h->d_gvals = h->L.grid_floats > 0 ? (float*)(h->buf + h->L.off_gvals) : nullptr;
   // zero deviations are the fluid at rest with density 1 (f_i = w_i); empty bins
   e = cudaMemsetAsync(h->buf, 0, h->L.total, h->stream);
   if (e == cudaSuccess)
@@ -525,6 +554,27 @@ static void mass_properties(int shape, const double a[3], double rho, double* V,
   }
 }
 
+// FP64 trilinear blend of a registered grid at body offset r (+inf outside)
+static double grid_blend_host(const hlbm_ctx::HostGrid& g, const double r[3]) {
+  int i0[3];
+  double t[3];
+  for (int j = 0; j < 3; ++j) {
+    const double x = r[j] / g.h + 0.5 * (g.n[j] - 1);
+    if (!(x >= 0.0 && x <= (double)(g.n[j] - 1))) return HUGE_VAL;
+    i0[j] = std::min((int)std::floor(x), g.n[j] - 2);
+    t[j] = x - i0[j];
+  }
+  auto at = [&](int dx, int dy, int dz) {
+    return (double)g.v[((size_t)(i0[2] + dz) * g.n[1] + (i0[1] + dy)) * g.n[0] + (i0[0] + dx)];
+  };
+  double e[2][2];
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy) e[dz][dy] = at(0, dy, dz) + t[0] * (at(1, dy, dz) - at(0, dy, dz));
+  const double f0 = e[0][0] + t[1] * (e[0][1] - e[0][0]);
+  const double f1 = e[1][0] + t[1] * (e[1][1] - e[1][0]);
+  return f0 + t[2] * (f1 - f0);
+}
+
 static void wrap_host(const BoxDesc& bd, double X[3]) {
   const int n[3] = {bd.nx, bd.ny, bd.nz};
   for (int j = 0; j < 3; ++j) {
@@ -540,6 +590,99 @@ static int upload_fields(hlbm_ctx* h, int p0, int n, const std::vector<double>& 
   for (int fld = 0; fld < PF_COUNT; ++fld)
     CK(cudaMemcpyAsync(h->P + (size_t)fld * h->L.cap + p0, tab.data() + (size_t)fld * n,
                        sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+  return HLBM_OK;
+}
+
+int hlbm_add_grid(hlbm_handle h, int nx, int ny, int nz, double spacing, const float* values, int* grid_id) {
+  if (!h) return HLBM_ERR_ARG;
+  if (!values || !grid_id || nx < 2 || ny < 2 || nz < 2 || !(spacing > 0.0) || !std::isfinite(spacing))
+    return fail(h, HLBM_ERR_ARG, "grid sizes must be >= 2, the spacing finite and > 0, the arrays non-NULL");
+  const long long nv = (long long)nx * ny * nz;
+  if ((int)h->grids.size() >= MAX_GRIDS) return fail(h, HLBM_ERR_CAPACITY, "HLBM_MAX_GRIDS grids already registered");
+  if (h->grid_used + nv > h->L.grid_floats)
+    return fail(h, HLBM_ERR_CAPACITY, "the grid samples exceed grid_floats of the parameters");
+  hlbm_ctx::HostGrid g;
+  g.n[0] = nx; g.n[1] = ny; g.n[2] = nz;
+  g.h = spacing;
+  g.v.assign(values, values + nv);
+  bool neg = false;
+  for (float v : g.v) {
+    if (!std::isfinite(v)) return fail(h, HLBM_ERR_ARG, "non-finite grid sample");
+    neg = neg || v < 0.0f;
+  }
+  if (!neg) return fail(h, HLBM_ERR_ARG, "a grid needs a negative sample");
+  const double half_eps = h->prm.eps / 2.0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const bool face = i == 0 || j == 0 || k == 0 || i == nx - 1 || j == ny - 1 || k == nz - 1;
+        if (face && !((double)g.v[((size_t)k * ny + j) * nx + i] >= half_eps))
+          return fail(h, HLBM_ERR_ARG, "grid samples on its faces must be >= eps/2");
+      }
+  // radii: the farthest corner of the grid cells holding a corner below 0
+  // (the body) and below eps/2 (where B of Eq. B can be positive)
+  g.rc = g.rinf = 0.0;
+  for (int k = 0; k + 1 < nz; ++k)
+    for (int j = 0; j + 1 < ny; ++j)
+      for (int i = 0; i + 1 < nx; ++i) {
+        double vmin = HUGE_VAL, cmax = 0.0;
+        for (int c = 0; c < 8; ++c) {
+          const int ii = i + (c & 1), jj = j + ((c >> 1) & 1), kk = k + (c >> 2);
+          vmin = std::min(vmin, (double)g.v[((size_t)kk * ny + jj) * nx + ii]);
+          const double x = (ii - 0.5 * (nx - 1)) * spacing, y = (jj - 0.5 * (ny - 1)) * spacing,
+                       z = (kk - 0.5 * (nz - 1)) * spacing;
+          cmax = std::max(cmax, std::sqrt(x * x + y * y + z * z));
+        }
+        if (vmin < 0.0) g.rc = std::max(g.rc, cmax);
+        if (vmin < half_eps) g.rinf = std::max(g.rinf, cmax);
+      }
+  if (!(g.rc <= 30.0)) return fail(h, HLBM_ERR_ARG, "circumscribed radius above 30 cells");
+  // volume and second moments per unit density: midpoint rule over 4^3
+  // sub-cells of every grid cell, a sub-cell counting where the blend < 0
+  const int sub = 4;
+  const double dv = (spacing / sub) * (spacing / sub) * (spacing / sub);
+  double V = 0.0, c1[3] = {0.0, 0.0, 0.0}, S[3][3] = {{0.0}};
+  for (int k = 0; k + 1 < nz; ++k)
+    for (int j = 0; j + 1 < ny; ++j)
+      for (int i = 0; i + 1 < nx; ++i)
+        for (int mz = 0; mz < sub; ++mz)
+          for (int my = 0; my < sub; ++my)
+            for (int mx = 0; mx < sub; ++mx) {
+              const double r[3] = {(i + (mx + 0.5) / sub - 0.5 * (nx - 1)) * spacing,
+                                   (j + (my + 0.5) / sub - 0.5 * (ny - 1)) * spacing,
+                                   (k + (mz + 0.5) / sub - 0.5 * (nz - 1)) * spacing};
+              if (!(grid_blend_host(g, r) < 0.0)) continue;
+              V += dv;
+              for (int a = 0; a < 3; ++a) {
+                c1[a] += r[a] * dv;
+                for (int b = 0; b < 3; ++b) S[a][b] += r[a] * r[b] * dv;
+              }
+            }
+  g.V = V;
+  g.I1[0] = S[1][1] + S[2][2];
+  g.I1[1] = S[0][0] + S[2][2];
+  g.I1[2] = S[0][0] + S[1][1];
+  const double imax = std::max(g.I1[0], std::max(g.I1[1], g.I1[2]));
+  bool principal = V > 0.0;
+  for (int a = 0; a < 3; ++a) principal = principal && std::fabs(c1[a] / V) <= spacing / 100.0;
+  principal = principal && std::fabs(S[0][1]) <= 1e-3 * imax && std::fabs(S[0][2]) <= 1e-3 * imax &&
+              std::fabs(S[1][2]) <= 1e-3 * imax;
+  if (!principal)
+    return fail(h, HLBM_ERR_ARG, "the grid's body frame must be its principal frame about the centre of mass");
+  g.off = h->grid_used;
+  GridDesc d{};
+  d.n[0] = nx; d.n[1] = ny; d.n[2] = nz;
+  d.ih = (float)(1.0 / spacing);
+  for (int j = 0; j < 3; ++j) d.half[j] = (float)(0.5 * (g.n[j] - 1));
+  d.off = g.off;
+  const int id = (int)h->grids.size();
+  CK(cudaMemcpyAsync(h->d_gvals + g.off, g.v.data(), sizeof(float) * nv, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_gdesc + id, &d, sizeof(GridDesc), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->grid_used += nv;
+  h->grids.push_back(std::move(g));
+  drop_graphs(h);  // the captured steps name the grids by pointer (set once grids exist)
+  *grid_id = id;
   return HLBM_OK;
 }
 
@@ -560,11 +703,20 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
     if (b < 0 || b >= (int)h->boxes.size()) return fail(h, HLBM_ERR_ARG, "box_id out of range");
     const BoxDesc& bd = h->boxes[b];
     const int s = shape[k];
-    if (s < HLBM_SPHERE || s > HLBM_CAPSULE) return fail(h, HLBM_ERR_ARG, "unknown shape");
+    if (s < HLBM_SPHERE || s > HLBM_GRID) return fail(h, HLBM_ERR_ARG, "unknown shape");
     double a[3];
-    for (int j = 0; j < 3; ++j) {
-      a[j] = (s == HLBM_SPHERE || (s == HLBM_CAPSULE && j == 1)) ? shape_params[3 * k] : shape_params[3 * k + j];
-      if (!(a[j] > 0.0) || !std::isfinite(a[j])) return fail(h, HLBM_ERR_ARG, "shape sizes must be finite and > 0");
+    int gid = -1;
+    if (s == HLBM_GRID) {
+      const double v = shape_params[3 * k];
+      if (!(v >= 0.0 && v < (double)h->grids.size() && v == std::floor(v)))
+        return fail(h, HLBM_ERR_ARG, "a grid particle must name a registered grid");
+      gid = (int)v;
+      for (int j = 0; j < 3; ++j) a[j] = h->grids[gid].rc;  // the record's radius
+    } else {
+      for (int j = 0; j < 3; ++j) {
+        a[j] = (s == HLBM_SPHERE || (s == HLBM_CAPSULE && j == 1)) ? shape_params[3 * k] : shape_params[3 * k + j];
+        if (!(a[j] > 0.0) || !std::isfinite(a[j])) return fail(h, HLBM_ERR_ARG, "shape sizes must be finite and > 0");
+      }
     }
     const double rho = rho_p[k];
     if (!(rho > 0.0) || !std::isfinite(rho)) return fail(h, HLBM_ERR_ARG, "rho_p must be finite and > 0");
@@ -577,7 +729,16 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
       for (int j = 0; j < 4; ++j) q[j] = quat[4 * k + j] / nq;
     }
     double V, m, I[3], rc, rinf;
-    mass_properties(s, a, rho, &V, &m, I, &rc, &rinf, h->prm.eps);
+    if (s == HLBM_GRID) {
+      const auto& g = h->grids[gid];
+      V = g.V;
+      m = rho * V;
+      for (int j = 0; j < 3; ++j) I[j] = rho * g.I1[j];
+      rc = g.rc;
+      rinf = g.rinf;
+    } else {
+      mass_properties(s, a, rho, &V, &m, I, &rc, &rinf, h->prm.eps);
+    }
     if (!(rc <= 30.0)) return fail(h, HLBM_ERR_ARG, "circumscribed radius above 30 cells");
     double x[3];
     const int nn[3] = {bd.nx, bd.ny, bd.nz};
@@ -587,7 +748,9 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
       if (!std::isfinite(x[j]) || !std::isfinite(u) || !std::isfinite(w))
         return fail(h, HLBM_ERR_ARG, "non-finite particle state");
       if ((bd.bc >> j) & 1) {
-        if (!(x[j] > -0.5 && x[j] < nn[j] - 0.5)) return fail(h, HLBM_ERR_ARG, "centre outside the box on a wall axis");
+        const bool cut = j == 2 && (bd.bc & HLBM_CUT_Z);  // a slab's cut faces: centres may lie beyond
+        if (!cut && !(x[j] > -0.5 && x[j] < nn[j] - 0.5))
+          return fail(h, HLBM_ERR_ARG, "centre outside the box on a wall axis");
       } else if (!(2.0 * (rinf + 2.0) < nn[j])) {
         return fail(h, HLBM_ERR_ARG, "particle spans half a periodic axis or more");
       }
@@ -596,7 +759,9 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
       T(PF_I + j, k) = I[j];
       T(PF_II + j, k) = 1.0 / I[j];
       T(PF_A + j, k) = a[j];
-      T(PF_IA + j, k) = (double)(float)(1.0 / a[j]);
+      // a grid particle keeps its grid id here (the record's inverse sizes
+      // are unused for it)
+      T(PF_IA + j, k) = s == HLBM_GRID ? (double)gid : (double)(float)(1.0 / a[j]);
     }
     wrap_host(bd, x);
     for (int j = 0; j < 3; ++j) T(PF_X + j, k) = x[j];
@@ -717,6 +882,7 @@ int hlbm_set_particle_state(hlbm_handle h, const double* X, const double* U, con
 
 int hlbm_step(hlbm_handle h, int nsteps) {
   if (!h) return HLBM_ERR_ARG;
+  if (h->split) return fail(h, HLBM_ERR_STATE, "a split step is open (finish it with hlbm_step_with_forces)");
   if (nsteps < 0) return fail(h, HLBM_ERR_ARG, "nsteps < 0");
   if (nsteps == 0) return HLBM_OK;
   if (!h->graphs_ok) {
@@ -736,6 +902,113 @@ int hlbm_step(hlbm_handle h, int nsteps) {
     h->moments_valid = h->mea_mode == HLBM_MEA_MOMENTS;
   }
   h->steps += nsteps;
+  return HLBM_OK;
+}
+
+// ------------------------------------------------------- z-slab sub-domains
+int hlbm_set_owned_planes(hlbm_handle h, int box, int z_lo, int z_hi) {
+  if (!h) return HLBM_ERR_ARG;
+  if (box < 0 || box >= (int)h->boxes.size()) return fail(h, HLBM_ERR_ARG, "bad box");
+  BoxDesc& bd = h->boxes[box];
+  if (!(bd.bc & HLBM_CUT_Z)) return fail(h, HLBM_ERR_ARG, "owned planes need a box with HLBM_CUT_Z");
+  if (z_lo < 0 || z_hi > bd.nz || z_lo >= z_hi) return fail(h, HLBM_ERR_ARG, "owned planes out of the box");
+  CK(cudaStreamSynchronize(h->stream));
+  bd.own_lo = z_lo;
+  bd.own_hi = z_hi;
+  CK(cudaMemcpyAsync(h->d_boxes + box, &bd, sizeof(BoxDesc), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->moments_valid = false;  // the recorded interior cells may hold ghost planes
+  return HLBM_OK;
+}
+
+int hlbm_plane_slots(hlbm_handle h, int box, int z, int dir, void* host, int put) {
+  if (!h) return HLBM_ERR_ARG;
+  if (box < 0 || box >= (int)h->boxes.size() || !host || (dir != 1 && dir != -1) || (put != 0 && put != 1))
+    return fail(h, HLBM_ERR_ARG, "bad box, direction or buffer");
+  const BoxDesc& bd = h->boxes[box];
+  if (z < 0 || z >= bd.nz) return fail(h, HLBM_ERR_ARG, "plane out of the box");
+  const long long ncell = (long long)bd.nx * bd.ny;
+  const size_t bytes = 5 * (size_t)ncell * (h->prm.precision == HLBM_FP32 ? 4 : 2);
+  if (bytes > sizeof(float) * Q * (size_t)h->L.stage_cells)
+    return fail(h, HLBM_ERR_CAPACITY, "plane larger than the staging area");
+  if (put) CK(cudaMemcpyAsync(h->stage, host, bytes, cudaMemcpyHostToDevice, h->stream));
+  CK(launch_plane_slots(lbm_args(h, 0), h->prm.precision, box, z, dir, (int)ncell, h->stage, put, h->stream));
+  if (!put) CK(cudaMemcpyAsync(host, h->stage, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (put) h->moments_valid = h->moments_valid && h->mea_mode == HLBM_MEA_MOMENTS;
+  return HLBM_OK;
+}
+
+int hlbm_step_forces(hlbm_handle h, double* F, double* T) {
+  if (!h) return HLBM_ERR_ARG;
+  if (h->split) return fail(h, HLBM_ERR_STATE, "a split step is already open");
+  const int n = h->np;
+  if (n > 0 && (!F || !T)) return fail(h, HLBM_ERR_ARG, "NULL force or torque array");
+  const int parity = (int)(h->steps & 1);
+  if (n == 0) {
+    h->split = 1;
+    return HLBM_OK;
+  }
+  const bool moments = h->moments_valid;
+  if (moments) {
+    LbmArgs la = lbm_args(h, parity);
+    CK(launch_mea_moments(la, h->prm.precision, parity, h->walls, h->nsm, h->stream));
+    std::vector<long long> acc((size_t)6 * n);
+    CK(cudaMemcpyAsync(acc.data(), h->acc, sizeof(long long) * acc.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemsetAsync(h->acc, 0, sizeof(long long) * acc.size(), h->stream));
+    const int st = read_status(h);
+    if (st != HLBM_OK) return st;
+    const double unit = 1.0 / (double)(1LL << ACC_FRAC_BITS);
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < 3; ++j) {
+        F[3 * k + j] = (double)acc[6 * (size_t)k + j] * unit;
+        T[3 * k + j] = (double)acc[6 * (size_t)k + 3 + j] * unit;
+      }
+  } else {
+    CK(launch_mea(part_args(h, parity), h->prm.precision, parity, h->stream));
+    std::vector<double> rows((size_t)6 * n);
+    CK(cudaMemcpy2DAsync(rows.data(), sizeof(double) * n, h->P + (size_t)PF_F * h->L.cap, sizeof(double) * h->L.cap,
+                         sizeof(double) * n, 6, cudaMemcpyDeviceToHost, h->stream));
+    const int st = read_status(h);
+    if (st != HLBM_OK) return st;
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < 3; ++j) {
+        F[3 * k + j] = rows[(size_t)j * n + k];
+        T[3 * k + j] = rows[(size_t)(3 + j) * n + k];
+      }
+  }
+  h->split = moments ? 2 : 1;
+  return HLBM_OK;
+}
+
+int hlbm_step_with_forces(hlbm_handle h, const double* F, const double* T) {
+  if (!h) return HLBM_ERR_ARG;
+  if (!h->split) return fail(h, HLBM_ERR_STATE, "no split step is open (call hlbm_step_forces first)");
+  const int n = h->np;
+  if (n > 0 && (!F || !T)) return fail(h, HLBM_ERR_ARG, "NULL force or torque array");
+  for (int k = 0; k < 3 * n; ++k)
+    if (!std::isfinite(F[k]) || !std::isfinite(T[k])) return fail(h, HLBM_ERR_ARG, "non-finite force or torque");
+  const int parity = (int)(h->steps & 1);
+  if (n > 0) {
+    std::vector<double> rows((size_t)6 * n);
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < 3; ++j) {
+        rows[(size_t)j * n + k] = F[3 * k + j];
+        rows[(size_t)(3 + j) * n + k] = T[3 * k + j];
+      }
+    CK(cudaMemcpy2DAsync(h->P + (size_t)PF_F * h->L.cap, sizeof(double) * h->L.cap, rows.data(), sizeof(double) * n,
+                         sizeof(double) * n, 6, cudaMemcpyHostToDevice, h->stream));
+    PartArgs pa = part_args(h, parity);
+    pa.from_acc = 0;
+    CK(launch_contact(pa, h->stream));
+    CK(launch_update(pa, h->stream));
+  }
+  CK(launch_collide(lbm_args(h, parity), h->prm.precision, parity, h->walls, n > 0, h->stream));
+  CK(cudaStreamSynchronize(h->stream));  // the host rows above are released
+  h->split = 0;
+  h->steps += 1;
+  h->moments_valid = h->mea_mode == HLBM_MEA_MOMENTS;
+  h->hst_valid = false;
   return HLBM_OK;
 }
 
@@ -1021,18 +1294,19 @@ int hlbm_interior_cells(hlbm_handle h, long long* n) {
 }  // extern "C"
 // ---------------------------------------------------------------- snapshots
 // Layout (host byte order, no padding): the header below; per box nx, ny,
-// nz, bc (int64); shape and box id per particle (int32); the particle
+// nz, bc (int64); per distance grid nx, ny, nz (int64), the spacing and the
+// samples (FP32); shape and box id per particle (int32); the particle
 // table, PF_COUNT rows of np doubles; the interior-cell list when the next
 // step takes its momentum exchange from it (ILIST_STRIPES int32 counts,
 // then per stripe its int2 entries and its float4 moments); the populations
 // as stored (the handle's own block layout and precision).
 namespace {
 
-constexpr char CK_MAGIC[8] = {'H', 'L', 'B', 'M', 'C', 'K', 'P', '2'};
+constexpr char CK_MAGIC[8] = {'H', 'L', 'B', 'M', 'C', 'K', 'P', '3'};
 
 struct CkHeader {
   char magic[8];
-  int64_t nboxes, precision, fp16_scale_log2, np, pf_count, steps, mea_mode, has_list, pop_bytes;
+  int64_t nboxes, precision, fp16_scale_log2, np, pf_count, steps, mea_mode, has_list, pop_bytes, ngrids;
   double tau, eps, gravity[3], fluid_force[3], contact_k, contact_zeta;
 };
 
@@ -1048,6 +1322,7 @@ int snapshot_plan(hlbm_ctx* h, size_t* total, bool* has_list, int cnt[ILIST_STRI
   *has_list = h->np > 0 && h->moments_valid && h->mea_mode == HLBM_MEA_MOMENTS && h->ilist_idx;
   size_t t = sizeof(CkHeader) + sizeof(int64_t) * 4 * h->boxes.size() + sizeof(int32_t) * 2 * (size_t)h->np +
              sizeof(double) * PF_COUNT * (size_t)h->np;
+  for (const auto& g : h->grids) t += sizeof(int64_t) * 3 + sizeof(double) + sizeof(float) * g.v.size();
   if (*has_list) {
     CK(cudaMemcpyAsync(cnt, h->ilist_count, sizeof(int) * ILIST_STRIPES, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1100,6 +1375,7 @@ int hlbm_save(hlbm_handle h, void* buf, size_t bytes) {
   hd.eps = h->prm.eps;
   hd.contact_k = h->contact_k;
   hd.contact_zeta = h->contact_zeta;
+  hd.ngrids = (int64_t)h->grids.size();
   for (int j = 0; j < 3; ++j) {
     hd.gravity[j] = h->prm.gravity[j];
     hd.fluid_force[j] = h->prm.fluid_force[j];
@@ -1108,6 +1384,12 @@ int hlbm_save(hlbm_handle h, void* buf, size_t bytes) {
   for (const BoxDesc& b : h->boxes) {
     const int64_t d[4] = {b.nx, b.ny, b.nz, b.bc};
     put(d, sizeof(d));
+  }
+  for (const auto& g : h->grids) {
+    const int64_t d[3] = {g.n[0], g.n[1], g.n[2]};
+    put(d, sizeof(d));
+    put(&g.h, sizeof(double));
+    put(g.v.data(), sizeof(float) * g.v.size());
   }
   const size_t np = (size_t)h->np;
   for (size_t k = 0; k < np; ++k) { const int32_t v = h->h_shape[k]; put(&v, sizeof(v)); }
@@ -1136,8 +1418,9 @@ int hlbm_save(hlbm_handle h, void* buf, size_t bytes) {
 int hlbm_load(hlbm_handle h, const void* buf, size_t bytes) {
   if (!h) return HLBM_ERR_ARG;
   if (!buf) return fail(h, HLBM_ERR_ARG, "NULL buffer");
-  if (h->steps != 0 || h->np != 0)
-    return fail(h, HLBM_ERR_STATE, "a snapshot loads into a new handle (no step taken, no particles added)");
+  if (h->steps != 0 || h->np != 0 || !h->grids.empty())
+    return fail(h, HLBM_ERR_STATE,
+                "a snapshot loads into a new handle (no step taken, no particles or grids added)");
   const char* i = (const char*)buf;
   const char* end = i + bytes;
   auto get = [&](void* dst, size_t n) -> bool {
@@ -1159,7 +1442,8 @@ int hlbm_load(hlbm_handle h, const void* buf, size_t bytes) {
   if (hd.np < 0 || hd.np > h->L.cap) return fail(h, HLBM_ERR_ARG, "snapshot holds more particles than max_particles");
   bool finite_force = true;
   for (int j = 0; j < 3; ++j) finite_force = finite_force && std::isfinite(hd.fluid_force[j]);
-  if (hd.steps < 0 || (hd.mea_mode != HLBM_MEA_KERNEL && hd.mea_mode != HLBM_MEA_MOMENTS) || !finite_force ||
+  if (hd.steps < 0 || hd.ngrids < 0 || hd.ngrids > MAX_GRIDS ||
+      (hd.mea_mode != HLBM_MEA_KERNEL && hd.mea_mode != HLBM_MEA_MOMENTS) || !finite_force ||
       !(hd.contact_k >= 0.0) || !std::isfinite(hd.contact_k) || !(hd.contact_zeta > 0.0) ||
       !std::isfinite(hd.contact_zeta))
     return fail(h, HLBM_ERR_ARG, "corrupt snapshot header");
@@ -1169,6 +1453,22 @@ int hlbm_load(hlbm_handle h, const void* buf, size_t bytes) {
     const BoxDesc& B = h->boxes[b];
     if (d[0] != B.nx || d[1] != B.ny || d[2] != B.nz || d[3] != B.bc)
       return fail(h, HLBM_ERR_ARG, "snapshot of other boxes or another storage precision");
+  }
+  // the distance grids, registered again (checks and derived properties)
+  for (int64_t k = 0; k < hd.ngrids; ++k) {
+    int64_t d[3];
+    double sp;
+    if (!get(d, sizeof(d)) || !get(&sp, sizeof(sp))) return fail(h, HLBM_ERR_ARG, "truncated snapshot");
+    if (d[0] < 2 || d[1] < 2 || d[2] < 2 || d[0] > (1 << 20) || d[1] > (1 << 20) || d[2] > (1 << 20))
+      return fail(h, HLBM_ERR_ARG, "corrupt grid in snapshot");
+    const size_t nv = (size_t)(d[0] * d[1] * d[2]);
+    if ((size_t)(end - i) < sizeof(float) * nv) return fail(h, HLBM_ERR_ARG, "truncated snapshot");
+    std::vector<float> v(nv);
+    std::memcpy(v.data(), i, sizeof(float) * nv);
+    i += sizeof(float) * nv;
+    int id = -1;
+    const int rc = hlbm_add_grid(h, (int)d[0], (int)d[1], (int)d[2], sp, v.data(), &id);
+    if (rc != HLBM_OK) return rc;
   }
   const int n = (int)hd.np;
   std::vector<int32_t> shp(n), bx(n);
@@ -1199,7 +1499,8 @@ int hlbm_load(hlbm_handle h, const void* buf, size_t bytes) {
     auto row = [&](int fld, int k) { return tab[(size_t)fld * n + k]; };
     for (int k = 0; k < n; ++k) {
       for (int j = 0; j < 3; ++j) {
-        a[3 * k + j] = row(PF_A + j, k);
+        // a grid particle names its grid (kept in PF_IA), the others their sizes
+        a[3 * k + j] = shp[k] == HLBM_GRID ? row(PF_IA + j, k) : row(PF_A + j, k);
         X[3 * k + j] = row(PF_X + j, k);
         U[3 * k + j] = row(PF_U + j, k);
         W[3 * k + j] = row(PF_W + j, k);

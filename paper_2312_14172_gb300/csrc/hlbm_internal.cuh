@@ -50,13 +50,23 @@ __host__ __device__ constexpr double wq(int i) {
 }
 
 struct BoxDesc {
-  int nx, ny, nz, bc;        // bc: bit a set = walls on axis a
+  int nx, ny, nz, bc;        // bc: bit a set = walls on axis a; BC_CUT_Z: see below
   int ntx, nty, ntz;         // bin tiles per axis (ntx = storage blocks per row)
+  int own_lo, own_hi;        // owned z planes [own_lo, own_hi) of a BC_CUT_Z box
   int pad0;
   long long cell_off;        // first cell of the box in the global cell numbering
   long long tile_off;        // first bin tile of the box
   long long blk_off;         // first storage block of the box
 };
+
+// A box with BC_CUT_Z (set together with the z-wall bit) is one z slab of a
+// larger lattice: its z faces bound the lattice as walls do (only its ghost
+// planes meet them), particle centres may lie beyond them, and only the
+// cells of the owned planes [own_lo, own_hi) enter the momentum exchange.
+constexpr int BC_CUT_Z = 8;
+__host__ __device__ __forceinline__ bool owned_plane(const BoxDesc& bd, int z) {
+  return !(bd.bc & BC_CUT_Z) || (z >= bd.own_lo && z < bd.own_hi);
+}
 
 // blocked population storage (layout above)
 constexpr int VB = 32;       // cells per storage block (= TILE_X)
@@ -89,16 +99,63 @@ constexpr int MAX_PLANES = 64;
 // stripes of the list of interior cells (a power of two)
 constexpr int ILIST_STRIPES = 64;
 
+// Signed-distance grids (shape 4): FP32 samples of a body-frame signed
+// distance, point (i, j, k) at ((i - half_0) h, (j - half_1) h, (k - half_2) h)
+// with half_j = (n_j - 1) / 2, x fastest, starting at element `off` of the
+// handle's grid array.
+constexpr int MAX_GRIDS = 64;
+struct GridDesc {
+  int n[3];
+  float ih;       // fp32(1 / h)
+  float half[3];  // fp32((n_j - 1) / 2)
+  int pad;
+  long long off;
+};
+struct GridSet {
+  const GridDesc* desc;  // MAX_GRIDS entries
+  const float* vals;
+};
+
+// The blend of the grid at body offset b, every operation rounded on its own
+// in this order (the FP32 inside test; the oracle rounds the same steps):
+//   x_j = b_j * ih + half_j; outside [0, n_j - 1]: +inf
+//   i_j = min(floor(x_j), n_j - 2), t_j = x_j - i_j
+//   lerp(a, b, t) = a + t * (b - a) along x (four), then y (two), then z.
+__device__ __forceinline__ float grid_blend_rn(const GridDesc& g, const float* v, const float b[3]) {
+  float t[3];
+  int i0[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float x = __fadd_rn(__fmul_rn(b[j], g.ih), g.half[j]);
+    if (!(x >= 0.0f && x <= (float)(g.n[j] - 1))) return __int_as_float(0x7f800000);
+    const int i = min((int)floorf(x), g.n[j] - 2);
+    i0[j] = i;
+    t[j] = __fsub_rn(x, (float)i);
+  }
+  const float* c = v + g.off + ((long long)i0[2] * g.n[1] + i0[1]) * g.n[0] + i0[0];
+  const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
+  auto lerp = [](float a, float b_, float tt) { return __fadd_rn(a, __fmul_rn(tt, __fsub_rn(b_, a))); };
+  const float e00 = lerp(c[0], c[1], t[0]);
+  const float e01 = lerp(c[sy], c[sy + 1], t[0]);
+  const float e10 = lerp(c[sz], c[sz + 1], t[0]);
+  const float e11 = lerp(c[sz + sy], c[sz + sy + 1], t[0]);
+  const float f0 = lerp(e00, e01, t[1]);
+  const float f1 = lerp(e10, e11, t[1]);
+  return lerp(f0, f1, t[2]);
+}
+
 // FP32 coupling record of one particle (128 bytes)
 struct __align__(16) Rec {
   float xh[3], xl[3];  // centre as float pair: X = xh + xl
   float u[3], w[3];    // velocity, angular velocity
   float M[9];          // rotation body -> world, row-major; a sphere's
                        // first four: its collision bounds (SPH_* below)
-  float a[3];          // radius / semi-axes / half-extents / capsule (r, r, h)
+  float a[3];          // radius / semi-axes / half-extents / capsule (r, r, h);
+                       // a grid's circumscribed radius
   float ia[3];         // fp32(1 / a_j) (ellipsoid inside test)
   float rinf2;         // square of a radius beyond which B = 0
-  float in2;           // fp32(r * r) (sphere and capsule inside tests)
+  float in2;           // fp32(r * r) (sphere and capsule inside tests); a
+                       // grid particle: its grid id (int bits)
   int shape;
   int box;
   int pid;
@@ -262,6 +319,7 @@ struct LbmArgs {
   long long ilist_cap;
   int np;                   // particles (list entries name 0 .. np-1)
   long long* acc;           // [cap][6] momentum exchange of a particle, fixed point
+  GridSet grids;            // signed-distance grids of shape-4 particles
   int* status;
 };
 
@@ -293,6 +351,7 @@ struct PartArgs {
   // contact between the particles' enclosing capsules and with the walls
   // (an extension; off when contact_k == 0): stiffness and range
   double contact_k, contact_zeta;
+  GridSet grids;            // signed-distance grids of shape-4 particles
   int nsm;                  // SMs of the GPU (update grid size)
   int ppb;                  // particles per update block (set by the launcher)
   int* ilist_count;         // [ILIST_STRIPES], reset by the update for the next collision
@@ -325,7 +384,7 @@ __device__ __forceinline__ float offset_fp32(int cell, int n, bool wall, float x
   return __fsub_rn(r0, xl);
 }
 
-__device__ __forceinline__ bool inside_from_offset(const Rec& R, const float r[3]) {
+__device__ __forceinline__ bool inside_from_offset(const Rec& R, const float r[3], GridSet gs = GridSet{}) {
   if (R.shape == 0) {
     float s = __fmul_rn(r[0], r[0]);
     s = __fadd_rn(s, __fmul_rn(r[1], r[1]));
@@ -349,6 +408,10 @@ __device__ __forceinline__ bool inside_from_offset(const Rec& R, const float r[3
     s = __fadd_rn(s, __fmul_rn(e2, e2));
     return s < 1.0f;
   }
+  if (R.shape == 4) {
+    if (!gs.desc) return false;
+    return grid_blend_rn(gs.desc[__float_as_int(R.in2)], gs.vals, b) < 0.0f;
+  }
   if (R.shape == 3) {
     const float c = b[2] < -R.a[2] ? -R.a[2] : (b[2] > R.a[2] ? R.a[2] : b[2]);
     const float t = __fsub_rn(b[2], c);
@@ -361,11 +424,11 @@ __device__ __forceinline__ bool inside_from_offset(const Rec& R, const float r[3
 }
 
 __device__ __forceinline__ bool inside_fp32(const Rec& R, const BoxDesc& bd, int x, int y, int z,
-                                            float r[3]) {
+                                            float r[3], GridSet gs = GridSet{}) {
   r[0] = offset_fp32(x, bd.nx, bd.bc & 1, R.xh[0], R.xl[0]);
   r[1] = offset_fp32(y, bd.ny, bd.bc & 2, R.xh[1], R.xl[1]);
   r[2] = offset_fp32(z, bd.nz, bd.bc & 4, R.xh[2], R.xl[2]);
-  return inside_from_offset(R, r);
+  return inside_from_offset(R, r, gs);
 }
 
 // launchers (stream-ordered, no synchronisation)
@@ -390,6 +453,10 @@ cudaError_t launch_gather(const LbmArgs& a, int precision, int parity, int box, 
                           long long n, float* stage, cudaStream_t s);
 cudaError_t launch_scatter(const LbmArgs& a, int precision, int parity, int box, long long c0,
                            long long n, const float* stage, cudaStream_t s);
+// the five stored slots with c_z = dir of the cells of plane z of one box
+// (ncell = nx ny of the box), to (put = 0) or from (put = 1) stage
+cudaError_t launch_plane_slots(const LbmArgs& a, int precision, int box, int z, int dir, int ncell, void* stage,
+                               int put, cudaStream_t s);
 // FP64 mass deviation and momentum of one box: `blocks` partial sums of 4
 // values into out[4 * blocks]
 cudaError_t launch_fluid_moments(const LbmArgs& a, int precision, int parity, int box, int blocks,

@@ -114,13 +114,32 @@ __device__ __forceinline__ float indicator(float d, float eps, float inv_eps) {
   return 0.5f - 0.5f * sinpi_ramp(d * inv_eps);
 }
 
+// trilinear blend of a distance grid at body offset b (FP32, contracted;
+// +inf outside the grid: no coupling there)
+__device__ __forceinline__ float grid_blend(const GridDesc& g, const float* v, float b0, float b1, float b2) {
+  const float x = fmaf(b0, g.ih, g.half[0]), y = fmaf(b1, g.ih, g.half[1]), z = fmaf(b2, g.ih, g.half[2]);
+  if (!(x >= 0.0f && x <= (float)(g.n[0] - 1) && y >= 0.0f && y <= (float)(g.n[1] - 1) && z >= 0.0f &&
+        z <= (float)(g.n[2] - 1)))
+    return __int_as_float(0x7f800000);
+  const int ix = min((int)x, g.n[0] - 2), iy = min((int)y, g.n[1] - 2), iz = min((int)z, g.n[2] - 2);
+  const float tx = x - (float)ix, ty = y - (float)iy, tz = z - (float)iz;
+  const float* c = v + g.off + ((long long)iz * g.n[1] + iy) * g.n[0] + ix;
+  const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
+  const float e00 = fmaf(tx, c[1] - c[0], c[0]), e01 = fmaf(tx, c[sy + 1] - c[sy], c[sy]);
+  const float e10 = fmaf(tx, c[sz + 1] - c[sz], c[sz]), e11 = fmaf(tx, c[sz + sy + 1] - c[sz + sy], c[sz + sy]);
+  const float f0 = fmaf(ty, e01 - e00, e00), f1 = fmaf(ty, e11 - e10, e10);
+  return fmaf(tz, f1 - f0, f0);
+}
+
 // signed distance of a particle at offset r (world frame), FP32
-__device__ __forceinline__ float sdf(const Rec& R, float rx, float ry, float rz, float r2) {
+__device__ __forceinline__ float sdf(const Rec& R, float rx, float ry, float rz, float r2, GridSet gs = GridSet{}) {
   if (R.shape == 0) return (r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f) - R.a[0];
   // body frame b = M^T r
   const float b0 = R.M[0] * rx + R.M[3] * ry + R.M[6] * rz;
   const float b1 = R.M[1] * rx + R.M[4] * ry + R.M[7] * rz;
   const float b2 = R.M[2] * rx + R.M[5] * ry + R.M[8] * rz;
+  if (R.shape == 4) return gs.desc ? grid_blend(gs.desc[__float_as_int(R.in2)], gs.vals, b0, b1, b2)
+                                   : __int_as_float(0x7f800000);
   if (R.shape == 3) {
     const float t = b2 - fminf(fmaxf(b2, -R.a[2]), R.a[2]);
     return sqrtf(b0 * b0 + b1 * b1 + t * t) - R.a[0];
@@ -186,6 +205,7 @@ __device__ __forceinline__ Brick brick_of(const LbmArgs& a) {
 //   cuboid     the box grown by eps/2 lies in the capsule along its longest
 //              half-extent h_k of radius |(h_i, h_j)| + eps/2 and half-length h_k
 //   capsule    itself grown by eps/2: radius a0 + eps/2 about its body-z segment
+//   grid       the sphere of its influence radius (rinf2 of the record)
 // The radius carries a margin of 1e-3 relative + 0.01 cells over FP32 rounding.
 struct Capsule {
   float u[3], h, r2;
@@ -198,6 +218,12 @@ __device__ __forceinline__ Capsule capsule_of(const Rec& R, float eps) {
     c.h = 0.0f;
     const float r = R.a[0] + 0.5f * eps;
     c.r2 = (r * 1.001f + 0.01f) * (r * 1.001f + 0.01f);
+    return c;
+  }
+  if (R.shape == 4) {
+    c.u[0] = 1.0f; c.u[1] = c.u[2] = 0.0f;
+    c.h = 0.0f;
+    c.r2 = R.rinf2;
     return c;
   }
   if (R.shape == 3) {
@@ -320,10 +346,12 @@ struct RowCoupling {
   int bestp[N], ip0[N], ip1[N];
 };
 
-template <int N>
+template <int N, bool GRIDS>
 __device__ __forceinline__ void couple_row(const Rec* srec, unsigned long long rm, const BoxDesc& bd,
                                            int x, int y, int z, float eps, float inv_eps, int* status,
-                                           RowCoupling<N>& cc) {
+                                           RowCoupling<N>& cc, GridSet grids) {
+  // without grid particles the grid branches fold away (null grid set)
+  const GridSet gs = GRIDS ? grids : GridSet{};
 #pragma unroll
   for (int j = 0; j < N; ++j) {
     cc.B[j] = 0.0f;
@@ -395,11 +423,11 @@ __device__ __forceinline__ void couple_row(const Rec* srec, unsigned long long r
         const float rx = arm_x(j);
         const float r2 = rx * rx + d2;
         if (r2 < R.rinf2 && capsule_dist2(cap, rx, ry, rz) < cap.r2) {
-          const float d = sdf(R, rx, ry, rz, r2);
+          const float d = sdf(R, rx, ry, rz, r2, gs);
           bool in;
           if (d < -1e-3f) in = true;
           else if (d > 1e-3f) in = false;
-          else { const float rr[3] = {rx, ry, rz}; in = inside_from_offset(R, rr); }
+          else { const float rr[3] = {rx, ry, rz}; in = inside_from_offset(R, rr, gs); }
           take(j, rx, in, indicator(d, eps, inv_eps));
         }
       }

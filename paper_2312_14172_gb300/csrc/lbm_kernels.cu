@@ -21,8 +21,11 @@ namespace hlbm {
 #define HLBM_CS_MINBLOCKS 4
 #endif
 
-template <typename S, int PAR, bool WALLS, bool COUPLE>
+// C: 0 no particles, 1 particles of the analytic shapes, 2 with distance
+// grids among them
+template <typename S, int PAR, bool WALLS, int C>
 __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(LbmArgs a) {
+  constexpr bool COUPLE = C > 0;
   __shared__ Rec srec[COUPLE ? MAX_CAND : 1];
   // per row of the brick (local y + sub_y * local z): the candidates whose
   // influence sphere meets the row
@@ -69,8 +72,8 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
     // positions only and runs while the loads above are in flight
     RowCoupling<1> cc;
     if (COUPLE)
-      couple_row<1>(srec, s_rowmask[threadIdx.y + a.sub_y * (z - z0)], bd, x, y, z, a.eps, a.inv_eps,
-                    a.status, cc);
+      couple_row<1, (C > 1)>(srec, s_rowmask[threadIdx.y + a.sub_y * (z - z0)], bd, x, y, z, a.eps,
+                             a.inv_eps, a.status, cc, a.grids);
     float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
           if (cz(i)) mom[0].w += (float)cz(i) * v;
         }
       }
-      append_interior<1>(a, g, cc, mom);
+      if (owned_plane(bd, z)) append_interior<1>(a, g, cc, mom);
     }
   }
   if (!early) pdl_trigger();
@@ -333,7 +336,7 @@ __global__ void __launch_bounds__(256, WALLS ? 4 : 5) mea_list_kernel(LbmArgs a)
   }
 }
 
-template <typename S, int PAR, bool W, bool C>
+template <typename S, int PAR, bool W, int C>
 static cudaError_t launch_cs(const LbmArgs& a, cudaStream_t s) {
   dim3 block(TILE_X, a.sub_y);
   LbmArgs b = a;
@@ -342,15 +345,18 @@ static cudaError_t launch_cs(const LbmArgs& a, cudaStream_t s) {
   return launch_k(collide_stream_kernel<S, PAR, W, C>, dim3((unsigned)a.nbricks), block, 0, s, a.pdl != 0, b);
 }
 
+template <typename S, int C>
+static cudaError_t launch_cs_c(const LbmArgs& a, int parity, bool walls, cudaStream_t s) {
+  // even steps never touch a neighbour: walls need no special case
+  if (parity == 0) return launch_cs<S, 0, false, C>(a, s);
+  return walls ? launch_cs<S, 1, true, C>(a, s) : launch_cs<S, 1, false, C>(a, s);
+}
+
 template <typename S>
 static cudaError_t launch_cs_prec(const LbmArgs& a, int parity, bool walls, bool couple,
                                   cudaStream_t s) {
-  if (parity == 0) {
-    // even steps never touch a neighbour: walls need no special case
-    return couple ? launch_cs<S, 0, false, true>(a, s) : launch_cs<S, 0, false, false>(a, s);
-  }
-  if (walls) return couple ? launch_cs<S, 1, true, true>(a, s) : launch_cs<S, 1, true, false>(a, s);
-  return couple ? launch_cs<S, 1, false, true>(a, s) : launch_cs<S, 1, false, false>(a, s);
+  if (!couple) return launch_cs_c<S, 0>(a, parity, walls, s);
+  return a.grids.desc ? launch_cs_c<S, 2>(a, parity, walls, s) : launch_cs_c<S, 1>(a, parity, walls, s);
 }
 
 cudaError_t launch_collide(const LbmArgs& a, int precision, int parity, bool walls, bool couple,
@@ -470,6 +476,35 @@ cudaError_t launch_fluid_moments(const LbmArgs& a, int precision, int parity, in
     if (parity == 0) fluid_moments_kernel<__half, 0><<<blocks, 256, 0, s>>>(a, box, out);
     else fluid_moments_kernel<__half, 1><<<blocks, 256, 0, s>>>(a, box, out);
   }
+  return cudaGetLastError();
+}
+
+// the five slots {i : c_iz = dir} of every cell of plane z of one box, as
+// stored, to or from stage[(k ny + y) nx + x] (k the slot's rank in the set)
+template <typename S>
+__global__ void plane_slots_kernel(LbmArgs a, int box, int z, int dir, S* stage, int put) {
+  const BoxDesc bd = a.boxes[box];
+  const long long n = (long long)bd.nx * bd.ny;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= 5 * n) return;
+  const int k = (int)(t / n);
+  const long long c = t - k * n;
+  const int y = (int)(c / bd.nx), x = (int)(c - (long long)y * bd.nx);
+  // slots with c_z = +1: 5, 11, 14, 15, 18; with c_z = -1 their opposites
+  const int plus[5] = {5, 11, 14, 15, 18};
+  const int i = dir > 0 ? plus[k] : opp(plus[k]);
+  S* f = reinterpret_cast<S*>(a.f) + elem_of(bd, x, y, z) + i * VB;
+  if (put) *f = stage[t];
+  else stage[t] = *f;
+}
+
+cudaError_t launch_plane_slots(const LbmArgs& a, int precision, int box, int z, int dir, int ncell, void* stage,
+                               int put, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((5LL * ncell + 255) / 256);
+  if (precision == 0)
+    plane_slots_kernel<float><<<blocks, 256, 0, s>>>(a, box, z, dir, reinterpret_cast<float*>(stage), put);
+  else
+    plane_slots_kernel<__half><<<blocks, 256, 0, s>>>(a, box, z, dir, reinterpret_cast<__half*>(stage), put);
   return cudaGetLastError();
 }
 

@@ -89,8 +89,11 @@ __device__ __forceinline__ void moments2(const typename T::raw (&d)[Q], float2& 
 template <typename S>
 struct PairBlocks { static constexpr int value = sizeof(S) == 4 ? HLBM_CP_MINBLOCKS_F32 : HLBM_CP_MINBLOCKS_F16; };
 
-template <typename S, int PAR, bool WALLS, bool COUPLE>
+// C: 0 no particles, 1 particles of the analytic shapes, 2 with distance
+// grids among them
+template <typename S, int PAR, bool WALLS, int C>
 __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel(LbmArgs a) {
+  constexpr bool COUPLE = C > 0;
   using T = Two<S>;
   __shared__ Rec srec[COUPLE ? MAX_CAND : 1];
   __shared__ unsigned long long s_rowmask[COUPLE ? TILE_Y * TILE_Z : 1];
@@ -152,8 +155,8 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
     // loads above are in flight
     RowCoupling<2> cc;
     if (COUPLE) {
-      couple_row<2>(srec, s_rowmask[threadIdx.y + a.sub_y * (z - z0)], bd, x0, y, z, a.eps, a.inv_eps,
-                    a.status, cc);
+      couple_row<2, (C > 1)>(srec, s_rowmask[threadIdx.y + a.sub_y * (z - z0)], bd, x0, y, z, a.eps,
+                             a.inv_eps, a.status, cc, a.grids);
       if (single) cc.ip0[1] = cc.ip1[1] = -1;
     }
     // mass and momentum of the arrivals
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
         }
       }
     }
-    if (COUPLE && a.ilist_idx)
+    if (COUPLE && a.ilist_idx && owned_plane(bd, z))
       append_interior<2>(a, (unsigned)(bd.cell_off + (z * bd.ny + y) * bd.nx + x0), cc, mom);
   };
   // one z slice at a time: an unrolled loop would hold two slices' arrivals
@@ -283,7 +286,7 @@ __global__ void __launch_bounds__(128, PairBlocks<S>::value) collide_pair_kernel
   if (!early) pdl_trigger();
 }
 
-template <typename S, int PAR, bool W, bool C>
+template <typename S, int PAR, bool W, int C>
 static cudaError_t launch_cp(const LbmArgs& a, cudaStream_t s) {
   dim3 block(TILE_X / 2, a.sub_y);
   LbmArgs b = a;
@@ -293,12 +296,17 @@ static cudaError_t launch_cp(const LbmArgs& a, cudaStream_t s) {
   return launch_k(collide_pair_kernel<S, PAR, W, C>, dim3((unsigned)a.nbricks), block, 0, s, a.pdl != 0, b);
 }
 
+template <typename S, int C>
+static cudaError_t launch_cp_c(const LbmArgs& a, int parity, bool walls, cudaStream_t s) {
+  if (parity == 0) return launch_cp<S, 0, false, C>(a, s);
+  return walls ? launch_cp<S, 1, true, C>(a, s) : launch_cp<S, 1, false, C>(a, s);
+}
+
 template <typename S>
 static cudaError_t launch_cp_prec(const LbmArgs& a, int parity, bool walls, bool couple,
                                   cudaStream_t s) {
-  if (parity == 0) return couple ? launch_cp<S, 0, false, true>(a, s) : launch_cp<S, 0, false, false>(a, s);
-  if (walls) return couple ? launch_cp<S, 1, true, true>(a, s) : launch_cp<S, 1, true, false>(a, s);
-  return couple ? launch_cp<S, 1, false, true>(a, s) : launch_cp<S, 1, false, false>(a, s);
+  if (!couple) return launch_cp_c<S, 0>(a, parity, walls, s);
+  return a.grids.desc ? launch_cp_c<S, 2>(a, parity, walls, s) : launch_cp_c<S, 1>(a, parity, walls, s);
 }
 
 cudaError_t launch_collide_pair(const LbmArgs& a, int precision, int parity, bool walls, bool couple,

@@ -100,7 +100,7 @@ template <typename S, int PAR, bool BLOCKED>
 __device__ __forceinline__ void mea_plane_sums(const Rec& R, const BoxDesc& bd, const double X[3],
                                                double rc, int iz, const S* f, long long plane,
                                                float inv_scale, int* s_start, int* s_xa,
-                                               float out[6]) {
+                                               float out[6], GridSet gs = GridSet{}) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n[3] = {bd.nx, bd.ny, bd.nz};
   // cells that can be inside: [floor(X - r_c), ceil(X + r_c)] per axis
@@ -110,8 +110,9 @@ __device__ __forceinline__ void mea_plane_sums(const Rec& R, const BoxDesc& bd, 
     for (int j = 0; j < 3; ++j) {
       int l = (int)floor(X[j] - rc), h = (int)ceil(X[j] + rc);
       if ((bd.bc >> j) & 1) {
-        l = max(l, 0);
-        h = min(h, n[j] - 1);
+        const bool cut = j == 2 && (bd.bc & BC_CUT_Z);  // owned planes only
+        l = max(l, cut ? bd.own_lo : 0);
+        h = min(h, cut ? bd.own_hi - 1 : n[j] - 1);
       }
       lo[j] = l;
       ext[j] = min(max(h - l + 1, 0), MAX_PLANES);
@@ -156,7 +157,7 @@ __device__ __forceinline__ void mea_plane_sums(const Rec& R, const BoxDesc& bd, 
       const int x = xu < 0 ? xu + n[0] : (xu >= n[0] ? xu - n[0] : xu);
       const int y = yu < 0 ? yu + n[1] : (yu >= n[1] ? yu - n[1] : yu);
       float rr[3];
-      if (!inside_fp32(R, bd, x, y, z, rr)) continue;
+      if (!inside_fp32(R, bd, x, y, z, rr, gs)) continue;
       float Fc[3], mg;
       if constexpr (BLOCKED) {
         mea_cell<S, PAR>(f, (long long)VB, make_nbr_blocked(bd, x, y, z), elem_of(bd, x, y, z), inv_scale,

@@ -42,6 +42,7 @@ __device__ __forceinline__ void make_record(const double X[3], const double U[3]
   }
   for (int k = 0; k < 9; ++k) R.M[k] = __double2float_rn(Rm[k]);
   R.in2 = __double2float_rn(A[0] * A[0]);
+  if (shape == 4) R.in2 = __int_as_float((int)iA[0]);  // a grid particle: its grid id
   if (shape == 0) {
     // a sphere needs no rotation: its slots hold the FP32 bounds of the
     // collision's per-cell tests (the same roundings as computed there)
@@ -79,7 +80,7 @@ __device__ void build_record(const double* P, int cap, int p, int shape, int box
 #define HLBM_MEA_MINBLOCKS 8
 #endif
 
-template <typename S, int PAR>
+template <typename S, int PAR, bool GRIDS>
 __global__ void __launch_bounds__(128, HLBM_MEA_MINBLOCKS) mea_kernel(PartArgs a) {
   pdl_trigger();
   pdl_wait();
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(128, HLBM_MEA_MINBLOCKS) mea_kernel(PartArgs a
   float sums[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (ok) {
     mea_plane_sums<S, PAR, true>(R, bd, X, rc, iz, reinterpret_cast<const S*>(a.f), 0, a.inv_scale, s_start,
-                                 s_xa, sums);
+                                 s_xa, sums, GRIDS ? a.grids : GridSet{});
   } else if (tid == 0) {
     atomicOr(a.status, ST_UNSTABLE);
   }
@@ -300,7 +301,9 @@ __device__ __forceinline__ BinRange update_particle(const PartArgs& a, int p) {
   const int n[3] = {bd.nx, bd.ny, bd.nz};
   for (int j = 0; j < 3; ++j) {
     if ((bd.bc >> j) & 1) {
-      if (!(X[j] > -0.5 && X[j] < n[j] - 0.5)) atomicOr(a.status, ST_LEFT_DOMAIN);
+      // a slab's cut z faces are not walls: centres may lie beyond them
+      const bool cut = j == 2 && (bd.bc & BC_CUT_Z);
+      if (!cut && !(X[j] > -0.5 && X[j] < n[j] - 0.5)) atomicOr(a.status, ST_LEFT_DOMAIN);
     } else {
       // a particle moves far less than a box length per step
       const double L = (double)n[j];
@@ -398,7 +401,7 @@ __device__ __forceinline__ void contact_capsule(const double* P, int cap, int p,
   for (int j = 0; j < 3; ++j) A[j] = pget(P, cap, PF_A + j, p);
   for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
   int k = 2;
-  if (shape == 0) {
+  if (shape == 0 || shape == 4) {  // a grid particle: the sphere of its circumscribed radius
     h = 0.0;
     r = A[0];
   } else if (shape == 3) {
@@ -416,7 +419,7 @@ __device__ __forceinline__ void contact_capsule(const double* P, int cap, int p,
       h = A[k];
     }
   }
-  if (shape == 0) {
+  if (shape == 0 || shape == 4) {
     e[0] = 0.0; e[1] = 0.0; e[2] = 1.0;
     return;
   }
@@ -427,7 +430,7 @@ __device__ __forceinline__ void contact_capsule(const double* P, int cap, int p,
 
 // FP32 bound on the reach of a particle's contact capsule from its centre
 __device__ __forceinline__ float contact_reach(const Rec& R) {
-  if (R.shape == 0) return R.a[0];
+  if (R.shape == 0 || R.shape == 4) return R.a[0];
   if (R.shape == 3) return R.a[0] + R.a[2];
   const float amax = fmaxf(R.a[0], fmaxf(R.a[1], R.a[2]));
   if (R.shape == 1) return amax;
@@ -531,7 +534,7 @@ __global__ void __launch_bounds__(256) contact_kernel(PartArgs a) {
   }
   if (lane == 0) {
     for (int c = 0; c < 3; ++c) {
-      if (!((bd.bc >> c) & 1)) continue;
+      if (!((bd.bc >> c) & 1) || (c == 2 && (bd.bc & BC_CUT_Z))) continue;
       for (int side = 0; side < 2; ++side) {
         const double dir = side == 0 ? -1.0 : 1.0;
         const double t = ei[c] * dir > 0.0 ? hi : (ei[c] * dir < 0.0 ? -hi : 0.0);
@@ -568,11 +571,14 @@ cudaError_t launch_mea(const PartArgs& a, int precision, int parity, cudaStream_
   if (a.np <= 0 || a.nchunks <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)a.nchunks;
   const bool pdl = a.pdl != 0;
-  if (precision == 0)
-    return parity == 0 ? launch_k(mea_kernel<float, 0>, dim3(grid), dim3(128), 0, s, pdl, a)
-                       : launch_k(mea_kernel<float, 1>, dim3(grid), dim3(128), 0, s, pdl, a);
-  return parity == 0 ? launch_k(mea_kernel<__half, 0>, dim3(grid), dim3(128), 0, s, pdl, a)
-                     : launch_k(mea_kernel<__half, 1>, dim3(grid), dim3(128), 0, s, pdl, a);
+  const bool g = a.grids.desc != nullptr;
+  auto go = [&](auto kern) { return launch_k(kern, dim3(grid), dim3(128), 0, s, pdl, a); };
+  if (precision == 0) {
+    if (parity == 0) return g ? go(mea_kernel<float, 0, true>) : go(mea_kernel<float, 0, false>);
+    return g ? go(mea_kernel<float, 1, true>) : go(mea_kernel<float, 1, false>);
+  }
+  if (parity == 0) return g ? go(mea_kernel<__half, 0, true>) : go(mea_kernel<__half, 0, false>);
+  return g ? go(mea_kernel<__half, 1, true>) : go(mea_kernel<__half, 1, false>);
 }
 
 cudaError_t launch_update(const PartArgs& a_in, cudaStream_t s) {

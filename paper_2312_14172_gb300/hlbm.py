@@ -17,8 +17,8 @@ LIB_PATH = os.path.join(HERE, "libhlbm.so")
 
 HLBM_OK, HLBM_ERR_ARG, HLBM_ERR_CUDA, HLBM_ERR_UNSTABLE, HLBM_ERR_CAPACITY, HLBM_ERR_STATE = 0, -1, -2, -3, -4, -5
 HLBM_FP32, HLBM_FP16 = 0, 1
-HLBM_SPHERE, HLBM_ELLIPSOID, HLBM_CUBOID, HLBM_CAPSULE = 0, 1, 2, 3
-HLBM_WALL_X, HLBM_WALL_Y, HLBM_WALL_Z = 1, 2, 4
+HLBM_SPHERE, HLBM_ELLIPSOID, HLBM_CUBOID, HLBM_CAPSULE, HLBM_GRID = 0, 1, 2, 3, 4
+HLBM_WALL_X, HLBM_WALL_Y, HLBM_WALL_Z, HLBM_CUT_Z = 1, 2, 4, 8
 HLBM_MEA_KERNEL, HLBM_MEA_MOMENTS = 0, 1
 
 ERRORS = {HLBM_ERR_ARG: "HLBM_ERR_ARG", HLBM_ERR_CUDA: "HLBM_ERR_CUDA",
@@ -30,7 +30,8 @@ EXPORTS = ["hlbm_default_params", "hlbm_required_bytes", "hlbm_init_lattice", "h
            "hlbm_add_particles", "hlbm_set_particle_state", "hlbm_step", "hlbm_sync",
            "hlbm_particle_state", "hlbm_get_populations", "hlbm_set_populations",
            "hlbm_num_particles", "hlbm_steps_done", "hlbm_set_launch", "hlbm_get_launch",
-           "hlbm_set_fluid_force", "hlbm_set_contact", "hlbm_fluid_momentum",
+           "hlbm_set_fluid_force", "hlbm_set_contact", "hlbm_fluid_momentum", "hlbm_add_grid",
+           "hlbm_set_owned_planes", "hlbm_plane_slots", "hlbm_step_forces", "hlbm_step_with_forces",
            "hlbm_set_mea_mode", "hlbm_get_mea_mode",
            "hlbm_autotune", "hlbm_kernel_times", "hlbm_interior_cells",
            "hlbm_checkpoint_bytes", "hlbm_save", "hlbm_load", "hlbm_last_error", "hlbm_destroy",
@@ -47,7 +48,8 @@ class hlbm_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("eps", ctypes.c_double),
                 ("gravity", ctypes.c_double * 3), ("fluid_force", ctypes.c_double * 3),
                 ("precision", ctypes.c_int), ("fp16_scale_log2", ctypes.c_int),
-                ("max_particles", ctypes.c_int), ("bin_capacity", ctypes.c_int)]
+                ("max_particles", ctypes.c_int), ("bin_capacity", ctypes.c_int),
+                ("grid_floats", ctypes.c_longlong)]
 
 
 class HLBMError(RuntimeError):
@@ -96,6 +98,11 @@ def load(path=LIB_PATH):
     L.hlbm_set_fluid_force.argtypes = [_h, _dp]
     L.hlbm_set_contact.argtypes = [_h, ctypes.c_double, ctypes.c_double]
     L.hlbm_fluid_momentum.argtypes = [_h, ctypes.c_int, _dp]
+    L.hlbm_add_grid.argtypes = [_h, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _fp, _ip]
+    L.hlbm_set_owned_planes.argtypes = [_h, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.hlbm_plane_slots.argtypes = [_h, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int]
+    L.hlbm_step_forces.argtypes = [_h, _dp, _dp]
+    L.hlbm_step_with_forces.argtypes = [_h, _dp, _dp]
     L.hlbm_get_mea_mode.argtypes = [_h]
     L.hlbm_autotune.argtypes = [_h, ctypes.c_int, _ip, _ip, _ip, _fp]
     L.hlbm_kernel_times.argtypes = [_h, ctypes.c_int, _fp]
@@ -128,7 +135,7 @@ def hlbm_default_params():
 
 
 def make_params(tau=0.6, eps=0.5, gravity=(0, 0, 0), fluid_force=(0, 0, 0), precision="fp32",
-                fp16_scale_log2=14, max_particles=0, bin_capacity=0):
+                fp16_scale_log2=14, max_particles=0, bin_capacity=0, grid_floats=0):
     p = hlbm_default_params()
     p.tau, p.eps = float(tau), float(eps)
     for j in range(3):
@@ -138,6 +145,7 @@ def make_params(tau=0.6, eps=0.5, gravity=(0, 0, 0), fluid_force=(0, 0, 0), prec
     p.fp16_scale_log2 = int(fp16_scale_log2)
     p.max_particles = int(max_particles)
     p.bin_capacity = int(bin_capacity)
+    p.grid_floats = int(grid_floats)
     return p
 
 
@@ -287,6 +295,47 @@ class Lattice:
         particles' enclosing capsules and with the walls."""
         _check(self.h, load().hlbm_set_contact(self.h, float(k), float(zeta)))
 
+    def add_grid(self, values, h):
+        """Register a signed-distance grid (FP32 samples values[z, y, x],
+        spacing h, body frame centred at the origin); returns its id."""
+        v = np.ascontiguousarray(values, dtype=np.float32)
+        nz, ny, nx = v.shape
+        gid = ctypes.c_int(-1)
+        _check(self.h, load().hlbm_add_grid(self.h, nx, ny, nz, float(h), v.ctypes.data_as(_fp),
+                                            ctypes.byref(gid)))
+        return gid.value
+
+    def set_owned_planes(self, z_lo, z_hi, box=0):
+        _check(self.h, load().hlbm_set_owned_planes(self.h, int(box), int(z_lo), int(z_hi)))
+
+    def plane_slots(self, z, direction, box=0):
+        """The five stored slots with c_z = direction of plane z, raw
+        storage values [5, ny, nx] (float32 or float16)."""
+        nx, ny, _ = self.boxes[box][:3]
+        out = np.empty((5, ny, nx), np.float32 if self.params.precision == HLBM_FP32 else np.float16)
+        _check(self.h, load().hlbm_plane_slots(self.h, int(box), int(z), int(direction), out.ctypes.data, 0))
+        return out
+
+    def set_plane_slots(self, z, direction, values, box=0):
+        nx, ny, _ = self.boxes[box][:3]
+        dt = np.float32 if self.params.precision == HLBM_FP32 else np.float16
+        v = np.ascontiguousarray(values, dtype=dt).reshape(5, ny, nx)
+        _check(self.h, load().hlbm_plane_slots(self.h, int(box), int(z), int(direction), v.ctypes.data, 1))
+
+    def step_forces(self):
+        """Open a split step: the partial momentum exchange over this
+        handle's owned cells, (F, T) of shape [n, 3]."""
+        n = self.num_particles
+        F, T = np.zeros((n, 3)), np.zeros((n, 3))
+        _check(self.h, load().hlbm_step_forces(self.h, F.ctypes.data_as(_dp), T.ctypes.data_as(_dp)))
+        return F, T
+
+    def step_with_forces(self, F, T):
+        """Close a split step with the total hydrodynamic force and torque."""
+        F = np.ascontiguousarray(F, np.float64)
+        T = np.ascontiguousarray(T, np.float64)
+        _check(self.h, load().hlbm_step_with_forces(self.h, F.ctypes.data_as(_dp), T.ctypes.data_as(_dp)))
+
     def fluid_momentum(self, box=0):
         """(sum of rho - 1, total momentum [3]) of one box, summed on the GPU."""
         out = np.zeros(4)
@@ -349,9 +398,13 @@ def from_workload(w, precision=None, stream=None, **kw):
     """Lattice of one workload description (see the workloads module)."""
     prec = precision or w.get("precision", "fp32")
     P = w["particles"]
+    grids = w.get("grids", ())
+    kw.setdefault("grid_floats", sum(int(np.asarray(v).size) for v, _ in grids))
     params = make_params(tau=w["tau"], eps=w["eps"], gravity=w["gravity"],
                          fluid_force=w.get("fluid_force", (0, 0, 0)), precision=prec,
                          max_particles=max(1, len(P["shape"])), **kw)
     lat = Lattice([tuple(w["n"]) + (w["bc"],)], params, stream=stream)
+    for values, h in grids:
+        lat.add_grid(values, h)
     lat.add_workload_particles(P)
     return lat

@@ -381,6 +381,67 @@ def bench_C19():
             [0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1]]
 
 
+def _grid_workload():
+    from paper_2312_14172_gb300 import workloads
+    w = workloads.grid_shapes(n=(62, 56, 60), count=16, r_eq=4.0, steps=50)
+    rng = np.random.default_rng(8)
+    w["particles"]["omega"] = rng.uniform(-3e-3, 3e-3, w["particles"]["omega"].shape)
+    w["particles"]["U"] = rng.uniform(-1e-3, 1e-3, w["particles"]["U"].shape)
+    return w
+
+
+@pytest.mark.parametrize("mode", ["kernel", "moments"])
+def test_grid_shapes_subbox(H, O, mode):
+    """Signed-distance grid particles (rounded boxes of four aspect ratios,
+    random orientations, spin and drift, eps = 1.5) against the oracle's grid
+    shapes: populations and motion after 50 steps."""
+    w = _grid_workload()
+    assert len(w["particles"]["shape"]) >= 12 and len(w["grids"]) == 4
+    sg, so, fg, fo, (X0, U0, W0) = _run_pair(H, O, w, 50, chunks=(1,), mode=mode)
+    _pops_close(fg, fo)
+    _motion_close(sg, so, X0, U0, W0)
+    assert np.allclose(sg["quat"], so["quat"], atol=1e-9)
+
+
+def test_grid_registration_and_snapshot(H):
+    """hlbm_add_grid refuses what the oracle refuses (faces below eps/2, no
+    negative sample, off-centre body, too many samples), a grid particle must
+    name a registered grid, and a snapshot carries the grids: the restored
+    run continues bit for bit."""
+    from paper_2312_14172_gb300 import workloads
+    w = _grid_workload()
+    lat = H.from_workload(w)
+    v, h = w["grids"][0]
+    bad = v.copy()
+    bad[0, 3, 3] = 0.0
+    for values in (bad, np.abs(v) + 1.0, np.roll(v, 3, axis=2)):
+        with pytest.raises(H.HLBMError):
+            lat.add_grid(values, h)
+    with pytest.raises(H.HLBMError):  # no room left: grid_floats holds the workload's grids
+        lat.add_grid(v, h)
+    lat.step(3)
+    snap = lat.save()
+    lat.step(4)
+    ref = lat.particle_state()
+    fr = lat.populations()
+    P = w["particles"]
+    lat2 = H.Lattice([tuple(w["n"]) + (w["bc"],)],
+                     H.make_params(tau=w["tau"], eps=w["eps"], gravity=w["gravity"], max_particles=len(P["shape"]),
+                                   grid_floats=sum(g[0].size for g in w["grids"])))
+    lat2.load_snapshot(snap)
+    lat2.step(4)
+    got = lat2.particle_state()
+    for key in ("X", "U", "omega", "quat", "F", "T"):
+        assert np.array_equal(got[key], ref[key]), key
+    assert np.array_equal(lat2.populations(), fr)
+    lat.close()
+    lat2.close()
+    lat3 = H.Lattice([(20, 20, 20, 0)], H.make_params(max_particles=1))
+    with pytest.raises(H.HLBMError):
+        lat3.add_particles([4], [[0, 0, 0]], [[10.0, 10.0, 10.0]], rho_p=[2.0])
+    lat3.close()
+
+
 def test_fp16_storage_error_is_small(H, O):
     from paper_2312_14172_gb300 import workloads
     w = workloads.single_sphere(n=40, radius=5.0, steps=100)

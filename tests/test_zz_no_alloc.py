@@ -215,21 +215,22 @@ def test_noalloc_wraps_centres_and_flags_invalid_particles(H):
     _run_twice(H, stored, bc, 0, 0, (shape, params, X + shift, U, omega, quat), same)
 
     # invalid particles appended after the four valid ones
-    bad_shape = np.array([0, 1, 2, 0, 0, 7], np.int32)
+    bad_shape = np.array([0, 1, 2, 0, 0, 7, 4], np.int32)
     bad_params = np.array([[4.0, 4, 4], [3.0, -1.0, 2.0], [2.0, 2.0, 2.0], [4.0, 4, 4], [19.0, 19, 19],
-                           [3.0, 3, 3]])
+                           [3.0, 3, 3], [0.0, 0, 0]])
     bad_X = np.array([[20.0, 18, 20], [20.0, 18, 20], [20.0, 18, 20], [20.0, 18, NZ - 0.25],
-                      [20.0, 18, 22], [20.0, 18, 20]])
-    bad_q = np.tile([1.0, 0, 0, 0], (6, 1))
+                      [20.0, 18, 22], [20.0, 18, 20], [20.0, 18, 20]])
+    bad_q = np.tile([1.0, 0, 0, 0], (7, 1))
     bad_q[2] = 0.0  # zero quaternion
-    bad_U = np.zeros((6, 3))
+    bad_U = np.zeros((7, 3))
     bad_U[0, 1] = np.nan  # non-finite velocity
     # 1: negative size; 3: centre beyond the upper z wall (n - 1/2);
-    # 4: 2 (r + 2) >= nx; 5: unknown shape
+    # 4: 2 (r + 2) >= nx; 5: unknown shape; 6: a distance grid (grids
+    # belong to a handle)
     n = 4 + len(bad_shape)
     allp = (np.concatenate([shape, bad_shape]), np.concatenate([params, bad_params]),
             np.concatenate([X, bad_X]), np.concatenate([U, bad_U]),
-            np.concatenate([omega, np.zeros((6, 3))]), np.concatenate([quat, bad_q]))
+            np.concatenate([omega, np.zeros((7, 3))]), np.concatenate([quat, bad_q]))
 
     def flagged(F, T, call):
         assert F.shape == (n, 3)
