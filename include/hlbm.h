@@ -272,10 +272,15 @@ int hlbm_get_mea_mode(hlbm_handle h);
 
 /* Times every momentum-exchange mode and launch shape (tile_y, tile_z,
  * cells_x; cells_x = 2 only with tile_y >= 2) on about 20 ms of steps
- * (nsteps to 4 nsteps) of the current state (the state advances by the
- * steps taken), times
- * the three fastest once more and keeps the fastest; writes the chosen shape
- * and its time per step in ms (any pointer may be NULL). */
+ * (nsteps to 4 nsteps) from the current state, times the three fastest once
+ * more and keeps the fastest; writes the chosen shape and its time per step
+ * in ms (any pointer may be NULL).  The run is left where it was: the
+ * handle's whole device state is copied to a temporary device buffer (of
+ * the handle's size; allocated and freed by this call) before the timed
+ * steps and copied back after them.  The choice is kept for the life of the
+ * process per (GPU model and SM count, boxes, precision, particle count,
+ * grids, contact on or off): a later call with the same key applies it
+ * without timing. */
 int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, int* cells_x, float* ms_per_step);
 
 /* Runs nsteps steps with each kernel launched on its own, bracketed by CUDA
@@ -384,7 +389,8 @@ int hlbm_mea_noalloc(const void* f, long long plane, int nx, int ny, int nz, int
  * A slab of planes [z0, z1) of a global lattice is a box of z1 - z0 + 2
  * planes with HLBM_WALL_Z | HLBM_CUT_Z: local plane 0 and the last plane are
  * ghost copies of the neighbours' boundary planes, hlbm_set_owned_planes(h,
- * box, 1, z1 - z0 + 1) marks the rest as owned.  Each slab holds copies of
+ * box, 1, z1 - z0 + 1) marks the rest as owned (a slab on a wall of the
+ * lattice has no ghost plane on that side: its box's z wall is the wall).  Each slab holds copies of
  * the particles whose influence reaches it (positions in its local frame,
  * the periodic image nearest to it).  A step of the whole lattice is then:
  *   1. before an odd step (steps done is odd), every ghost plane receives

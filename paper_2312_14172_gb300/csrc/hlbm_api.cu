@@ -15,6 +15,8 @@
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1170,12 +1172,86 @@ int hlbm_get_launch(hlbm_handle h, int* tile_y, int* tile_z, int* cells_x) {
   return HLBM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// choices of hlbm_autotune per (device, boxes, precision, particle count),
+// kept for the life of the process
+struct TuneChoice { int ty, tz, cx, mode; float ms; };
+std::mutex g_tune_mutex;
+std::map<std::string, TuneChoice> g_tune_cache;
+
+std::string tune_key(const hlbm_ctx* h) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "?";
+  std::string k = name + "|" + std::to_string(h->nsm) + "|p" + std::to_string(h->prm.precision) + "|n" +
+                  std::to_string(h->np) + "|g" + std::to_string(h->grids.size()) + "|c" +
+                  std::to_string(h->contact_k > 0.0);
+  for (const BoxDesc& b : h->boxes)
+    k += "|" + std::to_string(b.nx) + "x" + std::to_string(b.ny) + "x" + std::to_string(b.nz) + "b" +
+         std::to_string(b.bc);
+  return k;
+}
+}  // namespace
+
+extern "C" {
+
 int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, int* cells_x, float* ms_per_step) {
   if (!h) return HLBM_ERR_ARG;
   if (nsteps < 1) return fail(h, HLBM_ERR_ARG, "nsteps < 1");
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  if (h->split) return fail(h, HLBM_ERR_STATE, "a split step is open");
+  const std::string key = tune_key(h);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      const TuneChoice c = it->second;
+      int r = hlbm_set_mea_mode(h, c.mode);
+      if (r == HLBM_OK) r = hlbm_set_launch(h, c.ty, c.tz, c.cx);
+      if (r != HLBM_OK) return r;
+      if (tile_y) *tile_y = c.ty;
+      if (tile_z) *tile_z = c.tz;
+      if (cells_x) *cells_x = c.cx;
+      if (ms_per_step) *ms_per_step = c.ms;
+      return HLBM_OK;
+    }
+  }
+  // the timed steps run on the handle itself; its whole device state (one
+  // buffer) and the host-side step state are copied aside first and put
+  // back afterwards, so tuning leaves the run where it was
+  CK(cudaStreamSynchronize(h->stream));
+  char* backup = nullptr;
+  CK(cudaMalloc((void**)&backup, h->L.total));
+  {
+    const cudaError_t e = cudaMemcpyAsync(backup, h->buf, h->L.total, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) {
+      cudaFree(backup);
+      return fail(h, HLBM_ERR_CUDA, std::string("autotune backup: ") + cudaGetErrorString(e));
+    }
+  }
+  const long long steps0 = h->steps;
+  const bool moments0 = h->moments_valid, hst0 = h->hst_valid;
+  const long long hst_steps0 = h->hst_steps;
+  auto restore = [&]() -> int {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->buf, backup, h->L.total, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(backup);
+    h->steps = steps0;
+    h->moments_valid = moments0;
+    h->hst_valid = hst0;
+    h->hst_steps = hst_steps0;
+    if (e != cudaSuccess) return fail(h, HLBM_ERR_CUDA, std::string("autotune restore: ") + cudaGetErrorString(e));
+    return HLBM_OK;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    restore();
+    return fail(h, HLBM_ERR_CUDA, "autotune: cudaEventCreate failed");
+  }
   struct Cand { int ty, tz, cx, mode; float ms; };
   std::vector<Cand> cand;
   const int vals[4] = {1, 2, 4, 8};
@@ -1226,7 +1302,10 @@ int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, int* cell
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (rc == HLBM_OK) rc = read_status(h);
+  const int rrc = restore();
   if (rc != HLBM_OK) return rc;
+  if (rrc != HLBM_OK) return rrc;
   const Cand best = *std::min_element(cand.begin(), cand.end(),
                                       [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
   rc = hlbm_set_mea_mode(h, best.mode);
@@ -1236,7 +1315,14 @@ int hlbm_autotune(hlbm_handle h, int nsteps, int* tile_y, int* tile_z, int* cell
   if (cells_x) *cells_x = best.cx;
   if (ms_per_step) *ms_per_step = best.ms;
   if (rc != HLBM_OK) return rc;
-  return read_status(h);
+  // the restored state is the one before tuning: its recorded interior
+  // cells are valid for the mode in use then
+  h->moments_valid = moments0 && best.mode == HLBM_MEA_MOMENTS && h->mea_mode == HLBM_MEA_MOMENTS;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = TuneChoice{best.ty, best.tz, best.cx, best.mode, best.ms};
+  }
+  return HLBM_OK;
 }
 
 int hlbm_kernel_times(hlbm_handle h, int nsteps, float ms[3]) {

@@ -7,8 +7,9 @@ process holding a particle's centre integrates it) from the neighbourhood
 them to the responsible one, which sums them and sends the result back).
 Here the domain is cut into z slabs, one handle each (one GPU each, or
 several on one GPU); every slab is a box of its planes plus one ghost plane
-on each side (HLBM_WALL_Z | HLBM_CUT_Z, owned planes 1 .. m), and the step
-of include/hlbm.h's "Sub-domains" runs across them:
+on each side that faces another slab (HLBM_WALL_Z | HLBM_CUT_Z; on a wall of
+the lattice the box's own z wall is that wall), and the step of
+include/hlbm.h's "Sub-domains" runs across them:
 
   halo     before an odd step the ghost planes take the five crossing slots
            of the neighbours' boundary planes; after it the owned boundary
@@ -87,12 +88,13 @@ def holders(zc, reach, ranges, nz, periodic=True):
     return [s for s, (z0, z1) in enumerate(ranges) if _intersects(lo, hi, z0 - 1, z1 + 1, nz, periodic)]
 
 
-def local_z(zc, z0, z1, nz, periodic=True):
-    """Height of a centre in a slab's local frame (local plane 1 = global
-    plane z0): the periodic image nearest to the slab's middle."""
-    zl = zc - z0 + 1.0
+def local_z(zc, z0, z1, nz, periodic=True, lo=1):
+    """Height of a centre in a slab's local frame (local plane lo = global
+    plane z0; lo = 1 below a ghost plane, 0 on a wall): the periodic image
+    nearest to the slab's middle."""
+    zl = zc - z0 + lo
     if periodic:
-        mid = 0.5 * (z1 - z0 + 1)
+        mid = lo + 0.5 * (z1 - z0 - 1)
         zl -= nz * np.round((zl - mid) / nz)
     return zl
 
@@ -111,15 +113,20 @@ def sum_partials(partials, route_senders, n):
 
 # ------------------------------------------------------ one process, C-ABI
 class SlabLattice:
-    """A workload (see the workloads module; z must be periodic or walled)
-    on nslabs z-slab handles driven from this process.  margin: how far (in
-    cells) particles may move before the fixed sets of copies would no
-    longer cover them (checked every step)."""
+    """A workload (see the workloads module; z periodic or walled) on
+    nslabs >= 2 z-slab handles driven from this process.  A slab has a ghost
+    plane on each side that faces another slab; on a wall of the lattice its
+    owned planes reach the wall (the box's own z wall is the lattice's).
+    margin: how far (in cells) particles may move before the fixed sets of
+    copies would no longer cover them (checked every step).  Contact
+    (hlbm_set_contact) is not carried across slabs."""
 
     def __init__(self, w, nslabs, precision="fp32", mea_mode="kernel", margin=4.0, devices=None):
         n = w["n"]
         self.nz = n[2]
         self.periodic = not (w["bc"] & hlbm.HLBM_WALL_Z)
+        if nslabs < 2:
+            raise ValueError("a slab decomposition needs two slabs or more (one box is one handle)")
         self.ranges = slab_ranges(self.nz, nslabs)
         P = w["particles"]
         self.np = len(P["shape"])
@@ -133,69 +140,72 @@ class SlabLattice:
         self.hold = [holders(self.X0[p, 2], reach[p], self.ranges, self.nz, self.periodic) for p in range(self.np)]
         self.slabs = []
         for s, (z0, z1) in enumerate(self.ranges):
+            has_lo = self.periodic or s > 0
+            has_up = self.periodic or s < nslabs - 1
+            lo, m = (1 if has_lo else 0), z1 - z0
             ids = [p for p in range(self.np) if s in self.hold[p]]
             prm = hlbm.make_params(tau=w["tau"], eps=w["eps"], gravity=w["gravity"],
                                    fluid_force=w.get("fluid_force", (0, 0, 0)), precision=precision,
                                    max_particles=max(1, len(ids)),
                                    grid_floats=sum(int(np.asarray(v).size) for v, _ in grids))
             dev = None if devices is None else devices[s % len(devices)]
-            lat = hlbm.Lattice([(n[0], n[1], z1 - z0 + 2, bc)], prm, device=dev)
+            lat = hlbm.Lattice([(n[0], n[1], m + has_lo + has_up, bc)], prm, device=dev)
             for values, h in grids:
                 lat.add_grid(values, h)
-            lat.set_owned_planes(1, z1 - z0 + 1)
+            lat.set_owned_planes(lo, lo + m)
             lat.set_mea_mode(mea_mode)
             if ids:
                 X = self.X0[ids].copy()
-                X[:, 2] = [local_z(z, z0, z1, self.nz, self.periodic) for z in X[:, 2]]
+                X[:, 2] = [local_z(z, z0, z1, self.nz, self.periodic, lo) for z in X[:, 2]]
                 sub = {k: np.asarray(v)[ids] for k, v in P.items()}
                 sub["X"] = X
                 lat.add_workload_particles(sub)
-            self.slabs.append({"lat": lat, "ids": ids, "z0": z0, "z1": z1})
+            self.slabs.append({"lat": lat, "ids": ids, "z0": z0, "z1": z1, "lo": lo, "m": m})
         self.steps = 0
 
     def close(self):
         for sl in self.slabs:
             sl["lat"].close()
 
-    # --- halo of the in-place storage
+    # --- halo of the in-place storage: ghost plane lo - 1, owned planes
+    # lo .. lo + m - 1, ghost plane lo + m
     def _halo_before_odd(self):
-        S = len(self.slabs)
         for s, sl in enumerate(self.slabs):
-            m = sl["z1"] - sl["z0"]
-            lo, up = self._neighbour(s, -1), self._neighbour(s, +1)
-            if lo is not None:
-                lm = self.slabs[lo]["z1"] - self.slabs[lo]["z0"]
-                sl["lat"].set_plane_slots(0, MINUS_Z, self.slabs[lo]["lat"].plane_slots(lm, MINUS_Z))
-            if up is not None:
-                sl["lat"].set_plane_slots(m + 1, PLUS_Z, self.slabs[up]["lat"].plane_slots(1, PLUS_Z))
-        return S
+            L, U = self._neighbour(s, -1), self._neighbour(s, +1)
+            if L is not None:
+                nb = self.slabs[L]
+                sl["lat"].set_plane_slots(sl["lo"] - 1, MINUS_Z,
+                                          nb["lat"].plane_slots(nb["lo"] + nb["m"] - 1, MINUS_Z))
+            if U is not None:
+                nb = self.slabs[U]
+                sl["lat"].set_plane_slots(sl["lo"] + sl["m"], PLUS_Z, nb["lat"].plane_slots(nb["lo"], PLUS_Z))
 
     def _halo_after_odd(self):
-        # read every ghost first: the owned planes written below are ghosts'
-        # sources on the neighbours
+        # read every ghost first: the owned planes written below are the
+        # ghosts' sources on the neighbours
         got = []
         for s, sl in enumerate(self.slabs):
-            m = sl["z1"] - sl["z0"]
-            lo, up = self._neighbour(s, -1), self._neighbour(s, +1)
+            L, U = self._neighbour(s, -1), self._neighbour(s, +1)
             a = b = None
-            if lo is not None:
-                lm = self.slabs[lo]["z1"] - self.slabs[lo]["z0"]
-                a = self.slabs[lo]["lat"].plane_slots(lm + 1, PLUS_Z)
-            if up is not None:
-                b = self.slabs[up]["lat"].plane_slots(0, MINUS_Z)
-            got.append((a, b, m))
-        for sl, (a, b, m) in zip(self.slabs, got):
+            if L is not None:
+                nb = self.slabs[L]
+                a = nb["lat"].plane_slots(nb["lo"] + nb["m"], PLUS_Z)
+            if U is not None:
+                nb = self.slabs[U]
+                b = nb["lat"].plane_slots(nb["lo"] - 1, MINUS_Z)
+            got.append((a, b))
+        for sl, (a, b) in zip(self.slabs, got):
             if a is not None:
-                sl["lat"].set_plane_slots(1, PLUS_Z, a)
+                sl["lat"].set_plane_slots(sl["lo"], PLUS_Z, a)
             if b is not None:
-                sl["lat"].set_plane_slots(m, MINUS_Z, b)
+                sl["lat"].set_plane_slots(sl["lo"] + sl["m"] - 1, MINUS_Z, b)
 
     def _neighbour(self, s, side):
         S = len(self.slabs)
         t = s + side
         if 0 <= t < S:
             return t
-        return t % S if self.periodic and S > 1 else None
+        return t % S if self.periodic else None
 
     # --- one step of the whole lattice
     def step(self, nsteps=1):
@@ -241,7 +251,7 @@ class SlabLattice:
                     continue
                 for k in out:
                     out[k][p] = st[k][j]
-                out["X"][p, 2] += sl["z0"] - 1.0
+                out["X"][p, 2] += sl["z0"] - sl["lo"]
                 if self.periodic:
                     out["X"][p, 2] %= self.nz
                 done[p] = True
@@ -253,7 +263,7 @@ class SlabLattice:
         parts = []
         for sl in self.slabs:
             f = sl["lat"].populations()
-            parts.append(f[:, 1:1 + sl["z1"] - sl["z0"]])
+            parts.append(f[:, sl["lo"]:sl["lo"] + sl["m"]])
         return np.concatenate(parts, axis=1)
 
 

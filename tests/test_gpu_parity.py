@@ -662,6 +662,38 @@ def test_launch_shapes_agree(H, O):
             assert np.max(np.abs(s["F"] - ref[1]["F"])) <= tol_f * np.abs(ref[1]["F"]).max()
 
 
+def test_autotune_leaves_the_run_where_it_was(H):
+    """hlbm_autotune times its candidates on a copy of the state: a run that
+    tunes after 5 steps and then takes 5 more ends where a run that takes the
+    chosen shape and mode without tuning ends (bit for bit); a second tuning
+    of the same configuration takes the kept choice without timing."""
+    import time
+    from paper_2312_14172_gb300 import workloads
+    w = workloads.hindered_settling(n=(64, 40, 40), count=8, steps=10)
+    a = H.from_workload(w)
+    a.step(5)
+    ty, tz, cx, ms = a.autotune(nsteps=2)
+    assert a.steps_done == 5
+    mode = a.get_mea_mode()
+    a.step(5)
+    b = H.from_workload(w)
+    b.step(5)
+    b.set_launch(ty, tz, cx)
+    b.set_mea_mode(mode)
+    b.step(5)
+    sa, sb = a.particle_state(), b.particle_state()
+    for key in ("X", "U", "omega", "quat", "F", "T"):
+        assert np.array_equal(sa[key], sb[key]), key
+    assert np.array_equal(a.populations(), b.populations())
+    c = H.from_workload(w)
+    t0 = time.perf_counter()
+    again = c.autotune(nsteps=2)
+    assert again == (ty, tz, cx, ms) and time.perf_counter() - t0 < 0.5
+    assert c.get_launch() == (ty, tz, cx) and c.get_mea_mode() == mode
+    for lat in (a, b, c):
+        lat.close()
+
+
 @pytest.mark.parametrize("kind", ["spheres_walls", "nonspherical"])
 def test_moment_momentum_exchange_matches_kernel(H, O, kind):
     """The momentum exchange from the arrivals and the moments the previous
