@@ -267,6 +267,41 @@ def test_capsules_subbox(H, O, mode):
     assert np.allclose(sg["quat"], so["quat"], atol=1e-9)
 
 
+@pytest.mark.parametrize("cells_x", [1, 2])
+def test_particles_across_the_periodic_seams(H, O, cells_x):
+    """Particles across the periodic x, y and z seams, in the box's partial
+    last tile (nx = 100), capsules with axes along x, just off it and
+    oblique, an ellipsoid and a cuboid at random orientations: the
+    populations and the motion stay those of the oracle."""
+    n = (100, 36, 40)
+    lat, orc = _pair(H, O, n, 0, tau=0.7, eps=1.5, g=(0, 0, -1e-5), maxp=8)
+
+    def about_y(phi):
+        return [math.cos(phi / 2), 0.0, math.sin(phi / 2), 0.0]
+
+    rng = np.random.default_rng(11)
+    qr = rng.standard_normal((2, 4))
+    qr /= np.linalg.norm(qr, axis=1, keepdims=True)
+    shape = [0, 3, 1, 2, 3, 3, 0]
+    params = [[5.0] * 3, [2.5, 2.5, 5.0], [7.0, 3.0, 3.0], [4.0, 2.5, 2.0], [2.0, 2.0, 6.0], [2.0, 2.0, 5.0],
+              [3.0] * 3]
+    X = [[0.4, 10.0, 10.0], [92.5, 26.0, 30.0], [31.6, 20.0, 22.0], [64.2, 12.0, 30.0], [50.0, 28.0, 8.0],
+         [72.0, 4.0, 18.0], [80.0, 35.5, 0.2]]
+    quat = [[1.0, 0, 0, 0], about_y(math.pi / 2), list(qr[0]), list(qr[1]), about_y(math.pi / 2 - 0.04),
+            about_y(math.pi / 2 - 0.02), [1.0, 0, 0, 0]]
+    U = rng.uniform(-5e-3, 5e-3, (7, 3))
+    W = rng.uniform(-3e-3, 3e-3, (7, 3))
+    rho = [2.0] * 7
+    lat.add_particles(shape=shape, shape_params=params, X=X, U=U, omega=W, quat=quat, rho_p=rho)
+    orc.add_particles(shape, params, X, U, W, quat, rho)
+    lat.set_launch(4, 4, cells_x)
+    lat.step(30)
+    orc.step(30)
+    _pops_close(lat.populations(), orc.populations())
+    _motion_close(lat.particle_state(), orc.particle_state(), np.array(X), U, W)
+    lat.close()
+
+
 def _contact_workload():
     """Particles set in contact with each other and with the lower z wall:
     spheres, a capsule, an ellipsoid and a cuboid, pairs closing in."""
