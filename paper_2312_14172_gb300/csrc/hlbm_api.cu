@@ -70,6 +70,8 @@ bool make_layout(int nb, const hlbm_box* boxes, const hlbm_params* prm, Layout& 
     if (cells + n >= (1LL << 31)) { err = "all boxes together may hold at most 2^31 - 1 cells"; return false; }
     BoxDesc& d = bd[b];
     d.nx = B.nx; d.ny = B.ny; d.nz = B.nz; d.bc = B.bc_flags;
+    d.div_x = make_fastdiv((unsigned)B.nx);
+    d.div_y = make_fastdiv((unsigned)B.ny);
     d.own_lo = 0;
     d.own_hi = B.nz;
     d.ntx = (B.nx + TILE_X - 1) / TILE_X;

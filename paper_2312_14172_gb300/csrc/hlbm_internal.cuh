@@ -49,15 +49,47 @@ __host__ __device__ constexpr double wq(int i) {
   return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
 
+// Division of an unsigned 32-bit n by a divisor d >= 1 fixed at set-up, with
+// one high multiply (Granlund and Montgomery 1994, the unsigned case of
+// their Fig. 4.1): with l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1
+// and t = mulhi(m, n), n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0),
+// exact for every n.
+struct FastDiv {
+  unsigned m;
+  int s1, s2;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  FastDiv f;
+  f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+__device__ __forceinline__ unsigned fast_div(unsigned n, const FastDiv& f) {
+  const unsigned t = __umulhi(f.m, n);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 struct BoxDesc {
   int nx, ny, nz, bc;        // bc: bit a set = walls on axis a; BC_CUT_Z: see below
   int ntx, nty, ntz;         // bin tiles per axis (ntx = storage blocks per row)
   int own_lo, own_hi;        // owned z planes [own_lo, own_hi) of a BC_CUT_Z box
-  int pad0;
+  FastDiv div_x, div_y;      // division by nx and by ny
   long long cell_off;        // first cell of the box in the global cell numbering
   long long tile_off;        // first bin tile of the box
   long long blk_off;         // first storage block of the box
 };
+
+// coordinates of cell c (c < nx ny nz) of a box
+__device__ __forceinline__ void cell_coords(const BoxDesc& bd, unsigned c, int& x, int& y, int& z) {
+  const unsigned r = fast_div(c, bd.div_x);
+  const unsigned q = fast_div(r, bd.div_y);
+  x = (int)(c - r * (unsigned)bd.nx);
+  y = (int)(r - q * (unsigned)bd.ny);
+  z = (int)q;
+}
 
 // A box with BC_CUT_Z (set together with the z-wall bit) is one z slab of a
 // larger lattice: its z faces bound the lattice as walls do (only its ghost

@@ -13,6 +13,8 @@
 // deviations d_i = f_i - w_i (float, or half scaled by 2^s); all arithmetic
 // is FP32 on deviations, which keeps the small non-equilibrium parts exact to
 // FP32 rounding instead of to the rounding of f ~ w_i.
+#include <type_traits>
+
 #include "lbm_common.cuh"
 
 namespace hlbm {
@@ -182,12 +184,24 @@ __global__ void __launch_bounds__(256, HLBM_CS_MINBLOCKS) collide_stream_kernel(
 // A persistent grid walks the list (one entry per thread, all 19 loads of a
 // cell in flight together); each cell's terms are rounded to fixed point
 // (ACC_FRAC_BITS), and the lanes of a warp that belong to the same particle
-// are summed with integer shuffles before one 64-bit integer atomic per
-// particle, component and warp: the sums do not depend on the list's order.
+// are summed as integers before one 64-bit integer atomic per particle,
+// component and warp: the sums do not depend on the list's order.
 
-// resident blocks per SM: four with walls (64 registers, a few spills; the
-// integer group sums otherwise take 88 registers and leave two blocks), five
-// without (48 registers)
+// Exact warp sum of the 64-bit values of the lanes in mask (the others give
+// 0), from three limbs with single-instruction warp reductions: v =
+// a 2^42 + b 2^21 + c with c, b in [0, 2^21) and a = v >> 42 in [-2^21,
+// 2^21), so 32 lanes' limb sums stay within 32 bits.
+__device__ __forceinline__ long long warp_sum_i64(long long v) {
+  const unsigned c = (unsigned)v & 0x1fffffu;
+  const unsigned b = (unsigned)(v >> 21) & 0x1fffffu;
+  const int hi = (int)(v >> 42);
+  const unsigned sc = __reduce_add_sync(0xffffffffu, c);
+  const unsigned sb = __reduce_add_sync(0xffffffffu, b);
+  const int sa = __reduce_add_sync(0xffffffffu, hi);
+  return (long long)(((unsigned long long)(long long)sa << 42) + ((unsigned long long)sb << 21) + sc);
+}
+
+// resident blocks per SM: four with walls (64 registers), five without
 template <typename S, int PAR, bool WALLS>
 __global__ void __launch_bounds__(256, WALLS ? 4 : 5) mea_list_kernel(LbmArgs a) {
   pdl_trigger();
@@ -255,28 +269,33 @@ __global__ void __launch_bounds__(256, WALLS ? 4 : 5) mea_list_kernel(LbmArgs a)
     const long long cl = (long long)e.x - bd.cell_off;
     if (valid && (cl < 0 || cl >= (long long)bd.nx * bd.ny * bd.nz)) valid = false;
     if (listed && !valid) atomicOr(a.status, ST_INTERNAL);
-    if (valid) {
-      pid = e.y;
+    int x = 0, y = 0, z = 0;
+    if (valid) cell_coords(bd, (unsigned)cl, x, y, z);
+    // cells next to a wall take the wall selects; a warp without any runs
+    // the plain neighbour arithmetic (the same for cells off the walls)
+    bool edge = false;
+    if (WALLS && valid)
+      edge = ((bd.bc & 1) && (x == 0 || x == bd.nx - 1)) || ((bd.bc & 2) && (y == 0 || y == bd.ny - 1)) ||
+             ((bd.bc & 4) && (z == 0 || z == bd.nz - 1));
+    auto cell_terms = [&](auto wtag) {
+      constexpr bool W = decltype(wtag)::value;
       const Rec& R = a.rec[pid];
-      const int c = (int)cl;
-      const int x = c % bd.nx, t = c / bd.nx, y = t % bd.ny, z = t / bd.ny;
       float r[3];
       r[0] = offset_fp32(x, bd.nx, bd.bc & 1, R.xh[0], R.xl[0]);
       r[1] = offset_fp32(y, bd.ny, bd.bc & 2, R.xh[1], R.xl[1]);
       r[2] = offset_fp32(z, bd.nz, bd.bc & 4, R.xh[2], R.xl[2]);
       // arrivals f_i(x) (AA accessor): slot i of x (even parity), slot ibar of
       // x - c_i (odd parity), or slot i of x when x - c_i lies beyond a wall
-      const RowBlocks rb = row_blocks<WALLS>(bd, x, y, 1);
+      const RowBlocks rb = row_blocks<W>(bd, x, y, 1);
       int zb[3];
-      slice_blocks<WALLS>(bd, z, zb);
+      slice_blocks<W>(bd, z, zb);
       const S* own = cell_ptr(fbase, zb[1] + rb.yb[1] + rb.xb, rb.xin);
       float d[Q];
       unsigned walls = 0;  // bit i: x - c_i lies beyond a wall
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const int by = rb.yb[1 - cy(i)], bz = zb[1 - cz(i)];
-        const bool wall =
-            WALLS && i > 0 && (by < 0 || bz < 0 || (cx(i) > 0 && rb.wl) || (cx(i) < 0 && rb.wr));
+        const bool wall = W && i > 0 && (by < 0 || bz < 0 || (cx(i) > 0 && rb.wl) || (cx(i) < 0 && rb.wr));
         if (wall) walls |= 1u << i;
         if (PAR == 0 || i == 0) {
           d[i] = Pop<S>::ld(own + i * VB, a.inv_scale);
@@ -301,7 +320,7 @@ __global__ void __launch_bounds__(256, WALLS ? 4 : 5) mea_list_kernel(LbmArgs a)
       F[0] = (px - sd.y) - upx * dm;
       F[1] = (py - sd.z) - upy * dm;
       F[2] = (pz - sd.w) - upz * dm;
-      if (WALLS) {
+      if (W) {
 #pragma unroll
         for (int i = 1; i < Q; ++i)
           if ((walls >> i) & 1u) {
@@ -314,6 +333,12 @@ __global__ void __launch_bounds__(256, WALLS ? 4 : 5) mea_list_kernel(LbmArgs a)
       T[0] = r[1] * F[2] - r[2] * F[1];
       T[1] = r[2] * F[0] - r[0] * F[2];
       T[2] = r[0] * F[1] - r[1] * F[0];
+    };
+    if (valid) pid = e.y;
+    if (WALLS && __any_sync(0xffffffffu, edge)) {
+      if (valid) cell_terms(std::integral_constant<bool, WALLS>{});
+    } else if (valid) {
+      cell_terms(std::integral_constant<bool, false>{});
     }
     // sum the lanes of each particle present in the warp
     unsigned todo = __ballot_sync(0xffffffffu, valid);
@@ -321,16 +346,13 @@ __global__ void __launch_bounds__(256, WALLS ? 4 : 5) mea_list_kernel(LbmArgs a)
       const int leader = __ffs(todo) - 1;
       const int p = __shfl_sync(0xffffffffu, pid, leader);
       const bool mine = valid && pid == p;
-      const unsigned grp = __ballot_sync(0xffffffffu, mine);
-      todo &= ~grp;
+      todo &= ~__ballot_sync(0xffffffffu, mine);
 #pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        const float t = q < 3 ? F[q] : T[q - 3];
-        long long v = mine ? __float2ll_rn(__fmul_rn(t, (float)(1LL << ACC_FRAC_BITS))) : 0LL;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      for (int c = 0; c < 6; ++c) {
+        const float t = c < 3 ? F[c] : T[c - 3];
+        const long long v = warp_sum_i64(mine ? __float2ll_rn(__fmul_rn(t, (float)(1LL << ACC_FRAC_BITS))) : 0LL);
         if (lane == leader)
-          atomicAdd(reinterpret_cast<unsigned long long*>(&a.acc[(long long)p * 6 + q]), (unsigned long long)v);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&a.acc[(long long)p * 6 + c]), (unsigned long long)v);
       }
     }
   }

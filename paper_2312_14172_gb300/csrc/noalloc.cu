@@ -278,6 +278,8 @@ extern "C" int hlbm_mea_noalloc(const void* f, long long plane, int nx, int ny, 
   a.bd.ny = ny;
   a.bd.nz = nz;
   a.bd.bc = bc_flags;
+  a.bd.div_x = make_fastdiv((unsigned)nx);
+  a.bd.div_y = make_fastdiv((unsigned)ny);
   a.bd.cell_off = 0;
   a.inv_scale = precision == HLBM_FP16 ? (float)(1.0 / (double)(1 << fp16_scale_log2)) : 1.0f;
   a.n = n;
