@@ -190,59 +190,16 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// Newton-Euler step of one particle in registers (Eqs. particlemotiontrans,
-// motionrot), symplectic Euler: U += F / m with F = F_h + (rho_p - rho_f) V g,
-// X += U; spheres: omega += T / I; other shapes: body-frame Euler equations
+// Newton-Euler step (Eqs. particlemotiontrans, motionrot), symplectic Euler:
+// U += F / m with F = F_h + (rho_p - rho_f) V g, X += U; spheres:
+// omega += T / I; other shapes: body-frame Euler equations
 // omega_b += (T_b - omega_b x (I omega_b)) / I with the rotation of the old
 // quaternion; q += q (x) (0, omega_b) / 2, normalised (for a sphere in the
-// equal form (0, omega) (x) q / 2, which needs no rotation: GB300's FP64
-// pipe is narrow and this lane's FP64 chain bounds the kernel).  Returns
-// false when the new state is not finite.
-__device__ __forceinline__ bool newton_euler(const PartArgs& a, int shape, double im, double V, double rho,
-                                             const double I[3], const double iI[3], const double Fh[3],
-                                             const double Th[3], double X[3], double U[3], double W[3],
-                                             double q[4]) {
-  for (int j = 0; j < 3; ++j) {
-    const double F = Fh[j] + (rho - 1.0) * V * a.g[j];  // Fh: hydrodynamic (and contact) force
-    U[j] += F * im;
-    X[j] += U[j];
-  }
-  const double w = q[0], x = q[1], y = q[2], z = q[3];
-  double dq[4];
-  if (shape == 0) {
-    // q (x) (0, omega_b) equals (0, omega) (x) q: no rotation needed
-    for (int j = 0; j < 3; ++j) W[j] += Th[j] * iI[j];
-    dq[0] = -0.5 * (W[0] * x + W[1] * y + W[2] * z);
-    dq[1] = 0.5 * (w * W[0] + W[1] * z - W[2] * y);
-    dq[2] = 0.5 * (w * W[1] + W[2] * x - W[0] * z);
-    dq[3] = 0.5 * (w * W[2] + W[0] * y - W[1] * x);
-  } else {
-    double R[9], wb[3], Tb[3], Lb[3], gy[3];
-    rotation_rn(q, R);
-    for (int j = 0; j < 3; ++j) {
-      wb[j] = R[0 * 3 + j] * W[0] + R[1 * 3 + j] * W[1] + R[2 * 3 + j] * W[2];
-      Tb[j] = R[0 * 3 + j] * Th[0] + R[1 * 3 + j] * Th[1] + R[2 * 3 + j] * Th[2];
-    }
-    for (int j = 0; j < 3; ++j) Lb[j] = I[j] * wb[j];
-    cross3(wb, Lb, gy);
-    for (int j = 0; j < 3; ++j) wb[j] += (Tb[j] - gy[j]) * iI[j];
-    for (int j = 0; j < 3; ++j) W[j] = R[j * 3 + 0] * wb[0] + R[j * 3 + 1] * wb[1] + R[j * 3 + 2] * wb[2];
-    dq[0] = 0.5 * (-x * wb[0] - y * wb[1] - z * wb[2]);
-    dq[1] = 0.5 * (w * wb[0] + y * wb[2] - z * wb[1]);
-    dq[2] = 0.5 * (w * wb[1] + z * wb[0] - x * wb[2]);
-    dq[3] = 0.5 * (w * wb[2] + x * wb[1] - y * wb[0]);
-  }
-  double nq = 0.0;
-  for (int j = 0; j < 4; ++j) {
-    q[j] += dq[j];
-    nq += q[j] * q[j];
-  }
-  const double inq = rsqrt(nq);
-  for (int j = 0; j < 4; ++j) q[j] *= inq;
-  bool ok = true;
-  for (int j = 0; j < 3; ++j) ok = ok && isfinite(X[j]) && isfinite(U[j]) && isfinite(W[j]);
-  return ok;
-}
+// equal form (0, omega) (x) q / 2, which needs no rotation).  GB300's FP64
+// pipe is narrow: a warp's FP64 instruction takes it for many cycles however
+// few lanes are active, so the translation and the rotation of a block's
+// particles run on two warps (two SM sub-partitions) at once, each lane one
+// particle, and meet in shared memory for the record and the binning.
 
 // Tiles of one particle's bin range, kept in shared memory between the
 // Newton-Euler step and the binning.
@@ -253,51 +210,43 @@ struct BinRange {
   int count;  // tiles; 0 when the particle is not binned
 };
 
-// One particle per thread (GB300's FP64 units are few: the FP64 work of a
-// particle runs on one lane): the weight minus buoyancy, the Newton-Euler
-// step and the coupling record of the new state; returns the tiles the
-// particle's bins cover.
-__device__ __forceinline__ BinRange update_particle(const PartArgs& a, int p) {
+// force of the momentum exchange (row base PF_F) or torque (PF_T) of particle
+// p: written into the table by the bounding-box kernel, or accumulated from
+// the recorded moments (that accumulator is cleared for the next step); the
+// table keeps it, and the contact force or torque joins it as an acting one
+__device__ __forceinline__ void exchange_force(const PartArgs& a, int p, int row, int crow, int k0, double Fo[3]) {
+  long long* acc = a.acc + (long long)p * 6 + k0;
+  const double unit = 1.0 / (double)(1LL << ACC_FRAC_BITS);  // fixed point -> force and torque
+  for (int j = 0; j < 3; ++j) Fo[j] = a.from_acc ? (double)acc[j] * unit : pget(a.P, a.cap, row + j, p);
+  if (a.from_acc)
+    for (int j = 0; j < 3; ++j) acc[j] = 0;
+  for (int j = 0; j < 3; ++j) pset(a.P, a.cap, row + j, p, Fo[j]);
+  if (a.contact_k > 0.0)
+    for (int j = 0; j < 3; ++j) Fo[j] += pget(a.P, a.cap, crow + j, p);
+}
+
+// translation of particle p: force, U, X (wrapped on periodic axes), the
+// record's position and velocity, and the tiles its bins cover
+__device__ __forceinline__ void translate_particle(const PartArgs& a, int p, Rec& R, BinRange& br) {
   const double* __restrict__ P = a.P;
   const int cap = a.cap;
-  const int shape = a.shape[p], box = a.box[p];
-  const BoxDesc bd = a.boxes[box];
-  double X[3], U[3], W[3], q[4], I[3], iI[3], A[3], iA[3], Fh[3], Th[3];
+  const BoxDesc bd = a.boxes[a.box[p]];
+  double X[3], U[3], Fh[3];
   for (int j = 0; j < 3; ++j) {
     X[j] = pget(P, cap, PF_X + j, p);
     U[j] = pget(P, cap, PF_U + j, p);
-    W[j] = pget(P, cap, PF_W + j, p);
-    I[j] = pget(P, cap, PF_I + j, p);
-    iI[j] = pget(P, cap, PF_II + j, p);
-    A[j] = pget(P, cap, PF_A + j, p);
-    iA[j] = pget(P, cap, PF_IA + j, p);
   }
-  for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
   const double im = pget(P, cap, PF_IM, p), V = pget(P, cap, PF_V, p), rho = pget(P, cap, PF_RHO, p);
   const double rinf = pget(P, cap, PF_RINF, p), rc = pget(P, cap, PF_RC, p);
-  // force and torque of the momentum exchange: written into the table by the
-  // momentum-exchange kernel, or accumulated from the recorded moments (the
-  // accumulator is cleared for the next step)
-  long long* acc = a.acc + (long long)p * 6;
-  const double unit = 1.0 / (double)(1LL << ACC_FRAC_BITS);  // fixed point -> force and torque
+  exchange_force(a, p, PF_F, PF_FC, 0, Fh);
+  bool ok = true;
   for (int j = 0; j < 3; ++j) {
-    Fh[j] = a.from_acc ? (double)acc[j] * unit : pget(P, cap, PF_F + j, p);
-    Th[j] = a.from_acc ? (double)acc[3 + j] * unit : pget(P, cap, PF_T + j, p);
+    const double F = Fh[j] + (rho - 1.0) * V * a.g[j];  // Fh: hydrodynamic (and contact) force
+    U[j] += F * im;
+    X[j] += U[j];
+    ok = ok && isfinite(X[j]) && isfinite(U[j]);
   }
-  if (a.from_acc)
-    for (int j = 0; j < 6; ++j) acc[j] = 0;
-  // the table keeps the hydrodynamic force and torque; the contact force
-  // and torque join them as acting forces
-  for (int j = 0; j < 3; ++j) {
-    pset(a.P, cap, PF_F + j, p, Fh[j]);
-    pset(a.P, cap, PF_T + j, p, Th[j]);
-  }
-  if (a.contact_k > 0.0)
-    for (int j = 0; j < 3; ++j) {
-      Fh[j] += pget(P, cap, PF_FC + j, p);
-      Th[j] += pget(P, cap, PF_TC + j, p);
-    }
-  if (!newton_euler(a, shape, im, V, rho, I, iI, Fh, Th, X, U, W, q)) atomicOr(a.status, ST_UNSTABLE);
+  if (!ok) atomicOr(a.status, ST_UNSTABLE);
   const int n[3] = {bd.nx, bd.ny, bd.nz};
   for (int j = 0; j < 3; ++j) {
     if ((bd.bc >> j) & 1) {
@@ -314,40 +263,112 @@ __device__ __forceinline__ BinRange update_particle(const PartArgs& a, int p) {
   for (int j = 0; j < 3; ++j) {
     pset(a.P, cap, PF_X + j, p, X[j]);
     pset(a.P, cap, PF_U + j, p, U[j]);
-    pset(a.P, cap, PF_W + j, p, W[j]);
+    const float xh = __double2float_rn(X[j]);
+    R.xh[j] = xh;
+    R.xl[j] = __double2float_rn(X[j] - (double)xh);
+    R.u[j] = (float)U[j];
   }
-  for (int j = 0; j < 4; ++j) pset(a.P, cap, PF_Q + j, p, q[j]);
-  Rec R;
-  make_record(X, U, W, q, A, iA, rinf, (float)a.eps, p, shape, box, R);
-  a.rec[p] = R;
   // bin tiles touched by the influence sphere, widened so that the cells next
-  // to the particle's interior (which feed its momentum exchange) see it too
-  BinRange br;
+  // to the particle's interior (which feed its momentum exchange) see it too;
+  // the cell range is rounded outwards in FP32
   br.tile_off = bd.tile_off;
   br.ntx = bd.ntx;
   br.nty = bd.nty;
   br.count = 0;
-  const double rbin = fmax(rinf, rc + 1.5);
+  const float rb = __double2float_ru(fmax(rinf, rc + 1.5));
   const int T[3] = {TILE_X, TILE_Y, TILE_Z};
   for (int j = 0; j < 3; ++j) {
-    if (!(X[j] > -1.0e6 && X[j] < 1.0e6)) return br;  // flagged above; not binned
-    const int lo = (int)floor(X[j] - rbin) - 1, hi = (int)ceil(X[j] + rbin) + 1;
+    if (!(X[j] > -1.0e6 && X[j] < 1.0e6)) return;  // flagged above; not binned
+    const int lo = (int)floorf(__fsub_rd(__double2float_rd(X[j]), rb)) - 1;
+    const int hi = (int)ceilf(__fadd_ru(__double2float_ru(X[j]), rb)) + 1;
     br.at[j] = axis_tiles(lo, hi, n[j], T[j], (bd.bc >> j) & 1);
   }
   br.count = br.at[0].count() * br.at[1].count() * br.at[2].count();
-  return br;
+}
+
+// rotation of particle p: torque, omega, quaternion, the record's angular
+// velocity and orientation; the record's fixed fields (shape, box, id, sizes
+// and the bounds derived from them) come from its previous record
+__device__ __forceinline__ void rotate_particle(const PartArgs& a, int p, Rec& R) {
+  const double* __restrict__ P = a.P;
+  const int cap = a.cap;
+  const int shape = a.shape[p];
+  double W[3], q[4], I[3], iI[3], Th[3];
+  for (int j = 0; j < 3; ++j) {
+    W[j] = pget(P, cap, PF_W + j, p);
+    iI[j] = pget(P, cap, PF_II + j, p);
+    I[j] = shape == 0 ? 0.0 : pget(P, cap, PF_I + j, p);
+  }
+  for (int j = 0; j < 4; ++j) q[j] = pget(P, cap, PF_Q + j, p);
+  const Rec& old = a.rec[p];
+  for (int j = 0; j < 3; ++j) {
+    R.a[j] = old.a[j];
+    R.ia[j] = old.ia[j];
+  }
+  R.in2 = old.in2;
+  R.rinf2 = old.rinf2;
+  R.shape = old.shape;
+  R.box = old.box;
+  R.pid = old.pid;
+  if (shape == 0)
+    for (int k = 0; k < 9; ++k) R.M[k] = old.M[k];  // a sphere's collision bounds
+  exchange_force(a, p, PF_T, PF_TC, 3, Th);
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  double dq[4];
+  if (shape == 0) {
+    // q (x) (0, omega_b) equals (0, omega) (x) q: no rotation needed
+    for (int j = 0; j < 3; ++j) W[j] += Th[j] * iI[j];
+    dq[0] = -0.5 * (W[0] * x + W[1] * y + W[2] * z);
+    dq[1] = 0.5 * (w * W[0] + W[1] * z - W[2] * y);
+    dq[2] = 0.5 * (w * W[1] + W[2] * x - W[0] * z);
+    dq[3] = 0.5 * (w * W[2] + W[0] * y - W[1] * x);
+  } else {
+    double Rm[9], wb[3], Tb[3], Lb[3], gy[3];
+    rotation_rn(q, Rm);
+    for (int j = 0; j < 3; ++j) {
+      wb[j] = Rm[0 * 3 + j] * W[0] + Rm[1 * 3 + j] * W[1] + Rm[2 * 3 + j] * W[2];
+      Tb[j] = Rm[0 * 3 + j] * Th[0] + Rm[1 * 3 + j] * Th[1] + Rm[2 * 3 + j] * Th[2];
+    }
+    for (int j = 0; j < 3; ++j) Lb[j] = I[j] * wb[j];
+    cross3(wb, Lb, gy);
+    for (int j = 0; j < 3; ++j) wb[j] += (Tb[j] - gy[j]) * iI[j];
+    for (int j = 0; j < 3; ++j) W[j] = Rm[j * 3 + 0] * wb[0] + Rm[j * 3 + 1] * wb[1] + Rm[j * 3 + 2] * wb[2];
+    dq[0] = 0.5 * (-x * wb[0] - y * wb[1] - z * wb[2]);
+    dq[1] = 0.5 * (w * wb[0] + y * wb[2] - z * wb[1]);
+    dq[2] = 0.5 * (w * wb[1] + z * wb[0] - x * wb[2]);
+    dq[3] = 0.5 * (w * wb[2] + x * wb[1] - y * wb[0]);
+  }
+  double nq = 0.0;
+  for (int j = 0; j < 4; ++j) {
+    q[j] += dq[j];
+    nq += q[j] * q[j];
+  }
+  const double inq = rsqrt(nq);
+  for (int j = 0; j < 4; ++j) q[j] *= inq;
+  if (!(isfinite(W[0]) && isfinite(W[1]) && isfinite(W[2]))) atomicOr(a.status, ST_UNSTABLE);
+  for (int j = 0; j < 3; ++j) {
+    pset(a.P, cap, PF_W + j, p, W[j]);
+    R.w[j] = (float)W[j];
+  }
+  for (int j = 0; j < 4; ++j) pset(a.P, cap, PF_Q + j, p, q[j]);
+  if (shape != 0) {
+    double Rn[9];
+    rotation_rn(q, Rn);
+    for (int k = 0; k < 9; ++k) R.M[k] = __double2float_rn(Rn[k]);
+  }
 }
 
 // a.ppb particles per block of UPD_T threads (ppb a power of two up to
-// UPD_P): the first ppb threads each update one particle; then all threads
-// add the block's particles to the per-tile lists, UPD_T / ppb threads per
-// particle taking its tiles in turn.  Few particles get small groups, so
-// that the blocks spread over the GPU and each particle's tiles take one
-// round of atomics.
+// UPD_P): lane k of warp 0 moves particle k of the block, lane k of warp 1
+// turns it; then all threads store the records and add the block's
+// particles to the per-tile lists, UPD_T / ppb threads per particle taking
+// its tiles in turn.  Few particles get small groups, so that the blocks
+// spread over the GPU and each particle's tiles take one round of atomics.
 constexpr int UPD_P = 32, UPD_T = 256;
 
 __global__ void __launch_bounds__(UPD_T) update_kernel(PartArgs a) {
   __shared__ BinRange s_br[UPD_P];
+  __shared__ Rec s_rec[UPD_P];
   pdl_trigger();
   pdl_wait();
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -355,15 +376,21 @@ __global__ void __launch_bounds__(UPD_T) update_kernel(PartArgs a) {
   for (long long t = tid; t < a.ntiles; t += nthr) a.bin_count_clear[t] = 0;
   if (tid < ILIST_STRIPES && a.ilist_count) a.ilist_count[tid] = 0;  // the collision appends anew
   const int ppb = a.ppb;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (long long base = blockIdx.x * (long long)ppb; base < a.np; base += (long long)gridDim.x * ppb) {
-    if (threadIdx.x < ppb) {
-      const long long p = base + threadIdx.x;
-      BinRange br;
-      br.count = 0;
-      if (p < a.np) br = update_particle(a, (int)p);
-      s_br[threadIdx.x] = br;
+    if (warp < 2 && lane < ppb) {
+      const long long p = base + lane;
+      if (p < a.np) {
+        if (warp == 0) translate_particle(a, (int)p, s_rec[lane], s_br[lane]);
+        else rotate_particle(a, (int)p, s_rec[lane]);
+      } else if (warp == 0) {
+        s_br[lane].count = 0;
+      }
     }
     __syncthreads();
+    const long long nrec = min((long long)ppb, a.np - base);
+    for (int e = threadIdx.x; e < nrec * 32; e += UPD_T)
+      reinterpret_cast<int*>(&a.rec[base + (e >> 5)])[e & 31] = reinterpret_cast<const int*>(&s_rec[e >> 5])[e & 31];
     const int k = threadIdx.x % ppb, sub = threadIdx.x / ppb;
     const BinRange& br = s_br[k];
     const int cx_ = br.at[0].count(), cy_ = br.at[1].count();
