@@ -129,10 +129,49 @@ def profiled_traffic(workload, precision, cells, cells_x):
     return None if per_cell is None else per_cell * cells
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (the driver's libnvidia-ml):
+    SM clock, its maximum and the active clock-event reasons of one GPU."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, device):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        uuid = None
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(device).uuid)
+            uuid = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            uuid = None
+        if uuid is None or self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.dev)) != 0:
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device), ctypes.byref(self.dev)) != 0:
+                raise OSError("no NVML handle")
+        get = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.get_reasons = get or self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        v = ctypes.c_uint(0)
+        self.lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, ctypes.byref(v))
+        self.max_mhz = float(v.value)
+
+    def sample(self):
+        v = self.ct.c_uint(0)
+        r = self.ct.c_ulonglong(0)
+        if self.lib.nvmlDeviceGetClockInfo(self.dev, 1, self.ct.byref(v)) != 0:
+            return None
+        self.get_reasons(self.dev, self.ct.byref(r))
+        return float(v.value), [nm for bit, nm in self.REASONS.items() if r.value & bit]
+
+
 class ClockSampler:
-    """nvidia-smi samples (every 10 ms) of SM clock and throttle reasons; only
-    the samples stamped inside the timed window count (the nearest two when
-    the window is shorter than the sampling interval)."""
+    """SM clock and clock-event reasons sampled during the timed window:
+    NVML queried in a thread as fast as it answers (tens of samples even in a
+    window of a few milliseconds), else nvidia-smi every 10 ms (the nearest
+    two samples when the window is shorter than that interval)."""
 
     FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -142,8 +181,29 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.window = None
+        self.nvml = None
+        self.rows = []
+        self.thread = None
+        self.halt = False
 
     def start(self):
+        try:
+            self.nvml = _Nvml(self.device)
+        except Exception:
+            self.nvml = None
+        if self.nvml is not None:
+            import threading
+
+            def run():
+                while not self.halt:
+                    s = self.nvml.sample()
+                    if s is not None:
+                        self.rows.append((time.perf_counter(), s[0], self.nvml.max_mhz, s[1]))
+                    time.sleep(0.0002)
+
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
@@ -152,13 +212,12 @@ class ClockSampler:
         except OSError:
             self.proc = None
 
-    def mark(self, t0, t1):
-        """host wall-clock bounds of the timed region"""
-        self.window = (t0, t1)
+    def mark(self, t0, t1, wall0, wall1):
+        """bounds of the timed region: time.perf_counter() values t0, t1
+        (NVML samples) and time.time() values wall0, wall1 (nvidia-smi)"""
+        self.window = (t0, t1, wall0, wall1)
 
-    def stop(self):
-        if self.proc is None:
-            return None
+    def _smi_rows(self):
         self.proc.terminate()
         try:
             out, _ = self.proc.communicate(timeout=5)
@@ -178,17 +237,30 @@ class ClockSampler:
                              [nm for nm, v in zip(names, parts[4:8]) if v.lower().startswith("active")]))
             except ValueError:
                 continue
+        return rows
+
+    def stop(self):
+        if self.thread is not None:
+            self.halt = True
+            self.thread.join(timeout=5)
+            rows, source = list(self.rows), "nvml"
+            window = (self.window[0], self.window[1]) if self.window else None
+        elif self.proc is not None:
+            rows, source = self._smi_rows(), "nvidia-smi"
+            window = (self.window[2], self.window[3]) if self.window else None
+        else:
+            return None
         if not rows:
             return None
         sel = rows
-        if self.window is not None:
-            t0, t1 = self.window
+        if window is not None:
+            t0, t1 = window
             inside = [r for r in rows if t0 <= r[0] <= t1]
             sel = inside if inside else sorted(rows, key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))[:2]
         reasons = sorted({nm for r in sel for nm in r[3]})
         return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": sel[0][2], "reasons": reasons,
-                "samples": len(sel), "in_window": bool(self.window and any(
-                    self.window[0] <= r[0] <= self.window[1] for r in rows))}
+                "samples": len(sel), "source": source, "in_window": bool(window and any(
+                    window[0] <= r[0] <= window[1] for r in rows))}
 
 
 # D3Q19 velocities in the library's order (include/hlbm.h)
@@ -394,14 +466,14 @@ def run_gpu(args, ws, rank, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
-    t_host0 = time.time()
+    t_host0, t_wall0 = time.perf_counter(), time.time()
     e0.record(stream)
     lat.step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    t_host1 = time.time()
+    t_host1, t_wall1 = time.perf_counter(), time.time()
     barrier()
-    sampler.mark(t_host0, t_host1)
+    sampler.mark(t_host0, t_host1, t_wall0, t_wall1)
     clocks = sampler.stop()
     lat.sync()
     ms = e0.elapsed_time(e1)

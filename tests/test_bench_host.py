@@ -113,3 +113,19 @@ def test_settling_correlations_of_the_paper():
         c = bench.settling_correlations(phi, re)
         assert abs(c["barnea_mizrahi"] - bm) < 1e-15
         assert abs(c["richardson_zaki"] - (1 - phi) ** c["n_rz"]) < 1e-15
+
+
+def test_clock_sampler_keeps_the_samples_inside_the_timed_window():
+    """The clocks entry counts only samples taken inside the timed window
+    (median SM clock, the reasons seen there)."""
+    import threading
+    import bench
+    s = bench.ClockSampler(0)
+    s.rows = [(1.0, 1900.0, 2070.0, []), (2.0, 2000.0, 2070.0, ["sw_power_cap"]), (3.0, 2070.0, 2070.0, []),
+              (9.0, 500.0, 2070.0, ["hw_slowdown"])]
+    s.thread = threading.Thread(target=lambda: None)
+    s.thread.start()
+    s.mark(1.5, 3.5, 0.0, 0.0)
+    c = s.stop()
+    assert c["samples"] == 2 and c["sm_mhz"] == 2035.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"] and c["in_window"] and c["source"] == "nvml"
