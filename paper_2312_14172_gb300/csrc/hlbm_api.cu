@@ -157,6 +157,10 @@ struct hlbm_ctx {
   int2* ilist_idx = nullptr;
   float4* ilist_mom = nullptr;
   int nsm = 0;
+  // odd steps take the bricks in reverse order when the populations are
+  // within twice the L2 (a step then starts on what the last one ended
+  // with, still in L2); larger lattices gain nothing and keep one order
+  bool reverse_odd = false;
   int nchunks = 0;
   std::vector<int> h_nchunk;  // bounding-box planes per particle
   int mea_mode = HLBM_MEA_KERNEL;
@@ -233,6 +237,7 @@ static LbmArgs lbm_args(const hlbm_ctx* h, int parity) {
   a.cells_x = h->cells_x;
   a.nsub = (TILE_Y / h->sub_y) * (TILE_Z / h->sub_z);
   a.nbricks = h->L.ntiles * a.nsub;
+  a.reverse = parity && h->reverse_odd;
   a.omega = (float)(1.0 / h->prm.tau);
   for (int j = 0; j < 3; ++j) a.ff[j] = (float)h->prm.fluid_force[j];
   a.eps = (float)h->prm.eps;
@@ -468,6 +473,10 @@ int hlbm_init_batch(hlbm_handle* out, int nboxes, const hlbm_box* boxes, const h
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) h->nsm = 0;
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) l2 = 0;
+    const size_t s = h->prm.precision == HLBM_FP16 ? 2 : 4;
+    h->reverse_odd = l2 > 0 && (size_t)QVB * h->L.nblocks * s <= 2 * (size_t)l2;
   }
   for (int k = 0; k < 2; ++k) {
     h->cnt[k] = (int*)(h->buf + h->L.off_cnt[k]);

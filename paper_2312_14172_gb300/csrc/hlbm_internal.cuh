@@ -329,6 +329,9 @@ struct LbmArgs {
   int cells_x;              // cells per thread along x: 1, or 2 (every box has an even nx)
   int nsub;                 // bricks per bin tile = (8/sub_y)*(8/sub_z)
   long long nbricks;        // total bricks (grid size)
+  // bricks taken in reverse order (odd steps): a step then starts on the
+  // bricks the step before ended with, whose populations L2 still holds
+  int reverse;
   float omega;              // 1 / tau
   float ff[3];              // fluid force density
   float eps, inv_eps;

@@ -176,7 +176,7 @@ struct Brick {
 
 __device__ __forceinline__ Brick brick_of(const LbmArgs& a) {
   Brick k;
-  const long long brick = blockIdx.x;
+  const long long brick = a.reverse ? (long long)gridDim.x - 1 - blockIdx.x : (long long)blockIdx.x;
   k.tile = brick / a.nsub;
   const int sub = (int)(brick - k.tile * a.nsub);
   const int b = a.nboxes > 1 ? find_box(a.boxes, a.nboxes, k.tile) : 0;
