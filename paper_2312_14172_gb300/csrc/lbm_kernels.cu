@@ -202,8 +202,14 @@ __device__ __forceinline__ long long warp_sum_i64(long long v) {
 }
 
 // resident blocks per SM: four with walls (64 registers), five without
+#ifndef HLBM_ML_MINBLOCKS_W
+#define HLBM_ML_MINBLOCKS_W 4
+#endif
+#ifndef HLBM_ML_MINBLOCKS
+#define HLBM_ML_MINBLOCKS 5
+#endif
 template <typename S, int PAR, bool WALLS>
-__global__ void __launch_bounds__(256, WALLS ? 4 : 5) mea_list_kernel(LbmArgs a) {
+__global__ void __launch_bounds__(256, WALLS ? HLBM_ML_MINBLOCKS_W : HLBM_ML_MINBLOCKS) mea_list_kernel(LbmArgs a) {
   pdl_trigger();
   pdl_wait();
   // The list is walked in chunks of 32 entries, the stripes taken in turn
