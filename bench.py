@@ -84,6 +84,23 @@ def make_workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def l2_note(prec, cells):
+    """How the timed steps meet L2: the library takes odd steps' bricks in
+    reverse order when the populations are within twice the L2, so those
+    steps start on populations the step before left there."""
+    import torch
+    pop = BYTES_PER_CELL[prec] // 2 * cells
+    note = f"inputs larger than L2 ({pop / 1e6:.0f} MB of populations); no flush between steps"
+    try:
+        l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    except Exception:
+        l2 = 0
+    if l2 and pop <= 2 * l2:
+        note += (f"; within twice the {l2 / 1e6:.0f} MB L2, so odd steps take the bricks in reverse order "
+                 "and start on populations the previous step left in L2 (traffic: ncu, cold cache)")
+    return note
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -620,8 +637,7 @@ def run_gpu(args, ws, rank, local):
         "config": {"workload": w["name"], "cells": cells, "dims": list(w["n"]), "particles": npart,
                    "storage": prec, "tau": w["tau"], "eps": w["eps"], "bc": w["bc"],
                    "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu",
-                   "l2": f"inputs larger than L2 ({BYTES_PER_CELL[prec] // 2 * cells / 1e6:.0f} MB "
-                         "of populations); no flush between FP32 steps",
+                   "l2": l2_note(prec, cells),
                    "launch": {"tile_y": lat_launch[0], "tile_z": lat_launch[1],
                               "cells_per_thread": lat_launch[2],
                               "momentum_exchange": mea_mode,
