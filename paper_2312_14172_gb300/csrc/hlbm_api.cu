@@ -163,6 +163,7 @@ struct hlbm_ctx {
   bool reverse_odd = false;
   int nchunks = 0;
   std::vector<int> h_nchunk;  // bounding-box planes per particle
+  int mea_planes = 1;         // bounding-box planes per momentum-exchange block
   int mea_mode = HLBM_MEA_KERNEL;
   int* cnt[2] = {nullptr, nullptr};
   int* ids[2] = {nullptr, nullptr};
@@ -281,6 +282,7 @@ static PartArgs part_args(const hlbm_ctx* h, int parity) {
   a.p_chunk0 = h->p_chunk0;
   a.p_nchunk = h->p_nchunk;
   a.nchunks = h->nchunks;
+  a.mea_planes = h->mea_planes;
   a.partial = h->partial;
   a.done = h->done;
   a.acc = h->acc;
@@ -800,14 +802,23 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
   h->h_box.insert(h->h_box.end(), bx.begin(), bx.end());
   h->h_nchunk.insert(h->h_nchunk.end(), nch.begin(), nch.end());
   {
-    // one momentum-exchange block per (particle, bounding-box plane)
+    // one momentum-exchange block per particle and run of mea_planes
+    // bounding-box planes: one plane while the blocks of one plane each fill
+    // the GPU at most four times (the walk is latency-bound and a block's
+    // fixed cost is then spread over few waves), up to three for many
+    // particles, where each block's fixed cost counts in every wave
+    long long planes = 0;
+    for (int q = 0; q < h->np; ++q) planes += h->h_nchunk[q];
+    const long long resident = (long long)(h->nsm > 0 ? h->nsm : 152) * MEA_MINBLOCKS;
+    h->mea_planes = (int)std::min(3LL, std::max(1LL, planes / (4 * resident)));
+    const int G = h->mea_planes;
     std::vector<int> cp, cq, c0(h->np), cn(h->np);
     for (int q = 0; q < h->np; ++q) {
       c0[q] = (int)cp.size();
-      cn[q] = h->h_nchunk[q];
+      cn[q] = (h->h_nchunk[q] + G - 1) / G;
       for (int k = 0; k < cn[q]; ++k) {
         cp.push_back(q);
-        cq.push_back(k);
+        cq.push_back(k * G);
       }
     }
     h->nchunks = (int)cp.size();

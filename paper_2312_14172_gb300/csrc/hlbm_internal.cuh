@@ -96,6 +96,14 @@ __device__ __forceinline__ void cell_coords(const BoxDesc& bd, unsigned c, int& 
 // planes meet them), particle centres may lie beyond them, and only the
 // cells of the owned planes [own_lo, own_hi) enter the momentum exchange.
 constexpr int BC_CUT_Z = 8;
+
+// resident blocks per SM of the bounding-box momentum exchange (64
+// registers): the walk is latency-bound, and more resident blocks beat the
+// spills this costs
+#ifndef HLBM_MEA_MINBLOCKS
+#define HLBM_MEA_MINBLOCKS 8
+#endif
+constexpr int MEA_MINBLOCKS = HLBM_MEA_MINBLOCKS;
 __host__ __device__ __forceinline__ bool owned_plane(const BoxDesc& bd, int z) {
   return !(bd.bc & BC_CUT_Z) || (z >= bd.own_lo && z < bd.own_hi);
 }
@@ -377,6 +385,7 @@ struct PartArgs {
   const int* p_chunk0;      // [cap] first block of a particle
   const int* p_nchunk;      // [cap] blocks of a particle
   int nchunks;
+  int mea_planes;           // bounding-box planes per momentum-exchange block
   double* partial;          // [chunks][6] FP64 partial force/torque sums
   int* done;                // [cap] blocks finished per particle (reset to 0)
   // the same sums added up by the moments-mode momentum exchange from the

@@ -74,18 +74,14 @@ __device__ void build_record(const double* P, int cap, int p, int shape, int box
   make_record(X, U, W, q, A, iA, pget(P, cap, PF_RINF, p), eps, p, shape, box, R);
 }
 
-// eight resident blocks per SM (64 registers): the bounding-box walk is
-// latency-bound, and more resident blocks beat the spills this costs
-#ifndef HLBM_MEA_MINBLOCKS
-#define HLBM_MEA_MINBLOCKS 8
-#endif
-
+// MEA_MINBLOCKS resident blocks per SM; a block walks a.mea_planes
+// bounding-box planes of one particle
 template <typename S, int PAR, bool GRIDS>
-__global__ void __launch_bounds__(128, HLBM_MEA_MINBLOCKS) mea_kernel(PartArgs a) {
+__global__ void __launch_bounds__(128, MEA_MINBLOCKS) mea_kernel(PartArgs a) {
   pdl_trigger();
   pdl_wait();
   const int chunk = blockIdx.x;
-  const int p = a.chunk_p[chunk], iz = a.chunk_q[chunk];
+  const int p = a.chunk_p[chunk], iz0 = a.chunk_q[chunk];
   __shared__ Rec R;
   __shared__ double wsum[4][6];
   __shared__ int s_start[MAX_PLANES + 1], s_xa[MAX_PLANES];
@@ -107,8 +103,14 @@ __global__ void __launch_bounds__(128, HLBM_MEA_MINBLOCKS) mea_kernel(PartArgs a
   }
   float sums[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (ok) {
-    mea_plane_sums<S, PAR, true>(R, bd, X, rc, iz, reinterpret_cast<const S*>(a.f), 0, a.inv_scale, s_start,
-                                 s_xa, sums, GRIDS ? a.grids : GridSet{});
+    // planes iz0 .. iz0 + mea_planes - 1 (those past the box's extent add nothing)
+    for (int iz = iz0; iz < iz0 + a.mea_planes; ++iz) {
+      float ps[6];
+      mea_plane_sums<S, PAR, true>(R, bd, X, rc, iz, reinterpret_cast<const S*>(a.f), 0, a.inv_scale, s_start,
+                                   s_xa, ps, GRIDS ? a.grids : GridSet{});
+      for (int k = 0; k < 6; ++k) sums[k] += ps[k];
+      __syncthreads();  // s_start, s_xa are rewritten by the next plane
+    }
   } else if (tid == 0) {
     atomicOr(a.status, ST_UNSTABLE);
   }
