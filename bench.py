@@ -147,7 +147,7 @@ def profiled_traffic(workload, precision, cells, cells_x):
 
 
 class _Nvml:
-    """Read-only NVML queries through ctypes (the driver's libnvidia-ml):
+    """Read-only NVML queries through ctypes (libnvidia-ml of the NVIDIA driver):
     SM clock, its maximum and the active clock-event reasons of one GPU."""
 
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}

@@ -4,7 +4,7 @@ The GPU benchmark runs one replica per GPU (weak scaling, no data-path
 collective); its only exchanges are a barrier and the max over ranks of the
 timed region, and rank 0 alone prints.  These tests run that host logic with
 world size 2 on gloo: the max-over-ranks reduction and whole-job value, and
-the reference arm launched the way the driver launches it (torch.distributed
+the reference arm launched as a multi-GPU run launches it (torch.distributed
 run, two processes), where rank 0 prints one JSON line and rank 1 exits 0
 without work.
 """
