@@ -18,6 +18,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <array>
 #include <vector>
 
 #include "../../include/hlbm.h"
@@ -203,6 +204,7 @@ struct hlbm_ctx {
     double h;
     std::vector<float> v;
     double V, I1[3], rc, rinf;
+    double cap_h, cap_r;  // enclosing capsule about body z of the cells where B can be positive
     long long off;
   };
   std::vector<HostGrid> grids;
@@ -608,6 +610,84 @@ static int upload_fields(hlbm_ctx* h, int p0, int n, const std::vector<double>& 
   return HLBM_OK;
 }
 
+// Two capsules about the body z axis of a grid, each the best of 65
+// half-lengths.  Enclosing (g.cap_h, g.cap_r): the smallest that holds every
+// grid cell with a corner below eps/2 (the blend is a convex combination of
+// the corners, so B > 0 and the inside lie in those cells, and a cell whose
+// corners are in the capsule is in it).  Inscribed (d.in_h, d.in_r2): the
+// largest that meets only grid cells all of whose corners are below
+// -(eps/2 + 1e-3), kept 1e-3 cells off the others (a cell's distance from the
+// axis segment is bounded by its centre's minus its half-diagonal); there
+// the blend is below -eps/2, so the coupling needs no blend.
+static void grid_capsules(hlbm_ctx::HostGrid& g, double half_eps, GridDesc& d) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  auto val = [&](int i, int j, int k) { return (double)g.v[((size_t)k * ny + j) * nx + i]; };
+  auto pos = [&](double i, double j, double k, double r[3]) {
+    r[0] = (i - 0.5 * (nx - 1)) * g.h;
+    r[1] = (j - 0.5 * (ny - 1)) * g.h;
+    r[2] = (k - 0.5 * (nz - 1)) * g.h;
+  };
+  auto seg_d2 = [](const double r[3], double hh) {
+    const double t = r[2] - std::min(std::max(r[2], -hh), hh);
+    return r[0] * r[0] + r[1] * r[1] + t * t;
+  };
+  std::vector<std::array<double, 3>> hold, avoid;  // corners to hold, centres of cells to avoid
+  std::vector<char> mark((size_t)nx * ny * nz, 0);
+  const double deep = -(half_eps + 1e-3);
+  for (int k = 0; k + 1 < nz; ++k)
+    for (int j = 0; j + 1 < ny; ++j)
+      for (int i = 0; i + 1 < nx; ++i) {
+        double vmin = HUGE_VAL, vmax = -HUGE_VAL;
+        for (int c = 0; c < 8; ++c) {
+          const double v = val(i + (c & 1), j + ((c >> 1) & 1), k + (c >> 2));
+          vmin = std::min(vmin, v);
+          vmax = std::max(vmax, v);
+        }
+        if (vmin < half_eps)
+          for (int c = 0; c < 8; ++c) mark[((size_t)(k + (c >> 2)) * ny + j + ((c >> 1) & 1)) * nx + i + (c & 1)] = 1;
+        if (!(vmax < deep)) {
+          double r[3];
+          pos(i + 0.5, j + 0.5, k + 0.5, r);
+          avoid.push_back({r[0], r[1], r[2]});
+        }
+      }
+  double zmax = 0.0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        if (mark[((size_t)k * ny + j) * nx + i]) {
+          double r[3];
+          pos(i, j, k, r);
+          hold.push_back({r[0], r[1], r[2]});
+          zmax = std::max(zmax, std::fabs(r[2]));
+        }
+  g.cap_h = 0.0;
+  g.cap_r = g.rinf;
+  double best = HUGE_VAL;
+  for (int t = 0; t <= 64; ++t) {
+    const double hh = zmax * t / 64.0;
+    double r2 = 0.0;
+    for (const auto& c : hold) r2 = std::max(r2, seg_d2(c.data(), hh));
+    const double r = std::sqrt(r2), vol = M_PI * r * r * 2.0 * hh + 4.0 / 3.0 * M_PI * r * r * r;
+    if (vol < best) { best = vol; g.cap_h = hh; g.cap_r = r; }
+  }
+  const double half_diag = 0.5 * std::sqrt(3.0) * g.h;
+  double in_h = 0.0, in_r = -1.0;
+  best = 0.0;
+  for (int t = 0; t <= 64; ++t) {
+    const double hh = zmax * t / 64.0;
+    double r2 = HUGE_VAL;
+    for (const auto& c : avoid) r2 = std::min(r2, seg_d2(c.data(), hh));
+    const double r = std::sqrt(r2) - half_diag - 1e-3;
+    if (!(r > 0.0)) continue;
+    const double vol = M_PI * r * r * 2.0 * hh + 4.0 / 3.0 * M_PI * r * r * r;
+    if (vol > best) { best = vol; in_h = hh; in_r = r; }
+  }
+  d.in_h = (float)in_h;
+  d.in_r2 = in_r > 0.0 ? (float)(in_r * in_r) : -1.0f;
+  d.in_d = (float)(deep - 0.01);
+}
+
 int hlbm_add_grid(hlbm_handle h, int nx, int ny, int nz, double spacing, const float* values, int* grid_id) {
   if (!h) return HLBM_ERR_ARG;
   if (!values || !grid_id || nx < 2 || ny < 2 || nz < 2 || !(spacing > 0.0) || !std::isfinite(spacing))
@@ -689,6 +769,7 @@ int hlbm_add_grid(hlbm_handle h, int nx, int ny, int nz, double spacing, const f
   d.n[0] = nx; d.n[1] = ny; d.n[2] = nz;
   d.ih = (float)(1.0 / spacing);
   for (int j = 0; j < 3; ++j) d.half[j] = (float)(0.5 * (g.n[j] - 1));
+  grid_capsules(g, half_eps, d);
   d.off = g.off;
   const int id = (int)h->grids.size();
   CK(cudaMemcpyAsync(h->d_gvals + g.off, g.v.data(), sizeof(float) * nv, cudaMemcpyHostToDevice, h->stream));
@@ -777,6 +858,11 @@ int hlbm_add_particles(hlbm_handle h, int n, const int* box_id, const int* shape
       // a grid particle keeps its grid id here (the record's inverse sizes
       // are unused for it)
       T(PF_IA + j, k) = s == HLBM_GRID ? (double)gid : (double)(float)(1.0 / a[j]);
+    }
+    if (s == HLBM_GRID) {
+      // the record's ia[1], ia[2] hold the grid's enclosing capsule
+      T(PF_IA + 1, k) = h->grids[gid].cap_h;
+      T(PF_IA + 2, k) = h->grids[gid].cap_r;
     }
     wrap_host(bd, x);
     for (int j = 0; j < 3; ++j) T(PF_X + j, k) = x[j];

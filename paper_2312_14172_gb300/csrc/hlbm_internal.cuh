@@ -148,7 +148,11 @@ struct GridDesc {
   int n[3];
   float ih;       // fp32(1 / h)
   float half[3];  // fp32((n_j - 1) / 2)
-  int pad;
+  // a capsule about the body z axis (half-length in_h, squared radius in_r2;
+  // in_r2 < 0: none) every grid cell of which has all its corners below
+  // -(eps/2 + 1e-3): there B = 1 and the centre is inside, and the coupling
+  // takes the distance in_d (below -(eps/2 + 1e-3)) without blending
+  float in_h, in_r2, in_d;
   long long off;
 };
 struct GridSet {

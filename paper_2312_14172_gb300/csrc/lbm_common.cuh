@@ -138,8 +138,13 @@ __device__ __forceinline__ float sdf(const Rec& R, float rx, float ry, float rz,
   const float b0 = R.M[0] * rx + R.M[3] * ry + R.M[6] * rz;
   const float b1 = R.M[1] * rx + R.M[4] * ry + R.M[7] * rz;
   const float b2 = R.M[2] * rx + R.M[5] * ry + R.M[8] * rz;
-  if (R.shape == 4) return gs.desc ? grid_blend(gs.desc[__float_as_int(R.in2)], gs.vals, b0, b1, b2)
-                                   : __int_as_float(0x7f800000);
+  if (R.shape == 4) {
+    if (!gs.desc) return __int_as_float(0x7f800000);
+    const GridDesc& g = gs.desc[__float_as_int(R.in2)];
+    const float t = b2 - fminf(fmaxf(b2, -g.in_h), g.in_h);
+    if (b0 * b0 + b1 * b1 + t * t < g.in_r2) return g.in_d;  // deep inside: B = 1, inside
+    return grid_blend(g, gs.vals, b0, b1, b2);
+  }
   if (R.shape == 3) {
     const float t = b2 - fminf(fmaxf(b2, -R.a[2]), R.a[2]);
     return sqrtf(b0 * b0 + b1 * b1 + t * t) - R.a[0];
@@ -205,7 +210,8 @@ __device__ __forceinline__ Brick brick_of(const LbmArgs& a) {
 //   cuboid     the box grown by eps/2 lies in the capsule along its longest
 //              half-extent h_k of radius |(h_i, h_j)| + eps/2 and half-length h_k
 //   capsule    itself grown by eps/2: radius a0 + eps/2 about its body-z segment
-//   grid       the sphere of its influence radius (rinf2 of the record)
+//   grid       the capsule about its body z axis that holds every grid cell
+//              with a corner below eps/2 (computed when the grid is added)
 // The radius carries a margin of 1e-3 relative + 0.01 cells over FP32 rounding.
 struct Capsule {
   float u[3], h, r2;
@@ -221,9 +227,12 @@ __device__ __forceinline__ Capsule capsule_of(const Rec& R, float eps) {
     return c;
   }
   if (R.shape == 4) {
-    c.u[0] = 1.0f; c.u[1] = c.u[2] = 0.0f;
-    c.h = 0.0f;
-    c.r2 = R.rinf2;
+    // the capsule about body z that holds every grid cell with a corner
+    // below eps/2 (half-length and radius in the record's ia[1], ia[2])
+    c.u[0] = R.M[2]; c.u[1] = R.M[5]; c.u[2] = R.M[8];
+    c.h = R.ia[1];
+    const float r = R.ia[2] * 1.001f + 0.01f;
+    c.r2 = r * r;
     return c;
   }
   if (R.shape == 3) {
