@@ -76,14 +76,19 @@ __device__ void build_record(const double* P, int cap, int p, int shape, int box
 
 // MEA_MINBLOCKS resident blocks per SM; a block walks a.mea_planes
 // bounding-box planes of one particle
+#ifndef HLBM_MEA_THREADS
+#define HLBM_MEA_THREADS 128
+#endif
+constexpr int MEA_THREADS = HLBM_MEA_THREADS;
+
 template <typename S, int PAR, bool GRIDS>
-__global__ void __launch_bounds__(128, MEA_MINBLOCKS) mea_kernel(PartArgs a) {
+__global__ void __launch_bounds__(MEA_THREADS, MEA_MINBLOCKS * 128 / MEA_THREADS) mea_kernel(PartArgs a) {
   pdl_trigger();
   pdl_wait();
   const int chunk = blockIdx.x;
   const int p = a.chunk_p[chunk], iz0 = a.chunk_q[chunk];
   __shared__ Rec R;
-  __shared__ double wsum[4][6];
+  __shared__ double wsum[MEA_THREADS / 32][6];
   __shared__ int s_start[MAX_PLANES + 1], s_xa[MAX_PLANES];
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -601,7 +606,7 @@ cudaError_t launch_mea(const PartArgs& a, int precision, int parity, cudaStream_
   const unsigned grid = (unsigned)a.nchunks;
   const bool pdl = a.pdl != 0;
   const bool g = a.grids.desc != nullptr;
-  auto go = [&](auto kern) { return launch_k(kern, dim3(grid), dim3(128), 0, s, pdl, a); };
+  auto go = [&](auto kern) { return launch_k(kern, dim3(grid), dim3(MEA_THREADS), 0, s, pdl, a); };
   if (precision == 0) {
     if (parity == 0) return g ? go(mea_kernel<float, 0, true>) : go(mea_kernel<float, 0, false>);
     return g ? go(mea_kernel<float, 1, true>) : go(mea_kernel<float, 1, false>);
