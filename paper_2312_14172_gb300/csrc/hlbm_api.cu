@@ -189,6 +189,8 @@ struct hlbm_ctx {
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   // two steps in one graph: [m][parity] = step(parity, m) then step(1 - parity)
   cudaGraphExec_t exec2[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  // GRAPH_STEPS steps in one graph, the same way (when more than two)
+  cudaGraphExec_t execk[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool graphs_ok = false;
   bool moments_valid = false;  // the accumulator holds this state's momentum exchange
   int split = 0;  // a split step is open: 1 after its bounding-box exchange, 2 after its moments one
@@ -308,6 +310,13 @@ static PartArgs part_args(const hlbm_ctx* h, int parity) {
 // step runs from them; otherwise the bounding-box kernel computes it from
 // the populations alone (always on the first step after a change of state).
 // Kernels captured into a step's graph use programmatic dependent launch.
+// steps per captured graph for long runs (two-step and one-step graphs
+// take the rest)
+#ifndef HLBM_GRAPH_STEPS
+#define HLBM_GRAPH_STEPS 8
+#endif
+constexpr int GRAPH_STEPS = HLBM_GRAPH_STEPS;
+
 static cudaError_t enqueue_step(hlbm_ctx* h, int parity, bool moments, cudaStream_t s) {
   cudaError_t e;
   LbmArgs la = lbm_args(h, parity);
@@ -332,8 +341,10 @@ static void drop_graphs(hlbm_ctx* h) {
     for (int k = 0; k < 2; ++k) {
       if (h->exec[f][k]) cudaGraphExecDestroy(h->exec[f][k]);
       if (h->exec2[f][k]) cudaGraphExecDestroy(h->exec2[f][k]);
+      if (h->execk[f][k]) cudaGraphExecDestroy(h->execk[f][k]);
       h->exec[f][k] = nullptr;
       h->exec2[f][k] = nullptr;
+      h->execk[f][k] = nullptr;
     }
   h->graphs_ok = false;
 }
@@ -341,20 +352,24 @@ static void drop_graphs(hlbm_ctx* h) {
 static int build_graphs(hlbm_ctx* h) {
   drop_graphs(h);
   const bool mom = h->mea_mode == HLBM_MEA_MOMENTS;
-  for (int gi = 0; gi < 8; ++gi) {
-    const int two = gi >> 2, moments = (gi >> 1) & 1, parity = gi & 1;
+  for (int gi = 0; gi < 12; ++gi) {
+    const int kind = gi >> 2, moments = (gi >> 1) & 1, parity = gi & 1;
+    const int nst = kind == 0 ? 1 : (kind == 1 ? 2 : GRAPH_STEPS);
     if (moments && !mom) continue;
+    if (kind == 2 && GRAPH_STEPS <= 2) continue;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_step(h, parity, moments != 0, h->cap_stream);
-    if (e == cudaSuccess && two) e = enqueue_step(h, 1 - parity, mom, h->cap_stream);
+    for (int j = 1; j < nst && e == cudaSuccess; ++j) e = enqueue_step(h, (parity + j) & 1, mom, h->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       return fail(h, HLBM_ERR_CUDA, std::string("graph capture: ") +
                                         cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(two ? &h->exec2[moments][parity] : &h->exec[moments][parity], g, 0);
+    cudaGraphExec_t* dst = kind == 0 ? &h->exec[moments][parity]
+                                     : (kind == 1 ? &h->exec2[moments][parity] : &h->execk[moments][parity]);
+    e = cudaGraphInstantiate(dst, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, HLBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
@@ -1002,7 +1017,10 @@ int hlbm_step(hlbm_handle h, int nsteps) {
   for (int k = 0; k < nsteps;) {
     const int moments = (h->moments_valid && h->np > 0) ? 1 : 0;
     const int parity = (int)((h->steps + k) & 1);
-    if (nsteps - k >= 2) {
+    if (GRAPH_STEPS > 2 && nsteps - k >= GRAPH_STEPS) {
+      CK(cudaGraphLaunch(h->execk[moments][parity], h->stream));
+      k += GRAPH_STEPS;
+    } else if (nsteps - k >= 2) {
       CK(cudaGraphLaunch(h->exec2[moments][parity], h->stream));
       k += 2;
     } else {
